@@ -1,0 +1,259 @@
+"""Plain FP64 CPU oracle of the constant potential method (CPM) charge update.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. It shares no code with
+the CUDA library and imports nothing from it; the two meet only at the seeded
+input arrays.
+
+What it computes (ELECTRODE paper, arXiv 2203.15461):
+
+* The electrode energy is the quadratic form of Eq. (coulomb), Sec. II.A,
+  U(q) = 1/2 q^T A q - b^T q - v^T q, with the elastance A fixed by the
+  electrode sites and b the electrolyte term.  This module follows the sign
+  convention of the library API: ``b`` is the electrostatic potential of the
+  electrolyte at each site (the negative of the paper's b), so the minimiser
+  is q = S (v - b).
+* The electrode charges are Gaussians (Sec. III.B),
+  rho_i(r) = q_i (eta^2/pi)^{3/2} exp(-eta^2 |r - R_i|^2).  Two such Gaussians
+  interact as erf(eta_ij r)/r with 1/eta_ij^2 = 1/eta_i^2 + 1/eta_j^2; a
+  Gaussian and a point charge as erf(eta_i r)/r.  These pair energies are
+  summed over the periodic images by the Ewald split used by the paper's
+  ``ewald/electrode`` solver (SI Sec. 1.A): a real-space erfc part, a
+  reciprocal part over |k| <= kcut, the Ewald self term, the Gaussian self
+  energy and the neutralising-background constant.
+* Boundary corrections of Sec. II.E: the slab dipole term of Eq. (ew3dc_slab),
+  J = 2 pi M_z^2 / V, split into electrode and electrolyte parts as in the last
+  equation of Sec. II.E; the wire term of Eq. (ew3dc_wire),
+  J = pi (M_x^2 + M_y^2) / V; none for tin-foil 3D.
+* Inversion and the charge-neutral capacitance matrix of Eq. (S), Sec. II.A:
+  S = A^-1 - A^-1 e e^T A^-1 / (e^T A^-1 e).
+* The electrode-wise potentials of Sec. II.B: v = G psi, q* = S (v - b)
+  (Eq. electrode-wise in API sign), and the electrode-wise capacitance
+  C~ = G^T S G (Sec. II.C with S in place of A^-1; Sec. III.B uses it for C0).
+
+Readings of what the paper leaves open (units, cut-offs, the slab vacuum) are
+fixed by the arguments: positions in Angstrom, charges in e, potentials in V,
+A in V/e and S in e/V with the Coulomb constant K_E below.  Real-space pairs
+count when |r| < rcut over all images of the Ewald cell; reciprocal vectors
+count when |k|^2 <= kcut^2, computed as ((kx*kx + ky*ky) + kz*kz) with
+k = (2 pi / L) * n per axis.
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+(brute-force lattice sums, Gaussian-overlap quadrature, alpha independence,
+Gauss's law between plates, the co-axial capacitor of Sec. III.B).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import linalg as sla
+from scipy.special import erfc
+
+#: Coulomb constant e / (4 pi eps0 Angstrom) expressed in volts.
+K_E = 14.399645
+#: vacuum permittivity in e / (V Angstrom)
+EPS0 = 1.0 / (4.0 * math.pi * K_E)
+
+_BC = {"3d": 0, "slab": 1, "wire": 2}
+
+
+# --------------------------------------------------------------------------- reciprocal lattice
+
+def kvectors(box, kcut):
+    """Half-space reciprocal vectors 0 < |k| <= kcut of the Ewald cell ``box``.
+
+    Returns (nidx int64 (Nk,3), k (Nk,3), k2 (Nk,)).  Half space: nx > 0, or
+    nx == 0 and ny > 0, or nx == ny == 0 and nz > 0; the other half is its mirror
+    image and enters through the factor 2 in the weights.
+    """
+    box = np.asarray(box, dtype=np.float64)
+    tp = 2.0 * np.pi / box
+    nmax = [int(math.floor(kcut / tp[d])) + 1 for d in range(3)]
+    gx, gy, gz = np.meshgrid(np.arange(0, nmax[0] + 1), np.arange(-nmax[1], nmax[1] + 1),
+                             np.arange(-nmax[2], nmax[2] + 1), indexing="ij")
+    nidx = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1).astype(np.int64)
+    half = (nidx[:, 0] > 0) | ((nidx[:, 0] == 0) & (nidx[:, 1] > 0)) | \
+           ((nidx[:, 0] == 0) & (nidx[:, 1] == 0) & (nidx[:, 2] > 0))
+    nidx = nidx[half]
+    k = nidx * tp
+    k2 = k[:, 0] * k[:, 0] + k[:, 1] * k[:, 1] + k[:, 2] * k[:, 2]
+    keep = k2 <= kcut * kcut
+    return nidx[keep], k[keep], k2[keep]
+
+
+def kweights(k2, alpha, volume):
+    """Half-space Ewald weights 2 * (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2."""
+    return (8.0 * np.pi / volume) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+
+
+# --------------------------------------------------------------------------- real space
+
+def _image_range(dmin, dmax, L, rcut):
+    lo = int(math.floor((-rcut - dmax) / L))
+    hi = int(math.ceil((rcut - dmin) / L))
+    return range(lo, hi + 1)
+
+
+def _realspace(Ri, Rj, eta_pair, box, alpha, rcut, same=None):
+    """sum over images n with |Ri - Rj + n| < rcut of [erfc(alpha r) - erfc(eta r)] / r.
+
+    ``same`` (bool array like eta_pair) marks pairs that are one and the same
+    site: for those the n = 0 image is left out (it is the self energy).
+    """
+    d = Ri[:, None, :] - Rj[None, :, :]
+    out = np.zeros(d.shape[:2])
+    ranges = [_image_range(d[..., a].min(), d[..., a].max(), box[a], rcut) for a in range(3)]
+    for ix in ranges[0]:
+        for iy in ranges[1]:
+            for iz in ranges[2]:
+                s = np.array([ix * box[0], iy * box[1], iz * box[2]])
+                dd = d + s
+                r2 = dd[..., 0] * dd[..., 0] + dd[..., 1] * dd[..., 1] + dd[..., 2] * dd[..., 2]
+                m = r2 < rcut * rcut
+                if same is not None and ix == 0 and iy == 0 and iz == 0:
+                    m &= ~same
+                if not m.any():
+                    continue
+                r = np.sqrt(r2[m])
+                e = eta_pair[m] if np.ndim(eta_pair) else eta_pair
+                out[m] += (erfc(alpha * r) - erfc(e * r)) / r
+    return out
+
+
+# --------------------------------------------------------------------------- elastance A
+
+def assemble_A(el, rows=None, kchunk=2048):
+    """Elastance matrix A (Eq. coulomb) of electrode sites ``el`` in V/e.
+
+    ``rows`` selects a subset of rows (for sampled checks of large systems);
+    default all n rows, giving the full symmetric n x n matrix.
+    """
+    xyz = np.asarray(el.xyz, dtype=np.float64)
+    eta = np.asarray(el.eta, dtype=np.float64)
+    n = len(xyz)
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    box = np.asarray(el.box, dtype=np.float64)
+    V = float(box[0] * box[1] * box[2])
+    a = el.alpha
+    A = np.zeros((len(rows), n))
+    # real space: Gaussian-Gaussian pairs, erf(eta_ij r)/r minus the erf(alpha r)/r Ewald part
+    for c0 in range(0, len(rows), 256):
+        rr = rows[c0:c0 + 256]
+        ei, ej = eta[rr][:, None], eta[None, :]
+        eta_ij = ei * ej / np.sqrt(ei * ei + ej * ej)
+        same = rr[:, None] == np.arange(n)[None, :]
+        A[c0:c0 + 256] += _realspace(xyz[rr], xyz, eta_ij, box, a, el.rcut, same)
+    # reciprocal space: sum_k w_k cos(k.(R_i - R_j)) = sum_k w_k [c_i c_j + s_i s_j]
+    _, k, k2 = kvectors(box, el.kcut)
+    w = kweights(k2, a, V)
+    for c0 in range(0, len(k), kchunk):
+        kk, ww = k[c0:c0 + kchunk], w[c0:c0 + kchunk]
+        ph_all = xyz @ kk.T
+        ph_r = ph_all[rows]
+        A += (np.cos(ph_r) * ww) @ np.cos(ph_all).T + (np.sin(ph_r) * ww) @ np.sin(ph_all).T
+    # Ewald self term and Gaussian self energy, lim_{r->0} erf(eta r / sqrt2) / r
+    A[np.arange(len(rows)), rows] += (math.sqrt(2.0) * eta[rows] - 2.0 * a) / math.sqrt(math.pi)
+    # neutralising background
+    A += -math.pi / (V * a * a)
+    # boundary correction, electrode-electrode part (Sec. II.E)
+    if el.boundary == "slab":
+        A += (4.0 * math.pi / V) * np.outer(xyz[rows, 2], xyz[:, 2])
+    elif el.boundary == "wire":
+        A += (2.0 * math.pi / V) * (np.outer(xyz[rows, 0], xyz[:, 0]) + np.outer(xyz[rows, 1], xyz[:, 1]))
+    return K_E * A
+
+
+# --------------------------------------------------------------------------- electrolyte vector b
+
+def structure_factor(k, elyt):
+    """rho(k) = sum_j Q_j exp(i k . r_j) for the rows of ``k``."""
+    ph = np.asarray(elyt.xyz) @ k.T
+    Q = np.asarray(elyt.Q)
+    return Q @ np.cos(ph) + 1j * (Q @ np.sin(ph))
+
+
+def bvec(el, elyt, sites=None, kchunk=4096):
+    """Electrolyte potential b_i (V) at electrode sites ``sites`` (default all).
+
+    b_i = sum_j Q_j sum_n erf(eta_i |R_i - r_j + n|) / |...| by the same Ewald split as A,
+    plus the background and the electrolyte part of the boundary term.
+    """
+    xyz = np.asarray(el.xyz, dtype=np.float64)
+    sites = np.arange(len(xyz)) if sites is None else np.asarray(sites)
+    R = xyz[sites]
+    eta = np.asarray(el.eta)[sites]
+    r = np.asarray(elyt.xyz, dtype=np.float64)
+    Q = np.asarray(elyt.Q, dtype=np.float64)
+    box = np.asarray(el.box, dtype=np.float64)
+    V = float(box[0] * box[1] * box[2])
+    a = el.alpha
+    b = np.zeros(len(sites))
+    if len(Q):
+        for c0 in range(0, len(sites), 256):
+            pair = _realspace(R[c0:c0 + 256], r, eta[c0:c0 + 256][:, None] * np.ones((1, len(r))), box, a,
+                              el.rcut)
+            b[c0:c0 + 256] += pair @ Q
+        _, k, k2 = kvectors(box, el.kcut)
+        w = kweights(k2, a, V)
+        for c0 in range(0, len(k), kchunk):
+            kk = k[c0:c0 + kchunk]
+            rho = structure_factor(kk, elyt)
+            ph = R @ kk.T
+            b += (np.cos(ph) * rho.real + np.sin(ph) * rho.imag) @ w[c0:c0 + kchunk]
+    Qtot = float(Q.sum())
+    b += -math.pi * Qtot / (V * a * a)
+    if el.boundary == "slab":
+        b += (4.0 * math.pi / V) * R[:, 2] * float(Q @ r[:, 2]) if len(Q) else 0.0
+    elif el.boundary == "wire" and len(Q):
+        b += (2.0 * math.pi / V) * (R[:, 0] * float(Q @ r[:, 0]) + R[:, 1] * float(Q @ r[:, 1]))
+    return K_E * b
+
+
+# --------------------------------------------------------------------------- inversion and charges
+
+def capacitance_matrix(A, symm=True):
+    """A^-1 by Cholesky, then the neutral projection of Eq. (S) when ``symm``.
+
+    Raises numpy.linalg.LinAlgError when A is not positive definite.
+    """
+    n = A.shape[0]
+    L = np.linalg.cholesky(A)
+    Ainv = sla.cho_solve((L, True), np.eye(n))
+    if not symm:
+        return Ainv
+    e = np.ones(n)
+    d = Ainv @ e
+    return Ainv - np.outer(d, d) / (e @ d)
+
+
+def site_potentials(el, psi):
+    """v = G psi: the applied potential of each site's electrode (Sec. II.B)."""
+    return np.asarray(psi, dtype=np.float64)[np.asarray(el.group)]
+
+
+def charges(S, el, psi, b):
+    """q* = S (v - b) for one electrolyte vector b (n,) or several (n, m)."""
+    v = site_potentials(el, psi)
+    if np.ndim(b) == 2:
+        return S @ (v[:, None] - b)
+    return S @ (v - b)
+
+
+def electrode_capacitance(S, el):
+    """C~ = G^T S G, the electrode-wise capacitance matrix (N_g x N_g)."""
+    G = np.zeros((el.n, el.n_groups))
+    G[np.arange(el.n), np.asarray(el.group)] = 1.0
+    return G.T @ S @ G
+
+
+def energy(A, b, v, q):
+    """Electrode energy of Eq. (coulomb) in API sign: 1/2 q^T A q + b^T q - v^T q."""
+    return 0.5 * q @ A @ q + b @ q - v @ q
+
+
+def update(S, el, elyt, psi):
+    """One charge update: b for this electrolyte, q = S (v - b), and the total charge."""
+    b = bvec(el, elyt)
+    q = charges(S, el, psi, b)
+    return b, q, float(q.sum())

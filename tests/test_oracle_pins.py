@@ -1,0 +1,286 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names the part of the method it pins and why a plausible mistake
+there (a dropped term, a wrong sign, factor or index) would fail it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+from oracle import cpm_oracle as o
+from paper_2203_15461_gb300 import systems as s
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _sites(xyz, eta, box, boundary, alpha, rcut, ktol, group=None, n_groups=1):
+    n = len(xyz)
+    return s.Electrodes(xyz=np.asarray(xyz, float), eta=np.asarray(eta, float),
+                        group=np.zeros(n, np.int32) if group is None else np.asarray(group, np.int32),
+                        n_groups=n_groups, box=np.asarray(box, float), boundary=boundary, alpha=alpha,
+                        rcut=rcut, kcut=s.kcut_from_tol(alpha, ktol))
+
+
+# ----------------------------------------------------------------------------- units
+
+def test_coulomb_constant_from_codata():
+    """K_E = e / (4 pi eps0 * 1 Angstrom) in volts, from the SI-exact e and CODATA 2018 eps0."""
+    e = 1.602176634e-19
+    eps0 = 8.8541878128e-12
+    assert abs(e / (4 * math.pi * eps0 * 1e-10) / o.K_E - 1) < 1e-7
+
+
+# ----------------------------------------------------------------------------- pair law (Sec. III.B)
+
+@pytest.mark.parametrize("ei,ej,r", [(1.979, 1.979, 0.0), (1.805, 1.805, 0.0), (1.979, 1.979, 0.8),
+                                     (1.805, 1.2, 2.1), (1.805, 1.2, 0.25)])
+def test_gaussian_pair_law_by_quadrature(ei, ej, r):
+    """Two unit Gaussian clouds of Sec. III.B interact as erf(eta_ij r)/r, 1/eta_ij^2 = 1/eta_i^2 + 1/eta_j^2;
+    r = 0 with eta_i = eta_j is one cloud's self energy sqrt(2) eta/sqrt(pi).  This pins the combination
+    rule and the self term that brute-force sums below (and the oracle's A) rely on."""
+    E = bf.gaussian_pair_energy(ei, ej, r)
+    ref = bf._self_phi(ei) if (r == 0 and ei == ej) else (
+        2 * ei * ej / math.sqrt(ei * ei + ej * ej) / math.sqrt(math.pi) if r == 0 else bf._pair_phi(ei, ej, r))
+    assert abs(E / ref - 1) < 1e-10
+
+
+# ----------------------------------------------------------------------------- brute-force lattice sums
+
+def _small_system(seed, n, extent):
+    rng = np.random.default_rng(seed)
+    xyz = np.column_stack([rng.uniform(0, extent[0], n), rng.uniform(0, extent[1], n),
+                           rng.uniform(0, extent[2], n)])
+    eta = rng.uniform(1.2, 2.0, n)
+    q = rng.normal(size=n)
+    return xyz, eta, q - q.mean()
+
+
+def test_wire_elastance_matches_direct_line_sum():
+    """Ewald A + the 1D correction of Eq. (ew3dc_wire) converges, as the x/y vacuum grows, to the direct sum
+    over images along z.  Without the correction (or with the wrong sign or factor) the error at 60 A of
+    padding is ~1e-4."""
+    Lz = 6.0
+    xyz, eta, q = _small_system(5, 5, (6, 6, Lz))
+    Rs = [400, 800, 1600, 3200, 6400]
+    E_direct = bf.extrapolate(Rs, [bf.lattice_energy("wire", (0, 0, Lz), xyz, eta, q, R) for R in Rs], [2, 4])
+    Es, Ps = [], [60.0, 90.0, 120.0]
+    for P in Ps:
+        el = _sites(xyz + [P / 2, P / 2, 0], eta, (P, P, Lz), "wire", 0.35, 16.0, 1e-16)
+        Es.append(0.5 * q @ o.assemble_A(el) @ q / o.K_E)
+    E_ewald = bf.extrapolate(Ps, Es, [4, 6])
+    assert abs(E_ewald / E_direct - 1) < 2e-8
+    el3 = _sites(xyz + [30, 30, 0], eta, (60, 60, Lz), "3d", 0.35, 16.0, 1e-16)
+    assert abs(0.5 * q @ o.assemble_A(el3) @ q / o.K_E / E_direct - 1) > 1e-4
+
+
+def test_slab_elastance_matches_direct_plane_sum():
+    """Ewald A + the slab correction of Eq. (ew3dc_slab) (electrode-electrode part z_i z_j) equals the direct
+    sum over the 2D lattice of images (square truncation, extrapolated); tin-foil 3D does not."""
+    Lx, Ly = 7.0, 6.0
+    xyz, eta, q = _small_system(7, 5, (Lx, Ly, 4.0))
+    Rs = [30, 40, 60, 80, 120, 160]
+    E_direct = bf.extrapolate(Rs, [bf.lattice_energy("slab", (Lx, Ly, 0), xyz, eta, q, R) for R in Rs],
+                              [1, 2, 3, 4])
+    el = _sites(xyz, eta, (Lx, Ly, 40.0), "slab", 0.4, 14.0, 1e-16)
+    E = 0.5 * q @ o.assemble_A(el) @ q / o.K_E
+    assert abs(E / E_direct - 1) < 1e-7
+    el3 = _sites(xyz, eta, (Lx, Ly, 40.0), "3d", 0.4, 14.0, 1e-16)
+    assert abs(0.5 * q @ o.assemble_A(el3) @ q / o.K_E / E_direct - 1) > 1e-3
+
+
+def test_tinfoil_3d_elastance_matches_cube_sum_minus_surface_term():
+    """Tin-foil Ewald = direct sum over a growing cube of cells minus the surface term 2 pi |M|^2 / 3V
+    (de Leeuw, Perram and Smith); pins the reciprocal weights, self and background terms in 3D."""
+    L = (6.5, 6.5, 6.5)   # a cube of cubic cells has the sphere's depolarisation factors 1/3
+    xyz, eta, q = _small_system(11, 4, L)
+    Rs = [8, 10, 12, 16, 20, 24]
+    E_cube = bf.extrapolate(Rs, [bf.lattice_energy("3d", L, xyz, eta, q, R) for R in Rs], [1, 2, 3])
+    M = q @ xyz
+    V = L[0] * L[1] * L[2]
+    el = _sites(xyz, eta, L, "3d", 0.5, 12.0, 1e-16)
+    E = 0.5 * q @ o.assemble_A(el) @ q / o.K_E
+    assert abs(E - (E_cube - 2 * math.pi * (M @ M) / (3 * V))) < 1e-6 * abs(E)
+
+
+@pytest.mark.parametrize("kind", ["wire", "slab"])
+def test_electrolyte_vector_matches_direct_cross_sum(kind):
+    """q^T b equals the direct image sum of Gaussian-site / point-charge energies erf(eta_i r)/r, including the
+    electrolyte part of the boundary term (z_i M_z for the slab, x_i M_x + y_i M_y for the wire)."""
+    rng = np.random.default_rng(3)
+    if kind == "wire":
+        Lz = 5.0
+        xyz, eta, q = _small_system(13, 4, (5, 5, Lz))
+        rj = np.column_stack([rng.uniform(0, 5, 4), rng.uniform(0, 5, 4), rng.uniform(0, Lz, 4)])
+        Q = np.array([1.0, -1.0, 0.5, -0.5])
+        Rs = [400, 800, 1600, 3200, 6400]
+        ref = bf.extrapolate(Rs, [bf.lattice_cross("wire", (0, 0, Lz), xyz, eta, q, rj, Q, R) for R in Rs], [2, 4])
+        Es, Ps = [], [60.0, 90.0, 120.0]
+        for P in Ps:
+            sh = np.array([P / 2, P / 2, 0])
+            el = _sites(xyz + sh, eta, (P, P, Lz), "wire", 0.35, 16.0, 1e-16)
+            Es.append(q @ o.bvec(el, s.Electrolyte(xyz=rj + sh, Q=Q)) / o.K_E)
+        got = bf.extrapolate(Ps, Es, [4, 6])
+        assert abs(got / ref - 1) < 2e-8
+    else:
+        Lx, Ly = 6.0, 7.0
+        xyz, eta, q = _small_system(17, 4, (Lx, Ly, 3.0))
+        rj = np.column_stack([rng.uniform(0, Lx, 4), rng.uniform(0, Ly, 4), rng.uniform(3, 8, 4)])
+        Q = np.array([1.0, -1.0, 0.5, -0.5])
+        Rs = [30, 40, 60, 80, 120, 160]
+        ref = bf.extrapolate(Rs, [bf.lattice_cross("slab", (Lx, Ly, 0), xyz, eta, q, rj, Q, R) for R in Rs],
+                             [1, 2, 3, 4])
+        el = _sites(xyz, eta, (Lx, Ly, 60.0), "slab", 0.4, 14.0, 1e-16)
+        got = q @ o.bvec(el, s.Electrolyte(xyz=rj, Q=Q)) / o.K_E
+        assert abs(got / ref - 1) < 1e-7
+
+
+# ----------------------------------------------------------------------------- Ewald splitting
+
+def test_alpha_independence_of_A_b_S_q():
+    """A (with its background constant), b for a NON-neutral electrolyte, S and q do not depend on the Ewald
+    splitting alpha once both sums are converged.  A wrong reciprocal weight, self term, background term or
+    cut-off rule breaks this at the 1e-3 level."""
+    el0, ely, psi = s.workload_tiny_slab(seed=4)
+    pick = np.r_[0:21, 50:70]   # 21 cations, 20 anions: net charge +1 e
+    ely = s.Electrolyte(xyz=ely.xyz[pick], Q=ely.Q[pick])
+    assert abs(ely.Q.sum() - 1.0) < 1e-12
+    res = []
+    for a in (0.28, 0.34, 0.42):
+        rc = 6.0 / a   # erfc(6) ~ 2e-17
+        el = s.Electrodes(**{**el0.__dict__, "alpha": a, "rcut": rc, "kcut": s.kcut_from_tol(a, 1e-17)})
+        A = o.assemble_A(el)
+        b = o.bvec(el, ely)
+        S = o.capacitance_matrix(A)
+        res.append((A, b, S, o.charges(S, el, psi, b)))
+    for A, b, S, q in res[1:]:
+        A0, b0, S0, q0 = res[0]
+        assert np.linalg.norm(A - A0) / np.linalg.norm(A0) < 1e-11
+        assert np.linalg.norm(b - b0) / np.linalg.norm(b0) < 1e-11
+        assert np.linalg.norm(S - S0) / np.linalg.norm(S0) < 1e-10
+        assert np.linalg.norm(q - q0) / np.linalg.norm(q0) < 1e-10
+
+
+# ----------------------------------------------------------------------------- Eq. (S) and the charge solution
+
+@pytest.fixture(scope="module")
+def tiny():
+    el, ely, psi = s.workload_tiny_slab(seed=2)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    b = o.bvec(el, ely)
+    return el, ely, psi, A, S, b
+
+
+def test_A_symmetric_positive_definite(tiny):
+    el, _, _, A, _, _ = tiny
+    assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+
+
+def test_S_projection_properties(tiny):
+    """Eq. (S): S symmetric, S e = 0, and S is unchanged when c e e^T is added to A (so the background
+    constant and any uniform shift of A drop out)."""
+    el, _, _, A, S, _ = tiny
+    e = np.ones(el.n)
+    assert np.abs(S - S.T).max() <= 1e-12 * np.abs(S).max()
+    assert np.linalg.norm(S @ e) <= 1e-13 * np.linalg.norm(S) * math.sqrt(el.n)
+    S2 = o.capacitance_matrix(A + 3.7 * np.outer(e, e))
+    assert np.linalg.norm(S2 - S) <= 1e-11 * np.linalg.norm(S)
+    Sinv = o.capacitance_matrix(A, symm=False)
+    assert np.linalg.norm(Sinv @ A - np.eye(el.n)) < 1e-10
+
+
+def test_charges_neutral_optimal_and_kkt(tiny):
+    """q* = S(v - b) is neutral, satisfies A q* + b - v = lambda e (stationarity with the neutrality
+    multiplier) and no neutral perturbation lowers the Eq. (coulomb) energy."""
+    el, _, psi, A, S, b = tiny
+    q = o.charges(S, el, psi, b)
+    v = o.site_potentials(el, psi)
+    assert abs(q.sum()) < 1e-12
+    r = A @ q + b - v
+    assert np.abs(r - r.mean()).max() < 1e-10 * np.abs(v - b).max()
+    U0 = o.energy(A, b, v, q)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        d = rng.normal(size=el.n) * 1e-3
+        d -= d.mean()
+        assert o.energy(A, b, v, q + d) > U0
+
+
+def test_charges_linear_in_potential(tiny):
+    """Eq. (electrode-wise): at fixed b the charges are affine in psi; in vacuum they scale with psi."""
+    el, _, _, _, S, b = tiny
+    q = lambda p: o.charges(S, el, np.asarray(p, float), b)
+    lhs = q([0.3, 1.1]) + q([-0.2, 0.6]) - q([0.0, 0.0])
+    assert np.linalg.norm(lhs - q([0.1, 1.7])) < 1e-12 * np.linalg.norm(lhs)
+    z = np.zeros(el.n)
+    assert np.linalg.norm(o.charges(S, el, [0, 2.0], z) - 2 * o.charges(S, el, [0, 1.0], z)) < 1e-13
+
+
+def test_slab_translation_invariance():
+    """Shifting every electrode site and ion by the same z leaves q unchanged for a neutral electrolyte:
+    the origin of the dipole terms of Sec. II.E drops out after the neutral projection."""
+    el, ely, psi = s.workload_tiny_slab(seed=6)
+    q0 = o.charges(o.capacitance_matrix(o.assemble_A(el)), el, psi, o.bvec(el, ely))
+    sh = np.array([0.0, 0.0, 3.3])
+    el2 = s.Electrodes(**{**el.__dict__, "xyz": el.xyz + sh})
+    ely2 = s.Electrolyte(xyz=ely.xyz + sh, Q=ely.Q)
+    q1 = o.charges(o.capacitance_matrix(o.assemble_A(el2)), el2, psi, o.bvec(el2, ely2))
+    assert np.linalg.norm(q1 - q0) / np.linalg.norm(q0) < 1e-11
+
+
+# ----------------------------------------------------------------------------- physics closed forms
+
+def test_gauss_law_field_between_plates():
+    """Between two charged plates the potential is linear in z with slope sigma/eps0 (Gauss's law), sigma the
+    charge per area of the positive electrode.  Ties the normalisation of b (probe potential) to A."""
+    el = s.au111_slab()
+    S = o.capacitance_matrix(o.assemble_A(el))
+    q = S @ o.site_potentials(el, [0.0, 1.0])
+    Q2 = q[el.group == 1].sum()
+    zs = np.linspace(el.z_inner[0] + 7, el.z_inner[1] - 7, 7)
+    probes = np.column_stack([np.full(7, 3.1), np.full(7, 5.2), zs])
+    pel = s.Electrodes(xyz=probes, eta=np.full(7, 1.979), group=np.zeros(7, np.int32), n_groups=1, box=el.box,
+                       boundary="slab", alpha=el.alpha, rcut=el.rcut, kcut=el.kcut)
+    phi = o.bvec(pel, s.Electrolyte(xyz=el.xyz, Q=q))
+    slope, icpt = np.polyfit(zs, phi, 1)
+    assert abs(slope / (Q2 / (o.EPS0 * el.area)) - 1) < 1e-6
+    assert np.abs(np.polyval([slope, icpt], zs) - phi).max() < 1e-7
+
+
+def test_parallel_plate_capacitance_slope():
+    """Vacuum capacitor: 1/C0 is linear in the gap d with slope 1/(eps0 Area) (C0 = eps0 A / d_eff).
+    C0 = g_2^T S g_2 (Sec. II.C, III.B)."""
+    inv = []
+    ds = (20.0, 30.0, 40.0)
+    for d in ds:
+        el = s.au111_slab(gap=d)
+        C = o.electrode_capacitance(o.capacitance_matrix(o.assemble_A(el)), el)
+        assert abs(C[0, 0] - C[1, 1]) < 1e-12 and abs(C[0, 1] + C[1, 1]) < 1e-12
+        inv.append(1.0 / C[1, 1])
+    area = s.au111_slab().area
+    for sl in np.diff(inv) / np.diff(ds):
+        assert abs(sl * o.EPS0 * area - 1) < 1e-6
+
+
+def test_coaxial_capacitor_sec_IIIB():
+    """Sec. III.B: co-axial tubes with the 1D correction.  C0/L is the same for 1, 2 and 3 periodic cells (it
+    is a property per length), approaches 2 pi eps0 / ln(R2/R1) as the radii grow at a fixed ratio, and is
+    larger for wider Gaussians (smaller eta)."""
+    CL = []
+    for nc in (1, 2, 3):
+        el = s.coaxial_tubes(nc)
+        CL.append(o.electrode_capacitance(o.capacitance_matrix(o.assemble_A(el)), el)[1, 1] / el.box[2])
+    assert max(CL) - min(CL) < 1e-9 * CL[0]
+    ana = 2 * math.pi * o.EPS0 / math.log(2.0)
+    dev_small = CL[0] / ana - 1
+    el = s.coaxial_tubes(1, n_inner=20, n_outer=40, pad=2.0)
+    dev_large = o.electrode_capacitance(o.capacitance_matrix(o.assemble_A(el)), el)[1, 1] / el.box[2] / ana - 1
+    assert 0 < dev_large < dev_small < 0.1
+    C_eta = []
+    for eta in (1.5, 1.805, 2.2):
+        el = s.coaxial_tubes(1, eta=eta)
+        C_eta.append(o.electrode_capacitance(o.capacitance_matrix(o.assemble_A(el)), el)[1, 1])
+    assert C_eta[0] > C_eta[1] > C_eta[2]
