@@ -1,0 +1,344 @@
+"""Benchmark of the CPM charge update (b-vector + S (v - b)) on one GB300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--replicas M]
+
+Workload: the 4,320-site graphene-like EDL capacitor (3 layers per electrode, 60 A gap,
+1,800 rigid 3-site waters + 150 Na+ + 150 Cl-, slab correction).  One step updates
+M independent replicas of that system (each its own seeded electrolyte, positions
+random-walked by N(0, 0.05 A) per step): b for every replica, then q = S (v - b) and
+the FP64 neutrality fix.  ``value`` is updates per second (replica-updates) of the
+mixed path (FP32 b and S, FP64 neutrality and totals); the plain FP64 path is timed
+beside it.  Inputs are resident in HBM; L2 is flushed (256 MB write) before every
+timed step and only the step itself is inside the CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CPM charge updates/s (b-vector + S·b) batched-mixed vs plain FP64, 1 GB300"
+WORKLOAD = "edl_capacitor_4320"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _fp32_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_trajectories(el, base_elyt_fn, m, steps, seed):
+    """m replicas x steps configurations (random walk), replica-major per step: (steps, m*ne, 3), (m*ne,)."""
+    from paper_2203_15461_gb300 import systems as s
+    reps = [base_elyt_fn(seed + r) for r in range(m)]
+    ne = max(e.n for e in reps)
+    rng = np.random.default_rng(seed + 10007)
+    xyz = np.zeros((steps, m, ne, 3))
+    Q = np.zeros((m, ne))
+    for r, e in enumerate(reps):
+        Q[r, :e.n] = e.Q
+        cur = e.xyz.copy()
+        for t in range(steps):
+            cur = cur + rng.normal(scale=0.05, size=cur.shape)
+            xyz[t, r, :e.n] = cur
+    return xyz.reshape(steps, m * ne, 3), Q.reshape(-1), ne
+
+
+def time_path(torch, ctx, xyz_dev, Q_dev, psi_dev, m, ne, warmup, steps, flush, profile=False):
+    """Per-step CUDA-event timing on the context stream; L2 flushed before every step."""
+    n = ctx.n
+    b = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    q = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    qt = torch.empty((m,), dtype=torch.float64, device="cuda")
+    T = xyz_dev.shape[0]
+    for t in range(warmup):
+        ctx.cpm_bvec(m, ne, xyz_dev[t % T], Q_dev, b)
+        ctx.cpm_update(m, psi_dev, b, q, qt)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = ctx.cpm_launch_count()
+    if profile:
+        ctx.cpm_profile_read(reset=True)
+        ctx.cpm_profile(True)
+    for t in range(steps):
+        flush.zero_()
+        evs[t][0].record()
+        ctx.cpm_bvec(m, ne, xyz_dev[(warmup + t) % T], Q_dev, b)
+        ctx.cpm_update(m, psi_dev, b, q, qt)
+        evs[t][1].record()
+    torch.cuda.synchronize()
+    if profile:
+        ctx.cpm_profile(False)
+    launches = ctx.cpm_launch_count() - launches0
+    ms = [a.elapsed_time(bb) for a, bb in evs]
+    prof = ctx.cpm_profile_read(reset=True) if profile else None
+    return sum(ms), launches, prof, q, qt
+
+
+def kernel_work(ctx, el, nk, ne, m):
+    """Algorithmic work per launch of the per-step kernels (flops or bytes), see the design doc."""
+    n = el.n
+    return {
+        "sf": ("flop", 8.0 * ne * nk * m),            # one complex multiply-add per (charge, k)
+        "site": ("flop", 8.0 * n * nk * m),           # one complex multiply-add per (site, k)
+        "gemv": ("byte", 4.0 * n * n),               # S streamed once (FP32) per launch
+    }
+
+
+def cpu_baseline(el, ely, psi, frac=8):
+    """The oracle's update, timed on a bounded sample and scaled to one full update."""
+    from oracle import cpm_oracle as o
+    sites = np.arange(0, el.n, frac)
+    box = np.asarray(el.box)
+    V = float(np.prod(box))
+    _, k, k2 = o.kvectors(box, el.kcut)
+    ksub = np.arange(0, len(k), frac)
+    t0 = time.perf_counter()
+    bre = o.bvec(type(el)(**{**el.__dict__, "kcut": 1e-9}), ely, sites=sites)      # real space (+ tiny terms)
+    t1 = time.perf_counter()
+    rho = o.structure_factor(k[ksub], ely)
+    t2 = time.perf_counter()
+    w = o.kweights(k2[ksub], el.alpha, V)
+    ph = el.xyz[sites] @ k[ksub].T
+    _ = (np.cos(ph) * rho.real + np.sin(ph) * rho.imag) @ w
+    t3 = time.perf_counter()
+    Sfake = np.eye(el.n)
+    v = o.site_potentials(el, psi)
+    t4 = time.perf_counter()
+    _ = Sfake @ (v - np.zeros(el.n))
+    t5 = time.perf_counter()
+    per_update = (t1 - t0) * frac + (t2 - t1) * frac + (t3 - t2) * frac * frac + (t5 - t4)
+    return {"value": 1.0 / per_update, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"numpy FP64 oracle on the same system: real-space b at 1/{frac} of the sites, structure "
+                       f"factor over 1/{frac} of the k-vectors, site k-sum over both subsets, one n x n matvec; "
+                       f"each part scaled by its sampled fraction to one full update (elementwise numpy on one "
+                       f"thread, BLAS on {os.cpu_count()})"),
+            "sample_seconds": t5 - t0}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores, same workload, sampled per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2203_15461_gb300 import systems as s
+    el, ely, psi = s.workload_edl_capacitor(seed=1)
+    samples = []
+    for t in range(args.warmup + args.steps):
+        r = cpu_baseline(el, s.jitter(ely, 0.05, np.random.default_rng(t)), psi)
+        if t >= args.warmup:
+            samples.append(1.0 / r["value"])
+    tot = sum(samples)
+    val = args.steps / tot
+    line = {"metric": METRIC, "value": val, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sites": el.n, "n_charges": ely.n, "replicas_per_step": 1},
+            "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--replicas", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    args.steps = max(1, args.steps)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2203_15461_gb300 import systems as s
+    from paper_2203_15461_gb300.cpm import CPM
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    el, ely0, psi = s.workload_edl_capacitor(seed=1)
+    m, K, W = args.replicas, args.steps, args.warmup
+    seed = 1000 * (rank + 1)
+    T = K + W
+    xyz, Q, ne = make_trajectories(el, lambda sd: s.workload_edl_capacitor(seed=sd)[1], m, T, seed)
+    xyz_dev = torch.as_tensor(xyz, device="cuda")
+    Q_dev = torch.as_tensor(Q, device="cuda")
+    psi_dev = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    t_setup = time.perf_counter()
+    mixed = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32").setup(el)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    plain = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64").setup(el)
+    nk = int(len(mixed.cpm_kvectors()))
+
+    # mixed, batched: the headline
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ms, launches, prof, q_mix, _ = time_path(torch, mixed, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush,
+                                                 profile=True)
+    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * m * K / (ms_max / 1e3)
+
+    # plain FP64, one replica per step (the 1x of the metric)
+    K64 = max(3, min(K, 10))
+    x1, Q1, ne1 = xyz_dev[:, :ne], Q_dev[:ne], ne
+    ms64, _, _, q64, _ = time_path(torch, plain, x1, Q1, psi_dev[:1], 1, ne1, 3, K64, flush)
+    fp64_value = K64 / (ms64 / 1e3)
+    # mixed, one replica per step
+    ms1, _, _, q1, _ = time_path(torch, mixed, x1, Q1, psi_dev[:1], 1, ne1, 3, K, flush)
+    seq_value = K / (ms1 / 1e3)
+    # mixed vs FP64 on the same configuration
+    _, _, _, qa, qta = time_path(torch, plain, x1[:1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
+    _, _, _, qb, qtb = time_path(torch, mixed, x1[:1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
+    err_mixed = float(torch.linalg.norm(qb[0] - qa[0]) / torch.linalg.norm(qa[0]))
+    qtot_max = float(max(abs(qta).max(), abs(qtb).max()))
+
+    # end to end through the host-buffer entry point
+    hx = torch.empty((m * ne, 3), dtype=torch.float64).pin_memory()
+    hQ = torch.as_tensor(Q).pin_memory()
+    hpsi = torch.as_tensor(np.tile(psi, (m, 1))).pin_memory()
+    hq = torch.empty((m, el.n), dtype=torch.float64).pin_memory()
+    hqt = torch.empty((m,), dtype=torch.float64).pin_memory()
+    xyz_host = torch.as_tensor(xyz)
+    for t in range(W):
+        hx.copy_(xyz_host[t])
+        mixed.cpm_step_host(m, ne, hx, hQ, hpsi, hq, hqt)
+    e2e_times = []
+    for t in range(K):
+        hx.copy_(xyz_host[(W + t) % T])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mixed.cpm_step_host(m, ne, hx, hQ, hpsi, hq, hqt)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = {"value": world * m * K / sum(e2e_times), "unit": "updates/s",
+           "h2d_bytes_per_step": int(8 * (m * ne * 4 + m * el.n_groups)),
+           "d2h_bytes_per_step": int(8 * (m * el.n + m))}
+
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    work = kernel_work(mixed, el, nk, ne, m)
+    top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
+    avg_ms = prof[top][0] / prof[top][1]
+    kind, amount = work.get(top, ("flop", float("nan")))
+    if kind == "flop":
+        peak = _fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        achieved = amount / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": f"k_{top}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP32 FMA issue rate 152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = amount / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": f"k_{top}", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+    roof["share_of_step"] = prof[top][0] / ms
+
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sites": el.n, "n_charges": ne, "n_kvectors": nk,
+                       "replicas_per_step": m, "path": "mixed: FP32 b and S, FP64 neutrality and totals",
+                       "boundary": "slab EW3DC", "alpha": el.alpha, "rcut": el.rcut,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+            "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value, "sequential_mixed_value": seq_value,
+            "rel_err_mixed_vs_fp64": err_mixed, "max_abs_qtot": qtot_max, "setup_seconds": t_setup,
+            "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items()}}
+    clocks = clk.summary()
+    line["clocks"] = clocks
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(el, ely0, psi)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * cpm.h - C ABI of the GB300 constant potential method (CPM) library.
+ *
+ * The library computes the two parts of the CPM hot path of the ELECTRODE
+ * paper (arXiv 2203.15461):
+ *
+ *   1. once per electrode geometry: the elastance matrix A of Eq. (coulomb),
+ *      Sec. II.A (Gaussian electrode charges of Sec. III.B, Ewald real- and
+ *      reciprocal-space sums, self terms, and the slab / wire boundary terms of
+ *      Eqs. (ew3dc_slab) and (ew3dc_wire), Sec. II.E), its inverse and the
+ *      charge-neutral capacitance matrix S of Eq. (S), Sec. II.A;
+ *   2. per MD step and electrolyte configuration: the electrolyte potential b
+ *      at every electrode site and the electrode charges q = S (v - b) with
+ *      v = G psi (Eq. electrode-wise, Sec. II.B).
+ *
+ * Sign convention: b_i is the electrostatic potential of the electrolyte at
+ * site i (the paper's b with the opposite sign), so q = S (v - b).
+ * Units: Angstrom, elementary charge e, volt.  A is in V/e, S in e/V.
+ *
+ * Every entry point returns a cpm_status and never aborts the process.  All
+ * device work is issued on the stream given to cpm_create; calls return when
+ * the work is enqueued unless stated otherwise.  Errors raised by kernels
+ * (a non-positive Cholesky pivot, a non-finite input) are reported by the
+ * next call that synchronises (cpm_invert, cpm_sync, cpm_step_host).
+ *
+ * Array conventions: "device" pointers are CUDA global memory owned by the
+ * caller and only read (or written, for outputs) during the call's stream
+ * work; "host" pointers are ordinary host memory.  Coordinates are row-major
+ * (N x 3) doubles.  Batched vectors are replica-major: element (r, i) of an
+ * (m x n) batch is at [r * n + i].
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPM_OK = 0,
+    CPM_E_ARG = 1,        /* invalid argument (null pointer, bad size or enum) */
+    CPM_E_OOM = 2,        /* a device allocation failed */
+    CPM_E_BUDGET = 3,     /* the request exceeds the context's device-memory budget */
+    CPM_E_NOT_SPD = 4,    /* A is not positive definite (a Cholesky pivot <= 0 or not finite) */
+    CPM_E_STATE = 5,      /* call out of order (e.g. cpm_update before cpm_invert) */
+    CPM_E_CUDA = 6,       /* a CUDA runtime error; see cpm_last_error */
+    CPM_E_TIMEOUT = 7,    /* a bounded device wait expired */
+    CPM_E_NONFINITE = 8   /* an input or result is NaN or infinite */
+} cpm_status;
+
+/* Periodicity and boundary correction (Sec. II.E). */
+typedef enum {
+    CPM_BC_3D = 0,    /* 3D periodic, tin-foil: no correction */
+    CPM_BC_SLAB = 1,  /* x, y periodic; z padded with vacuum; J = 2 pi M_z^2 / V (Eq. ew3dc_slab) */
+    CPM_BC_WIRE = 2   /* z periodic; x, y padded with vacuum; J = pi (M_x^2 + M_y^2) / V (Eq. ew3dc_wire) */
+} cpm_boundary;
+
+/* Arithmetic of a per-step stage. */
+typedef enum {
+    CPM_PREC_FP64 = 0,  /* IEEE double throughout */
+    CPM_PREC_FP32 = 1   /* single precision products and accumulation, FP64 neutrality and totals */
+} cpm_precision;
+
+typedef struct {
+    double box[3];       /* Ewald cell (Lx, Ly, Lz) in Angstrom, vacuum padding included */
+    int32_t boundary;    /* cpm_boundary */
+    double alpha;        /* Ewald splitting parameter (1/Angstrom) */
+    double rcut;         /* real-space cut-off: pairs with |r| < rcut over all images count */
+    double kcut;         /* reciprocal cut-off: k = 2 pi (nx/Lx, ny/Ly, nz/Lz) counts when
+                            ((kx*kx + ky*ky) + kz*kz) <= kcut*kcut */
+    int32_t symm;        /* 1: S of Eq. (S) (neutral electrodes); 0: S = A^-1 */
+    int32_t s_prec;      /* cpm_precision of the S (v - b) product */
+    int32_t k_prec;      /* cpm_precision of the b-vector sums (real and reciprocal space) */
+    size_t hbm_budget;   /* bytes of device memory this context may allocate; 0 = no limit */
+} cpm_params;
+
+typedef struct cpm_ctx cpm_ctx;
+
+/*
+ * Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns all
+ * device state it allocates and frees it in cpm_destroy.
+ * Errors: CPM_E_ARG for a null `p`/`out` or non-positive box, alpha, rcut or
+ * kcut; CPM_E_CUDA when no CUDA device is usable (there is no CPU fallback).
+ */
+cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out);
+
+/* Free every device buffer of the context and the context itself.  NULL is a no-op. */
+void cpm_destroy(cpm_ctx* ctx);
+
+/*
+ * Assemble the elastance matrix A (n x n, V/e) of the electrode sites
+ * (Eq. coulomb, Sec. II.A; Gaussian charges of Sec. III.B):
+ *   A_ij = K_E [ sum'_images (erfc(alpha r) - erfc(eta_ij r)) / r
+ *               + sum_{0<|k|<=kcut} (4 pi / V) exp(-k^2/4alpha^2) / k^2 cos(k.(R_i - R_j))
+ *               + delta_ij (sqrt(2) eta_i - 2 alpha) / sqrt(pi) - pi / (V alpha^2) + B_ij ],
+ *   eta_ij = eta_i eta_j / sqrt(eta_i^2 + eta_j^2),
+ *   B_ij = (4 pi / V) z_i z_j (slab), (2 pi / V)(x_i x_j + y_i y_j) (wire), 0 (3D).
+ * xyz: device, n x 3 doubles; eta: device, n doubles (1/Angstrom, > 0);
+ * group: device, n int32 in [0, n_groups) - the electrode of each site
+ * (indicator matrix G of Sec. II.B).  Inputs are copied; the caller may free
+ * them once the stream has passed this call.  Replaces any previous geometry.
+ * Errors: CPM_E_ARG (n < 1, n_groups < 1, null pointers), CPM_E_BUDGET, CPM_E_OOM.
+ */
+cpm_status cpm_assemble(cpm_ctx* ctx, int64_t n, const double* xyz, const double* eta,
+                        const int32_t* group, int32_t n_groups);
+
+/*
+ * Factor A = L L^T (FP64 blocked Cholesky), form A^-1 and, with symm = 1, the
+ * neutral capacitance matrix S = A^-1 - A^-1 e e^T A^-1 / (e^T A^-1 e)
+ * (Eq. S, Sec. II.A), the electrode response SG = S G (n x N_g) and the
+ * neutraliser u = A^-1 e / (e^T A^-1 e).  Synchronises the stream.
+ * Errors: CPM_E_STATE (no geometry), CPM_E_NOT_SPD, CPM_E_OOM, CPM_E_CUDA.
+ */
+cpm_status cpm_invert(cpm_ctx* ctx);
+
+/*
+ * Electrolyte potential at every electrode site for m electrolyte
+ * configurations of n_e point charges each (pad with Q = 0 charges for
+ * replicas with fewer):
+ *   b_i = K_E [ sum_j Q_j sum'_images (erfc(alpha r) - erfc(eta_i r)) / r
+ *               + sum_k w_k Re(exp(-i k.R_i) rho(k)) - pi Q_tot / (V alpha^2) + B_i ],
+ *   rho(k) = sum_j Q_j exp(i k.r_j),  w_k = (8 pi / V) exp(-k^2/4alpha^2)/k^2 (half space),
+ *   B_i = (4 pi / V) z_i M_z (slab), (2 pi / V)(x_i M_x + y_i M_y) (wire), M = sum_j Q_j r_j.
+ * xyz: device, (m * n_e) x 3 doubles; Q: device, m * n_e doubles;
+ * b_out: device, m x n doubles.  Charges with Q == 0 are skipped.
+ * Errors: CPM_E_STATE (no geometry), CPM_E_ARG, CPM_E_OOM, CPM_E_BUDGET.
+ */
+cpm_status cpm_bvec(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
+                    double* b_out);
+
+/*
+ * Electrode charges q = S (G psi - b) for m electrolyte vectors, then (symm = 1)
+ * the neutrality fix q <- q - u (e^T q) in FP64 and qtot = e^T q.
+ * psi: device, m x n_groups doubles (electrode potentials, V); b: device, m x n
+ * (the output of cpm_bvec); q_out: device, m x n; qtot_out: device, m doubles
+ * (may be NULL).
+ * Errors: CPM_E_STATE (not inverted), CPM_E_ARG.
+ */
+cpm_status cpm_update(cpm_ctx* ctx, int32_t m, const double* psi, const double* b, double* q_out,
+                      double* qtot_out);
+
+/*
+ * One complete charge update from HOST buffers: copy the m * n_e charges and the
+ * potentials to the device, run cpm_bvec and cpm_update, copy q and qtot back
+ * and synchronise.  xyz: host, (m * n_e) x 3; Q: host, m * n_e; psi: host,
+ * m x n_groups; q_out: host, m x n; qtot_out: host, m (may be NULL).
+ * Host buffers may be pageable; page-locked memory gives faster copies.
+ */
+cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
+                         const double* psi, double* q_out, double* qtot_out);
+
+/* Wait for all work of the context and report any deferred kernel error. */
+cpm_status cpm_sync(cpm_ctx* ctx);
+
+/* Text of the last error of this context (empty when none).  Valid until the next call. */
+const char* cpm_last_error(const cpm_ctx* ctx);
+
+/* Matrices for cpm_get_matrix. */
+typedef enum { CPM_MAT_A = 0, CPM_MAT_S = 1, CPM_MAT_SG = 2, CPM_MAT_U = 3 } cpm_matrix;
+
+/*
+ * Copy a context matrix into `out` (device): A (n x n, after cpm_assemble),
+ * S (n x n), SG (n x n_groups, row-major) or u (n) after cpm_invert.
+ * Synchronises the stream.
+ */
+cpm_status cpm_get_matrix(cpm_ctx* ctx, int32_t which, double* out);
+
+/* Electrode-wise capacitance C~ = G^T S G (Sec. II.C, III.B); host out, n_groups x n_groups. */
+cpm_status cpm_capacitance(cpm_ctx* ctx, double* C_out);
+
+/*
+ * Reciprocal vectors in use: writes at most `cap` integer triples (nx, ny, nz) of
+ * the half-space set 0 < |k| <= kcut to host `nidx_out` and their count to
+ * *nk (the full count even when it exceeds cap).  Valid after cpm_assemble.
+ */
+cpm_status cpm_kvectors(cpm_ctx* ctx, int32_t* nidx_out, int64_t cap, int64_t* nk);
+
+/* Save / load S and SG with a header that records n, the parameters and a
+ * hash of the geometry (the write_inv / read_inv files of SI Sec. 1.A).
+ * Load requires cpm_assemble of the same geometry first. */
+cpm_status cpm_save(cpm_ctx* ctx, const char* path);
+cpm_status cpm_load(cpm_ctx* ctx, const char* path);
+
+/* Bytes of device memory currently held by the context. */
+size_t cpm_device_bytes(const cpm_ctx* ctx);
+
+/* Number of kernels the per-step calls (cpm_bvec, cpm_update, cpm_step_host) have launched. */
+int64_t cpm_launch_count(const cpm_ctx* ctx);
+
+/* Kernels that cpm_profile can time (per-step path). */
+typedef enum {
+    CPM_K_STATS = 0,    /* per-replica total charge and dipole */
+    CPM_K_CELLS = 1,    /* cell-list binning, scan and scatter */
+    CPM_K_REAL = 2,     /* real-space b */
+    CPM_K_PHASES = 3,   /* electrolyte phase tables */
+    CPM_K_SF = 4,       /* structure factor rho(k) */
+    CPM_K_SFRED = 5,    /* structure-factor split reduction and weighting */
+    CPM_K_SITE = 6,     /* reciprocal-space potential at the sites */
+    CPM_K_COMBINE = 7,  /* b assembly (background, boundary term) */
+    CPM_K_GEMV = 8,     /* S (G psi - b) */
+    CPM_K_NEUTRAL = 9,  /* neutrality fix and total charge */
+    CPM_K_COUNT = 10
+} cpm_kernel;
+
+/*
+ * Tracing: with enable = 1 every later launch of the kernels above is bracketed
+ * by CUDA events on the context stream; enable = 0 stops recording.  The events
+ * stay pending until cpm_profile_read, which synchronises and returns the summed
+ * device time (ms) and the launch count of one kernel since the last reset
+ * (reset = 1 clears all counters after reading).
+ */
+cpm_status cpm_profile(cpm_ctx* ctx, int32_t enable);
+cpm_status cpm_profile_read(cpm_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_H */

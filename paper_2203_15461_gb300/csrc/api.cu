@@ -1,0 +1,474 @@
+// C ABI of the CPM library: argument checks, device-memory ownership, call ordering and the
+// host-buffer entry point.  All arithmetic runs in the kernels of the other translation units.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace cpm {
+
+cpm_status set_err(cpm_ctx* c, cpm_status s, const char* fmt, ...) {
+    if (!c) return s;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return s;
+}
+
+cpm_status cuda_check(cpm_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return CPM_OK;
+    if (e == cudaErrorMemoryAllocation) return set_err(c, CPM_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return set_err(c, CPM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cpm_status dev_alloc(cpm_ctx* c, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->p.hbm_budget && c->bytes + bytes > c->p.hbm_budget)
+        return set_err(c, CPM_E_BUDGET, "device budget of %zu bytes exceeded (%zu held, %zu requested)",
+                       c->p.hbm_budget, c->bytes, bytes);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return set_err(c, CPM_E_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->bytes += bytes;
+    c->owned.push_back(*ptr);
+    c->owned.push_back((void*)bytes);
+    return CPM_OK;
+}
+
+void dev_free(cpm_ctx* c, void* ptr) {
+    if (!ptr) return;
+    for (size_t i = 0; i < c->owned.size(); i += 2) {
+        if (c->owned[i] == ptr) {
+            c->bytes -= (size_t)c->owned[i + 1];
+            c->owned.erase(c->owned.begin() + i, c->owned.begin() + i + 2);
+            break;
+        }
+    }
+    cudaFree(ptr);
+}
+
+static cudaEvent_t take_event(cpm_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+void prof_begin(cpm_ctx* c, int k) {
+    if (!c->prof_on) return;
+    cudaEvent_t e = take_event(c);
+    if (!e) return;
+    cudaEventRecord(e, c->stream);
+    c->prof_open[k] = e;
+}
+
+void prof_end(cpm_ctx* c, int k) {
+    if (!c->prof_on || !c->prof_open[k]) return;
+    cudaEvent_t e = take_event(c);
+    if (!e) return;
+    cudaEventRecord(e, c->stream);
+    c->prof_pending[k].push_back({c->prof_open[k], e});
+    c->prof_open[k] = nullptr;
+}
+
+cpm_status ensure_scratch(cpm_ctx* c, size_t bytes) {
+    if (c->scratch_bytes >= bytes) return CPM_OK;
+    dev_free(c, c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    CPM_TRY(dev_alloc(c, &c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    return CPM_OK;
+}
+
+
+__global__ void k_soa(const double* xyz, const double* eta, const int32_t* grp, int64_t n, int ng, Geometry g,
+                      double* sx, float* s32, int* group, unsigned* status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int d = 0; d < 3; ++d) {
+        double x = xyz[3 * i + d];
+        sx[d * n + i] = x;
+        double w = x - g.boxL[d] * floor(x * g.inv[d]);
+        s32[d * n + i] = (float)w;
+        if (!isfinite(x)) atomicOr(status, ST_NONFINITE);
+    }
+    double e = eta[i];
+    if (!(e > 0.0) || !isfinite(e)) atomicOr(status, ST_NONFINITE);
+    sx[3 * n + i] = e;
+    s32[3 * n + i] = (float)e;
+    int gg = grp[i];
+    if (gg < 0 || gg >= ng) atomicOr(status, ST_NONFINITE);
+    group[i] = gg;
+}
+
+static void free_geometry(cpm_ctx* c) {
+    free_ktable(c);
+    void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz};
+    for (void* p : ptrs) dev_free(c, p);
+    c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
+    c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
+    c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
+    c->S32 = nullptr;
+    c->n = 0;
+    c->assembled = c->inverted = false;
+}
+
+static uint64_t fnv1a(uint64_t h, const void* data, size_t bytes) {
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < bytes; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+}  // namespace cpm
+
+using namespace cpm;
+
+extern "C" {
+
+cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
+    if (!p || !out) return CPM_E_ARG;
+    *out = nullptr;
+    for (int d = 0; d < 3; ++d)
+        if (!(p->box[d] > 0.0)) return CPM_E_ARG;
+    if (!(p->alpha > 0.0) || !(p->rcut > 0.0) || !(p->kcut > 0.0)) return CPM_E_ARG;
+    if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_WIRE) return CPM_E_ARG;
+    if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32) ||
+        (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32))
+        return CPM_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return CPM_E_CUDA;
+    }
+    cpm_ctx* c = new cpm_ctx();
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+    Geometry& g = c->g;
+    for (int d = 0; d < 3; ++d) { g.boxL[d] = p->box[d]; g.inv[d] = 1.0 / p->box[d]; }
+    g.V = p->box[0] * p->box[1] * p->box[2];
+    g.alpha = p->alpha; g.rcut = p->rcut; g.kcut = p->kcut; g.bc = p->boundary;
+    cpm_status s = dev_alloc(c, (void**)&c->status, 256);
+    if (s == CPM_OK) s = dev_alloc(c, (void**)&c->red, sizeof(double) * (64 + 64 * 64));
+    if (s != CPM_OK) { cpm_destroy(c); return s; }
+    cudaMemsetAsync(c->status, 0, 256, c->stream);
+    *out = c;
+    return CPM_OK;
+}
+
+void cpm_destroy(cpm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    for (size_t i = 0; i < c->owned.size(); i += 2) cudaFree(c->owned[i]);
+    for (int k = 0; k < CPM_K_COUNT; ++k)
+        for (auto& pr : c->prof_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* cpm_last_error(const cpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t cpm_device_bytes(const cpm_ctx* c) { return c ? c->bytes : 0; }
+
+int64_t cpm_launch_count(const cpm_ctx* c) { return c ? c->launches : 0; }
+
+cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* eta, const int32_t* group,
+                        int32_t n_groups) {
+    if (!c) return CPM_E_ARG;
+    c->err.clear();
+    if (n < 1 || n_groups < 1 || n_groups > 16 || !xyz || !eta || !group)
+        return set_err(c, CPM_E_ARG, "cpm_assemble: need n >= 1, 1 <= n_groups <= 16 and non-null inputs");
+    if (n > (int64_t)46000) return set_err(c, CPM_E_ARG, "cpm_assemble: n = %lld exceeds 46000", (long long)n);
+    free_geometry(c);
+    c->n = n;
+    c->ng = n_groups;
+    cudaStream_t st = c->stream;
+    CPM_TRY(dev_alloc(c, (void**)&c->sx, sizeof(double) * 4 * n));
+    CPM_TRY(dev_alloc(c, (void**)&c->sxyz, sizeof(double) * 3 * n));
+    CPM_TRY(dev_alloc(c, (void**)&c->s32, sizeof(float) * 4 * n));
+    CPM_TRY(dev_alloc(c, (void**)&c->group, sizeof(int) * n));
+    CPM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), st));
+    CPM_CUDA(c, cudaMemcpyAsync(c->sxyz, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    k_soa<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xyz, eta, group, n, n_groups, c->g, c->sx, c->s32, c->group,
+                                                       c->status);
+    CPM_LAUNCH(c, "k_soa");
+    // geometry hash for cpm_save / cpm_load
+    {
+        std::vector<double> hx(4 * n);
+        std::vector<int> hg(n);
+        unsigned hst = 0;
+        CPM_CUDA(c, cudaMemcpyAsync(hx.data(), c->sx, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
+        CPM_CUDA(c, cudaMemcpyAsync(hg.data(), c->group, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+        CPM_CUDA(c, cudaMemcpyAsync(&hst, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CPM_CUDA(c, cudaStreamSynchronize(st));
+        if (hst) {
+            free_geometry(c);
+            return set_err(c, CPM_E_NONFINITE, "cpm_assemble: non-finite coordinate, eta <= 0 or group out of range");
+        }
+        uint64_t h = 1469598103934665603ull;
+        h = fnv1a(h, hx.data(), hx.size() * sizeof(double));
+        h = fnv1a(h, hg.data(), hg.size() * sizeof(int));
+        h = fnv1a(h, &c->p, sizeof(double) * 3);
+        c->geom_hash = h;
+    }
+    CPM_TRY(build_ktable(c));
+    const KTable& k = c->kt;
+    const size_t pe = phase_elems(k, n);
+    const int64_t tX = (int64_t)(k.NX + 1) * n, tY = (int64_t)(2 * k.NY + 1) * n, tZ = (int64_t)pe - tX - tY;
+    CPM_TRY(dev_alloc(c, (void**)&c->site64.X, sizeof(double2) * tX));
+    CPM_TRY(dev_alloc(c, (void**)&c->site64.Y, sizeof(double2) * tY));
+    CPM_TRY(dev_alloc(c, (void**)&c->site64.Z, sizeof(double2) * tZ));
+    CPM_TRY(dev_alloc(c, (void**)&c->site32.X, sizeof(float2) * tX));
+    CPM_TRY(dev_alloc(c, (void**)&c->site32.Y, sizeof(float2) * tY));
+    CPM_TRY(dev_alloc(c, (void**)&c->site32.Z, sizeof(float2) * tZ));
+    c->site64.P = c->site32.P = n;
+    CPM_TRY(launch_phases<double>(st, c->g, k, c->sxyz, n, c->site64.X, c->site64.Y, c->site64.Z));
+    CPM_TRY(launch_phases<float>(st, c->g, k, c->sxyz, n, c->site32.X, c->site32.Y, c->site32.Z));
+    CPM_LAUNCH(c, "k_phases(sites)");
+    const size_t nn = (size_t)n * n;
+    CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));
+    CPM_TRY(dev_alloc(c, (void**)&c->W, sizeof(double) * nn));
+    CPM_TRY(dev_alloc(c, (void**)&c->S, sizeof(double) * nn));
+    CPM_TRY(dev_alloc(c, (void**)&c->S32, sizeof(float) * nn));
+    CPM_TRY(dev_alloc(c, (void**)&c->SG, sizeof(double) * n * n_groups));
+    CPM_TRY(dev_alloc(c, (void**)&c->u, sizeof(double) * n));
+    CPM_TRY(dev_alloc(c, (void**)&c->dvec, sizeof(double) * n));
+    CPM_TRY(assemble_A(c));
+    CPM_CUDA(c, cudaStreamSynchronize(st));
+    c->assembled = true;
+    return CPM_OK;
+}
+
+cpm_status cpm_invert(cpm_ctx* c) {
+    if (!c) return CPM_E_ARG;
+    c->err.clear();
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_invert before cpm_assemble");
+    c->inverted = false;
+    CPM_TRY(invert_and_project(c));
+    c->inverted = true;
+    return CPM_OK;
+}
+
+cpm_status cpm_bvec(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q, double* b_out) {
+    if (!c) return CPM_E_ARG;
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_bvec before cpm_assemble");
+    if (m < 1 || n_e < 0 || !b_out || (n_e > 0 && (!xyz || !Q)))
+        return set_err(c, CPM_E_ARG, "cpm_bvec: need m >= 1, n_e >= 0 and non-null buffers");
+    if ((int64_t)m * n_e > (int64_t)1 << 30) return set_err(c, CPM_E_ARG, "cpm_bvec: m * n_e too large");
+    return bvec(c, m, n_e, xyz, Q, b_out);
+}
+
+cpm_status cpm_update(cpm_ctx* c, int32_t m, const double* psi, const double* b, double* q_out, double* qtot_out) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_update before cpm_invert");
+    if (m < 1 || !psi || !b || !q_out) return set_err(c, CPM_E_ARG, "cpm_update: need m >= 1 and non-null buffers");
+    return update(c, m, psi, b, q_out, qtot_out);
+}
+
+cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q, const double* psi,
+                         double* q_out, double* qtot_out) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_step_host before cpm_invert");
+    if (m < 1 || n_e < 0 || !psi || !q_out || (n_e > 0 && (!xyz || !Q)))
+        return set_err(c, CPM_E_ARG, "cpm_step_host: need m >= 1, n_e >= 0 and non-null buffers");
+    const size_t pt = (size_t)m * n_e;
+    const size_t need = sizeof(double) * (4 * pt + (size_t)m * c->ng + 2 * (size_t)m * c->n + m) + 8 * 256;
+    if (c->dstage_bytes < need) {
+        dev_free(c, c->dstage);
+        c->dstage = nullptr;
+        c->dstage_bytes = 0;
+        CPM_TRY(dev_alloc(c, &c->dstage, need));
+        c->dstage_bytes = need;
+    }
+    char* base = (char*)c->dstage;
+    auto take = [&](size_t bytes) { char* p = base; base += (bytes + 255) & ~(size_t)255; return (double*)p; };
+    double* dxyz = take(sizeof(double) * 3 * pt);
+    double* dQ = take(sizeof(double) * pt);
+    double* dpsi = take(sizeof(double) * m * c->ng);
+    double* db = take(sizeof(double) * m * c->n);
+    double* dq = take(sizeof(double) * m * c->n);
+    double* dqt = take(sizeof(double) * m);
+    cudaStream_t st = c->stream;
+    if (pt) {
+        CPM_CUDA(c, cudaMemcpyAsync(dxyz, xyz, sizeof(double) * 3 * pt, cudaMemcpyHostToDevice, st));
+        CPM_CUDA(c, cudaMemcpyAsync(dQ, Q, sizeof(double) * pt, cudaMemcpyHostToDevice, st));
+    }
+    CPM_CUDA(c, cudaMemcpyAsync(dpsi, psi, sizeof(double) * m * c->ng, cudaMemcpyHostToDevice, st));
+    CPM_TRY(bvec(c, m, n_e, dxyz, dQ, db));
+    CPM_TRY(update(c, m, dpsi, db, dq, dqt));
+    CPM_CUDA(c, cudaMemcpyAsync(q_out, dq, sizeof(double) * m * c->n, cudaMemcpyDeviceToHost, st));
+    if (qtot_out) CPM_CUDA(c, cudaMemcpyAsync(qtot_out, dqt, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(c, cudaStreamSynchronize(st));
+    return CPM_OK;
+}
+
+cpm_status cpm_sync(cpm_ctx* c) {
+    if (!c) return CPM_E_ARG;
+    unsigned hst = 0;
+    CPM_CUDA(c, cudaMemcpyAsync(&hst, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hst & ST_NOT_SPD) return set_err(c, CPM_E_NOT_SPD, "elastance matrix is not positive definite");
+    if (hst & ST_NONFINITE) return set_err(c, CPM_E_NONFINITE, "non-finite input");
+    if (hst & ST_TIMEOUT) return set_err(c, CPM_E_TIMEOUT, "bounded device wait expired");
+    return CPM_OK;
+}
+
+cpm_status cpm_get_matrix(cpm_ctx* c, int32_t which, double* out) {
+    if (!c || !out) return CPM_E_ARG;
+    const double* src = nullptr;
+    size_t cnt = 0;
+    const size_t n = (size_t)c->n;
+    switch (which) {
+        case CPM_MAT_A: if (!c->assembled) return CPM_E_STATE; src = c->A; cnt = n * n; break;
+        case CPM_MAT_S: if (!c->inverted) return CPM_E_STATE; src = c->S; cnt = n * n; break;
+        case CPM_MAT_SG: if (!c->inverted) return CPM_E_STATE; src = c->SG; cnt = n * c->ng; break;
+        case CPM_MAT_U: if (!c->inverted) return CPM_E_STATE; src = c->u; cnt = n; break;
+        default: return CPM_E_ARG;
+    }
+    CPM_CUDA(c, cudaMemcpyAsync(out, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CPM_OK;
+}
+
+cpm_status cpm_capacitance(cpm_ctx* c, double* C) {
+    if (!c || !C) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_capacitance before cpm_invert");
+    const int64_t n = c->n;
+    const int ng = c->ng;
+    std::vector<double> sg((size_t)n * ng);
+    std::vector<int> gr(n);
+    CPM_CUDA(c, cudaMemcpyAsync(sg.data(), c->SG, sizeof(double) * sg.size(), cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(gr.data(), c->group, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int a = 0; a < ng * ng; ++a) C[a] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int h = 0; h < ng; ++h) C[gr[i] * ng + h] += sg[(size_t)i * ng + h];
+    return CPM_OK;
+}
+
+cpm_status cpm_kvectors(cpm_ctx* c, int32_t* nidx, int64_t cap, int64_t* nk) {
+    if (!c || !nk) return CPM_E_ARG;
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_kvectors before cpm_assemble");
+    *nk = c->kt.nk;
+    const int64_t cnt = std::min<int64_t>(cap, c->kt.nk);
+    if (cnt <= 0 || !nidx) return CPM_OK;
+    std::vector<int4> kl(cnt);
+    CPM_CUDA(c, cudaMemcpyAsync(kl.data(), c->kt.klist, sizeof(int4) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < cnt; ++i) {
+        nidx[3 * i] = kl[i].z;
+        nidx[3 * i + 1] = kl[i].w;
+        nidx[3 * i + 2] = kl[i].y;
+    }
+    return CPM_OK;
+}
+
+struct FileHeader {
+    char magic[8];
+    int32_t version, ng;
+    int64_t n;
+    uint64_t hash;
+    double alpha, rcut, kcut;
+    int32_t boundary, symm;
+};
+
+cpm_status cpm_save(cpm_ctx* c, const char* path) {
+    if (!c || !path) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_save before cpm_invert");
+    const size_t n = (size_t)c->n;
+    FileHeader h{};
+    memcpy(h.magic, "CPMSMAT", 8);
+    h.version = 1; h.ng = c->ng; h.n = c->n; h.hash = c->geom_hash;
+    h.alpha = c->p.alpha; h.rcut = c->p.rcut; h.kcut = c->p.kcut; h.boundary = c->p.boundary; h.symm = c->p.symm;
+    std::vector<double> buf(n * n + n * c->ng + n);
+    CPM_CUDA(c, cudaMemcpyAsync(buf.data(), c->S, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(buf.data() + n * n, c->SG, sizeof(double) * n * c->ng, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(buf.data() + n * n + n * c->ng, c->u, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    FILE* f = fopen(path, "wb");
+    if (!f) return set_err(c, CPM_E_ARG, "cpm_save: cannot open %s", path);
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? CPM_OK : set_err(c, CPM_E_ARG, "cpm_save: write failed for %s", path);
+}
+
+__global__ void k_tofloat(const double* a, float* b, int64_t cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) b[i] = (float)a[i];
+}
+
+cpm_status cpm_load(cpm_ctx* c, const char* path) {
+    if (!c || !path) return CPM_E_ARG;
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_load before cpm_assemble");
+    FILE* f = fopen(path, "rb");
+    if (!f) return set_err(c, CPM_E_ARG, "cpm_load: cannot open %s", path);
+    FileHeader h{};
+    const size_t n = (size_t)c->n;
+    bool ok = fread(&h, sizeof h, 1, f) == 1 && memcmp(h.magic, "CPMSMAT", 8) == 0 && h.version == 1;
+    if (!ok || h.n != c->n || h.ng != c->ng || h.hash != c->geom_hash || h.alpha != c->p.alpha ||
+        h.rcut != c->p.rcut || h.kcut != c->p.kcut || h.boundary != c->p.boundary || h.symm != c->p.symm) {
+        fclose(f);
+        return set_err(c, CPM_E_ARG, "cpm_load: %s does not match this geometry and parameters", path);
+    }
+    std::vector<double> buf(n * n + n * c->ng + n);
+    ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return set_err(c, CPM_E_ARG, "cpm_load: short file %s", path);
+    CPM_CUDA(c, cudaMemcpyAsync(c->S, buf.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->SG, buf.data() + n * n, sizeof(double) * n * c->ng, cudaMemcpyHostToDevice,
+                                c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->u, buf.data() + n * n + n * c->ng, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                c->stream));
+    k_tofloat<<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(c->S, c->S32, (int64_t)(n * n));
+    CPM_LAUNCH(c, "k_tofloat");
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->inverted = true;
+    return CPM_OK;
+}
+
+cpm_status cpm_profile(cpm_ctx* c, int32_t enable) {
+    if (!c) return CPM_E_ARG;
+    c->prof_on = enable != 0;
+    return CPM_OK;
+}
+
+cpm_status cpm_profile_read(cpm_ctx* c, int32_t k, double* total_ms, int64_t* launches, int32_t reset) {
+    if (!c || k < 0 || k >= CPM_K_COUNT) return CPM_E_ARG;
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int j = 0; j < CPM_K_COUNT; ++j) {
+        for (auto& pr : c->prof_pending[j]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+                c->prof_ms[j] += ms;
+                c->prof_cnt[j] += 1;
+            } else {
+                cudaGetLastError();
+            }
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        c->prof_pending[j].clear();
+    }
+    if (total_ms) *total_ms = c->prof_ms[k];
+    if (launches) *launches = c->prof_cnt[k];
+    if (reset)
+        for (int j = 0; j < CPM_K_COUNT; ++j) { c->prof_ms[j] = 0; c->prof_cnt[j] = 0; }
+    return CPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,549 @@
+// Electrolyte vector b: the potential of the electrolyte point charges at every electrode
+// site (Sec. II.A: "the main computational burden" of each MD step), for m electrolyte
+// configurations at once.
+//
+//   b_i = K_E [ sum_j Q_j sum'_n (erfc(alpha r) - erfc(eta_i r)) / r     real space, cell list
+//             + sum_k w_k Re[exp(-i k.R_i) rho(k)]                      reciprocal space
+//             - pi Q_tot / (V alpha^2) + B_i ]                          background, Sec. II.E
+//
+// Reciprocal space in two contractions over the column layout of the k set
+// (column c = (nx, ny), harmonic nz):
+//   structure factor  rho[c][nz] = sum_j (Q_j X_j[nx_c] Y_j[ny_c]) Z_j[nz]
+//   site potential    b_i      += sum_c Re[ conj(X_i[nx_c] Y_i[ny_c]) sum_nz w[c][nz] rho[c][nz] conj(Z_i[nz]) ]
+// both register-tiled on the CUDA cores (complex products of phase-table entries).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cpm {
+
+
+template <typename T> struct V4;
+template <> struct V4<float> { using t = float4; };
+template <> struct V4<double> { using t = double4; };
+
+struct CellGrid {
+    int nc[3];
+    int S[3];        // stencil half-widths (cells)
+    double h[3];     // cell edges
+    int ncells;
+};
+
+static CellGrid make_grid(const Geometry& g) {
+    CellGrid cg;
+    for (int d = 0; d < 3; ++d) {
+        int nc = (int)floor(g.boxL[d] / (0.5 * g.rcut));
+        nc = std::max(1, std::min(nc, 256));
+        cg.nc[d] = nc;
+        cg.h[d] = g.boxL[d] / nc;
+        cg.S[d] = (int)ceil(g.rcut / cg.h[d]);
+    }
+    cg.ncells = cg.nc[0] * cg.nc[1] * cg.nc[2];
+    return cg;
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// ----------------------------------------------------------------------------- per-replica totals
+// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates; one block per replica.
+__global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* stats) {
+    __shared__ double sh[4][256];
+    const int r = blockIdx.x;
+    double a[4] = {0, 0, 0, 0};
+    for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
+        int64_t p = (int64_t)r * ne + j;
+        double q = Q[p];
+        a[0] += q;
+        a[1] += q * xyz[3 * p];
+        a[2] += q * xyz[3 * p + 1];
+        a[3] += q * xyz[3 * p + 2];
+    }
+    for (int t = 0; t < 4; ++t) sh[t][threadIdx.x] = a[t];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int t = 0; t < 4; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) stats[4 * r + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ----------------------------------------------------------------------------- cell list
+template <typename T>
+__global__ void k_bin(const double* xyz, const double* Q, int64_t ptot, int64_t ne, Geometry g, CellGrid cg,
+                      int* key, int* count, typename V4<T>::t* wpos, T* Qv) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ptot) return;
+    int r = (int)(p / ne);
+    double w[3];
+    int ci[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = xyz[3 * p + d];
+        w[d] = x - g.boxL[d] * floor(x * g.inv[d]);
+        if (w[d] >= g.boxL[d]) w[d] -= g.boxL[d];
+        if (w[d] < 0) w[d] = 0;
+        ci[d] = min(cg.nc[d] - 1, (int)(w[d] / cg.h[d]));
+    }
+    int k = r * cg.ncells + (ci[2] * cg.nc[1] + ci[1]) * cg.nc[0] + ci[0];
+    key[p] = k;
+    atomicAdd(&count[k], 1);
+    typename V4<T>::t v;
+    v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)Q[p];
+    wpos[p] = v;
+    Qv[p] = (T)Q[p];
+}
+
+// Per-replica exclusive scan of cell counts into global start offsets (replica r starts at r * ne).
+__global__ void k_cellscan(const int* count, int* start, int ncells, int64_t ne, int m) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = (int)(r * ne);
+    __syncthreads();
+    for (int base = 0; base < ncells; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < ncells ? count[r * ncells + i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - v;
+        if (i < ncells) start[r * ncells + i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (r == m - 1 && threadIdx.x == 0) start[m * ncells] = (int)(m * ne);
+}
+
+template <typename T>
+__global__ void k_scatter(const int* key, const int* start, int* cursor, const typename V4<T>::t* wpos,
+                          int64_t ptot, typename V4<T>::t* sorted) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ptot) return;
+    int k = key[p];
+    int slot = start[k] + atomicAdd(&cursor[k], 1);
+    sorted[slot] = wpos[p];
+}
+
+template <typename T> __device__ __forceinline__ T erfc_t(T x);
+template <> __device__ __forceinline__ float erfc_t<float>(float x) { return erfcf(x); }
+template <> __device__ __forceinline__ double erfc_t<double>(double x) { return erfc(x); }
+
+// Real-space part: one warp per (replica, site); lanes split the stencil cells.
+template <typename T>
+__global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, int64_t n, int m, Geometry g,
+                                                CellGrid cg, const int* __restrict__ start,
+                                                const typename V4<T>::t* __restrict__ sorted, double* out) {
+    int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)m * n) return;
+    const int r = (int)(wid / n);
+    const int64_t i = wid % n;
+    double sw[3];
+    int ci[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = sx[d * n + i];
+        sw[d] = x - g.boxL[d] * floor(x * g.inv[d]);
+        if (sw[d] >= g.boxL[d]) sw[d] -= g.boxL[d];
+        if (sw[d] < 0) sw[d] = 0;
+        ci[d] = min(cg.nc[d] - 1, (int)(sw[d] / cg.h[d]));
+    }
+    const T ex = (T)sx[3 * n + i];
+    const T a = (T)g.alpha;
+    const T rc2 = (T)(g.rcut * g.rcut);
+    const T px = (T)sw[0], py = (T)sw[1], pz = (T)sw[2];
+    const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
+    const int nst = wx * wy * wz;
+    T acc = 0;
+    for (int s = lane; s < nst; s += 32) {
+        int dx = s % wx - cg.S[0], dy = (s / wx) % wy - cg.S[1], dz = s / (wx * wy) - cg.S[2];
+        int ux = ci[0] + dx, uy = ci[1] + dy, uz = ci[2] + dz;
+        int fx = floordiv(ux, cg.nc[0]), fy = floordiv(uy, cg.nc[1]), fz = floordiv(uz, cg.nc[2]);
+        int cx = ux - fx * cg.nc[0], cy = uy - fy * cg.nc[1], cz = uz - fz * cg.nc[2];
+        const T shx = (T)(fx * g.boxL[0]), shy = (T)(fy * g.boxL[1]), shz = (T)(fz * g.boxL[2]);
+        int cell = r * cg.ncells + (cz * cg.nc[1] + cy) * cg.nc[0] + cx;
+        int p1 = start[cell + 1];
+        for (int p = start[cell]; p < p1; ++p) {
+            typename V4<T>::t q = sorted[p];
+            if (q.w == (T)0) continue;
+            T ddx = px - (q.x + shx), ddy = py - (q.y + shy), ddz = pz - (q.z + shz);
+            T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2 < rc2) {
+                T rr = sqrt(r2);
+                acc += q.w * (erfc_t<T>(a * rr) - erfc_t<T>(ex * rr)) / rr;
+            }
+        }
+    }
+    double acc64 = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_down_sync(0xffffffffu, acc64, o);
+    if (lane == 0) out[(int64_t)r * n + i] = acc64;
+}
+
+// ----------------------------------------------------------------------------- reciprocal space
+constexpr int SF_BM = 64, SF_BN = 64, SF_BK = 16;
+
+template <typename T>
+__device__ __forceinline__ int tile_maxext(const int* colext, int c0, int ncols) {
+    __shared__ int mx;
+    if (threadIdx.x == 0) mx = -1;
+    __syncthreads();
+    if (threadIdx.x < SF_BM && c0 + (int)threadIdx.x < ncols) atomicMax(&mx, colext[c0 + threadIdx.x]);
+    __syncthreads();
+    return mx;
+}
+
+// rho_part[s][r][c][nz] = sum over the s-th particle chunk of replica r of Q_j X_j Y_j Z_j.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const int* __restrict__ colext, int ncols,
+                                            int NY, int NZ, int nzw, const c2<T>* __restrict__ EX,
+                                            const c2<T>* __restrict__ EY, const c2<T>* __restrict__ EZ,
+                                            const T* __restrict__ Qv, int64_t ptot, int64_t ne, int splits,
+                                            int64_t chunk, int m, c2<T>* __restrict__ rho_part) {
+    __shared__ c2<T> Ps[SF_BK][SF_BM + 1];
+    __shared__ c2<T> Zs[SF_BK][SF_BN + 1];
+    const int c0 = blockIdx.x * SF_BM, z0 = blockIdx.y * SF_BN;
+    const int r = blockIdx.z / splits, s = blockIdx.z % splits;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    c2<T>* outp = rho_part + ((int64_t)s * m + r) * ncols * nzw;
+    const int mx = tile_maxext<T>(colext, c0, ncols);
+    const bool skip = (z0 - NZ > mx) || (z0 + SF_BN - 1 - NZ < -mx);
+    typedef c2<T> V;
+    V acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = cmake<T>(0, 0);
+    const int64_t jb = (int64_t)r * ne + (int64_t)s * chunk;
+    const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
+    if (!skip) {
+        for (int64_t j0 = jb; j0 < je; j0 += SF_BK) {
+            for (int e = threadIdx.x; e < SF_BK * SF_BM; e += 256) {
+                int kk = e % SF_BK, mm = e / SF_BK;
+                int64_t j = j0 + kk;
+                int c = c0 + mm;
+                V v = cmake<T>(0, 0);
+                if (j < je && c < ncols) {
+                    int2 cn = cols[c];
+                    V xy = cmul(EX[(int64_t)cn.x * ptot + j], EY[(int64_t)(cn.y + NY) * ptot + j]);
+                    T qj = Qv[j];
+                    v.x = qj * xy.x; v.y = qj * xy.y;
+                }
+                Ps[kk][mm] = v;
+                int z = z0 + mm;
+                V zv = cmake<T>(0, 0);
+                if (j < je && z < nzw) zv = EZ[(int64_t)z * ptot + j];
+                Zs[kk][mm] = zv;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < SF_BK; ++kk) {
+                V av[4], bv[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) av[p] = Ps[kk][ty + 16 * p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) bv[q] = Zs[kk][tx + 16 * q];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
+                        acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
+                    }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        int c = c0 + ty + 16 * p;
+        if (c >= ncols) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int z = z0 + tx + 16 * q;
+            if (z < nzw) outp[(int64_t)c * nzw + z] = acc[p][q];
+        }
+    }
+}
+
+// wrho[r][c][nz] = w[c][nz] * sum_s rho_part[s][r][c][nz]  (Neumaier-compensated over the splits)
+template <typename T>
+__global__ void k_sf_reduce(const c2<T>* rho_part, const T* w, int64_t per_rep, int m, int splits, c2<T>* wrho) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= per_rep * m) return;
+    T sx = 0, sy = 0, cx = 0, cy = 0;
+    for (int s = 0; s < splits; ++s) {
+        c2<T> v = rho_part[(int64_t)s * per_rep * m + t];
+        T tx = sx + v.x;
+        cx += fabs(sx) >= fabs(v.x) ? (sx - tx) + v.x : (v.x - tx) + sx;
+        sx = tx;
+        T ty = sy + v.y;
+        cy += fabs(sy) >= fabs(v.y) ? (sy - ty) + v.y : (v.y - ty) + sy;
+        sy = ty;
+    }
+    T wt = w[t % per_rep];
+    wrho[t] = cmake<T>(wt * (sx + cx), wt * (sy + cy));
+}
+
+// partial[r][tile][i] = sum over the tile's columns c of Re[conj(X_i Y_i) sum_nz wrho[c][nz] conj(Z_i[nz])]
+template <typename T>
+__global__ void __launch_bounds__(256) k_site(const int2* __restrict__ cols, const int* __restrict__ colext,
+                                              int ncols, int NY, int NZ, int nzw, const c2<T>* __restrict__ wrho,
+                                              const c2<T>* __restrict__ SX, const c2<T>* __restrict__ SY,
+                                              const c2<T>* __restrict__ SZ, int64_t n, int nctiles,
+                                              T* __restrict__ partial) {
+    __shared__ c2<T> As[SF_BK][SF_BM + 1];
+    __shared__ c2<T> Bs[SF_BK][SF_BN + 1];
+    __shared__ T red[16][SF_BN + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * SF_BN;
+    const int c0 = blockIdx.y * SF_BM;
+    const int r = blockIdx.z;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const c2<T>* rho = wrho + (int64_t)r * ncols * nzw;
+    const int mx = tile_maxext<T>(colext, c0, ncols);
+    typedef c2<T> V;
+    V acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = cmake<T>(0, 0);
+    if (mx >= 0) {
+        const int zb = NZ - mx, ze = NZ + mx + 1;
+        for (int z0 = zb; z0 < ze; z0 += SF_BK) {
+            for (int e = threadIdx.x; e < SF_BK * SF_BM; e += 256) {
+                int kk = e % SF_BK, mm = e / SF_BK;
+                int z = z0 + kk, c = c0 + mm;
+                As[kk][mm] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : cmake<T>(0, 0);
+                int nn = e % SF_BN;
+                kk = e / SF_BN;
+                z = z0 + kk;
+                int64_t i = i0 + nn;
+                Bs[kk][nn] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : cmake<T>(0, 0);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < SF_BK; ++kk) {
+                V av[4], bv[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) av[p] = As[kk][ty + 16 * p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {   // a * conj(b)
+                        acc[p][q].x += av[p].x * bv[q].x + av[p].y * bv[q].y;
+                        acc[p][q].y += av[p].y * bv[q].x - av[p].x * bv[q].y;
+                    }
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue: multiply by conj(X_i Y_i) per column, sum the columns of this thread, then over ty
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int64_t i = i0 + tx + 16 * q;
+        T s = 0;
+        if (i < n) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                int c = c0 + ty + 16 * p;
+                if (c < ncols) {
+                    int2 cn = cols[c];
+                    V xy = cmul(SX[(int64_t)cn.x * n + i], SY[(int64_t)(cn.y + NY) * n + i]);
+                    s += xy.x * acc[p][q].x + xy.y * acc[p][q].y;
+                }
+            }
+        }
+        red[ty][tx + 16 * q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < SF_BN) {
+        T s = 0;
+        for (int t = 0; t < 16; ++t) s += red[t][threadIdx.x];
+        int64_t i = i0 + threadIdx.x;
+        if (i < n) partial[((int64_t)r * nctiles + blockIdx.y) * n + i] = s;
+    }
+}
+
+// b[r][i] = K_E (recip + real - pi Q_tot / (V alpha^2) + boundary)
+template <typename T>
+__global__ void k_combine(const T* partial, int nctiles, const double* real, const double* stats,
+                          const double* sx, int64_t n, int m, Geometry g, double* b) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * n) return;
+    const int r = (int)(t / n);
+    const int64_t i = t % n;
+    double s = 0.0;
+    for (int k = 0; k < nctiles; ++k) s += (double)partial[((int64_t)r * nctiles + k) * n + i];
+    s += real[t];
+    const double* st = stats + 4 * r;
+    s += -PI * st[0] / (g.V * g.alpha * g.alpha);
+    if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];
+    else if (g.bc == CPM_BC_WIRE) s += (2.0 * PI / g.V) * (sx[i] * st[1] + sx[n + i] * st[2]);
+    b[t] = KE * s;
+}
+
+// ----------------------------------------------------------------------------- driver
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+struct BvecPlan {
+    CellGrid cg;
+    int splits, nctiles, ctiles, ztiles;
+    int64_t chunk;
+    size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
+        off_start, off_wpos, off_sorted, total;
+};
+
+template <typename T>
+static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
+    BvecPlan<T> p;
+    const KTable& k = c->kt;
+    p.cg = make_grid(c->g);
+    p.ctiles = (k.ncols + SF_BM - 1) / SF_BM;
+    p.ztiles = (k.nzw + SF_BN - 1) / SF_BN;
+    p.nctiles = p.ctiles;
+    const int64_t base = (int64_t)p.ctiles * p.ztiles * m;
+    int64_t want = (4 * 152 + base - 1) / std::max<int64_t>(base, 1);
+    int64_t maxs = std::max<int64_t>(1, (ne + 255) / 256);
+    p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(maxs, 64)));
+    p.chunk = (ne + p.splits - 1) / p.splits;
+    p.chunk = ((p.chunk + SF_BK - 1) / SF_BK) * SF_BK;
+    const int64_t ptot = (int64_t)m * ne;
+    const size_t pe = phase_elems(k, ptot);
+    const size_t grid = (size_t)k.ncols * k.nzw;
+    size_t o = 0;
+    const int64_t tabX = (int64_t)(k.NX + 1) * ptot, tabY = (int64_t)(2 * k.NY + 1) * ptot;
+    p.off_EX = o; o += al(sizeof(c2<T>) * tabX);
+    p.off_EY = o; o += al(sizeof(c2<T>) * tabY);
+    p.off_EZ = o; o += al(sizeof(c2<T>) * (pe - tabX - tabY));
+    p.off_Q = o; o += al(sizeof(T) * ptot);
+    p.off_rp = o; o += al(sizeof(c2<T>) * grid * m * p.splits);
+    p.off_wr = o; o += al(sizeof(c2<T>) * grid * m);
+    p.off_part = o; o += al(sizeof(T) * (size_t)m * p.nctiles * c->n);
+    p.off_real = o; o += al(sizeof(double) * (size_t)m * c->n);
+    p.off_stats = o; o += al(sizeof(double) * 4 * m);
+    p.off_key = o; o += al(sizeof(int) * ptot);
+    p.off_cnt = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
+    p.off_cur = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
+    p.off_start = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
+    p.off_wpos = o; o += al(sizeof(typename V4<T>::t) * ptot);
+    p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
+    p.total = o;
+    return p;
+}
+
+template <typename T>
+size_t bvec_scratch_bytes(const cpm_ctx* c, int m, int64_t ne) { return plan_bvec<T>(c, m, ne).total; }
+
+template <typename T> static const Phases<T>& site_tables(const cpm_ctx* c);
+template <> const Phases<double>& site_tables<double>(const cpm_ctx* c) { return c->site64; }
+template <> const Phases<float>& site_tables<float>(const cpm_ctx* c) { return c->site32; }
+
+template <typename T>
+cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out, char* scr) {
+    const BvecPlan<T> p = plan_bvec<T>(c, m, ne);
+    const KTable& k = c->kt;
+    cudaStream_t st = c->stream;
+    const int64_t n = c->n, ptot = (int64_t)m * ne;
+    c2<T>* EX = (c2<T>*)(scr + p.off_EX);
+    c2<T>* EY = (c2<T>*)(scr + p.off_EY);
+    c2<T>* EZ = (c2<T>*)(scr + p.off_EZ);
+    T* Qv = (T*)(scr + p.off_Q);
+    c2<T>* rp = (c2<T>*)(scr + p.off_rp);
+    c2<T>* wr = (c2<T>*)(scr + p.off_wr);
+    T* part = (T*)(scr + p.off_part);
+    double* real = (double*)(scr + p.off_real);
+    double* stats = (double*)(scr + p.off_stats);
+    int* key = (int*)(scr + p.off_key);
+    int* cnt = (int*)(scr + p.off_cnt);
+    int* cur = (int*)(scr + p.off_cur);
+    int* start = (int*)(scr + p.off_start);
+    typedef typename V4<T>::t V4T;
+    V4T* wpos = (V4T*)(scr + p.off_wpos);
+    V4T* sorted = (V4T*)(scr + p.off_sorted);
+    const int nc = m * p.cg.ncells;
+    c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 4 : 0);
+
+    prof_begin(c, CPM_K_STATS);
+    k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats);
+    prof_end(c, CPM_K_STATS);
+    CPM_LAUNCH(c, "k_stats");
+    prof_begin(c, CPM_K_CELLS);
+    if (ptot > 0) {
+        CPM_CUDA(c, cudaMemsetAsync(cnt, 0, p.off_start - p.off_cnt, st));   // counts and cursors
+        k_bin<T><<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, Q, ptot, ne, c->g, p.cg, key, cnt, wpos, Qv);
+        CPM_LAUNCH(c, "k_bin");
+    } else {
+        CPM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), st));
+    }
+    k_cellscan<<<m, 1024, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
+    CPM_LAUNCH(c, "k_cellscan");
+    if (ptot > 0) {
+        k_scatter<T><<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, wpos, ptot, sorted);
+        CPM_LAUNCH(c, "k_scatter");
+    }
+    prof_end(c, CPM_K_CELLS);
+    prof_begin(c, CPM_K_REAL);
+    k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
+                                                                                sorted, real);
+    prof_end(c, CPM_K_REAL);
+    CPM_LAUNCH(c, "k_real_b");
+    // reciprocal space
+    if (k.nk > 0 && ptot > 0) {
+        prof_begin(c, CPM_K_PHASES);
+        CPM_TRY(launch_phases<T>(st, c->g, k, xyz, ptot, EX, EY, EZ));
+        prof_end(c, CPM_K_PHASES);
+        prof_begin(c, CPM_K_SF);
+        dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
+        k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne, p.splits,
+                                     p.chunk, m, rp);
+        prof_end(c, CPM_K_SF);
+        CPM_LAUNCH(c, "k_sf");
+        prof_begin(c, CPM_K_SFRED);
+        const int64_t per_rep = (int64_t)k.ncols * k.nzw;
+        const T* w = std::is_same<T, float>::value ? (const T*)k.w32 : (const T*)k.w;
+        k_sf_reduce<T><<<(unsigned)((per_rep * m + 255) / 256), 256, 0, st>>>(rp, w, per_rep, m, p.splits, wr);
+        prof_end(c, CPM_K_SFRED);
+        CPM_LAUNCH(c, "k_sf_reduce");
+        prof_begin(c, CPM_K_SITE);
+        const Phases<T>& sp = site_tables<T>(c);
+        dim3 gs((unsigned)((n + SF_BN - 1) / SF_BN), p.ctiles, m);
+        k_site<T><<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, wr, sp.X, sp.Y, sp.Z, n,
+                                      p.nctiles, part);
+        prof_end(c, CPM_K_SITE);
+        CPM_LAUNCH(c, "k_site");
+    } else {
+        CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, st));
+    }
+    prof_begin(c, CPM_K_COMBINE);
+    k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, stats, c->sx, n, m,
+                                                                          c->g, b_out);
+    prof_end(c, CPM_K_COMBINE);
+    CPM_LAUNCH(c, "k_combine");
+    return CPM_OK;
+}
+
+cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out) {
+    const bool f32 = c->p.k_prec == CPM_PREC_FP32;
+    const size_t need = f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne);
+    CPM_TRY(ensure_scratch(c, need));
+    char* scr = (char*)c->scratch;
+    return f32 ? bvec_run<float>(c, m, ne, xyz, Q, b_out, scr) : bvec_run<double>(c, m, ne, xyz, Q, b_out, scr);
+}
+
+}  // namespace cpm

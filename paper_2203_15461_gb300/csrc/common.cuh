@@ -1,0 +1,189 @@
+// Internal declarations shared by the CPM CUDA translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "cpm.h"
+
+namespace cpm {
+
+// Coulomb constant e / (4 pi eps0 Angstrom) in volts.
+constexpr double KE = 14.399645;
+constexpr double PI = 3.141592653589793;
+
+// ----------------------------------------------------------------------------- complex helpers
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+template <typename T> using c2 = typename C2<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ c2<T> cmake(T a, T b) { c2<T> r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+    V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+
+// ----------------------------------------------------------------------------- device status word
+// Kernels never trap: they set one of these bits and return.  The host reads the
+// word when it synchronises.
+enum : unsigned { ST_NOT_SPD = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+
+// ----------------------------------------------------------------------------- reciprocal-space table
+// Half-space reciprocal vectors organised as "columns" (nx, ny) with nx >= 0 and
+// (nx > 0 or ny >= 0), each with the nz harmonics -NZ..NZ on a dense grid of
+// width nzw = 2 NZ + 1.  The Ewald weight of an entry is zero outside the
+// half-space ball 0 < |k| <= kcut, so the dense grid and the compact list hold
+// the same set of vectors.
+struct KTable {
+    int NX = 0, NY = 0, NZ = 0;
+    int ncols = 0, nzw = 0;
+    int64_t nk = 0;                 // number of vectors with nonzero weight
+    int2* cols = nullptr;           // [ncols] (nx, ny)
+    int* colext = nullptr;          // [ncols] largest |nz| with nonzero weight, -1 if none
+    int64_t* coloff = nullptr;      // [ncols + 1] offsets of each column in the compact list
+    double* w = nullptr;            // [ncols * nzw] dense weights (8 pi / V) e^{-k^2/4a^2} / k^2
+    float* w32 = nullptr;
+    int4* klist = nullptr;          // [nk] compact list: (column, nz, nx, ny)
+    double* kw = nullptr;           // [nk] weight of each compact entry
+};
+
+// Phase tables of a point set: X[h][p] = exp(2 pi i h x_p / Lx) for h = 0..NX,
+// Y[h + NY][p] for h = -NY..NY, Z[h + NZ][p] for h = -NZ..NZ (point-minor layout).
+template <typename T> struct Phases {
+    c2<T>* X = nullptr;
+    c2<T>* Y = nullptr;
+    c2<T>* Z = nullptr;
+    int64_t P = 0;       // points per set (ld of the tables)
+};
+
+struct Geometry {
+    double boxL[3];
+    double inv[3];       // 1 / L
+    double V;
+    double alpha, rcut, kcut;
+    int bc;
+};
+
+}  // namespace cpm
+
+// ----------------------------------------------------------------------------- context
+struct cpm_ctx {
+    cpm_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    size_t bytes = 0;
+    std::vector<void*> owned;
+    cpm::Geometry g{};
+
+    // electrode geometry (SoA)
+    int64_t n = 0;
+    int ng = 0;
+    double* sx = nullptr;        // [4 * n]: x | y | z | eta
+    double* sxyz = nullptr;      // [n * 3] row-major copy of the site coordinates
+    int* group = nullptr;
+    float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
+    cpm::KTable kt;
+    cpm::Phases<double> site64;
+    cpm::Phases<float> site32;
+    uint64_t geom_hash = 0;
+
+    // dense matrices
+    double* A = nullptr;
+    double* W = nullptr;         // Cholesky factor, then its inverse, then A^-1
+    double* S = nullptr;
+    float* S32 = nullptr;
+    double* SG = nullptr;        // [n * ng]
+    double* u = nullptr;         // [n]
+    double* dvec = nullptr;      // [n] scratch
+    double* red = nullptr;       // [64] scratch scalars
+    unsigned* status = nullptr;  // device status word
+    bool assembled = false, inverted = false;
+
+    // per-step scratch, grown on demand
+    int cap_m = 0;
+    int64_t cap_ne = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // host staging for cpm_step_host
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+    void* dstage = nullptr;
+    size_t dstage_bytes = 0;
+
+    int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
+
+    // tracing (cpm_profile)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[CPM_K_COUNT];
+    cudaEvent_t prof_open[CPM_K_COUNT] = {};
+    double prof_ms[CPM_K_COUNT] = {};
+    int64_t prof_cnt[CPM_K_COUNT] = {};
+};
+
+namespace cpm {
+
+// error helpers (api.cu)
+cpm_status set_err(cpm_ctx* c, cpm_status s, const char* fmt, ...);
+cpm_status cuda_check(cpm_ctx* c, cudaError_t e, const char* what);
+cpm_status dev_alloc(cpm_ctx* c, void** ptr, size_t bytes);
+void dev_free(cpm_ctx* c, void* ptr);
+
+#define CPM_CUDA(ctx, call)                                                     \
+    do {                                                                        \
+        cudaError_t e__ = (call);                                               \
+        if (e__ != cudaSuccess) return ::cpm::cuda_check((ctx), e__, #call);    \
+    } while (0)
+#define CPM_LAUNCH(ctx, what)                                                   \
+    do {                                                                        \
+        cudaError_t e__ = cudaGetLastError();                                   \
+        if (e__ != cudaSuccess) return ::cpm::cuda_check((ctx), e__, what);     \
+    } while (0)
+#define CPM_TRY(expr)                                                           \
+    do {                                                                        \
+        cpm_status s__ = (expr);                                                \
+        if (s__ != CPM_OK) return s__;                                          \
+    } while (0)
+
+// api.cu: bracket one kernel launch with events when tracing is on
+void prof_begin(cpm_ctx* c, int k);
+void prof_end(cpm_ctx* c, int k);
+
+// ktables.cu
+cpm_status build_ktable(cpm_ctx* c);
+void free_ktable(cpm_ctx* c);
+template <typename T>
+cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
+                         c2<T>* X, c2<T>* Y, c2<T>* Z);
+size_t phase_elems(const KTable& k, int64_t P);
+
+// api.cu
+cpm_status ensure_scratch(cpm_ctx* c, size_t bytes);
+
+// assemble.cu
+cpm_status assemble_A(cpm_ctx* c);
+
+// dense.cu
+cpm_status invert_and_project(cpm_ctx* c);
+cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int lower,
+                        int tri, const unsigned* status);
+
+// bvec.cu
+cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
+
+// update.cu
+cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot);
+
+}  // namespace cpm

@@ -1,0 +1,228 @@
+// Reciprocal-space tables (the k-vector set and Ewald weights) and per-point phase tables.
+//
+// The k-vector set is the half space of k = 2 pi (nx/Lx, ny/Ly, nz/Lz) with
+// 0 < |k| <= kcut; each vector carries the weight 2 (4 pi / V) exp(-k^2/4 alpha^2)/k^2
+// of the Ewald reciprocal sum (ELECTRODE's ewald/electrode solver, SI Sec. 1.A),
+// the factor 2 standing for the mirror vector -k.  Membership is decided with
+// correctly rounded multiplies and adds in a fixed order so that the set does
+// not depend on FMA contraction.
+#include "common.cuh"
+
+namespace cpm {
+
+__device__ __forceinline__ double k2_of(double tx, double ty, double tz, int nx, int ny, int nz) {
+    double kx = __dmul_rn(tx, (double)nx), ky = __dmul_rn(ty, (double)ny), kz = __dmul_rn(tz, (double)nz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
+}
+
+// Single-block exclusive scan of `cnt` (int64) into `off` (cnt + 1 entries), deterministic.
+__device__ void block_exclusive_scan(const int64_t* in, int64_t* off, int64_t cnt) {
+    __shared__ int64_t s[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < cnt; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < cnt ? in[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+            int64_t t = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < cnt) off[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[cnt] = carry;
+}
+
+// Columns (nx, ny) of the half plane whose transverse |k| is within kcut, in (nx, ny) order.
+__global__ void k_columns(int NX, int NY, double tx, double ty, double kc2, int64_t* flags, int64_t* off,
+                          int2* cols, int* ncols) {
+    const int64_t ncand = (int64_t)(NX + 1) * (2 * NY + 1);
+    for (int64_t i = threadIdx.x; i < ncand; i += blockDim.x) {
+        int nx = (int)(i / (2 * NY + 1)), ny = (int)(i % (2 * NY + 1)) - NY;
+        bool half = nx > 0 || ny >= 0;
+        flags[i] = (half && k2_of(tx, ty, 0.0, nx, ny, 0) <= kc2) ? 1 : 0;
+    }
+    __syncthreads();
+    block_exclusive_scan(flags, off, ncand);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < ncand; i += blockDim.x) {
+        if (flags[i]) {
+            int nx = (int)(i / (2 * NY + 1)), ny = (int)(i % (2 * NY + 1)) - NY;
+            cols[off[i]] = make_int2(nx, ny);
+        }
+    }
+    if (threadIdx.x == 0) *ncols = (int)off[ncand];
+}
+
+__global__ void k_weights(const int2* cols, int ncols, int NZ, double tx, double ty, double tz, double kc2,
+                          double pref, double inv4a2, double* w, float* w32, int* colext) {
+    const int nzw = 2 * NZ + 1;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ncols * nzw) return;
+    int c = (int)(i / nzw), nz = (int)(i % nzw) - NZ;
+    int2 cn = cols[c];
+    bool half = cn.x > 0 || cn.y > 0 || nz > 0;
+    double k2 = k2_of(tx, ty, tz, cn.x, cn.y, nz);
+    double wt = 0.0;
+    if (half && k2 <= kc2) {
+        wt = pref * exp(-k2 * inv4a2) / k2;
+        atomicMax(&colext[c], nz < 0 ? -nz : nz);
+    }
+    w[i] = wt;
+    w32[i] = (float)wt;
+}
+
+__global__ void k_colcounts(const int2* cols, const int* colext, int ncols, int64_t* cnt) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int e = colext[c];
+    bool origin = cols[c].x == 0 && cols[c].y == 0;
+    cnt[c] = e < 0 ? 0 : (origin ? e : 2 * e + 1);
+}
+
+__global__ void k_scan1(const int64_t* cnt, int64_t* off, int64_t n) { block_exclusive_scan(cnt, off, n); }
+
+__global__ void k_compact(const int2* cols, const int* colext, const int64_t* coloff, const double* w, int ncols,
+                          int NZ, int4* klist, double* kw) {
+    const int nzw = 2 * NZ + 1;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ncols * nzw) return;
+    int c = (int)(i / nzw), nz = (int)(i % nzw) - NZ;
+    double wt = w[i];
+    if (wt == 0.0) return;
+    int2 cn = cols[c];
+    int lo = (cn.x == 0 && cn.y == 0) ? 1 : -colext[c];
+    int64_t o = coloff[c] + (nz - lo);
+    klist[o] = make_int4(c, nz, cn.x, cn.y);
+    kw[o] = wt;
+}
+
+void free_ktable(cpm_ctx* c) {
+    KTable& k = c->kt;
+    dev_free(c, k.cols); dev_free(c, k.colext); dev_free(c, k.coloff); dev_free(c, k.w);
+    dev_free(c, k.w32); dev_free(c, k.klist); dev_free(c, k.kw);
+    k = KTable{};
+}
+
+cpm_status build_ktable(cpm_ctx* c) {
+    free_ktable(c);
+    KTable& k = c->kt;
+    const Geometry& g = c->g;
+    const double tx = (2.0 * PI) / g.boxL[0], ty = (2.0 * PI) / g.boxL[1], tz = (2.0 * PI) / g.boxL[2];
+    const double kc2 = g.kcut * g.kcut;
+    k.NX = (int)(g.kcut / tx) + 1;
+    k.NY = (int)(g.kcut / ty) + 1;
+    k.NZ = (int)(g.kcut / tz) + 1;
+    k.nzw = 2 * k.NZ + 1;
+    const int64_t ncand = (int64_t)(k.NX + 1) * (2 * k.NY + 1);
+    int64_t *flags = nullptr, *off = nullptr;
+    int* dn = nullptr;
+    CPM_TRY(dev_alloc(c, (void**)&flags, ncand * sizeof(int64_t)));
+    CPM_TRY(dev_alloc(c, (void**)&off, (ncand + 1) * sizeof(int64_t)));
+    CPM_TRY(dev_alloc(c, (void**)&dn, sizeof(int)));
+    CPM_TRY(dev_alloc(c, (void**)&k.cols, ncand * sizeof(int2)));
+    k_columns<<<1, 1024, 0, c->stream>>>(k.NX, k.NY, tx, ty, kc2, flags, off, k.cols, dn);
+    CPM_LAUNCH(c, "k_columns");
+    CPM_CUDA(c, cudaMemcpyAsync(&k.ncols, dn, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, flags); dev_free(c, off); dev_free(c, dn);
+
+    const int64_t grid = (int64_t)k.ncols * k.nzw;
+    CPM_TRY(dev_alloc(c, (void**)&k.w, grid * sizeof(double)));
+    CPM_TRY(dev_alloc(c, (void**)&k.w32, grid * sizeof(float)));
+    CPM_TRY(dev_alloc(c, (void**)&k.colext, k.ncols * sizeof(int)));
+    CPM_TRY(dev_alloc(c, (void**)&k.coloff, (k.ncols + 1) * sizeof(int64_t)));
+    CPM_CUDA(c, cudaMemsetAsync(k.colext, 0xff, k.ncols * sizeof(int), c->stream));   // -1
+    const double pref = 8.0 * PI / g.V, inv4a2 = 1.0 / (4.0 * g.alpha * g.alpha);
+    k_weights<<<(unsigned)((grid + 255) / 256), 256, 0, c->stream>>>(k.cols, k.ncols, k.NZ, tx, ty, tz, kc2, pref,
+                                                                    inv4a2, k.w, k.w32, k.colext);
+    CPM_LAUNCH(c, "k_weights");
+    int64_t* cnt = nullptr;
+    CPM_TRY(dev_alloc(c, (void**)&cnt, k.ncols * sizeof(int64_t)));
+    k_colcounts<<<(k.ncols + 255) / 256, 256, 0, c->stream>>>(k.cols, k.colext, k.ncols, cnt);
+    CPM_LAUNCH(c, "k_colcounts");
+    k_scan1<<<1, 1024, 0, c->stream>>>(cnt, k.coloff, k.ncols);
+    CPM_LAUNCH(c, "k_scan1");
+    CPM_CUDA(c, cudaMemcpyAsync(&k.nk, k.coloff + k.ncols, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, cnt);
+    CPM_TRY(dev_alloc(c, (void**)&k.klist, (k.nk > 0 ? k.nk : 1) * sizeof(int4)));
+    CPM_TRY(dev_alloc(c, (void**)&k.kw, (k.nk > 0 ? k.nk : 1) * sizeof(double)));
+    k_compact<<<(unsigned)((grid + 255) / 256), 256, 0, c->stream>>>(k.cols, k.colext, k.coloff, k.w, k.ncols,
+                                                                     k.NZ, k.klist, k.kw);
+    CPM_LAUNCH(c, "k_compact");
+    return CPM_OK;
+}
+
+// ----------------------------------------------------------------------------- phase tables
+// The phase 2 pi h x / L is reduced exactly: the fractional coordinate x / L mod 1
+// is held as a 64-bit fixed-point number, so h times it modulo one turn is an
+// exact integer product; only the final conversion to a half-turn count in
+// [-1, 1) for sincospi rounds.
+__device__ __forceinline__ uint64_t frac_fixed(double x, double invL) {
+    double s = x * invL;
+    s -= floor(s);
+    double t = s * 18446744073709551616.0;   // 2^64
+    return t >= 18446744073709551616.0 ? 0ull : (uint64_t)t;
+}
+
+template <typename T> __device__ __forceinline__ c2<T> phase_of(uint64_t u, int h);
+template <> __device__ __forceinline__ double2 phase_of<double>(uint64_t u, int h) {
+    int64_t p = (int64_t)(u * (uint64_t)(int64_t)h);
+    double s, co;
+    sincospi((double)p * 0x1p-63, &s, &co);
+    return make_double2(co, s);
+}
+template <> __device__ __forceinline__ float2 phase_of<float>(uint64_t u, int h) {
+    int64_t p = (int64_t)(u * (uint64_t)(int64_t)h);
+    float s, co;
+    sincospif((float)p * 0x1p-63f, &s, &co);
+    return make_float2(co, s);
+}
+
+template <typename T>
+__global__ void k_phases(const double* __restrict__ xyz, int64_t P, double ix, double iy, double iz, int NX,
+                         int NY, int NZ, c2<T>* X, c2<T>* Y, c2<T>* Z) {
+    const int nslot = (NX + 1) + (2 * NY + 1) + (2 * NZ + 1);
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * nslot) return;
+    int slot = (int)(t / P);
+    int64_t p = t % P;
+    if (slot <= NX) {
+        X[(int64_t)slot * P + p] = phase_of<T>(frac_fixed(xyz[3 * p + 0], ix), slot);
+    } else if (slot <= NX + 2 * NY + 1) {
+        int r = slot - (NX + 1);
+        Y[(int64_t)r * P + p] = phase_of<T>(frac_fixed(xyz[3 * p + 1], iy), r - NY);
+    } else {
+        int r = slot - (NX + 1) - (2 * NY + 1);
+        Z[(int64_t)r * P + p] = phase_of<T>(frac_fixed(xyz[3 * p + 2], iz), r - NZ);
+    }
+}
+
+template <typename T>
+cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
+                         c2<T>* X, c2<T>* Y, c2<T>* Z) {
+    const int nslot = (k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1);
+    const int64_t tot = P * nslot;
+    if (tot == 0) return CPM_OK;
+    k_phases<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], k.NX, k.NY,
+                                                               k.NZ, X, Y, Z);
+    return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
+}
+template cpm_status launch_phases<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
+                                         float2*, float2*, float2*);
+template cpm_status launch_phases<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
+                                          double2*, double2*, double2*);
+
+size_t phase_elems(const KTable& k, int64_t P) {
+    return (size_t)P * ((k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1));
+}
+
+}  // namespace cpm

@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances: FP64 path q within 1e-10 relative L2 of the oracle, mixed path within
+1e-5, total electrode charge within 1e-12 e for both; A within 1e-12 and S within
+1e-10 (relative, FP64); the k-vector set bit-exact.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import dev, make_ctx, need_gpu, rel_l2, run_bvec, run_update, torch
+from oracle import cpm_oracle as o
+from paper_2203_15461_gb300 import systems as s
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    need_gpu()
+    el, ely, psi = s.workload_tiny_slab(seed=3)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    return el, ely, psi, A, S
+
+
+def _kset(nidx):
+    return set(map(tuple, np.asarray(nidx, dtype=np.int64).tolist()))
+
+
+@pytest.mark.parametrize("which", ["tiny", "edl", "coax"])
+def test_kvector_set_bit_exact(which):
+    need_gpu()
+    el = {"tiny": lambda: s.au111_slab(), "edl": lambda: s.graphene_plates(18, 10, 3, 60.0),
+          "coax": lambda: s.coaxial_tubes(2)}[which]()
+    ctx = make_ctx(el)
+    xyz = dev(el.xyz)
+    ctx.cpm_assemble(xyz, dev(el.eta), dev(el.group, torch.int32), el.n_groups)
+    got = ctx.cpm_kvectors()
+    nidx, _, _ = o.kvectors(el.box, el.kcut)
+    assert len(got) == len(nidx)
+    assert _kset(got) == _kset(nidx)
+    if which == "tiny":
+        assert len(got) == 3293
+
+
+def test_elastance_and_capacitance_parity(tiny):
+    el, _, _, A, S = tiny
+    ctx = make_ctx(el).setup(el)
+    Ag = ctx.cpm_get_matrix("A").cpu().numpy()
+    assert np.abs(Ag - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.array_equal(Ag, Ag.T)
+    Sg = ctx.cpm_get_matrix("S").cpu().numpy()
+    assert rel_l2(Sg, S) <= 1e-10
+    C = ctx.cpm_capacitance()
+    assert np.abs(C - o.electrode_capacitance(S, el)).max() <= 1e-10 * abs(C[0, 0])
+
+
+@pytest.mark.parametrize("k_prec,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+def test_bvec_parity_replicas_ragged(tiny, k_prec, tol):
+    """Three replicas of different sizes (zero-charge padding) and one empty electrolyte."""
+    el, ely, _, _, _ = tiny
+    e2 = s.ions_in_gap(el, 60, seed=11)
+    e3 = s.Electrolyte(xyz=ely.xyz[:37], Q=ely.Q[:37])      # non-neutral: background term
+    ctx = make_ctx(el, k_prec=k_prec)
+    ctx.cpm_assemble(dev(el.xyz), dev(el.eta), dev(el.group, torch.int32), el.n_groups)
+    b = run_bvec(ctx, [ely, e2, e3])
+    for r, e in enumerate([ely, e2, e3]):
+        ref = o.bvec(el, e)
+        assert rel_l2(b[r], ref) <= tol
+    empty = run_bvec(ctx, [s.Electrolyte(xyz=np.zeros((0, 3)), Q=np.zeros(0))])
+    assert np.abs(empty).max() == 0.0
+
+
+@pytest.mark.parametrize("s_prec,k_prec,tol", [("fp64", "fp64", 1e-10), ("fp32", "fp32", 1e-5)])
+def test_charge_update_parity(tiny, s_prec, k_prec, tol):
+    el, ely, psi, A, S = tiny
+    ctx = make_ctx(el, s_prec=s_prec, k_prec=k_prec).setup(el)
+    elyts = [s.jitter(ely, 0.05, np.random.default_rng(k)) for k in range(4)]
+    b = run_bvec(ctx, elyts)
+    q, qt = run_update(ctx, psi, b)
+    for r, e in enumerate(elyts):
+        q_ref = o.charges(S, el, psi, o.bvec(el, e))
+        assert rel_l2(q[r], q_ref) <= tol
+        assert abs(q[r].sum()) <= 1e-12
+        assert abs(qt[r]) <= 1e-12
+
+
+def test_vacuum_capacitor_charges_match_SG(tiny):
+    """No electrolyte: b = 0 and q = S G psi exactly as the oracle."""
+    el, _, psi, _, S = tiny
+    ctx = make_ctx(el).setup(el)
+    b = run_bvec(ctx, [s.Electrolyte(xyz=np.zeros((0, 3)), Q=np.zeros(0))])
+    q, _ = run_update(ctx, psi, b)
+    assert rel_l2(q[0], S @ o.site_potentials(el, psi)) <= 1e-12
+
+
+def test_symm_off_gives_inverse(tiny):
+    el, ely, psi, A, _ = tiny
+    ctx = make_ctx(el, symm=False).setup(el)
+    Ainv = o.capacitance_matrix(A, symm=False)
+    assert rel_l2(ctx.cpm_get_matrix("S").cpu().numpy(), Ainv) <= 1e-10
+    b = run_bvec(ctx, [ely])
+    q, qt = run_update(ctx, psi, b)
+    ref = Ainv @ (o.site_potentials(el, psi) - o.bvec(el, ely))
+    assert rel_l2(q[0], ref) <= 1e-10
+    assert abs(qt[0] - ref.sum()) <= 1e-10
+
+
+def test_step_host_equals_device_path(tiny):
+    el, ely, psi, _, _ = tiny
+    ctx = make_ctx(el).setup(el)
+    b = run_bvec(ctx, [ely])
+    q_dev, qt_dev = run_update(ctx, psi, b)
+    q = np.zeros((1, el.n))
+    qt = np.zeros(1)
+    ctx.cpm_step_host(1, ely.n, np.ascontiguousarray(ely.xyz), np.ascontiguousarray(ely.Q), psi.copy(), q, qt)
+    assert np.array_equal(q, q_dev) and np.array_equal(qt, qt_dev)
+
+
+def test_save_load_roundtrip(tiny, tmp_path):
+    el, ely, psi, _, _ = tiny
+    a = make_ctx(el).setup(el)
+    path = str(tmp_path / "S.bin")
+    a.cpm_save(path)
+    b = make_ctx(el)
+    b.cpm_assemble(dev(el.xyz), dev(el.eta), dev(el.group, torch.int32), el.n_groups)
+    b.cpm_load(path)
+    assert torch.equal(a.cpm_get_matrix("S"), b.cpm_get_matrix("S"))
+    other = s.au111_slab(gap=22.0)
+    c = make_ctx(other)
+    c.cpm_assemble(dev(other.xyz), dev(other.eta), dev(other.group, torch.int32), other.n_groups)
+    with pytest.raises(Exception, match="CPM_E_ARG"):
+        c.cpm_load(path)
+
+
+def test_errors_are_status_codes(tiny):
+    from paper_2203_15461_gb300.cpm import CPMError
+    el, ely, psi, _, _ = tiny
+    ctx = make_ctx(el)
+    b = torch.zeros((1, el.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(CPMError, match="CPM_E_STATE"):
+        ctx.cpm_update(1, dev(psi[None]), b, torch.empty_like(b))
+    bad = el.eta.copy()
+    bad[5] = -1.0
+    with pytest.raises(CPMError, match="CPM_E_NONFINITE"):
+        ctx.cpm_assemble(dev(el.xyz), dev(bad), dev(el.group, torch.int32), el.n_groups)
+    g = el.group.copy()
+    g[0] = 7
+    with pytest.raises(CPMError, match="CPM_E_NONFINITE"):
+        ctx.cpm_assemble(dev(el.xyz), dev(el.eta), dev(g, torch.int32), el.n_groups)
+    small = make_ctx(el, hbm_budget=1 << 20)
+    with pytest.raises(CPMError, match="CPM_E_BUDGET"):
+        small.cpm_assemble(dev(el.xyz), dev(el.eta), dev(el.group, torch.int32), el.n_groups)
+
+
+def test_wire_coaxial_parity():
+    need_gpu()
+    el = s.coaxial_tubes(2)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    ctx = make_ctx(el).setup(el)
+    assert np.abs(ctx.cpm_get_matrix("A").cpu().numpy() - A).max() <= 1e-12 * np.abs(A).max()
+    C = ctx.cpm_capacitance()
+    assert abs(C[1, 1] / o.electrode_capacitance(S, el)[1, 1] - 1) <= 1e-10
+    rng = np.random.default_rng(2)
+    ely = s.Electrolyte(xyz=np.column_stack([rng.uniform(35, 45, 20), rng.uniform(35, 45, 20),
+                                             rng.uniform(0, el.box[2], 20)]), Q=np.tile([1.0, -1.0], 10))
+    b = run_bvec(ctx, [ely])
+    assert rel_l2(b[0], o.bvec(el, ely)) <= 1e-11
+
+
+def test_tinfoil_3d_parity():
+    need_gpu()
+    rng = np.random.default_rng(9)
+    n = 40
+    box = np.array([14.0, 15.0, 16.0])
+    el = s.Electrodes(xyz=rng.uniform(0, 1, (n, 3)) * box, eta=rng.uniform(1.5, 2.0, n),
+                      group=(np.arange(n) % 2).astype(np.int32), n_groups=2, box=box, boundary="3d", alpha=0.35,
+                      rcut=10.0, kcut=s.kcut_from_tol(0.35, 1e-10))
+    A = o.assemble_A(el)
+    ctx = make_ctx(el).setup(el)
+    assert np.abs(ctx.cpm_get_matrix("A").cpu().numpy() - A).max() <= 1e-12 * np.abs(A).max()
+    ely = s.Electrolyte(xyz=rng.uniform(0, 1, (30, 3)) * box, Q=np.tile([1.0, -1.0], 15))
+    b = run_bvec(ctx, [ely])
+    assert rel_l2(b[0], o.bvec(el, ely)) <= 1e-11

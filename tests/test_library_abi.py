@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2203_15461_gb300 import cpm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(cpm.LIB_PATH):
+        from paper_2203_15461_gb300 import build
+        build.build()
+    return cpm.load_library()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(cpm_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"cpm_create", "cpm_assemble", "cpm_invert", "cpm_bvec", "cpm_update"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi():
+    assert _declared() <= set(cpm._SIGS)
+
+
+def test_create_rejects_bad_arguments_without_touching_a_gpu(lib):
+    p = cpm.cpm_params()
+    p.box[:] = [10.0, 10.0, -1.0]
+    p.alpha, p.rcut, p.kcut = 0.3, 10.0, 2.0
+    h = ctypes.c_void_p()
+    assert lib.cpm_create(ctypes.byref(p), None, ctypes.byref(h)) == 1   # CPM_E_ARG
+    assert lib.cpm_create(None, None, ctypes.byref(h)) == 1
+    lib.cpm_destroy(None)
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    p = cpm.cpm_params()
+    p.box[:] = [10.0, 10.0, 10.0]
+    p.alpha, p.rcut, p.kcut = 0.3, 10.0, 2.0
+    h = ctypes.c_void_p()
+    assert lib.cpm_create(ctypes.byref(p), None, ctypes.byref(h)) == 6   # CPM_E_CUDA
+    with pytest.raises(cpm.CPMError, match="CPM_E_CUDA"):
+        cpm.CPM((10, 10, 10), "slab", 0.3, 10.0, 2.0)
