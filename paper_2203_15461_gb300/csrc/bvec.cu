@@ -129,14 +129,27 @@ __global__ void k_cellscan(const int* count, int* start, int ncells, int64_t ne,
     if (r == m - 1 && threadIdx.x == 0) start[m * ncells] = (int)(m * ne);
 }
 
-template <typename T>
-__global__ void k_scatter(const int* key, const int* start, int* cursor, const typename V4<T>::t* wpos,
-                          int64_t ptot, typename V4<T>::t* sorted) {
+__global__ void k_scatter(const int* key, const int* start, int* cursor, int64_t ptot, int* order) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ptot) return;
     int k = key[p];
-    int slot = start[k] + atomicAdd(&cursor[k], 1);
-    sorted[slot] = wpos[p];
+    order[start[k] + atomicAdd(&cursor[k], 1)] = (int)p;
+}
+
+// One thread per cell: put the cell's charges in ascending input order (so that every sum
+// over a cell runs in the same order on every call), then gather their positions.
+template <typename T>
+__global__ void k_cellsort(const int* start, int ncells_total, int* order, const typename V4<T>::t* wpos,
+                           typename V4<T>::t* sorted) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells_total) return;
+    const int b = start[c], e = start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+        int v = order[i], j = i - 1;
+        while (j >= b && order[j] > v) { order[j + 1] = order[j]; --j; }
+        order[j + 1] = v;
+    }
+    for (int i = b; i < e; ++i) sorted[i] = wpos[order[i]];
 }
 
 template <typename T> __device__ __forceinline__ T erfc_t(T x);
@@ -406,7 +419,7 @@ struct BvecPlan {
     int splits, nctiles, ctiles, ztiles;
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
-        off_start, off_wpos, off_sorted, total;
+        off_start, off_wpos, off_sorted, off_order, total;
 };
 
 template <typename T>
@@ -443,6 +456,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_start = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
     p.off_wpos = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
+    p.off_order = o; o += al(sizeof(int) * ptot);
     p.total = o;
     return p;
 }
@@ -476,8 +490,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     typedef typename V4<T>::t V4T;
     V4T* wpos = (V4T*)(scr + p.off_wpos);
     V4T* sorted = (V4T*)(scr + p.off_sorted);
+    int* order = (int*)(scr + p.off_order);
     const int nc = m * p.cg.ncells;
-    c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 4 : 0);
+    c->launches += 4 + (ptot > 0 ? 3 : 0) + ((k.nk > 0 && ptot > 0) ? 4 : 0);
 
     prof_begin(c, CPM_K_STATS);
     k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats);
@@ -494,8 +509,10 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     k_cellscan<<<m, 1024, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
     CPM_LAUNCH(c, "k_cellscan");
     if (ptot > 0) {
-        k_scatter<T><<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, wpos, ptot, sorted);
+        k_scatter<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, ptot, order);
         CPM_LAUNCH(c, "k_scatter");
+        k_cellsort<T><<<(nc + 127) / 128, 128, 0, st>>>(start, nc, order, wpos, sorted);
+        CPM_LAUNCH(c, "k_cellsort");
     }
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);

@@ -50,6 +50,6 @@ def run_update(ctx, psi, b):
     m = b.shape[0]
     q = torch.empty((m, ctx.n), dtype=torch.float64, device="cuda")
     qt = torch.empty((m,), dtype=torch.float64, device="cuda")
-    ctx.cpm_update(m, dev(np.broadcast_to(psi, (m, len(psi)))), dev(b), q, qt)
+    ctx.cpm_update(m, dev(np.tile(psi, (m, 1))), dev(b), q, qt)
     torch.cuda.synchronize()
     return q.cpu().numpy(), qt.cpu().numpy()
