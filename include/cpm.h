@@ -216,6 +216,34 @@ typedef enum {
 cpm_status cpm_profile(cpm_ctx* ctx, int32_t enable);
 cpm_status cpm_profile_read(cpm_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches, int32_t reset);
 
+/*
+ * cpm_bvec_noalloc - the electrolyte potential b of cpm_bvec for ONE electrolyte
+ * configuration (FP64), computed without allocating any device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc: code running inside another framework's memory pool or
+ * allocator hooks, a CUDA-graph node that must not allocate, or an embedding that
+ * forbids allocation after start-up.  It needs no context: the caller passes the
+ * parameters, the sites (site_xyz: device, n x 3; site_eta: device, n), the charges
+ * (xyz: device, n_e x 3; Q: device, n_e) and the output b_out (device, n doubles),
+ * and the work is issued on `cuda_stream` (a cudaStream_t, NULL = default stream).
+ *
+ * Scratch: a fixed device array of 262,144 complex doubles (4 MiB) built into the
+ * library, which every GPU that loads the library holds until the process exits.
+ * The reciprocal-space grid, (NX + 1)(2 NY + 1)(2 NZ + 1) entries with
+ * N_d = floor(kcut L_d / 2 pi) + 1, must fit in it; a larger grid returns
+ * CPM_E_BUDGET and launches nothing.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Real-space pairs are summed directly over all
+ * charges and images (no cell list), so the cost grows as n * n_e.
+ * Errors: CPM_E_ARG (bad parameters or pointers), CPM_E_BUDGET (grid too large),
+ * CPM_E_CUDA (no device, or a launch failed).
+ */
+cpm_status cpm_bvec_noalloc(const cpm_params* p, int64_t n, const double* site_xyz, const double* site_eta,
+                            int64_t n_e, const double* xyz, const double* Q, double* b_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ _SIGS = {
     "cpm_load": ([_P, ctypes.c_char_p], _I32),
     "cpm_device_bytes": ([_P], ctypes.c_size_t),
     "cpm_launch_count": ([_P], _I64),
+    "cpm_bvec_noalloc": ([ctypes.POINTER(cpm_params), _I64, _P, _P, _I64, _P, _P, _P, _P], _I32),
     "cpm_profile": ([_P, _I32], _I32),
     "cpm_profile_read": ([_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32], _I32),
 }
@@ -94,6 +95,21 @@ def _stream_handle(stream) -> int:
         return 0   # the library itself reports that no device is usable
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
+
+
+def cpm_bvec_noalloc(params: cpm_params, site_xyz, site_eta, xyz, Q, b_out, stream=None) -> None:
+    """b for one electrolyte configuration without any device allocation (see include/cpm.h).
+
+    For callers that cannot allocate device memory: the library's fixed 4 MiB scratch
+    array holds the reciprocal-space grid, shared by all calls (serialise overlapping calls).
+    """
+    lib = load_library()
+    n_e = int(xyz.shape[0]) if xyz is not None else 0
+    st = lib.cpm_bvec_noalloc(ctypes.byref(params), int(site_xyz.shape[0]), _ptr(site_xyz), _ptr(site_eta), n_e,
+                              _ptr(xyz) if n_e else None, _ptr(Q) if n_e else None, _ptr(b_out),
+                              _P(_stream_handle(stream)))
+    if st != 0:
+        raise CPMError(st, "cpm_bvec_noalloc failed")
 
 
 class CPM:
