@@ -203,7 +203,8 @@ typedef enum {
     CPM_K_COMBINE = 7,  /* b assembly (background, boundary term) */
     CPM_K_GEMV = 8,     /* S (G psi - b) */
     CPM_K_NEUTRAL = 9,  /* neutrality fix and total charge */
-    CPM_K_COUNT = 10
+    CPM_K_COL0 = 10,    /* FP64 k_perp = 0 column of the single-precision path */
+    CPM_K_COUNT = 11
 } cpm_kernel;
 
 /*

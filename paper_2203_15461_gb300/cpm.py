@@ -61,7 +61,7 @@ _SIGS = {
     "cpm_profile": ([_P, _I32], _I32),
     "cpm_profile_read": ([_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32], _I32),
 }
-KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral"]
+KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral", "col0"]
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:

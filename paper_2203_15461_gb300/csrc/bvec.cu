@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
                                             int64_t chunk, int m, c2<T>* __restrict__ rho_part) {
     __shared__ c2<T> Ps[SF_BK][SF_BM + 1];
     __shared__ c2<T> Zs[SF_BK][SF_BN + 1];
-    const int c0 = blockIdx.x * SF_BM, z0 = blockIdx.y * SF_BN;
+    // z tiles are centred on nz = 0: tile t covers grid indices zbase + t*BN ... + BN - 1
+    const int zbase = NZ - SF_BN / 2 - SF_BN * ((int)gridDim.y / 2);
+    const int c0 = blockIdx.x * SF_BM, z0 = zbase + blockIdx.y * SF_BN;
     const int r = blockIdx.z / splits, s = blockIdx.z % splits;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     c2<T>* outp = rho_part + ((int64_t)s * m + r) * ncols * nzw;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
                 Ps[kk][mm] = v;
                 int z = z0 + mm;
                 V zv = cmake<T>(0, 0);
-                if (j < je && z < nzw) zv = EZ[(int64_t)z * ptot + j];
+                if (j < je && z >= 0 && z < nzw) zv = EZ[(int64_t)z * ptot + j];
                 Zs[kk][mm] = zv;
             }
             __syncthreads();
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int z = z0 + tx + 16 * q;
-            if (z < nzw) outp[(int64_t)c * nzw + z] = acc[p][q];
+            if (z >= 0 && z < nzw) outp[(int64_t)c * nzw + z] = acc[p][q];
         }
     }
 }
@@ -392,9 +394,92 @@ __global__ void __launch_bounds__(256) k_site(const int2* __restrict__ cols, con
     }
 }
 
+// ----------------------------------------------------------------------------- k_perp = 0 column in FP64
+// The single-precision path sums the column (0, 0, nz), nz = 1..ext0, in FP64: its weights
+// are the largest of the whole set (they carry the laterally averaged charge profile), so
+// its terms dominate the rounding of a single-precision sum.  Phases by an FP64 recurrence
+// in nz from an exactly reduced first harmonic.
+__device__ __forceinline__ double2 z_phase1(double z, double invLz) {
+    double s = z * invLz;
+    s -= floor(s);
+    double t = s * 18446744073709551616.0;
+    uint64_t u = t >= 18446744073709551616.0 ? 0ull : (uint64_t)t;
+    double sn, cs;
+    sincospi((double)(int64_t)u * 0x1p-63, &sn, &cs);
+    return make_double2(cs, sn);
+}
+
+// part[r][chunk][nz - 1] = sum over the chunk's charges of Q_j exp(i kz z_j); one block per chunk.
+__global__ void __launch_bounds__(256) k_col0_rho(const double* __restrict__ xyz, const double* __restrict__ Q,
+                                                  int64_t ne, double invLz, int nz0, double2* __restrict__ part) {
+    __shared__ double2 red[8];
+    const int r = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double q = 0.0;
+    double2 e1 = make_double2(1.0, 0.0);
+    if (j < ne) {
+        q = Q[(int64_t)r * ne + j];
+        e1 = z_phase1(xyz[3 * ((int64_t)r * ne + j) + 2], invLz);
+    }
+    double2 e = e1;
+    double2* out = part + ((int64_t)r * gridDim.x + blockIdx.x) * nz0;
+    for (int nz = 1; nz <= nz0; ++nz) {
+        double re = q * e.x, im = q * e.y;
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) red[warp] = make_double2(re, im);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double2 t = red[0];
+            for (int w = 1; w < 8; ++w) { t.x += red[w].x; t.y += red[w].y; }
+            out[nz - 1] = t;
+        }
+        __syncthreads();
+        e = cmul(e, e1);
+    }
+}
+
+// wrho0[r][nz - 1] = w(0, 0, nz) * sum over chunks of part
+__global__ void k_col0_reduce(const double2* __restrict__ part, int nchunks, int nz0, const double* __restrict__ w,
+                              int NZ, int m, double2* __restrict__ wrho0) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * nz0) return;
+    const int r = t / nz0, k = t % nz0;
+    double2 a = make_double2(0.0, 0.0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        double2 v = part[((int64_t)r * nchunks + ch) * nz0 + k];
+        a.x += v.x;
+        a.y += v.y;
+    }
+    const double wt = w[NZ + k + 1];   // column 0 occupies the first row of the dense grid
+    wrho0[t] = make_double2(wt * a.x, wt * a.y);
+}
+
+// b0[r][i] = sum_nz Re[exp(-i kz z_i) wrho0[r][nz]]
+__global__ void k_col0_site(const double* __restrict__ sx, int64_t n, int m, double invLz, int nz0,
+                            const double2* __restrict__ wrho0, double* __restrict__ b0) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * n) return;
+    const int r = (int)(t / n);
+    const int64_t i = t % n;
+    const double2 e1 = z_phase1(sx[2 * n + i], invLz);
+    double2 e = e1;
+    double acc = 0.0;
+    const double2* wr = wrho0 + (int64_t)r * nz0;
+    for (int nz = 1; nz <= nz0; ++nz) {
+        double2 v = wr[nz - 1];
+        acc += e.x * v.x + e.y * v.y;
+        e = cmul(e, e1);
+    }
+    b0[t] = acc;
+}
+
 // b[r][i] = K_E (recip + real - pi Q_tot / (V alpha^2) + boundary)
 template <typename T>
-__global__ void k_combine(const T* partial, int nctiles, const double* real, const double* stats,
+__global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const double* stats,
                           const double* sx, int64_t n, int m, Geometry g, double* b) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
@@ -403,6 +488,7 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     double s = 0.0;
     for (int k = 0; k < nctiles; ++k) s += (double)partial[((int64_t)r * nctiles + k) * n + i];
     s += real[t];
+    if (b0) s += b0[t];
     const double* st = stats + 4 * r;
     s += -PI * st[0] / (g.V * g.alpha * g.alpha);
     if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];
@@ -419,7 +505,8 @@ struct BvecPlan {
     int splits, nctiles, ctiles, ztiles;
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
-        off_start, off_wpos, off_sorted, off_order, total;
+        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, total;
+    int c0chunks;
 };
 
 template <typename T>
@@ -428,7 +515,9 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const KTable& k = c->kt;
     p.cg = make_grid(c->g);
     p.ctiles = (k.ncols + SF_BM - 1) / SF_BM;
-    p.ztiles = (k.nzw + SF_BN - 1) / SF_BN;
+    // odd number 2h + 1 of BN-wide z tiles centred on nz = 0, covering -NZ..NZ
+    const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
+    p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
     const int64_t base = (int64_t)p.ctiles * p.ztiles * m;
     int64_t want = (4 * 152 + base - 1) / std::max<int64_t>(base, 1);
@@ -457,6 +546,11 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_wpos = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_order = o; o += al(sizeof(int) * ptot);
+    p.c0chunks = (int)std::max<int64_t>(1, (ne + 255) / 256);
+    const int nz0 = std::max(k.ext0, 1);
+    p.off_c0part = o; o += al(sizeof(double2) * (size_t)m * p.c0chunks * nz0);
+    p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
+    p.off_b0 = o; o += al(sizeof(double) * (size_t)m * c->n);
     p.total = o;
     return p;
 }
@@ -547,9 +641,26 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     } else {
         CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, st));
     }
+    double* b0 = nullptr;
+    if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0) {
+        // the k_perp = 0 column in FP64 (its single-precision weights are zero)
+        double2* c0part = (double2*)(scr + p.off_c0part);
+        double2* c0w = (double2*)(scr + p.off_c0w);
+        b0 = (double*)(scr + p.off_b0);
+        prof_begin(c, CPM_K_COL0);
+        k_col0_rho<<<dim3(p.c0chunks, m), 256, 0, st>>>(xyz, Q, ne, c->g.inv[2], k.ext0, c0part);
+        CPM_LAUNCH(c, "k_col0_rho");
+        k_col0_reduce<<<(m * k.ext0 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
+        CPM_LAUNCH(c, "k_col0_reduce");
+        k_col0_site<<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g.inv[2], k.ext0, c0w,
+                                                                               b0);
+        CPM_LAUNCH(c, "k_col0_site");
+        prof_end(c, CPM_K_COL0);
+        c->launches += 3;
+    }
     prof_begin(c, CPM_K_COMBINE);
-    k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, stats, c->sx, n, m,
-                                                                          c->g, b_out);
+    k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, stats, c->sx, n,
+                                                                          m, c->g, b_out);
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;

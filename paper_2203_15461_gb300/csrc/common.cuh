@@ -47,6 +47,7 @@ enum : unsigned { ST_NOT_SPD = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
 struct KTable {
     int NX = 0, NY = 0, NZ = 0;
     int ncols = 0, nzw = 0;
+    int ext0 = -1;                  // largest nz of the k_perp = 0 column (column 0), -1 if empty
     int64_t nk = 0;                 // number of vectors with nonzero weight
     int2* cols = nullptr;           // [ncols] (nx, ny)
     int* colext = nullptr;          // [ncols] largest |nz| with nonzero weight, -1 if none
@@ -120,6 +121,8 @@ struct cpm_ctx {
     size_t pinned_bytes = 0;
     void* dstage = nullptr;
     size_t dstage_bytes = 0;
+    void* ubuf = nullptr;        // cpm_update scratch (split partial sums, b hi/lo)
+    size_t ubuf_bytes = 0;
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 

@@ -40,7 +40,9 @@ __device__ void block_exclusive_scan(const int64_t* in, int64_t* off, int64_t cn
     if (threadIdx.x == 0) off[cnt] = carry;
 }
 
-// Columns (nx, ny) of the half plane whose transverse |k| is within kcut, in (nx, ny) order.
+// Columns (nx, ny) of the half plane whose transverse |k| is within kcut, sorted by the
+// transverse |k|^2 (ties by (nx, ny)), so that the first column is k_perp = 0 and columns
+// with similar nz extents share tiles.
 __global__ void k_columns(int NX, int NY, double tx, double ty, double kc2, int64_t* flags, int64_t* off,
                           int2* cols, int* ncols) {
     const int64_t ncand = (int64_t)(NX + 1) * (2 * NY + 1);
@@ -58,7 +60,23 @@ __global__ void k_columns(int NX, int NY, double tx, double ty, double kc2, int6
             cols[off[i]] = make_int2(nx, ny);
         }
     }
-    if (threadIdx.x == 0) *ncols = (int)off[ncand];
+    __syncthreads();
+    const int nc = (int)off[ncand];
+    int2* tmp = reinterpret_cast<int2*>(flags);   // flags are no longer needed
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int2 a = cols[c];
+        double ka = k2_of(tx, ty, 0.0, a.x, a.y, 0);
+        int rank = 0;
+        for (int d = 0; d < nc; ++d) {
+            int2 b = cols[d];
+            double kb = k2_of(tx, ty, 0.0, b.x, b.y, 0);
+            rank += (kb < ka || (kb == ka && d < c)) ? 1 : 0;
+        }
+        tmp[rank] = a;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) cols[c] = tmp[c];
+    if (threadIdx.x == 0) *ncols = nc;
 }
 
 __global__ void k_weights(const int2* cols, int ncols, int NZ, double tx, double ty, double tz, double kc2,
@@ -76,7 +94,9 @@ __global__ void k_weights(const int2* cols, int ncols, int NZ, double tx, double
         atomicMax(&colext[c], nz < 0 ? -nz : nz);
     }
     w[i] = wt;
-    w32[i] = (float)wt;
+    // The k_perp = 0 column carries the largest weights (the laterally averaged charge
+    // profile); the single-precision path leaves it to an FP64 kernel.
+    w32[i] = (cn.x == 0 && cn.y == 0) ? 0.0f : (float)wt;
 }
 
 __global__ void k_colcounts(const int2* cols, const int* colext, int ncols, int64_t* cnt) {
@@ -144,6 +164,7 @@ cpm_status build_ktable(cpm_ctx* c) {
     k_weights<<<(unsigned)((grid + 255) / 256), 256, 0, c->stream>>>(k.cols, k.ncols, k.NZ, tx, ty, tz, kc2, pref,
                                                                     inv4a2, k.w, k.w32, k.colext);
     CPM_LAUNCH(c, "k_weights");
+    CPM_CUDA(c, cudaMemcpyAsync(&k.ext0, k.colext, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     int64_t* cnt = nullptr;
     CPM_TRY(dev_alloc(c, (void**)&cnt, k.ncols * sizeof(int64_t)));
     k_colcounts<<<(k.ncols + 255) / 256, 256, 0, c->stream>>>(k.cols, k.colext, k.ncols, cnt);

@@ -6,45 +6,103 @@
 
 namespace cpm {
 
-constexpr int GV_ROWS = 16;   // rows per block
-constexpr int GV_M = 4;       // right-hand sides per pass
+// S is symmetric, so q_i = sum_j S_ji b_j: one thread per output i reads column i of S (row
+// j = column j, coalesced across the block), the b_j are broadcast from shared memory, and the
+// rows j are split over blocks (partial sums reduced in FP64 in a fixed order).
+//
+// Single precision: the sum is centred per output, sum_j S_ij (b_j - b_i), which equals S b
+// because the rows of S sum to zero (Eq. S).  S rounded to FP32 then only perturbs the
+// products where b_j differs from b_i, i.e. mostly far sites where S_ij is small; b enters as
+// an FP32 hi + lo pair so the differences are formed to about 2^-24 of themselves, and each
+// thread's partial sum is Kahan-compensated.
+constexpr int GT_COLS = 128;   // outputs (threads) per block
+constexpr int GT_JT = 64;      // rows of S staged per iteration
+constexpr int GT_MR = 8;       // replicas per block
 
-template <typename TS> struct Acc;
-template <> struct Acc<float> { using t = float; };
-template <> struct Acc<double> { using t = double; };
+template <typename TS> struct LaneSum {
+    TS s = 0;
+    __device__ __forceinline__ void add(TS x) { s += x; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <> struct LaneSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
-// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_j S[i][j] b[r][j]; a warp per row, GV_M replicas per pass.
+// bhl[t] = (hi, lo) with hi = float(b[t]) and lo = float(b[t] - hi)
+__global__ void k_split_b(const double* __restrict__ b, int64_t cnt, float2* __restrict__ bhl) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    double v = b[t];
+    float hi = (float)v;
+    bhl[t] = make_float2(hi, (float)(v - (double)hi));
+}
+
+template <typename TS> struct BVal;
+template <> struct BVal<float> { using t = float2; };
+template <> struct BVal<double> { using t = double; };
+
+__device__ __forceinline__ float centred(float2 bj, float2 bi) { return (bj.x - bi.x) + (bj.y - bi.y); }
+__device__ __forceinline__ double centred(double bj, double) { return bj; }
+
+// part[split][r][i] = sum over this split's rows j of S_ji x_j (x_j = b_j - b_i in FP32, b_j in FP64)
 template <typename TS>
-__global__ void __launch_bounds__(256) k_gemv(const TS* __restrict__ S, const double* __restrict__ SG, int ng,
-                                              const double* __restrict__ psi, const double* __restrict__ b,
-                                              int64_t n, int m, double* __restrict__ q) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r0 = 0; r0 < m; r0 += GV_M) {
-        const int mm = min(GV_M, m - r0);
-        for (int64_t row = (int64_t)blockIdx.x * GV_ROWS + warp; row < min(n, (int64_t)(blockIdx.x + 1) * GV_ROWS);
-             row += 8) {
-            const TS* Sr = S + row * n;
-            TS acc[GV_M];
+__global__ void __launch_bounds__(GT_COLS) k_gemv_t(const TS* __restrict__ S, const typename BVal<TS>::t* __restrict__ bv,
+                                                     int64_t n, int m, int64_t jchunk, double* __restrict__ part) {
+    typedef typename BVal<TS>::t B;
+    __shared__ B bs[GT_MR][GT_JT];
+    const int64_t i = (int64_t)blockIdx.x * GT_COLS + threadIdx.x;
+    const int split = blockIdx.y;
+    const int r0 = blockIdx.z * GT_MR;
+    const int mm = min(GT_MR, m - r0);
+    const int64_t jb = (int64_t)split * jchunk, je = min(n, jb + jchunk);
+    B bi[GT_MR];
+    LaneSum<TS> acc[GT_MR];
 #pragma unroll
-            for (int t = 0; t < GV_M; ++t) acc[t] = 0;
-            for (int64_t j = lane; j < n; j += 32) {
-                TS s = Sr[j];
+    for (int t = 0; t < GT_MR; ++t) bi[t] = (t < mm && i < n) ? bv[(int64_t)(r0 + t) * n + i] : B{};
+    for (int64_t j0 = jb; j0 < je; j0 += GT_JT) {
+        for (int e = threadIdx.x; e < GT_MR * GT_JT; e += GT_COLS) {
+            int t = e / GT_JT, jj = e % GT_JT;
+            int64_t j = j0 + jj;
+            bs[t][jj] = (t < mm && j < je) ? bv[(int64_t)(r0 + t) * n + j] : B{};
+        }
+        __syncthreads();
+        const int jn = (int)min((int64_t)GT_JT, je - j0);
+        if (i < n) {
+            for (int jj = 0; jj < jn; ++jj) {
+                const TS sv = S[(j0 + jj) * n + i];
 #pragma unroll
-                for (int t = 0; t < GV_M; ++t)
-                    if (t < mm) acc[t] += s * (TS)b[(int64_t)(r0 + t) * n + j];
-            }
-#pragma unroll
-            for (int t = 0; t < GV_M; ++t) {
-                double v = (double)acc[t];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0 && t < mm) {
-                    double sv = 0.0;
-                    for (int g = 0; g < ng; ++g) sv += SG[row * ng + g] * psi[(int64_t)(r0 + t) * ng + g];
-                    q[(int64_t)(r0 + t) * n + row] = sv - v;
-                }
+                for (int t = 0; t < GT_MR; ++t)
+                    if (t < mm) acc[t].add(sv * (TS)centred(bs[t][jj], bi[t]));
             }
         }
+        __syncthreads();
     }
+    if (i < n) {
+#pragma unroll
+        for (int t = 0; t < GT_MR; ++t)
+            if (t < mm) part[((int64_t)split * m + r0 + t) * n + i] = acc[t].value();
+    }
+}
+
+// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
+__global__ void k_gemv_reduce(const double* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
+                              const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * n) return;
+    const int r = (int)(t / n);
+    const int64_t i = t % n;
+    double v = 0.0;
+    for (int sp = 0; sp < splits; ++sp) v += part[((int64_t)sp * m + r) * n + i];
+    double sv = 0.0;
+    for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
+    q[t] = sv - v;
 }
 
 // One block per replica: s = e^T q; q <- q - u s (symm); qtot = e^T q with Neumaier compensation.
@@ -92,13 +150,33 @@ __global__ void k_neutral(double* q, const double* u, int64_t n, int symm, doubl
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot) {
     const int64_t n = c->n;
     cudaStream_t st = c->stream;
-    const unsigned blocks = (unsigned)((n + GV_ROWS - 1) / GV_ROWS);
-    c->launches += 2;
+    const bool f32 = c->p.s_prec == CPM_PREC_FP32;
+    const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
+    const int rchunks = (m + GT_MR - 1) / GT_MR;
+    int64_t splits = (4 * 152 + colblocks * rchunks - 1) / (colblocks * rchunks);
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n + GT_JT - 1) / GT_JT));
+    const int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
+    splits = (n + jchunk - 1) / jchunk;
+    const size_t need = ((sizeof(double) * splits * m * n + 255) & ~(size_t)255) + sizeof(float2) * m * n;
+    if (c->ubuf_bytes < need) {
+        dev_free(c, c->ubuf);
+        c->ubuf = nullptr;
+        c->ubuf_bytes = 0;
+        CPM_TRY(dev_alloc(c, &c->ubuf, need));
+        c->ubuf_bytes = need;
+    }
+    double* part = (double*)c->ubuf;
+    float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
+    c->launches += f32 ? 4 : 3;
     prof_begin(c, CPM_K_GEMV);
-    if (c->p.s_prec == CPM_PREC_FP32)
-        k_gemv<float><<<blocks, 256, 0, st>>>(c->S32, c->SG, c->ng, psi, b, n, m, q);
-    else
-        k_gemv<double><<<blocks, 256, 0, st>>>(c->S, c->SG, c->ng, psi, b, n, m, q);
+    dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
+    if (f32) {
+        k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
+        k_gemv_t<float><<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
+    } else {
+        k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
+    }
+    k_gemv_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q);
     prof_end(c, CPM_K_GEMV);
     CPM_LAUNCH(c, "k_gemv");
     prof_begin(c, CPM_K_NEUTRAL);

@@ -183,3 +183,57 @@ def test_tinfoil_3d_parity():
     ely = s.Electrolyte(xyz=rng.uniform(0, 1, (30, 3)) * box, Q=np.tile([1.0, -1.0], 15))
     b = run_bvec(ctx, [ely])
     assert rel_l2(b[0], o.bvec(el, ely)) <= 1e-11
+
+
+# ----------------------------------------------------------------------------- full-size workloads
+
+@pytest.fixture(scope="module")
+def edl():
+    """4,320-site EDL capacitor (1,800 waters + 300 ions): GPU FP64 and mixed contexts."""
+    need_gpu()
+    el, ely, psi = s.workload_edl_capacitor(seed=1)
+    c64 = make_ctx(el).setup(el)
+    c32 = make_ctx(el, s_prec="fp32", k_prec="fp32").setup(el)
+    return el, ely, psi, c64, c32
+
+
+def test_edl_capacitor_sampled_elastance_rows(edl):
+    el, _, _, c64, _ = edl
+    rows = np.random.default_rng(0).choice(el.n, 12, replace=False)
+    A_rows = o.assemble_A(el, rows=rows)
+    Ag = c64.cpm_get_matrix("A").cpu().numpy()[rows]
+    assert np.abs(Ag - A_rows).max() <= 1e-12 * np.abs(A_rows).max()
+
+
+def test_edl_capacitor_b_sampled_and_q_optimal(edl):
+    """b at sampled sites against the oracle; q satisfies the stationarity condition A q + b - v = lambda e
+    on sampled rows of the oracle's A; the mixed path agrees with FP64 within 1e-5 and both are neutral."""
+    el, ely, psi, c64, c32 = edl
+    sites = np.random.default_rng(1).choice(el.n, 12, replace=False)
+    b64 = run_bvec(c64, [ely])
+    assert rel_l2(b64[0][sites], o.bvec(el, ely, sites=sites)) <= 1e-11
+    q64, qt64 = run_update(c64, psi, b64)
+    A_rows = o.assemble_A(el, rows=sites)
+    v = o.site_potentials(el, psi)
+    r = A_rows @ q64[0] + b64[0][sites] - v[sites]
+    assert np.abs(r - r.mean()).max() <= 1e-9 * np.abs(v - b64[0]).max()
+    b32 = run_bvec(c32, [ely])
+    q32, qt32 = run_update(c32, psi, b32)
+    assert rel_l2(q32[0], q64[0]) <= 1e-5
+    assert abs(qt64[0]) <= 1e-12 and abs(qt32[0]) <= 1e-12
+    assert abs(q64[0].sum()) <= 1e-12 and abs(q32[0].sum()) <= 1e-12
+
+
+def test_batched_replicas_of_the_tiny_capacitor(tiny):
+    """256 replicas sharing one S (each its own seeded electrolyte) in one launch sequence; replicas checked
+    against the oracle one by one."""
+    el, _, psi, _, S = tiny
+    elyts = [s.ions_in_gap(el, 100, seed=1000 + r) for r in range(256)]
+    for s_prec, k_prec, tol in (("fp64", "fp64", 1e-10), ("fp32", "fp32", 1e-5)):
+        ctx = make_ctx(el, s_prec=s_prec, k_prec=k_prec).setup(el)
+        b = run_bvec(ctx, elyts)
+        q, qt = run_update(ctx, psi, b)
+        for r in (0, 77, 255):
+            q_ref = o.charges(S, el, psi, o.bvec(el, elyts[r]))
+            assert rel_l2(q[r], q_ref) <= tol
+        assert np.abs(qt).max() <= 1e-12
