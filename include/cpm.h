@@ -61,7 +61,9 @@ typedef enum {
 /* Arithmetic of a per-step stage. */
 typedef enum {
     CPM_PREC_FP64 = 0,  /* IEEE double throughout */
-    CPM_PREC_FP32 = 1   /* single precision products and accumulation, FP64 neutrality and totals */
+    CPM_PREC_FP32 = 1,  /* single precision products and accumulation, FP64 neutrality and totals */
+    CPM_PREC_BF16X3 = 2 /* s_prec only: S and b each split into three bf16 terms, six products per
+                           step on the tensor cores (tcgen05), FP32 accumulation, FP64 split sums */
 } cpm_precision;
 
 typedef struct {

@@ -116,9 +116,11 @@ __global__ void k_soa(const double* xyz, const double* eta, const int32_t* grp, 
 static void free_geometry(cpm_ctx* c) {
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
-                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz};
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
+    c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
+    c->Sb = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -145,7 +147,7 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
         if (!(p->box[d] > 0.0)) return CPM_E_ARG;
     if (!(p->alpha > 0.0) || !(p->rcut > 0.0) || !(p->kcut > 0.0)) return CPM_E_ARG;
     if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_WIRE) return CPM_E_ARG;
-    if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32) ||
+    if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32 && p->s_prec != CPM_PREC_BF16X3) ||
         (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32))
         return CPM_E_ARG;
     int ndev = 0;
@@ -218,6 +220,19 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
             free_geometry(c);
             return set_err(c, CPM_E_NONFINITE, "cpm_assemble: non-finite coordinate, eta <= 0 or group out of range");
         }
+        // distinct site heights: the k_perp = 0 column of b depends on z only
+        std::vector<double> zs(hx.begin() + 2 * n, hx.begin() + 3 * n);
+        std::vector<double> zu = zs;
+        std::sort(zu.begin(), zu.end());
+        zu.erase(std::unique(zu.begin(), zu.end()), zu.end());
+        std::vector<int> zm(n);
+        for (int64_t i = 0; i < n; ++i) zm[i] = (int)(std::lower_bound(zu.begin(), zu.end(), zs[i]) - zu.begin());
+        c->nzu = (int)zu.size();
+        CPM_TRY(dev_alloc(c, (void**)&c->zmap, sizeof(int) * n));
+        CPM_TRY(dev_alloc(c, (void**)&c->zuniq, sizeof(double) * zu.size()));
+        CPM_CUDA(c, cudaMemcpyAsync(c->zmap, zm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        CPM_CUDA(c, cudaMemcpyAsync(c->zuniq, zu.data(), sizeof(double) * zu.size(), cudaMemcpyHostToDevice, st));
+        CPM_CUDA(c, cudaStreamSynchronize(st));
         uint64_t h = 1469598103934665603ull;
         h = fnv1a(h, hx.data(), hx.size() * sizeof(double));
         h = fnv1a(h, hg.data(), hg.size() * sizeof(int));
@@ -257,6 +272,8 @@ cpm_status cpm_invert(cpm_ctx* c) {
     c->err.clear();
     if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_invert before cpm_assemble");
     c->inverted = false;
+    dev_free(c, c->Sb);
+    c->Sb = nullptr;
     CPM_TRY(invert_and_project(c));
     c->inverted = true;
     return CPM_OK;
@@ -434,6 +451,8 @@ cpm_status cpm_load(cpm_ctx* c, const char* path) {
                                 c->stream));
     CPM_CUDA(c, cudaMemcpyAsync(c->u, buf.data() + n * n + n * c->ng, sizeof(double) * n, cudaMemcpyHostToDevice,
                                 c->stream));
+    dev_free(c, c->Sb);
+    c->Sb = nullptr;
     k_tofloat<<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(c->S, c->S32, (int64_t)(n * n));
     CPM_LAUNCH(c, "k_tofloat");
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -20,7 +20,7 @@ namespace cpm {
 
 template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
-template <> struct V4<double> { using t = double4; };
+template <> struct V4<double> { using t = double4_32a; };
 
 struct CellGrid {
     int nc[3];
@@ -409,36 +409,58 @@ __device__ __forceinline__ double2 z_phase1(double z, double invLz) {
     return make_double2(cs, sn);
 }
 
-// part[r][chunk][nz - 1] = sum over the chunk's charges of Q_j exp(i kz z_j); one block per chunk.
-__global__ void __launch_bounds__(256) k_col0_rho(const double* __restrict__ xyz, const double* __restrict__ Q,
-                                                  int64_t ne, double invLz, int nz0, double2* __restrict__ part) {
-    __shared__ double2 red[8];
-    const int r = blockIdx.y;
-    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+// part[r][chunk][nz - 1] for nz in one block of 8 harmonics: each thread takes 8 charges of the
+// chunk (1,024 charges per block), starts the harmonic run from an exactly reduced phase and
+// steps it by an FP64 recurrence, then the block sums its threads in a fixed order.
+constexpr int C0_THREADS = 128, C0_PER_THREAD = 8, C0_NB = 8;
+
+__global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const double* __restrict__ xyz, const double* __restrict__ Q,
+                                                       int64_t ne, double invLz, int nz0, double2* __restrict__ part) {
+    __shared__ double2 red[C0_THREADS / 32][C0_NB];
+    const int chunk = blockIdx.x, nb = blockIdx.y, r = blockIdx.z;
+    const int nzs = nb * C0_NB + 1;   // first harmonic of this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double q = 0.0;
-    double2 e1 = make_double2(1.0, 0.0);
-    if (j < ne) {
-        q = Q[(int64_t)r * ne + j];
-        e1 = z_phase1(xyz[3 * ((int64_t)r * ne + j) + 2], invLz);
+    double2 acc[C0_NB];
+#pragma unroll
+    for (int k = 0; k < C0_NB; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int t = 0; t < C0_PER_THREAD; ++t) {
+        const int64_t j = (int64_t)chunk * C0_THREADS * C0_PER_THREAD + (int64_t)t * C0_THREADS + threadIdx.x;
+        if (j >= ne) break;
+        const int64_t p = (int64_t)r * ne + j;
+        const double q = Q[p];
+        if (q == 0.0) continue;
+        double s = xyz[3 * p + 2] * invLz;
+        s -= floor(s);
+        double tt = s * 18446744073709551616.0;
+        const uint64_t u = tt >= 18446744073709551616.0 ? 0ull : (uint64_t)tt;
+        double sn, cs;
+        sincospi((double)(int64_t)(u * (uint64_t)nzs) * 0x1p-63, &sn, &cs);
+        double2 e = make_double2(cs, sn);
+        sincospi((double)(int64_t)u * 0x1p-63, &sn, &cs);
+        const double2 e1 = make_double2(cs, sn);
+#pragma unroll
+        for (int k = 0; k < C0_NB; ++k) {
+            acc[k].x += q * e.x;
+            acc[k].y += q * e.y;
+            e = cmul(e, e1);
+        }
     }
-    double2 e = e1;
-    double2* out = part + ((int64_t)r * gridDim.x + blockIdx.x) * nz0;
-    for (int nz = 1; nz <= nz0; ++nz) {
-        double re = q * e.x, im = q * e.y;
+#pragma unroll
+    for (int k = 0; k < C0_NB; ++k) {
         for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
+            acc[k].x += __shfl_down_sync(0xffffffffu, acc[k].x, o);
+            acc[k].y += __shfl_down_sync(0xffffffffu, acc[k].y, o);
         }
-        if (lane == 0) red[warp] = make_double2(re, im);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double2 t = red[0];
-            for (int w = 1; w < 8; ++w) { t.x += red[w].x; t.y += red[w].y; }
-            out[nz - 1] = t;
+        if (lane == 0) red[warp][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < C0_NB) {
+        const int k = threadIdx.x, nz = nzs + k;
+        if (nz <= nz0) {
+            double2 t = red[0][k];
+            for (int w = 1; w < C0_THREADS / 32; ++w) { t.x += red[w][k].x; t.y += red[w][k].y; }
+            part[((int64_t)r * gridDim.x + chunk) * nz0 + nz - 1] = t;
         }
-        __syncthreads();
-        e = cmul(e, e1);
     }
 }
 
@@ -458,14 +480,13 @@ __global__ void k_col0_reduce(const double2* __restrict__ part, int nchunks, int
     wrho0[t] = make_double2(wt * a.x, wt * a.y);
 }
 
-// b0[r][i] = sum_nz Re[exp(-i kz z_i) wrho0[r][nz]]
-__global__ void k_col0_site(const double* __restrict__ sx, int64_t n, int m, double invLz, int nz0,
+// b0[r][u] = sum_nz Re[exp(-i kz z_u) wrho0[r][nz]] for each distinct site height z_u
+__global__ void k_col0_site(const double* __restrict__ zu, int nzu, int m, double invLz, int nz0,
                             const double2* __restrict__ wrho0, double* __restrict__ b0) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)m * n) return;
-    const int r = (int)(t / n);
-    const int64_t i = t % n;
-    const double2 e1 = z_phase1(sx[2 * n + i], invLz);
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * nzu) return;
+    const int r = t / nzu, iu = t % nzu;
+    const double2 e1 = z_phase1(zu[iu], invLz);
     double2 e = e1;
     double acc = 0.0;
     const double2* wr = wrho0 + (int64_t)r * nz0;
@@ -479,8 +500,8 @@ __global__ void k_col0_site(const double* __restrict__ sx, int64_t n, int m, dou
 
 // b[r][i] = K_E (recip + real - pi Q_tot / (V alpha^2) + boundary)
 template <typename T>
-__global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const double* stats,
-                          const double* sx, int64_t n, int m, Geometry g, double* b) {
+__global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const int* zmap,
+                          int nzu, const double* stats, const double* sx, int64_t n, int m, Geometry g, double* b) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
@@ -488,7 +509,7 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     double s = 0.0;
     for (int k = 0; k < nctiles; ++k) s += (double)partial[((int64_t)r * nctiles + k) * n + i];
     s += real[t];
-    if (b0) s += b0[t];
+    if (b0) s += b0[(int64_t)r * nzu + zmap[i]];
     const double* st = stats + 4 * r;
     s += -PI * st[0] / (g.V * g.alpha * g.alpha);
     if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];
@@ -546,11 +567,11 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_wpos = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_order = o; o += al(sizeof(int) * ptot);
-    p.c0chunks = (int)std::max<int64_t>(1, (ne + 255) / 256);
+    p.c0chunks = (int)std::max<int64_t>(1, (ne + C0_THREADS * C0_PER_THREAD - 1) / (C0_THREADS * C0_PER_THREAD));
     const int nz0 = std::max(k.ext0, 1);
     p.off_c0part = o; o += al(sizeof(double2) * (size_t)m * p.c0chunks * nz0);
     p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
-    p.off_b0 = o; o += al(sizeof(double) * (size_t)m * c->n);
+    p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
     p.total = o;
     return p;
 }
@@ -648,19 +669,19 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         double2* c0w = (double2*)(scr + p.off_c0w);
         b0 = (double*)(scr + p.off_b0);
         prof_begin(c, CPM_K_COL0);
-        k_col0_rho<<<dim3(p.c0chunks, m), 256, 0, st>>>(xyz, Q, ne, c->g.inv[2], k.ext0, c0part);
+        const int nblk = (k.ext0 + C0_NB - 1) / C0_NB;
+        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(xyz, Q, ne, c->g.inv[2], k.ext0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
         k_col0_reduce<<<(m * k.ext0 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
         CPM_LAUNCH(c, "k_col0_reduce");
-        k_col0_site<<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g.inv[2], k.ext0, c0w,
-                                                                               b0);
+        k_col0_site<<<(m * c->nzu + 127) / 128, 128, 0, st>>>(c->zuniq, c->nzu, m, c->g.inv[2], k.ext0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
         c->launches += 3;
     }
     prof_begin(c, CPM_K_COMBINE);
-    k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, stats, c->sx, n,
-                                                                          m, c->g, b_out);
+    k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
+                                                                          stats, c->sx, n, m, c->g, b_out);
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;

@@ -93,6 +93,9 @@ struct cpm_ctx {
     double* sx = nullptr;        // [4 * n]: x | y | z | eta
     double* sxyz = nullptr;      // [n * 3] row-major copy of the site coordinates
     int* group = nullptr;
+    int* zmap = nullptr;         // [n] index of each site's height in zuniq
+    double* zuniq = nullptr;     // distinct site heights (exact values)
+    int nzu = 0;
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
     cpm::KTable kt;
     cpm::Phases<double> site64;
@@ -123,6 +126,9 @@ struct cpm_ctx {
     size_t dstage_bytes = 0;
     void* ubuf = nullptr;        // cpm_update scratch (split partial sums, b hi/lo)
     size_t ubuf_bytes = 0;
+    void* Sb = nullptr;          // S as three bf16 planes [3][n][ld] for the tensor-core update
+    void* tbuf = nullptr;        // tensor-core update scratch (K-split partials, b planes)
+    size_t tbuf_bytes = 0;
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 
@@ -188,5 +194,8 @@ cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* 
 
 // update.cu
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot);
+
+// tc_gemm.cu
+cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);
 
 }  // namespace cpm

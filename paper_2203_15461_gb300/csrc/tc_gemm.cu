@@ -1,0 +1,382 @@
+// Batched charge update on the 5th-generation tensor cores:
+//
+//   D[i][r] = sum_j S[i][j] b[r][j]       (q_r = S G psi_r - D[:, r], Eq. electrode-wise, Sec. II.B)
+//
+// for m replicas sharing one capacitance matrix S.  Both operands are split into three bf16
+// terms, S = S0 + S1 + S2 and b = B0 + B1 + B2 (24 significant bits each), and the six
+// products of combined order <= 2 (S0B0, S0B1, S1B0, S0B2, S1B1, S2B0) are accumulated in
+// FP32 in tensor memory, which keeps the single-precision accuracy of S.
+//
+// One CTA computes a 128-row x BN-replica tile over one K range: TMA loads the six operand
+// tiles of a 64-wide K step into 128-byte-swizzled shared memory, one thread issues the
+// tcgen05.mma instructions, the accumulator lives in TMEM and four warps read it back with
+// tcgen05.ld.  Partial sums of the K ranges are added in FP64 by the reduction kernel.
+// Every mbarrier wait is bounded: on expiry the CTA records a timeout in the status word,
+// lets its copies in flight land, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace cpm {
+
+constexpr int TC_BM = 128;          // rows of S per CTA (MMA M)
+constexpr int TC_BK = 64;           // K elements per stage (128 bytes of bf16 per row)
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false when the limit expired or another role raised the abort flag
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: bf16 x bf16 -> f32, both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int BN> struct TcCfg {
+    static constexpr int A_BYTES = TC_BM * 128;            // one bf16 split of the S tile
+    static constexpr int B_BYTES = BN * 128;               // one bf16 split of the b tile
+    static constexpr int STAGE = 3 * A_BYTES + 3 * B_BYTES;
+    static constexpr int STAGES = (220 * 1024) / STAGE >= 4 ? 4 : (220 * 1024) / STAGE;
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
+};
+
+struct TcMaps {
+    CUtensorMap a[3];
+    CUtensorMap b[3];
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__ TcMaps maps, int n, int m,
+                                                         int kchunk, float* __restrict__ part,
+                                                         unsigned* __restrict__ status) {
+    typedef TcCfg<BN> C;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* done = empty + C::STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * TC_BM, r0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * kchunk;
+    const int nsteps = kchunk / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: six TMA tiles per K step
+        int issued = 0, waited_free = 0;
+        for (int t = 0; t < nsteps; ++t) {
+            const int s = t % C::STAGES;
+            if (t >= C::STAGES) {
+                if (!mbar_wait(&empty[s], ((t / C::STAGES) - 1) & 1, abort)) break;
+                ++waited_free;
+            }
+            uint8_t* st = smem + s * C::STAGE;
+            mbar_expect_tx(&full[s], C::STAGE);
+            const int kx = kb + t * TC_BK;
+            for (int q = 0; q < 3; ++q) tma_load_2d(st + q * C::A_BYTES, &maps.a[q], kx, i0, &full[s]);
+            for (int q = 0; q < 3; ++q) tma_load_2d(st + 3 * C::A_BYTES + q * C::B_BYTES, &maps.b[q], kx, r0, &full[s]);
+            ++issued;
+        }
+        if (*abort) {
+            // let the copies already issued land before the CTA exits (bounded)
+            for (int t = 0; t < issued; ++t) {
+                const int s = t % C::STAGES;
+                for (uint32_t it = 0; it < TC_WAIT_LIMIT && !mbar_try(&full[s], (t / C::STAGES) & 1); ++it) {}
+            }
+        }
+        (void)waited_free;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16(TC_BM, BN);
+        const int pa[6] = {0, 0, 1, 0, 1, 2};
+        const int pb[6] = {0, 1, 0, 2, 1, 0};
+        bool ok = true;
+        for (int t = 0; t < nsteps; ++t) {
+            const int s = t % C::STAGES;
+            if (!mbar_wait(&full[s], (t / C::STAGES) & 1, abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = su32(smem + s * C::STAGE);
+            const uint32_t sb = sa + 3 * C::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint64_t ad = sdesc_sw128(sa + pa[p] * C::A_BYTES + kk * 32);
+                    const uint64_t bd = sdesc_sw128(sb + pb[p] * C::B_BYTES + kk * 32);
+                    umma_bf16(tmem, ad, bd, idesc, (t > 0 || kk > 0 || p > 0) ? 1u : 0u);
+                }
+            }
+            umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(done);
+    }
+    // epilogue: every thread owns one row of the 128-row tile
+    __syncwarp();
+    const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0, abort) ? 1 : 0) != 0;
+    tc_fence_after();
+    if (have) {
+        const int i = i0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(trow + c0, v);
+            if (i < n) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int r = r0 + c0 + k;
+                    if (r < m) part[((int64_t)blockIdx.z * m + r) * n + i] = v[k];
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(status, ST_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ----------------------------------------------------------------------------- operand splits
+// x = x0 + x1 + x2 with bf16 terms: x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)
+__global__ void k_split3(const double* __restrict__ x, int64_t rows, int64_t cols, int64_t ld,
+                         __nv_bfloat16* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * ld) return;
+    const int64_t r = t / ld, c = t % ld;
+    double v = c < cols ? x[r * cols + c] : 0.0;
+    __nv_bfloat16 h0 = __double2bfloat16(v);
+    double r1 = v - (double)__bfloat162float(h0);
+    __nv_bfloat16 h1 = __double2bfloat16(r1);
+    double r2 = r1 - (double)__bfloat162float(h1);
+    __nv_bfloat16 h2 = __double2bfloat16(r2);
+    const int64_t plane = rows * ld;
+    out[t] = h0;
+    out[plane + t] = h1;
+    out[2 * plane + t] = h2;
+}
+
+// ----------------------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// bf16 matrix [rows x ld] (ld a multiple of 64), box {64, box_rows}, 128-byte swizzle
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld, int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int64_t tc_ld(int64_t n) { return ((n + TC_BK - 1) / TC_BK) * TC_BK; }
+
+// S (FP64, n x n) -> three bf16 planes [3][n][ld] in c->Sb
+cpm_status tc_prepare_s(cpm_ctx* c) {
+    const int64_t n = c->n, ld = tc_ld(n);
+    dev_free(c, c->Sb);
+    c->Sb = nullptr;
+    CPM_TRY(dev_alloc(c, (void**)&c->Sb, sizeof(__nv_bfloat16) * 3 * n * ld));
+    k_split3<<<(unsigned)((n * ld + 255) / 256), 256, 0, c->stream>>>(c->S, n, n, ld, (__nv_bfloat16*)c->Sb);
+    CPM_LAUNCH(c, "k_split3(S)");
+    return CPM_OK;
+}
+
+template <int BN>
+static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_t ld, float* part, int* splits_out) {
+    typedef TcCfg<BN> C;
+    const int mt = (n + TC_BM - 1) / TC_BM, nt = (m + BN - 1) / BN;
+    const int ksteps = (int)(ld / TC_BK);
+    int splits = std::max(1, std::min(ksteps, (2 * 152 + mt * nt - 1) / (mt * nt)));
+    const int kchunk_steps = (ksteps + splits - 1) / splits;
+    splits = (ksteps + kchunk_steps - 1) / kchunk_steps;
+    CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sb<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    k_tc_sb<BN><<<dim3(mt, nt, splits), TC_THREADS, C::SMEM, c->stream>>>(maps, n, m, kchunk_steps * TC_BK, part,
+                                                                          c->status);
+    CPM_LAUNCH(c, "k_tc_sb");
+    *splits_out = splits;
+    return CPM_OK;
+}
+
+// part[split][r][i] = sum over the split's K range of S[i][j] b[r][j]; returns the split count
+cpm_status tc_sb(cpm_ctx* c, int m, const double* b, float* part, int* splits, void* bsplit) {
+    const int64_t n = c->n, ld = tc_ld(n);
+    k_split3<<<(unsigned)((m * ld + 255) / 256), 256, 0, c->stream>>>(b, m, n, ld, (__nv_bfloat16*)bsplit);
+    CPM_LAUNCH(c, "k_split3(b)");
+    const int BN = m <= 32 ? 32 : (m <= 64 ? 64 : 128);
+    TcMaps maps;
+    const __nv_bfloat16* Sb = (const __nv_bfloat16*)c->Sb;
+    const __nv_bfloat16* Bb = (const __nv_bfloat16*)bsplit;
+    for (int q = 0; q < 3; ++q) {
+        if (!make_map(&maps.a[q], Sb + (size_t)q * n * ld, n, ld, TC_BM) ||
+            !make_map(&maps.b[q], Bb + (size_t)q * m * ld, m, ld, BN))
+            return set_err(c, CPM_E_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+    if (BN == 32) return launch_tc<32>(c, maps, (int)n, m, ld, part, splits);
+    if (BN == 64) return launch_tc<64>(c, maps, (int)n, m, ld, part, splits);
+    return launch_tc<128>(c, maps, (int)n, m, ld, part, splits);
+}
+
+size_t tc_part_bytes(int64_t n, int m);
+size_t tc_bsplit_bytes(int64_t n, int m);
+
+// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
+__global__ void k_tc_reduce(const float* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
+                            const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * n) return;
+    const int r = (int)(t / n);
+    const int64_t i = t % n;
+    double v = 0.0;
+    for (int sp = 0; sp < splits; ++sp) v += (double)part[((int64_t)sp * m + r) * n + i];
+    double sv = 0.0;
+    for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
+    q[t] = sv - v;
+}
+
+cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q) {
+    const int64_t n = c->n;
+    if (!c->Sb) CPM_TRY(tc_prepare_s(c));
+    const size_t pb = (tc_part_bytes(n, m) + 255) & ~(size_t)255;
+    const size_t need = pb + tc_bsplit_bytes(n, m);
+    if (c->tbuf_bytes < need) {
+        dev_free(c, c->tbuf);
+        c->tbuf = nullptr;
+        c->tbuf_bytes = 0;
+        CPM_TRY(dev_alloc(c, &c->tbuf, need));
+        c->tbuf_bytes = need;
+    }
+    float* part = (float*)c->tbuf;
+    void* bsplit = (char*)c->tbuf + pb;
+    int splits = 0;
+    CPM_TRY(tc_sb(c, m, b, part, &splits, bsplit));
+    k_tc_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, c->stream>>>(part, splits, c->SG, c->ng, psi, n, m, q);
+    CPM_LAUNCH(c, "k_tc_reduce");
+    c->launches += 3;
+    return CPM_OK;
+}
+
+size_t tc_part_bytes(int64_t n, int m) {
+    const int64_t ksteps = tc_ld(n) / TC_BK;
+    return sizeof(float) * (size_t)std::min<int64_t>(ksteps, 2 * 152) * m * n;
+}
+size_t tc_bsplit_bytes(int64_t n, int m) { return sizeof(__nv_bfloat16) * 3 * (size_t)m * tc_ld(n); }
+
+}  // namespace cpm

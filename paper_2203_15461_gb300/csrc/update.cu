@@ -150,6 +150,17 @@ __global__ void k_neutral(double* q, const double* u, int64_t n, int symm, doubl
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot) {
     const int64_t n = c->n;
     cudaStream_t st = c->stream;
+    if (c->p.s_prec == CPM_PREC_BF16X3) {
+        prof_begin(c, CPM_K_GEMV);
+        CPM_TRY(tc_update(c, m, psi, b, q));
+        prof_end(c, CPM_K_GEMV);
+        c->launches += 1;
+        prof_begin(c, CPM_K_NEUTRAL);
+        k_neutral<<<m, 1024, 0, st>>>(q, c->u, n, c->p.symm, qtot);
+        prof_end(c, CPM_K_NEUTRAL);
+        CPM_LAUNCH(c, "k_neutral");
+        return CPM_OK;
+    }
     const bool f32 = c->p.s_prec == CPM_PREC_FP32;
     const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
     const int rchunks = (m + GT_MR - 1) / GT_MR;
