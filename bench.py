@@ -181,6 +181,74 @@ def cpu_baseline(el, ely, psi, frac=8):
             "sample_seconds": t5 - t0}
 
 
+def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256):
+    """256 replicas of the 216-site Au(111) capacitor per step (one shared S), graph-captured."""
+    el, _, psi = s.workload_tiny_slab(seed=1)
+    xyz, Q, ne = make_trajectories(el, lambda sd: s.ions_in_gap(el, 100, seed=sd), m, K + W, 5000)
+    out = {"workload": "au111_tiny_216 x 256 replicas", "replicas_per_step": m}
+    for s_prec in ("fp32", "bf16x3"):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = CPM.for_electrodes(el, s_prec=s_prec, k_prec="fp32", stream=st).setup(el)
+            dx = torch.as_tensor(xyz[0], device="cuda").clone()
+            dQ = torch.as_tensor(Q, device="cuda")
+            dp = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
+            b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+            q = torch.empty_like(b)
+            qt = torch.empty(m, dtype=torch.float64, device="cuda")
+            xs = torch.as_tensor(xyz, device="cuda")
+        st.synchronize()
+        tot = 0.0
+        for t in range(W + K):
+            with torch.cuda.stream(st):
+                flush.zero_()
+                dx.copy_(xs[t])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ctx.cpm_step_graph(m, ne, dx, dQ, dp, b, q, qt)
+                e1.record(st)
+            st.synchronize()
+            if t >= W:
+                tot += e0.elapsed_time(e1)
+        out[f"value_{s_prec}_S"] = m * K / (tot / 1e3)
+        out[f"ms_per_step_{s_prec}_S"] = tot / K
+        out[f"max_abs_qtot_{s_prec}_S"] = float(qt.abs().max())
+        ctx.close()
+    out["unit"] = "updates/s"
+    return out
+
+
+def bench_serving(torch, s, n_req=600, rate=4000.0):
+    """Poisson stream of charge-update requests over three slab geometries (216, 512 and 2,048 sites)."""
+    from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
+    geoms = {"au111_216": s.workload_tiny_slab(seed=1)[0], "graphene_512": s.workload_serving_geometry(512)[0],
+             "graphene_2048": s.workload_serving_geometry(2048)[0]}
+    be = GpuBackend(s_prec="fp32", k_prec="fp32", max_batch=16)
+    sch = Scheduler(be, hbm_budget=4 << 30, max_batch=16)
+    for k, el in geoms.items():
+        sch.add_geometry(k, el, context_bytes(el.n, 2 * el.n, 16))
+    rng = np.random.default_rng(11)
+    pools = {k: [s.workload_serving_geometry(el.n, seed=40 + j)[1] if k != "au111_216" else
+                 s.ions_in_gap(el, 100, seed=40 + j) for j in range(8)] for k, el in geoms.items()}
+    keys = list(geoms)
+    reqs = []
+    for i in range(n_req):
+        k = keys[int(rng.integers(len(keys)))]
+        e = pools[k][int(rng.integers(8))]
+        reqs.append(Request(rid=i, key=k, xyz=e.xyz + rng.normal(scale=0.05, size=e.xyz.shape), Q=e.Q,
+                            psi=np.array([0.0, rng.uniform(0.0, 2.0)])))
+    # warm the three contexts outside the measured stream
+    warm = [Request(rid=-1 - j, key=k, xyz=pools[k][0].xyz, Q=pools[k][0].Q, psi=np.zeros(2)) for j, k in enumerate(keys)]
+    run_stream(warm, sch, arrivals=np.zeros(len(warm)))
+    sch.finished.clear()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    wall = run_stream(reqs, sch, arrivals=arrivals)
+    st = latency_stats(sch.finished)
+    st.update({"requests": n_req, "offered_rate_per_s": rate, "updates_per_s": n_req / wall,
+               "geometries": {k: el.n for k, el in geoms.items()}, "max_batch": 16, "path": "mixed"})
+    return st
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle on the host cores, same workload, sampled per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -298,6 +366,11 @@ def main():
            "h2d_bytes_per_step": int(8 * (m * ne * 4 + m * el.n_groups)),
            "d2h_bytes_per_step": int(8 * (m * el.n + m))}
 
+    # batched replicas of the tiny capacitor: 256 electrolytes sharing one S, one CUDA graph per step
+    batched = bench_batched_tiny(torch, CPM, s, flush, K, W)
+    # serving stream: Poisson arrivals over three geometries, continuous batching
+    serving = bench_serving(torch, s)
+
     # roofline of the dominant kernel
     peaks, src = _peaks()
     work = kernel_work(mixed, el, nk, ne, m)
@@ -327,7 +400,8 @@ def main():
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
             "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value, "sequential_mixed_value": seq_value,
             "rel_err_mixed_vs_fp64": err_mixed, "max_abs_qtot": qtot_max, "setup_seconds": t_setup,
-            "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items()}}
+            "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items()},
+            "batched_tiny_256": batched, "serving": serving}
     clocks = clk.summary()
     line["clocks"] = clocks
     if rank == 0 and not args.no_cpu_baseline:

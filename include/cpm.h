@@ -155,6 +155,17 @@ cpm_status cpm_update(cpm_ctx* ctx, int32_t m, const double* psi, const double* 
 cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
                          const double* psi, double* q_out, double* qtot_out);
 
+/*
+ * cpm_bvec followed by cpm_update as one CUDA graph (device buffers as in those calls;
+ * b_out receives b).  The first call for given (m, n_e, buffer addresses) reserves the
+ * scratch, captures the launches on the context stream and instantiates the graph; later
+ * calls with the same arguments replay it with one launch.  Different arguments re-capture
+ * (one graph per context).  Needs a context created on a non-default stream.
+ * Errors: as cpm_bvec / cpm_update; CPM_E_ARG for the default stream.
+ */
+cpm_status cpm_step_graph(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
+                          const double* psi, double* b_out, double* q_out, double* qtot_out);
+
 /* Wait for all work of the context and report any deferred kernel error. */
 cpm_status cpm_sync(cpm_ctx* ctx);
 

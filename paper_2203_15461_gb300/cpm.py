@@ -48,6 +48,7 @@ _SIGS = {
     "cpm_bvec": ([_P, _I32, _I64, _P, _P, _P], _I32),
     "cpm_update": ([_P, _I32, _P, _P, _P, _P], _I32),
     "cpm_step_host": ([_P, _I32, _I64, _P, _P, _P, _P, _P], _I32),
+    "cpm_step_graph": ([_P, _I32, _I64, _P, _P, _P, _P, _P, _P], _I32),
     "cpm_sync": ([_P], _I32),
     "cpm_last_error": ([_P], ctypes.c_char_p),
     "cpm_get_matrix": ([_P, _I32, _P], _I32),
@@ -184,6 +185,11 @@ class CPM:
         self._check(self.lib.cpm_step_host(self.handle, int(m), int(n_e), hp(xyz) if n_e else None,
                                            hp(Q) if n_e else None, hp(psi), hp(q_out), hp(qtot_out)))
 
+    def cpm_step_graph(self, m: int, n_e: int, xyz, Q, psi, b_out, q_out, qtot_out=None):
+        self._check(self.lib.cpm_step_graph(self.handle, int(m), int(n_e), _ptr(xyz) if n_e else None,
+                                            _ptr(Q) if n_e else None, _ptr(psi), _ptr(b_out), _ptr(q_out),
+                                            _ptr(qtot_out) if qtot_out is not None else None))
+
     def cpm_sync(self):
         self._check(self.lib.cpm_sync(self.handle))
 
@@ -239,6 +245,7 @@ class CPM:
         xyz = torch.as_tensor(np.ascontiguousarray(el.xyz, dtype=np.float64), device=dev)
         eta = torch.as_tensor(np.ascontiguousarray(el.eta, dtype=np.float64), device=dev)
         grp = torch.as_tensor(np.ascontiguousarray(el.group, dtype=np.int32), device=dev)
+        torch.cuda.synchronize()
         self.cpm_assemble(xyz, eta, grp, el.n_groups)
         self.cpm_invert()
         return self

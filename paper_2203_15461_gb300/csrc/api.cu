@@ -84,6 +84,7 @@ void prof_end(cpm_ctx* c, int k) {
 
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes) {
     if (c->scratch_bytes >= bytes) return CPM_OK;
+    c->graph_valid = false;
     dev_free(c, c->scratch);
     c->scratch = nullptr;
     c->scratch_bytes = 0;
@@ -113,14 +114,23 @@ __global__ void k_soa(const double* xyz, const double* eta, const int32_t* grp, 
     group[i] = gg;
 }
 
+static void drop_graph(cpm_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_valid = false;
+}
+
 static void free_geometry(cpm_ctx* c) {
+    drop_graph(c);
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
-                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb};
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
-    c->Sb = nullptr;
+    c->Sb = nullptr; c->SZ = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -174,6 +184,7 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
 void cpm_destroy(cpm_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    drop_graph(c);
     for (size_t i = 0; i < c->owned.size(); i += 2) cudaFree(c->owned[i]);
     for (int k = 0; k < CPM_K_COUNT; ++k)
         for (auto& pr : c->prof_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -274,6 +285,7 @@ cpm_status cpm_invert(cpm_ctx* c) {
     c->inverted = false;
     dev_free(c, c->Sb);
     c->Sb = nullptr;
+    drop_graph(c);
     CPM_TRY(invert_and_project(c));
     c->inverted = true;
     return CPM_OK;
@@ -329,6 +341,45 @@ cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, 
     CPM_CUDA(c, cudaMemcpyAsync(q_out, dq, sizeof(double) * m * c->n, cudaMemcpyDeviceToHost, st));
     if (qtot_out) CPM_CUDA(c, cudaMemcpyAsync(qtot_out, dqt, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     CPM_CUDA(c, cudaStreamSynchronize(st));
+    return CPM_OK;
+}
+
+cpm_status cpm_step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q, const double* psi,
+                          double* b_out, double* q_out, double* qtot_out) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_step_graph before cpm_invert");
+    if (m < 1 || n_e < 0 || !psi || !b_out || !q_out || (n_e > 0 && (!xyz || !Q)))
+        return set_err(c, CPM_E_ARG, "cpm_step_graph: need m >= 1, n_e >= 0 and non-null buffers");
+    if (!c->stream) return set_err(c, CPM_E_ARG, "cpm_step_graph: needs a context created on a non-default stream");
+    const void* ptrs[7] = {xyz, Q, psi, b_out, q_out, qtot_out, nullptr};
+    CPM_TRY(reserve_bvec(c, m, n_e));
+    CPM_TRY(reserve_update(c, m));
+    bool same = c->graph_valid && c->graph_m == m && c->graph_ne == n_e;
+    for (int k = 0; k < 6 && same; ++k) same = c->graph_ptrs[k] == ptrs[k];
+    if (!same) {
+        drop_graph(c);
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        const int64_t l0 = c->launches;
+        CPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out);
+        cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out) : s1;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->prof_on = prof;
+        if (s2 != CPM_OK) { if (g) cudaGraphDestroy(g); return s2; }
+        if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
+        c->graph = g;
+        CPM_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+        c->graph_valid = true;
+        c->graph_m = m;
+        c->graph_ne = n_e;
+        for (int k = 0; k < 7; ++k) c->graph_ptrs[k] = ptrs[k];
+    }
+    CPM_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_launches;
     return CPM_OK;
 }
 
@@ -453,6 +504,7 @@ cpm_status cpm_load(cpm_ctx* c, const char* path) {
                                 c->stream));
     dev_free(c, c->Sb);
     c->Sb = nullptr;
+    drop_graph(c);
     k_tofloat<<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(c->S, c->S32, (int64_t)(n * n));
     CPM_LAUNCH(c, "k_tofloat");
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));

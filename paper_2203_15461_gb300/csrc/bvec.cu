@@ -136,20 +136,22 @@ __global__ void k_scatter(const int* key, const int* start, int* cursor, int64_t
     order[start[k] + atomicAdd(&cursor[k], 1)] = (int)p;
 }
 
-// One thread per cell: put the cell's charges in ascending input order (so that every sum
-// over a cell runs in the same order on every call), then gather their positions.
+// One warp per cell: every charge's rank in the cell is the number of the cell's charges with a
+// smaller input index, so the sorted order (and every sum over a cell) is the same on every
+// call, whatever order the atomic scatter produced.
 template <typename T>
-__global__ void k_cellsort(const int* start, int ncells_total, int* order, const typename V4<T>::t* wpos,
+__global__ void k_cellsort(const int* start, int ncells_total, const int* order, const typename V4<T>::t* wpos,
                            typename V4<T>::t* sorted) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= ncells_total) return;
     const int b = start[c], e = start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = order[i], j = i - 1;
-        while (j >= b && order[j] > v) { order[j + 1] = order[j]; --j; }
-        order[j + 1] = v;
+    for (int i = b + lane; i < e; i += 32) {
+        const int v = order[i];
+        int rank = 0;
+        for (int j = b; j < e; ++j) rank += order[j] < v ? 1 : 0;
+        sorted[b + rank] = wpos[v];
     }
-    for (int i = b; i < e; ++i) sorted[i] = wpos[order[i]];
 }
 
 template <typename T> __device__ __forceinline__ T erfc_t(T x);
@@ -626,7 +628,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     if (ptot > 0) {
         k_scatter<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, ptot, order);
         CPM_LAUNCH(c, "k_scatter");
-        k_cellsort<T><<<(nc + 127) / 128, 128, 0, st>>>(start, nc, order, wpos, sorted);
+        k_cellsort<T><<<(unsigned)(((int64_t)nc * 32 + 255) / 256), 256, 0, st>>>(start, nc, order, wpos, sorted);
         CPM_LAUNCH(c, "k_cellsort");
     }
     prof_end(c, CPM_K_CELLS);
@@ -685,6 +687,11 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;
+}
+
+cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
+    const bool f32 = c->p.k_prec == CPM_PREC_FP32;
+    return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }
 
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out) {

@@ -126,7 +126,18 @@ struct cpm_ctx {
     size_t dstage_bytes = 0;
     void* ubuf = nullptr;        // cpm_update scratch (split partial sums, b hi/lo)
     size_t ubuf_bytes = 0;
+    // cpm_step_graph: one captured bvec + update sequence
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+    int graph_m = 0;
+    int64_t graph_ne = 0;
+    const void* graph_ptrs[7] = {};
+    int64_t graph_launches = 0;
     void* Sb = nullptr;          // S as three bf16 planes [3][n][ld] for the tensor-core update
+    double* SZ = nullptr;        // [n][tc_ngrp] S times the centring-group indicators
+    int tc_ngrp = 0;
+    bool tc_use_z = false;
     void* tbuf = nullptr;        // tensor-core update scratch (K-split partials, b planes)
     size_t tbuf_bytes = 0;
 
@@ -191,11 +202,15 @@ cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, d
 
 // bvec.cu
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
+cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
 
 // update.cu
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot);
 
+cpm_status reserve_update(cpm_ctx* c, int m);
+
 // tc_gemm.cu
 cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);
+cpm_status tc_reserve(cpm_ctx* c, int m);
 
 }  // namespace cpm

@@ -238,13 +238,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
 }
 
 // ----------------------------------------------------------------------------- operand splits
-// x = x0 + x1 + x2 with bf16 terms: x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)
+// x = x0 + x1 + x2 with bf16 terms: x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).
+// With `gmean`, row r is first centred by its group means: x[r][c] - gmean[r][gid[c]].
 __global__ void k_split3(const double* __restrict__ x, int64_t rows, int64_t cols, int64_t ld,
-                         __nv_bfloat16* __restrict__ out) {
+                         __nv_bfloat16* __restrict__ out, const double* __restrict__ gmean = nullptr,
+                         const int* __restrict__ gid = nullptr, int ngrp = 0) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= rows * ld) return;
     const int64_t r = t / ld, c = t % ld;
     double v = c < cols ? x[r * cols + c] : 0.0;
+    if (gmean && c < cols) v -= gmean[r * ngrp + gid[c]];
     __nv_bfloat16 h0 = __double2bfloat16(v);
     double r1 = v - (double)__bfloat162float(h0);
     __nv_bfloat16 h1 = __double2bfloat16(r1);
@@ -316,9 +319,11 @@ static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_
 }
 
 // part[split][r][i] = sum over the split's K range of S[i][j] b[r][j]; returns the split count
-cpm_status tc_sb(cpm_ctx* c, int m, const double* b, float* part, int* splits, void* bsplit) {
+cpm_status tc_sb(cpm_ctx* c, int m, const double* b, float* part, int* splits, void* bsplit, const double* gmean,
+                 const int* gid, int ngrp) {
     const int64_t n = c->n, ld = tc_ld(n);
-    k_split3<<<(unsigned)((m * ld + 255) / 256), 256, 0, c->stream>>>(b, m, n, ld, (__nv_bfloat16*)bsplit);
+    k_split3<<<(unsigned)((m * ld + 255) / 256), 256, 0, c->stream>>>(b, m, n, ld, (__nv_bfloat16*)bsplit, gmean, gid,
+                                                                      ngrp);
     CPM_LAUNCH(c, "k_split3(b)");
     const int BN = m <= 32 ? 32 : (m <= 64 ? 64 : 128);
     TcMaps maps;
@@ -336,40 +341,103 @@ cpm_status tc_sb(cpm_ctx* c, int m, const double* b, float* part, int* splits, v
 
 size_t tc_part_bytes(int64_t n, int m);
 size_t tc_bsplit_bytes(int64_t n, int m);
+cpm_status tc_sb(cpm_ctx* c, int m, const double* b, float* part, int* splits, void* bsplit, const double* gmean,
+                 const int* gid, int ngrp);
 
-// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
+// Layer groups for centring: the distinct site heights when there are at most 64 of them
+// (layered electrodes), else the electrodes themselves.
+// SZ[i][g] = sum over sites j of group g of S[i][j] (FP64), one thread per (i, g).
+__global__ void k_sgroups(const double* __restrict__ S, const int* __restrict__ gid, int64_t n, int ngrp,
+                          double* __restrict__ SZ) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * ngrp) return;
+    const int64_t i = t / ngrp;
+    const int g = (int)(t % ngrp);
+    double a = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        if (gid[j] == g) a += S[i * n + j];
+    SZ[t] = a;
+}
+
+// gmean[r][g] = mean of b[r][i] over the sites of group g; one warp per (r, g), fixed order
+__global__ void k_gmeans(const double* __restrict__ b, const int* __restrict__ gid, int64_t n, int m, int ngrp,
+                         double* __restrict__ gmean) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)m * ngrp) return;
+    const int r = (int)(w / ngrp), g = (int)(w % ngrp);
+    double a = 0.0;
+    int cnt = 0;
+    for (int64_t i = lane; i < n; i += 32)
+        if (gid[i] == g) { a += b[(int64_t)r * n + i]; ++cnt; }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) gmean[w] = cnt ? a / cnt : 0.0;
+}
+
+// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_g' SZ[i][g'] gmean[r][g'] - sum_split part[split][r][i]
 __global__ void k_tc_reduce(const float* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
-                            const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
+                            const double* __restrict__ psi, const double* __restrict__ SZ,
+                            const double* __restrict__ gmean, int ngrp, int64_t n, int m, double* __restrict__ q) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
     const int64_t i = t % n;
     double v = 0.0;
     for (int sp = 0; sp < splits; ++sp) v += (double)part[((int64_t)sp * m + r) * n + i];
+    for (int g = 0; g < ngrp; ++g) v += SZ[i * ngrp + g] * gmean[(int64_t)r * ngrp + g];
     double sv = 0.0;
     for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
     q[t] = sv - v;
 }
 
-cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q) {
+cpm_status tc_reserve(cpm_ctx* c, int m) {
     const int64_t n = c->n;
-    if (!c->Sb) CPM_TRY(tc_prepare_s(c));
+    if (!c->Sb) {
+        c->graph_valid = false;
+        CPM_TRY(tc_prepare_s(c));
+        // centring groups and their responses S G_z
+        c->tc_use_z = c->nzu <= 64;
+        c->tc_ngrp = c->tc_use_z ? c->nzu : c->ng;
+        dev_free(c, c->SZ);
+        c->SZ = nullptr;
+        CPM_TRY(dev_alloc(c, (void**)&c->SZ, sizeof(double) * n * c->tc_ngrp));
+        const int* gid = c->tc_use_z ? c->zmap : c->group;
+        k_sgroups<<<(unsigned)((n * c->tc_ngrp + 255) / 256), 256, 0, c->stream>>>(c->S, gid, n, c->tc_ngrp, c->SZ);
+        CPM_LAUNCH(c, "k_sgroups");
+    }
     const size_t pb = (tc_part_bytes(n, m) + 255) & ~(size_t)255;
-    const size_t need = pb + tc_bsplit_bytes(n, m);
+    const size_t need = pb + tc_bsplit_bytes(n, m) + 256 + sizeof(double) * (size_t)m * c->tc_ngrp;
     if (c->tbuf_bytes < need) {
         dev_free(c, c->tbuf);
         c->tbuf = nullptr;
         c->tbuf_bytes = 0;
+        c->graph_valid = false;
         CPM_TRY(dev_alloc(c, &c->tbuf, need));
         c->tbuf_bytes = need;
     }
+    return CPM_OK;
+}
+
+cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q) {
+    const int64_t n = c->n;
+    CPM_TRY(tc_reserve(c, m));
+    const size_t pb = (tc_part_bytes(n, m) + 255) & ~(size_t)255;
     float* part = (float*)c->tbuf;
     void* bsplit = (char*)c->tbuf + pb;
+    double* gmean = (double*)((char*)bsplit + ((tc_bsplit_bytes(n, m) + 255) & ~(size_t)255));
+    const int* gid = c->tc_use_z ? c->zmap : c->group;
+    k_gmeans<<<(unsigned)(((int64_t)m * c->tc_ngrp * 32 + 255) / 256), 256, 0, c->stream>>>(b, gid, n, m, c->tc_ngrp,
+                                                                                              gmean);
+    CPM_LAUNCH(c, "k_gmeans");
     int splits = 0;
-    CPM_TRY(tc_sb(c, m, b, part, &splits, bsplit));
-    k_tc_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, c->stream>>>(part, splits, c->SG, c->ng, psi, n, m, q);
+    CPM_TRY(tc_sb(c, m, b, part, &splits, bsplit, gmean, gid, c->tc_ngrp));
+    k_tc_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, c->stream>>>(part, splits, c->SG, c->ng, psi, c->SZ, gmean,
+                                                                        c->tc_ngrp, n, m, q);
     CPM_LAUNCH(c, "k_tc_reduce");
-    c->launches += 3;
+    c->launches += 4;
     return CPM_OK;
 }
 

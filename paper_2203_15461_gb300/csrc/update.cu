@@ -147,6 +147,35 @@ __global__ void k_neutral(double* q, const double* u, int64_t n, int symm, doubl
     if (threadIdx.x == 0 && qtot) qtot[r] = sh[0] + shc[0];
 }
 
+// split count and row chunk of the centred product; grows the scratch when needed
+static cpm_status reserve_update_plan(cpm_ctx* c, int m, int64_t* splits_out, int64_t* jchunk_out) {
+    const int64_t n = c->n;
+    const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
+    const int rchunks = (m + GT_MR - 1) / GT_MR;
+    int64_t splits = (4 * 152 + colblocks * rchunks - 1) / (colblocks * rchunks);
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n + GT_JT - 1) / GT_JT));
+    const int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
+    splits = (n + jchunk - 1) / jchunk;
+    const size_t need = ((sizeof(double) * splits * m * n + 255) & ~(size_t)255) + sizeof(float2) * m * n;
+    if (c->ubuf_bytes < need) {
+        dev_free(c, c->ubuf);
+        c->ubuf = nullptr;
+        c->ubuf_bytes = 0;
+        c->graph_valid = false;
+        CPM_TRY(dev_alloc(c, &c->ubuf, need));
+        c->ubuf_bytes = need;
+    }
+    *splits_out = splits;
+    *jchunk_out = jchunk;
+    return CPM_OK;
+}
+
+cpm_status reserve_update(cpm_ctx* c, int m) {
+    if (c->p.s_prec == CPM_PREC_BF16X3) return tc_reserve(c, m);
+    int64_t s, j;
+    return reserve_update_plan(c, m, &s, &j);
+}
+
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot) {
     const int64_t n = c->n;
     cudaStream_t st = c->stream;
@@ -162,20 +191,10 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
         return CPM_OK;
     }
     const bool f32 = c->p.s_prec == CPM_PREC_FP32;
+    int64_t splits = 0, jchunk = 0;
+    CPM_TRY(reserve_update_plan(c, m, &splits, &jchunk));
     const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
     const int rchunks = (m + GT_MR - 1) / GT_MR;
-    int64_t splits = (4 * 152 + colblocks * rchunks - 1) / (colblocks * rchunks);
-    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n + GT_JT - 1) / GT_JT));
-    const int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
-    splits = (n + jchunk - 1) / jchunk;
-    const size_t need = ((sizeof(double) * splits * m * n + 255) & ~(size_t)255) + sizeof(float2) * m * n;
-    if (c->ubuf_bytes < need) {
-        dev_free(c, c->ubuf);
-        c->ubuf = nullptr;
-        c->ubuf_bytes = 0;
-        CPM_TRY(dev_alloc(c, &c->ubuf, need));
-        c->ubuf_bytes = need;
-    }
     double* part = (double*)c->ubuf;
     float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
     c->launches += f32 ? 4 : 3;

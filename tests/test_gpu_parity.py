@@ -237,3 +237,33 @@ def test_batched_replicas_of_the_tiny_capacitor(tiny):
             q_ref = o.charges(S, el, psi, o.bvec(el, elyts[r]))
             assert rel_l2(q[r], q_ref) <= tol
         assert np.abs(qt).max() <= 1e-12
+
+
+def test_step_graph_replays_the_same_launches(tiny):
+    """cpm_step_graph: one captured bvec + update graph, replayed for new inputs in the same buffers."""
+    el, ely, psi, _, S = tiny
+    st = torch.cuda.Stream()
+    ctx = make_ctx(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
+    m = 4
+    elyts = [s.ions_in_gap(el, 100, seed=700 + r) for r in range(2 * m)]
+    from gpu_util import stack_replicas
+    x1, Q1, ne = stack_replicas(elyts[:m])
+    x2, Q2, _ = stack_replicas(elyts[m:], n_e=ne)
+    dx, dQ = dev(x1), dev(Q1)
+    dpsi = dev(np.tile(psi, (m, 1)))
+    b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+    q = torch.empty_like(b)
+    qt = torch.empty(m, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(st):
+        ctx.cpm_step_graph(m, ne, dx, dQ, dpsi, b, q, qt)
+    st.synchronize()
+    first = q.cpu().numpy().copy()
+    with torch.cuda.stream(st):
+        dx.copy_(dev(x2)); dQ.copy_(dev(Q2))
+        ctx.cpm_step_graph(m, ne, dx, dQ, dpsi, b, q, qt)
+    st.synchronize()
+    second = q.cpu().numpy().copy()
+    ref = make_ctx(el, s_prec="fp32", k_prec="fp32").setup(el)
+    for got, batch in ((first, elyts[:m]), (second, elyts[m:])):
+        qr, _ = run_update(ref, psi, run_bvec(ref, batch))
+        assert np.array_equal(got, qr)
