@@ -126,11 +126,12 @@ static void free_geometry(cpm_ctx* c) {
     drop_graph(c);
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
-                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ};
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
+    c->rtab = nullptr; c->rtab_id = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -239,6 +240,18 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
         std::vector<int> zm(n);
         for (int64_t i = 0; i < n; ++i) zm[i] = (int)(std::lower_bound(zu.begin(), zu.end(), zs[i]) - zu.begin());
         c->nzu = (int)zu.size();
+        // distinct Gaussian widths: one real-space pair-function table each (at most 16)
+        std::vector<double> es(hx.begin() + 3 * n, hx.begin() + 4 * n);
+        std::vector<double> eu = es;
+        std::sort(eu.begin(), eu.end());
+        eu.erase(std::unique(eu.begin(), eu.end()), eu.end());
+        if (eu.size() <= 16) {
+            std::vector<int> em(n);
+            for (int64_t i = 0; i < n; ++i) em[i] = (int)(std::lower_bound(eu.begin(), eu.end(), es[i]) - eu.begin());
+            CPM_TRY(dev_alloc(c, (void**)&c->rtab_id, sizeof(int) * n));
+            CPM_CUDA(c, cudaMemcpyAsync(c->rtab_id, em.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+            CPM_TRY(build_pair_tables(c, eu));
+        }
         CPM_TRY(dev_alloc(c, (void**)&c->zmap, sizeof(int) * n));
         CPM_TRY(dev_alloc(c, (void**)&c->zuniq, sizeof(double) * zu.size()));
         CPM_CUDA(c, cudaMemcpyAsync(c->zmap, zm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));

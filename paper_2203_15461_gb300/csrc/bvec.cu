@@ -158,11 +158,45 @@ template <typename T> __device__ __forceinline__ T erfc_t(T x);
 template <> __device__ __forceinline__ float erfc_t<float>(float x) { return erfcf(x); }
 template <> __device__ __forceinline__ double erfc_t<double>(double x) { return erfc(x); }
 
-// Real-space part: one warp per (replica, site); lanes split the stencil cells.
+// Pair function f(r) = (erfc(alpha r) - erfc(eta r)) / r of a site's Gaussian width eta, tabulated
+// for the single-precision path: cubic Hermite pieces on RT_N equal intervals of [0, rcut], built
+// in FP64 from f and f' (f is even and smooth, f(0) = 2 (eta - alpha) / sqrt(pi)); the
+// interpolation error is below 1e-8 of f(0) for the widths and cut-offs used here.
+constexpr int RT_N = 1024;
+
+__device__ inline void pair_f_df(double r, double a, double e, double* f, double* df) {
+    if (r == 0.0) {
+        *f = 2.0 * (e - a) / sqrt(PI);
+        *df = 0.0;
+        return;
+    }
+    const double v = (erf(e * r) - erf(a * r)) / r;
+    *f = v;
+    *df = (2.0 / sqrt(PI)) * (e * exp(-e * e * r * r) - a * exp(-a * a * r * r)) / r - v / r;
+}
+
+__global__ void k_pair_tables(const double* __restrict__ etas, int ntab, double alpha, double rcut,
+                              float4* __restrict__ tab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntab * RT_N) return;
+    const int id = t / RT_N, k = t % RT_N;
+    const double h = rcut / RT_N, e = etas[id];
+    double f0, d0, f1, d1;
+    pair_f_df(k * h, alpha, e, &f0, &d0);
+    pair_f_df((k + 1) * h, alpha, e, &f1, &d1);
+    d0 *= h;
+    d1 *= h;
+    tab[t] = make_float4((float)f0, (float)d0, (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1), (float)(2.0 * (f0 - f1) + d0 + d1));
+}
+
+// Real-space part: one warp per (replica, site); lanes split the stencil cells, skipping cells whose
+// nearest point is beyond rcut.  Single precision reads the tabulated pair function when tables exist.
 template <typename T>
 __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, int64_t n, int m, Geometry g,
                                                 CellGrid cg, const int* __restrict__ start,
-                                                const typename V4<T>::t* __restrict__ sorted, double* out) {
+                                                const typename V4<T>::t* __restrict__ sorted,
+                                                const float4* __restrict__ tab, const int* __restrict__ tabid,
+                                                double* out) {
     int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= (int64_t)m * n) return;
@@ -181,12 +215,19 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     const T a = (T)g.alpha;
     const T rc2 = (T)(g.rcut * g.rcut);
     const T px = (T)sw[0], py = (T)sw[1], pz = (T)sw[2];
+    const float4* tb = (tab && tabid) ? tab + (int64_t)tabid[i] * RT_N : nullptr;
+    const float inv_h = (float)(RT_N / g.rcut);
     const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
     const int nst = wx * wy * wz;
     T acc = 0;
     for (int s = lane; s < nst; s += 32) {
         int dx = s % wx - cg.S[0], dy = (s / wx) % wy - cg.S[1], dz = s / (wx * wy) - cg.S[2];
         int ux = ci[0] + dx, uy = ci[1] + dy, uz = ci[2] + dz;
+        // distance from the site to the (unwrapped) cell box
+        const double gx = fmax(0.0, fmax(ux * cg.h[0] - sw[0], sw[0] - (ux + 1) * cg.h[0]));
+        const double gy = fmax(0.0, fmax(uy * cg.h[1] - sw[1], sw[1] - (uy + 1) * cg.h[1]));
+        const double gz = fmax(0.0, fmax(uz * cg.h[2] - sw[2], sw[2] - (uz + 1) * cg.h[2]));
+        if (gx * gx + gy * gy + gz * gz >= g.rcut * g.rcut) continue;
         int fx = floordiv(ux, cg.nc[0]), fy = floordiv(uy, cg.nc[1]), fz = floordiv(uz, cg.nc[2]);
         int cx = ux - fx * cg.nc[0], cy = uy - fy * cg.nc[1], cz = uz - fz * cg.nc[2];
         const T shx = (T)(fx * g.boxL[0]), shy = (T)(fy * g.boxL[1]), shz = (T)(fz * g.boxL[2]);
@@ -199,13 +240,37 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
             T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
             if (r2 < rc2) {
                 T rr = sqrt(r2);
-                acc += q.w * (erfc_t<T>(a * rr) - erfc_t<T>(ex * rr)) / rr;
+                if (std::is_same<T, float>::value && tb) {
+                    const float u = (float)rr * inv_h;
+                    const int k = min((int)u, RT_N - 1);
+                    const float t = u - (float)k;
+                    const float4 cf = tb[k];
+                    acc += q.w * (T)(cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
+                } else {
+                    acc += q.w * (erfc_t<T>(a * rr) - erfc_t<T>(ex * rr)) / rr;
+                }
             }
         }
     }
     double acc64 = (double)acc;
     for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_down_sync(0xffffffffu, acc64, o);
     if (lane == 0) out[(int64_t)r * n + i] = acc64;
+}
+
+cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
+    dev_free(c, c->rtab);
+    c->rtab = nullptr;
+    CPM_TRY(dev_alloc(c, (void**)&c->rtab, sizeof(float4) * RT_N * etas.size()));
+    double* de = nullptr;
+    CPM_TRY(dev_alloc(c, (void**)&de, sizeof(double) * etas.size()));
+    CPM_CUDA(c, cudaMemcpyAsync(de, etas.data(), sizeof(double) * etas.size(), cudaMemcpyHostToDevice, c->stream));
+    const int tot = (int)etas.size() * RT_N;
+    k_pair_tables<<<(tot + 127) / 128, 128, 0, c->stream>>>(de, (int)etas.size(), c->g.alpha, c->g.rcut,
+                                                             (float4*)c->rtab);
+    CPM_LAUNCH(c, "k_pair_tables");
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, de);
+    return CPM_OK;
 }
 
 // ----------------------------------------------------------------------------- reciprocal space
@@ -634,7 +699,8 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
     k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
-                                                                                sorted, real);
+                                                                                sorted, (const float4*)c->rtab,
+                                                                                c->rtab_id, real);
     prof_end(c, CPM_K_REAL);
     CPM_LAUNCH(c, "k_real_b");
     // reciprocal space

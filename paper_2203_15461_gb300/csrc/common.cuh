@@ -96,6 +96,8 @@ struct cpm_ctx {
     int* zmap = nullptr;         // [n] index of each site's height in zuniq
     double* zuniq = nullptr;     // distinct site heights (exact values)
     int nzu = 0;
+    void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
+    int* rtab_id = nullptr;      // [n] table of each site
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
     cpm::KTable kt;
     cpm::Phases<double> site64;
@@ -203,6 +205,7 @@ cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, d
 // bvec.cu
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
+cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
 
 // update.cu
 cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot);
