@@ -22,14 +22,7 @@ template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
 template <> struct V4<double> { using t = double4_32a; };
 
-struct CellGrid {
-    int nc[3];
-    int S[3];        // stencil half-widths (cells)
-    double h[3];     // cell edges
-    int ncells;
-};
-
-static CellGrid make_grid(const Geometry& g) {
+CellGrid make_grid(const Geometry& g) {
     CellGrid cg;
     for (int d = 0; d < 3; ++d) {
         int nc = (int)floor(g.boxL[d] / (0.5 * g.rcut));
@@ -217,6 +210,9 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     const T px = (T)sw[0], py = (T)sw[1], pz = (T)sw[2];
     const float4* tb = (tab && tabid) ? tab + (int64_t)tabid[i] * RT_N : nullptr;
     const float inv_h = (float)(RT_N / g.rcut);
+    const float hf[3] = {(float)cg.h[0], (float)cg.h[1], (float)cg.h[2]};
+    const float swf[3] = {(float)sw[0], (float)sw[1], (float)sw[2]};
+    const float rcf2 = (float)(g.rcut * g.rcut);
     const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
     const int nst = wx * wy * wz;
     T acc = 0;
@@ -224,10 +220,10 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
         int dx = s % wx - cg.S[0], dy = (s / wx) % wy - cg.S[1], dz = s / (wx * wy) - cg.S[2];
         int ux = ci[0] + dx, uy = ci[1] + dy, uz = ci[2] + dz;
         // distance from the site to the (unwrapped) cell box
-        const double gx = fmax(0.0, fmax(ux * cg.h[0] - sw[0], sw[0] - (ux + 1) * cg.h[0]));
-        const double gy = fmax(0.0, fmax(uy * cg.h[1] - sw[1], sw[1] - (uy + 1) * cg.h[1]));
-        const double gz = fmax(0.0, fmax(uz * cg.h[2] - sw[2], sw[2] - (uz + 1) * cg.h[2]));
-        if (gx * gx + gy * gy + gz * gz >= g.rcut * g.rcut) continue;
+        const float gx = fmaxf(0.f, fmaxf(ux * hf[0] - swf[0], swf[0] - (ux + 1) * hf[0]));
+        const float gy = fmaxf(0.f, fmaxf(uy * hf[1] - swf[1], swf[1] - (uy + 1) * hf[1]));
+        const float gz = fmaxf(0.f, fmaxf(uz * hf[2] - swf[2], swf[2] - (uz + 1) * hf[2]));
+        if (gx * gx + gy * gy + gz * gz >= rcf2 * 1.0001f) continue;
         int fx = floordiv(ux, cg.nc[0]), fy = floordiv(uy, cg.nc[1]), fz = floordiv(uz, cg.nc[2]);
         int cx = ux - fx * cg.nc[0], cy = uy - fy * cg.nc[1], cz = uz - fz * cg.nc[2];
         const T shx = (T)(fx * g.boxL[0]), shy = (T)(fy * g.boxL[1]), shz = (T)(fz * g.boxL[2]);
@@ -255,6 +251,74 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     double acc64 = (double)acc;
     for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_down_sync(0xffffffffu, acc64, o);
     if (lane == 0) out[(int64_t)r * n + i] = acc64;
+}
+
+// Real space, single precision, site tiles: the sites are pre-sorted by cell into chunks of
+// RS_TILE (one thread each); a block streams the charges of every cell in the chunk's stencil
+// box through shared memory, so each charge is read once per chunk instead of once per site.
+constexpr int RS_TILE = 128;
+
+__global__ void __launch_bounds__(RS_TILE) k_real_tiled(const float* __restrict__ s32, const int* __restrict__ perm,
+                                                        const int4* __restrict__ chunk_lo, const int4* __restrict__ chunk_hi,
+                                                        int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
+                                                        const float4* __restrict__ sorted, const float4* __restrict__ tab,
+                                                        const int* __restrict__ tabid, double* __restrict__ out) {
+    __shared__ float4 sh[RS_TILE];
+    const int ch = blockIdx.x, r = blockIdx.y;
+    const int64_t slot = (int64_t)ch * RS_TILE + threadIdx.x;
+    const int i = slot < n ? perm[slot] : -1;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    const float4* tb = tab;
+    if (i >= 0) {
+        px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
+        tb = tab + (int64_t)tabid[i] * RT_N;
+    }
+    const float rc2 = (float)(g.rcut * g.rcut);
+    const float inv_h = (float)(RT_N / g.rcut);
+    const int4 lo = chunk_lo[ch], hi = chunk_hi[ch];
+    float acc = 0.f;
+    for (int uz = lo.z - cg.S[2]; uz <= hi.z + cg.S[2]; ++uz) {
+        const int fz = floordiv(uz, cg.nc[2]);
+        const int cz = uz - fz * cg.nc[2];
+        const float shz = (float)(fz * g.boxL[2]);
+        for (int uy = lo.y - cg.S[1]; uy <= hi.y + cg.S[1]; ++uy) {
+            const int fy = floordiv(uy, cg.nc[1]);
+            const int cy = uy - fy * cg.nc[1];
+            const float shy = (float)(fy * g.boxL[1]);
+            for (int ux = lo.x - cg.S[0]; ux <= hi.x + cg.S[0]; ++ux) {
+                const int fx = floordiv(ux, cg.nc[0]);
+                const int cx = ux - fx * cg.nc[0];
+                const float shx = (float)(fx * g.boxL[0]);
+                const int cell = r * cg.ncells + (cz * cg.nc[1] + cy) * cg.nc[0] + cx;
+                const int b = start[cell], e = start[cell + 1];
+                for (int p0 = b; p0 < e; p0 += RS_TILE) {
+                    const int cnt = min(RS_TILE, e - p0);
+                    if ((int)threadIdx.x < cnt) {
+                        float4 q = sorted[p0 + threadIdx.x];
+                        q.x += shx; q.y += shy; q.z += shz;
+                        sh[threadIdx.x] = q;
+                    }
+                    __syncthreads();
+                    if (i >= 0) {
+                        for (int k = 0; k < cnt; ++k) {
+                            const float4 q = sh[k];
+                            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < rc2) {
+                                const float u = sqrtf(r2) * inv_h;
+                                const int kk = min((int)u, RT_N - 1);
+                                const float t = u - (float)kk;
+                                const float4 cf = tb[kk];
+                                acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+    }
+    if (i >= 0) out[(int64_t)r * n + i] = (double)acc;
 }
 
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
@@ -356,6 +420,92 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int z = z0 + tx + 16 * q;
+            if (z >= 0 && z < nzw) outp[(int64_t)c * nzw + z] = acc[p][q];
+        }
+    }
+}
+
+// Single-precision structure factor with a 64-column x 128-harmonic accumulator tile per block:
+// warp w owns harmonics [16w, 16w + 16) of the tile's z range and skips the contraction when that
+// slab lies outside the largest |nz| of the tile's columns (columns are sorted by k_perp, so the
+// slab test removes most of the padding of the dense grid); the charge operand Q_j X_j Y_j of the
+// tile's columns is formed once per chunk of charges and shared by all 128 harmonics.
+constexpr int S2_BM = 64, S2_BZ = 128, S2_BK = 16;
+
+__global__ void __launch_bounds__(256, 2) k_sf32(const int2* __restrict__ cols, const int* __restrict__ colext,
+                                                 int ncols, int NY, int NZ, int nzw, const float2* __restrict__ EX,
+                                                 const float2* __restrict__ EY, const float2* __restrict__ EZ,
+                                                 const float* __restrict__ Qv, int64_t ptot, int64_t ne, int splits,
+                                                 int64_t chunk, int m, int nsup, float2* __restrict__ rho_part) {
+    __shared__ float2 Ps[S2_BK][S2_BM + 1];
+    __shared__ float2 Zs[S2_BK][S2_BZ + 1];
+    const int c0 = blockIdx.x * S2_BM;
+    const int zbase = NZ - S2_BZ / 2 - S2_BZ * (nsup / 2) + S2_BZ * (int)blockIdx.y;   // grid index of row 0
+    const int r = blockIdx.z / splits, s = blockIdx.z % splits;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cg = lane & 15, zh = lane >> 4;
+    float2* outp = rho_part + ((int64_t)s * m + r) * ncols * nzw;
+    const int mx = tile_maxext<float>(colext, c0, ncols);
+    // harmonics of this warp: zbase + 16 warp + zh + 2 q, q = 0..7  (nz = index - NZ)
+    const int wz0 = zbase + 16 * warp - NZ, wz1 = wz0 + 15;
+    const bool active = mx >= 0 && !(wz0 > mx || wz1 < -mx);
+    const bool block_any = mx >= 0 && !(zbase - NZ > mx || zbase + S2_BZ - 1 - NZ < -mx);
+    float2 acc[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
+    const int64_t jb = (int64_t)r * ne + (int64_t)s * chunk;
+    const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
+    if (block_any) {
+        for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
+            for (int e = threadIdx.x; e < S2_BK * S2_BM; e += 256) {
+                const int kk = e % S2_BK, mm = e / S2_BK;
+                const int64_t j = j0 + kk;
+                const int c = c0 + mm;
+                float2 v = make_float2(0.f, 0.f);
+                if (j < je && c < ncols) {
+                    const int2 cn = cols[c];
+                    const float2 xy = cmul(EX[(int64_t)cn.x * ptot + j], EY[(int64_t)(cn.y + NY) * ptot + j]);
+                    const float qj = Qv[j];
+                    v = make_float2(qj * xy.x, qj * xy.y);
+                }
+                Ps[kk][mm] = v;
+            }
+            for (int e = threadIdx.x; e < S2_BK * S2_BZ; e += 256) {
+                const int kk = e % S2_BK, zz = e / S2_BK;
+                const int64_t j = j0 + kk;
+                const int z = zbase + zz;
+                Zs[kk][zz] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll 2
+                for (int kk = 0; kk < S2_BK; ++kk) {
+                    float2 av[4], bv[8];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) av[p] = Ps[kk][cg + 16 * p];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) bv[q] = Zs[kk][16 * warp + zh + 2 * q];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
+                            acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
+                        }
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int c = c0 + cg + 16 * p;
+        if (c >= ncols) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int z = zbase + 16 * warp + zh + 2 * q;
             if (z >= 0 && z < nzw) outp[(int64_t)c * nzw + z] = acc[p][q];
         }
     }
@@ -607,9 +757,12 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
-    const int64_t base = (int64_t)p.ctiles * p.ztiles * m;
+    // the single-precision structure factor uses 128-harmonic super-tiles (k_sf32)
+    const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
+    const int yt = std::is_same<T, float>::value ? 2 * zh2 + 1 : p.ztiles;
+    const int64_t base = (int64_t)p.ctiles * yt * m;
     int64_t want = (4 * 152 + base - 1) / std::max<int64_t>(base, 1);
-    int64_t maxs = std::max<int64_t>(1, (ne + 255) / 256);
+    int64_t maxs = std::max<int64_t>(1, (ne + 127) / 128);
     p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(maxs, 64)));
     p.chunk = (ne + p.splits - 1) / p.splits;
     p.chunk = ((p.chunk + SF_BK - 1) / SF_BK) * SF_BK;
@@ -698,9 +851,16 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
-    k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
-                                                                                sorted, (const float4*)c->rtab,
-                                                                                c->rtab_id, real);
+    if (std::is_same<T, float>::value && c->rtab && c->sperm) {
+        k_real_tiled<<<dim3((unsigned)c->nschunk, m), RS_TILE, 0, st>>>(c->s32, c->sperm, (const int4*)c->schunk_lo,
+                                                                        (const int4*)c->schunk_hi, n, c->g, p.cg, start,
+                                                                        (const float4*)sorted, (const float4*)c->rtab,
+                                                                        c->rtab_id, real);
+    } else {
+        k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
+                                                                                    sorted, (const float4*)c->rtab,
+                                                                                    c->rtab_id, real);
+    }
     prof_end(c, CPM_K_REAL);
     CPM_LAUNCH(c, "k_real_b");
     // reciprocal space
@@ -709,9 +869,18 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         CPM_TRY(launch_phases<T>(st, c->g, k, xyz, ptot, EX, EY, EZ));
         prof_end(c, CPM_K_PHASES);
         prof_begin(c, CPM_K_SF);
-        dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
-        k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne, p.splits,
-                                     p.chunk, m, rp);
+        if (std::is_same<T, float>::value) {
+            const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
+            const int nsup = 2 * zh2 + 1;
+            dim3 gsf(p.ctiles, nsup, m * p.splits);
+            k_sf32<<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)EX,
+                                        (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne, p.splits,
+                                        p.chunk, m, nsup, (float2*)rp);
+        } else {
+            dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
+            k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne,
+                                         p.splits, p.chunk, m, rp);
+        }
         prof_end(c, CPM_K_SF);
         CPM_LAUNCH(c, "k_sf");
         prof_begin(c, CPM_K_SFRED);

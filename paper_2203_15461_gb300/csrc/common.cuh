@@ -67,6 +67,13 @@ template <typename T> struct Phases {
     int64_t P = 0;       // points per set (ld of the tables)
 };
 
+struct CellGrid {
+    int nc[3];
+    int S[3];        // stencil half-widths (cells)
+    double h[3];     // cell edges
+    int ncells;
+};
+
 struct Geometry {
     double boxL[3];
     double inv[3];       // 1 / L
@@ -96,6 +103,10 @@ struct cpm_ctx {
     int* zmap = nullptr;         // [n] index of each site's height in zuniq
     double* zuniq = nullptr;     // distinct site heights (exact values)
     int nzu = 0;
+    int* sperm = nullptr;        // sites sorted by real-space cell (chunks of 128)
+    void* schunk_lo = nullptr;   // int4 per chunk: lowest cell coordinates of its sites
+    void* schunk_hi = nullptr;   // int4 per chunk: highest cell coordinates
+    int nschunk = 0;
     void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
     int* rtab_id = nullptr;      // [n] table of each site
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
@@ -203,6 +214,8 @@ cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, d
                         int tri, const unsigned* status);
 
 // bvec.cu
+struct Geometry;
+CellGrid make_grid(const Geometry& g);
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
