@@ -186,6 +186,17 @@ cpm_status cpm_get_matrix(cpm_ctx* ctx, int32_t which, double* out);
 cpm_status cpm_capacitance(cpm_ctx* ctx, double* C_out);
 
 /*
+ * The same C~ without the inverse (after cpm_assemble only): solves A X = [e, g_1 .. g_Ng] with
+ * an FP32 Cholesky factor of A and FP64 iterative refinement (residuals against the FP64 A),
+ * then C~_gh = g_g^T A^-1 g_h - (g_g^T A^-1 e)(g_h^T A^-1 e) / (e^T A^-1 e) (symm = 1; the
+ * second term is dropped for symm = 0), as in Eq. (S) and Sec. II.C.  C_out: host,
+ * n_groups x n_groups; iters_out, resid_out (may be NULL): refinement sweeps and the final
+ * max-norm residual.  Allocates and frees its own work space (about 4 n^2 + 40 n (1 + N_g) bytes).
+ * Errors: CPM_E_STATE, CPM_E_NOT_SPD (FP32 factor failed), CPM_E_OOM, CPM_E_BUDGET.
+ */
+cpm_status cpm_capacitance_ir(cpm_ctx* ctx, double* C_out, int32_t* iters_out, double* resid_out);
+
+/*
  * Reciprocal vectors in use: writes at most `cap` integer triples (nx, ny, nz) of
  * the half-space set 0 < |k| <= kcut to host `nidx_out` and their count to
  * *nk (the full count even when it exceeds cap).  Valid after cpm_assemble.

@@ -54,6 +54,7 @@ _SIGS = {
     "cpm_get_matrix": ([_P, _I32, _P], _I32),
     "cpm_capacitance": ([_P, _P], _I32),
     "cpm_kvectors": ([_P, _P, _I64, ctypes.POINTER(_I64)], _I32),
+    "cpm_capacitance_ir": ([_P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_D)], _I32),
     "cpm_save": ([_P, ctypes.c_char_p], _I32),
     "cpm_load": ([_P, ctypes.c_char_p], _I32),
     "cpm_device_bytes": ([_P], ctypes.c_size_t),
@@ -204,6 +205,13 @@ class CPM:
         C = np.zeros((self.n_groups, self.n_groups))
         self._check(self.lib.cpm_capacitance(self.handle, C.ctypes.data))
         return C
+
+    def cpm_capacitance_ir(self):
+        """(C~, refinement sweeps, final residual) from the FP32 factor with FP64 refinement."""
+        C = np.zeros((self.n_groups, self.n_groups))
+        it, res = _I32(0), _D(0.0)
+        self._check(self.lib.cpm_capacitance_ir(self.handle, C.ctypes.data, ctypes.byref(it), ctypes.byref(res)))
+        return C, int(it.value), float(res.value)
 
     def cpm_kvectors(self) -> np.ndarray:
         nk = _I64(0)

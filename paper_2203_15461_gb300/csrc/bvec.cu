@@ -715,6 +715,85 @@ __global__ void k_col0_site(const double* __restrict__ zu, int nzu, int m, doubl
     b0[t] = acc;
 }
 
+// Single-precision site potential with a 64-column x 128-site tile per block (4 columns x 8 sites
+// per thread): warp w owns sites [16w, 16w + 16) of the tile; the contraction over nz runs only
+// over the tile's nz range; the epilogue weights each column by conj(X_i Y_i) and reduces the
+// 16 column groups of a half warp with shuffles.
+constexpr int T2_BC = 64, T2_BS = 128, T2_BK = 16;
+
+__global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols, const int* __restrict__ colext,
+                                                   int ncols, int NY, int NZ, int nzw, const float2* __restrict__ wrho,
+                                                   const float2* __restrict__ SX, const float2* __restrict__ SY,
+                                                   const float2* __restrict__ SZ, int64_t n, int nctiles,
+                                                   float* __restrict__ partial) {
+    __shared__ float2 As[T2_BK][T2_BC + 1];
+    __shared__ float2 Bs[T2_BK][T2_BS + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * T2_BS;
+    const int c0 = blockIdx.y * T2_BC;
+    const int r = blockIdx.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cg = lane & 15, sh = lane >> 4;
+    const float2* rho = wrho + (int64_t)r * ncols * nzw;
+    const int mx = tile_maxext<float>(colext, c0, ncols);
+    float2 acc[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
+    if (mx >= 0) {
+        const int zb = NZ - mx, ze = NZ + mx + 1;
+        for (int z0 = zb; z0 < ze; z0 += T2_BK) {
+            for (int e = threadIdx.x; e < T2_BK * T2_BC; e += 256) {
+                const int kk = e % T2_BK, cc = e / T2_BK;
+                const int z = z0 + kk, c = c0 + cc;
+                As[kk][cc] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : make_float2(0.f, 0.f);
+            }
+            for (int e = threadIdx.x; e < T2_BK * T2_BS; e += 256) {
+                const int ss = e % T2_BS, kk = e / T2_BS;
+                const int z = z0 + kk;
+                const int64_t i = i0 + ss;
+                Bs[kk][ss] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int kk = 0; kk < T2_BK; ++kk) {
+                float2 av[4], bv[8];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) av[p] = As[kk][cg + 16 * p];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) bv[q] = Bs[kk][16 * warp + sh + 2 * q];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {   // a * conj(b)
+                        acc[p][q].x += av[p].x * bv[q].x + av[p].y * bv[q].y;
+                        acc[p][q].y += av[p].y * bv[q].x - av[p].x * bv[q].y;
+                    }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t i = i0 + 16 * warp + sh + 2 * q;
+        float v = 0.f;
+        if (i < n) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int c = c0 + cg + 16 * p;
+                if (c < ncols) {
+                    const int2 cn = cols[c];
+                    const float2 xy = cmul(SX[(int64_t)cn.x * n + i], SY[(int64_t)(cn.y + NY) * n + i]);
+                    v += xy.x * acc[p][q].x + xy.y * acc[p][q].y;
+                }
+            }
+        }
+        // reduce over the 16 column groups of this half warp
+        for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (cg == 0 && i < n) partial[((int64_t)r * nctiles + blockIdx.y) * n + i] = v;
+    }
+}
+
 // b[r][i] = K_E (recip + real - pi Q_tot / (V alpha^2) + boundary)
 template <typename T>
 __global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const int* zmap,
@@ -743,7 +822,7 @@ struct BvecPlan {
     int splits, nctiles, ctiles, ztiles;
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
-        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, total;
+        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, total;
     int c0chunks;
 };
 
@@ -792,6 +871,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_c0part = o; o += al(sizeof(double2) * (size_t)m * p.c0chunks * nz0);
     p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
+    p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
     p.total = o;
     return p;
 }
@@ -827,7 +907,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     V4T* sorted = (V4T*)(scr + p.off_sorted);
     int* order = (int*)(scr + p.off_order);
     const int nc = m * p.cg.ncells;
-    c->launches += 4 + (ptot > 0 ? 3 : 0) + ((k.nk > 0 && ptot > 0) ? 4 : 0);
+    c->launches += 4 + (ptot > 0 ? 3 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
 
     prof_begin(c, CPM_K_STATS);
     k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats);
@@ -866,7 +946,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     // reciprocal space
     if (k.nk > 0 && ptot > 0) {
         prof_begin(c, CPM_K_PHASES);
-        CPM_TRY(launch_phases<T>(st, c->g, k, xyz, ptot, EX, EY, EZ));
+        CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ));
         prof_end(c, CPM_K_PHASES);
         prof_begin(c, CPM_K_SF);
         if (std::is_same<T, float>::value) {
@@ -891,9 +971,16 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         CPM_LAUNCH(c, "k_sf_reduce");
         prof_begin(c, CPM_K_SITE);
         const Phases<T>& sp = site_tables<T>(c);
-        dim3 gs((unsigned)((n + SF_BN - 1) / SF_BN), p.ctiles, m);
-        k_site<T><<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, wr, sp.X, sp.Y, sp.Z, n,
-                                      p.nctiles, part);
+        if (std::is_same<T, float>::value) {
+            dim3 gs((unsigned)((n + T2_BS - 1) / T2_BS), p.ctiles, m);
+            k_site32<<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)wr,
+                                         (const float2*)sp.X, (const float2*)sp.Y, (const float2*)sp.Z, n, p.nctiles,
+                                         (float*)part);
+        } else {
+            dim3 gs((unsigned)((n + SF_BN - 1) / SF_BN), p.ctiles, m);
+            k_site<T><<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, wr, sp.X, sp.Y, sp.Z, n,
+                                          p.nctiles, part);
+        }
         prof_end(c, CPM_K_SITE);
         CPM_LAUNCH(c, "k_site");
     } else {

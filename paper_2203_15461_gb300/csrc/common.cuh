@@ -200,6 +200,9 @@ template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
                          c2<T>* X, c2<T>* Y, c2<T>* Z);
 size_t phase_elems(const KTable& k, int64_t P);
+template <typename T>
+cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z);
 
 // api.cu
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes);

@@ -267,3 +267,15 @@ def test_step_graph_replays_the_same_launches(tiny):
     for got, batch in ((first, elyts[:m]), (second, elyts[m:])):
         qr, _ = run_update(ref, psi, run_bvec(ref, batch))
         assert np.array_equal(got, qr)
+
+
+@pytest.mark.parametrize("which", ["tiny", "coax"])
+def test_capacitance_by_fp32_factor_and_fp64_refinement(which):
+    """C~ from the FP32 Cholesky factor with FP64 iterative refinement equals C~ from the FP64 inverse."""
+    need_gpu()
+    el = s.au111_slab() if which == "tiny" else s.coaxial_tubes(2)
+    ctx = make_ctx(el).setup(el)
+    C64 = ctx.cpm_capacitance()
+    C, it, res = ctx.cpm_capacitance_ir()
+    assert it >= 1 and res < 1e-12
+    assert np.abs(C - C64).max() <= 1e-10 * np.abs(C64).max()
