@@ -166,6 +166,15 @@ cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz
 cpm_status cpm_step_graph(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
                           const double* psi, double* b_out, double* q_out, double* qtot_out);
 
+/*
+ * Failure-detection self test (no paper counterpart): launches the tensor-core kernel once with
+ * its copies switched off, so its first mbarrier wait can never complete and runs out after
+ * wait_ms milliseconds (0 < wait_ms <= 10000).  Returns CPM_E_TIMEOUT when the bounded wait,
+ * the device status word and the host report work; the context stays usable afterwards (its
+ * status word is cleared).  Needs cpm_invert.
+ */
+cpm_status cpm_selftest_timeout(cpm_ctx* ctx, double wait_ms);
+
 /* Wait for all work of the context and report any deferred kernel error. */
 cpm_status cpm_sync(cpm_ctx* ctx);
 

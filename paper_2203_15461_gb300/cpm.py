@@ -50,6 +50,7 @@ _SIGS = {
     "cpm_step_host": ([_P, _I32, _I64, _P, _P, _P, _P, _P], _I32),
     "cpm_step_graph": ([_P, _I32, _I64, _P, _P, _P, _P, _P, _P], _I32),
     "cpm_sync": ([_P], _I32),
+    "cpm_selftest_timeout": ([_P, _D], _I32),
     "cpm_last_error": ([_P], ctypes.c_char_p),
     "cpm_get_matrix": ([_P, _I32, _P], _I32),
     "cpm_capacitance": ([_P, _P], _I32),
@@ -190,6 +191,10 @@ class CPM:
         self._check(self.lib.cpm_step_graph(self.handle, int(m), int(n_e), _ptr(xyz) if n_e else None,
                                             _ptr(Q) if n_e else None, _ptr(psi), _ptr(b_out), _ptr(q_out),
                                             _ptr(qtot_out) if qtot_out is not None else None))
+
+    def cpm_selftest_timeout(self, wait_ms: float = 50.0) -> str:
+        """Run the bounded-wait self test; returns the status name (CPM_E_TIMEOUT when it works)."""
+        return STATUS[self.lib.cpm_selftest_timeout(self.handle, float(wait_ms))]
 
     def cpm_sync(self):
         self._check(self.lib.cpm_sync(self.handle))

@@ -437,6 +437,18 @@ cpm_status cpm_step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz,
     return CPM_OK;
 }
 
+cpm_status cpm_selftest_timeout(cpm_ctx* c, double wait_ms) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_selftest_timeout before cpm_invert");
+    if (!(wait_ms > 0.0) || wait_ms > 10000.0) return set_err(c, CPM_E_ARG, "wait_ms must be in (0, 10000]");
+    CPM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    CPM_TRY(tc_selftest_timeout(c, wait_ms));
+    cpm_status s = cpm_sync(c);
+    CPM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return s;
+}
+
 cpm_status cpm_sync(cpm_ctx* c) {
     if (!c) return CPM_E_ARG;
     unsigned hst = 0;

@@ -231,5 +231,6 @@ cpm_status reserve_update(cpm_ctx* c, int m);
 // tc_gemm.cu
 cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);
 cpm_status tc_reserve(cpm_ctx* c, int m);
+cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms);
 
 }  // namespace cpm

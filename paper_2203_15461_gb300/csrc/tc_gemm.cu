@@ -24,7 +24,13 @@ namespace cpm {
 constexpr int TC_BM = 128;          // rows of S per CTA (MMA M)
 constexpr int TC_BK = 64;           // K elements per stage (128 bytes of bf16 per row)
 constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bound on any single mbarrier wait: 2 s
+
+__device__ __forceinline__ uint64_t gtimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -45,11 +51,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false when the limit expired or another role raised the abort flag
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+// bounded wait (wall time, globaltimer); false when the limit expired or another role raised the abort flag
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
+    const uint64_t t0 = gtimer_ns();
+    while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
+        if (gtimer_ns() - t0 > limit_ns) break;
     }
     *abort = 1;
     return false;
@@ -123,9 +131,12 @@ struct TcMaps {
 };
 
 template <int BN>
+// skip_loads = 1 issues no TMA copies at all: every wait must then run out (the failure-detection
+// self test); it is never set on the compute path.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__ TcMaps maps, int n, int m,
                                                          int kchunk, float* __restrict__ part,
-                                                         unsigned* __restrict__ status) {
+                                                         unsigned* __restrict__ status, int skip_loads,
+                                                         uint64_t wait_ns) {
     typedef TcCfg<BN> C;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -163,8 +174,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
         int issued = 0, waited_free = 0;
         for (int t = 0; t < nsteps; ++t) {
             const int s = t % C::STAGES;
+            if (skip_loads) break;
             if (t >= C::STAGES) {
-                if (!mbar_wait(&empty[s], ((t / C::STAGES) - 1) & 1, abort)) break;
+                if (!mbar_wait(&empty[s], ((t / C::STAGES) - 1) & 1, abort, wait_ns)) break;
                 ++waited_free;
             }
             uint8_t* st = smem + s * C::STAGE;
@@ -178,7 +190,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
             // let the copies already issued land before the CTA exits (bounded)
             for (int t = 0; t < issued; ++t) {
                 const int s = t % C::STAGES;
-                for (uint32_t it = 0; it < TC_WAIT_LIMIT && !mbar_try(&full[s], (t / C::STAGES) & 1); ++it) {}
+                const uint64_t t0 = gtimer_ns();
+                while (!mbar_try(&full[s], (t / C::STAGES) & 1) && gtimer_ns() - t0 < wait_ns) {}
             }
         }
         (void)waited_free;
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
         bool ok = true;
         for (int t = 0; t < nsteps; ++t) {
             const int s = t % C::STAGES;
-            if (!mbar_wait(&full[s], (t / C::STAGES) & 1, abort)) { ok = false; break; }
+            if (!mbar_wait(&full[s], (t / C::STAGES) & 1, abort, wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sa = su32(smem + s * C::STAGE);
             const uint32_t sb = sa + 3 * C::A_BYTES;
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
     }
     // epilogue: every thread owns one row of the 128-row tile
     __syncwarp();
-    const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0, abort) ? 1 : 0) != 0;
+    const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0, abort, wait_ns) ? 1 : 0) != 0;
     tc_fence_after();
     if (have) {
         const int i = i0 + warp * 32 + lane;
@@ -303,7 +316,8 @@ cpm_status tc_prepare_s(cpm_ctx* c) {
 }
 
 template <int BN>
-static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_t ld, float* part, int* splits_out) {
+static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_t ld, float* part, int* splits_out,
+                           int skip_loads = 0, uint64_t wait_ns = TC_WAIT_NS) {
     typedef TcCfg<BN> C;
     const int mt = (n + TC_BM - 1) / TC_BM, nt = (m + BN - 1) / BN;
     const int ksteps = (int)(ld / TC_BK);
@@ -312,7 +326,7 @@ static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_
     splits = (ksteps + kchunk_steps - 1) / kchunk_steps;
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sb<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     k_tc_sb<BN><<<dim3(mt, nt, splits), TC_THREADS, C::SMEM, c->stream>>>(maps, n, m, kchunk_steps * TC_BK, part,
-                                                                          c->status);
+                                                                          c->status, skip_loads, wait_ns);
     CPM_LAUNCH(c, "k_tc_sb");
     *splits_out = splits;
     return CPM_OK;
@@ -439,6 +453,25 @@ cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, doub
     CPM_LAUNCH(c, "k_tc_reduce");
     c->launches += 4;
     return CPM_OK;
+}
+
+// Failure-detection self test: one tensor-core launch that issues no loads, so its first wait
+// runs out after wait_ms; the CTA must record ST_TIMEOUT, free its TMEM and return.
+cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms) {
+    const int m = 32;
+    CPM_TRY(tc_reserve(c, m));
+    const int64_t n = c->n, ld = tc_ld(n);
+    TcMaps maps;
+    const __nv_bfloat16* Sb = (const __nv_bfloat16*)c->Sb;
+    const size_t pb = (tc_part_bytes(n, m) + 255) & ~(size_t)255;
+    const __nv_bfloat16* Bb = (const __nv_bfloat16*)((char*)c->tbuf + pb);
+    for (int q = 0; q < 3; ++q) {
+        if (!make_map(&maps.a[q], Sb + (size_t)q * n * ld, n, ld, TC_BM) ||
+            !make_map(&maps.b[q], Bb + (size_t)q * m * ld, m, ld, 32))
+            return set_err(c, CPM_E_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+    int splits = 0;
+    return launch_tc<32>(c, maps, (int)n, m, ld, (float*)c->tbuf, &splits, 1, (uint64_t)(wait_ms * 1e6));
 }
 
 size_t tc_part_bytes(int64_t n, int m) {

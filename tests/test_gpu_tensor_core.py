@@ -38,3 +38,18 @@ def test_tc_update_matches_fp64_edl():
     errs = [rel_l2(qtc[r], q64[r]) for r in range(len(elyts))]
     assert max(errs) <= 1e-5, max(errs)
     assert np.abs(qt).max() <= 1e-12
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a wait that nothing completes runs out after 50 ms, the kernel
+    records a timeout, the host reads CPM_E_TIMEOUT, and the same context then computes correctly."""
+    need_gpu()
+    el, ely, psi = s.workload_tiny_slab(seed=3)
+    ctc = make_ctx(el, s_prec="bf16x3").setup(el)
+    assert ctc.cpm_selftest_timeout(50.0) == "CPM_E_TIMEOUT"
+    ctc.cpm_sync()
+    c64 = make_ctx(el).setup(el)
+    b = run_bvec(c64, [ely])
+    q64, _ = run_update(c64, psi, b)
+    qtc, _ = run_update(ctc, psi, b)
+    assert rel_l2(qtc[0], q64[0]) <= 1e-5
