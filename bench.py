@@ -92,6 +92,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed(rank: int) -> int:
+    """Electrolyte seeds of a rank's replicas: ranks work on disjoint, independent replicas."""
+    return 1000 * (rank + 1)
+
+
+def aggregate(ms_local: float, m: int, K: int, world: int, dist=None):
+    """Whole-job throughput: world x m x K updates over the slowest rank's time (max over ranks)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device="cuda" if dist and dist.get_backend() == "nccl" else "cpu")
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * m * K / (ms_max / 1e3), ms_max
+
+
 def make_trajectories(el, base_elyt_fn, m, steps, seed):
     """m replicas x steps configurations (random walk), replica-major per step: (steps, m*ne, 3), (m*ne,)."""
     from paper_2203_15461_gb300 import systems as s
@@ -303,7 +318,7 @@ def main():
 
     el, ely0, psi = s.workload_edl_capacitor(seed=1)
     m, K, W = args.replicas, args.steps, args.warmup
-    seed = 1000 * (rank + 1)
+    seed = rank_seed(rank)
     T = K + W
     xyz, Q, ne = make_trajectories(el, lambda sd: s.workload_edl_capacitor(seed=sd)[1], m, T, seed)
     xyz_dev = torch.as_tensor(xyz, device="cuda")
@@ -325,11 +340,7 @@ def main():
     with Clocks(local) as clk:
         ms, launches, prof, q_mix, _ = time_path(torch, mixed, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush,
                                                  profile=True)
-    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * m * K / (ms_max / 1e3)
+    value, ms_max = aggregate(ms, m, K, world, dist if world > 1 else None)
 
     # plain FP64, one replica per step (the 1x of the metric)
     K64 = max(3, min(K, 10))
