@@ -626,57 +626,104 @@ __device__ __forceinline__ double2 z_phase1(double z, double invLz) {
     return make_double2(cs, sn);
 }
 
+// Double-float arithmetic (pairs of floats, about 48 significant bits; Dekker 1971, Knuth TAOCP
+// vol. 2): the k_perp = 0 column needs better than FP32 accuracy, and FP32 pairs run far faster
+// than FP64 on this GPU.
+struct dfl { float hi, lo; };
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+    float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl df_fast(float a, float b) {
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = df_two_sum(a.hi, b.hi), t = df_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = df_fast(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_of(double x) {
+    float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+struct dcx { dfl re, im; };
+__device__ __forceinline__ dcx dcx_mul(dcx a, dcx b) {
+    return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+
+// e1[p] = exp(i 2 pi z_p / Lz) as a double-float pair, one FP64 sincospi per charge
+__global__ void k_col0_phase1(const double* __restrict__ xyz, int64_t ptot, double invLz, float4* __restrict__ e1) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ptot) return;
+    const double2 e = z_phase1(xyz[3 * p + 2], invLz);
+    const dfl re = df_of(e.x), im = df_of(e.y);
+    e1[p] = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // part[r][chunk][nz - 1] for nz in one block of 8 harmonics: each thread takes 8 charges of the
-// chunk (1,024 charges per block), starts the harmonic run from an exactly reduced phase and
-// steps it by an FP64 recurrence, then the block sums its threads in a fixed order.
+// chunk (1,024 charges per block), raises exp(i theta) to the block's first harmonic and steps
+// through the block by a double-float recurrence; the block sums its threads in a fixed order.
 constexpr int C0_THREADS = 128, C0_PER_THREAD = 8, C0_NB = 8;
 
-__global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const double* __restrict__ xyz, const double* __restrict__ Q,
-                                                       int64_t ne, double invLz, int nz0, double2* __restrict__ part) {
+__global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restrict__ e1s, const double* __restrict__ Q,
+                                                       int64_t ne, int nz0, double2* __restrict__ part) {
     __shared__ double2 red[C0_THREADS / 32][C0_NB];
     const int chunk = blockIdx.x, nb = blockIdx.y, r = blockIdx.z;
     const int nzs = nb * C0_NB + 1;   // first harmonic of this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double2 acc[C0_NB];
+    dcx acc[C0_NB];
 #pragma unroll
-    for (int k = 0; k < C0_NB; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < C0_NB; ++k) acc[k] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int t = 0; t < C0_PER_THREAD; ++t) {
         const int64_t j = (int64_t)chunk * C0_THREADS * C0_PER_THREAD + (int64_t)t * C0_THREADS + threadIdx.x;
         if (j >= ne) break;
         const int64_t p = (int64_t)r * ne + j;
-        const double q = Q[p];
-        if (q == 0.0) continue;
-        double s = xyz[3 * p + 2] * invLz;
-        s -= floor(s);
-        double tt = s * 18446744073709551616.0;
-        const uint64_t u = tt >= 18446744073709551616.0 ? 0ull : (uint64_t)tt;
-        double sn, cs;
-        sincospi((double)(int64_t)(u * (uint64_t)nzs) * 0x1p-63, &sn, &cs);
-        double2 e = make_double2(cs, sn);
-        sincospi((double)(int64_t)u * 0x1p-63, &sn, &cs);
-        const double2 e1 = make_double2(cs, sn);
+        const double qd = Q[p];
+        if (qd == 0.0) continue;
+        const dfl q = df_of(qd);
+        const float4 f = e1s[p];
+        const dcx e1 = {{f.x, f.y}, {f.z, f.w}};
+        // e = e1^nzs by binary powering
+        dcx e = {{1.f, 0.f}, {0.f, 0.f}}, base = e1;
+        for (int pw = nzs; pw > 0; pw >>= 1) {
+            if (pw & 1) e = dcx_mul(e, base);
+            base = dcx_mul(base, base);
+        }
 #pragma unroll
         for (int k = 0; k < C0_NB; ++k) {
-            acc[k].x += q * e.x;
-            acc[k].y += q * e.y;
-            e = cmul(e, e1);
+            acc[k].re = df_add(acc[k].re, df_mul(q, e.re));
+            acc[k].im = df_add(acc[k].im, df_mul(q, e.im));
+            e = dcx_mul(e, e1);
         }
     }
 #pragma unroll
     for (int k = 0; k < C0_NB; ++k) {
+        double re = (double)acc[k].re.hi + (double)acc[k].re.lo;
+        double im = (double)acc[k].im.hi + (double)acc[k].im.lo;
         for (int o = 16; o > 0; o >>= 1) {
-            acc[k].x += __shfl_down_sync(0xffffffffu, acc[k].x, o);
-            acc[k].y += __shfl_down_sync(0xffffffffu, acc[k].y, o);
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) red[warp][k] = acc[k];
+        if (lane == 0) red[warp][k] = make_double2(re, im);
     }
     __syncthreads();
     if (threadIdx.x < C0_NB) {
         const int k = threadIdx.x, nz = nzs + k;
         if (nz <= nz0) {
-            double2 t = red[0][k];
-            for (int w = 1; w < C0_THREADS / 32; ++w) { t.x += red[w][k].x; t.y += red[w][k].y; }
-            part[((int64_t)r * gridDim.x + chunk) * nz0 + nz - 1] = t;
+            double2 tt = red[0][k];
+            for (int w = 1; w < C0_THREADS / 32; ++w) { tt.x += red[w][k].x; tt.y += red[w][k].y; }
+            part[((int64_t)r * gridDim.x + chunk) * nz0 + nz - 1] = tt;
         }
     }
 }
@@ -822,7 +869,7 @@ struct BvecPlan {
     int splits, nctiles, ctiles, ztiles;
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
-        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, total;
+        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
     int c0chunks;
 };
 
@@ -872,6 +919,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
     p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
+    p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
     p.total = o;
     return p;
 }
@@ -994,14 +1042,17 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         b0 = (double*)(scr + p.off_b0);
         prof_begin(c, CPM_K_COL0);
         const int nblk = (k.ext0 + C0_NB - 1) / C0_NB;
-        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(xyz, Q, ne, c->g.inv[2], k.ext0, c0part);
+        float4* e1s = (float4*)(scr + p.off_c0e1);
+        k_col0_phase1<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, ptot, c->g.inv[2], e1s);
+        CPM_LAUNCH(c, "k_col0_phase1");
+        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, Q, ne, k.ext0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
         k_col0_reduce<<<(m * k.ext0 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
         CPM_LAUNCH(c, "k_col0_reduce");
         k_col0_site<<<(m * c->nzu + 127) / 128, 128, 0, st>>>(c->zuniq, c->nzu, m, c->g.inv[2], k.ext0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
-        c->launches += 3;
+        c->launches += 4;
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
