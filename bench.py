@@ -155,14 +155,32 @@ def time_path(torch, ctx, xyz_dev, Q_dev, psi_dev, m, ne, warmup, steps, flush, 
     return sum(ms), launches, prof, q, qt
 
 
-def kernel_work(ctx, el, nk, ne, m):
+def real_pairs(el, xyz_steps, Q, ne, m, step):
+    """(site, charge) pairs within rcut over the periodic images of the Ewald cell, summed over replicas."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(el.box, dtype=np.float64)
+    sites = np.mod(el.xyz, box)
+    tree = cKDTree(sites, boxsize=box)
+    tot = 0
+    for r in range(m):
+        x = xyz_steps[step, r * ne:(r + 1) * ne]
+        q = Q[r * ne:(r + 1) * ne]
+        x = np.mod(x[q != 0.0], box)
+        tot += int(tree.count_neighbors(cKDTree(x, boxsize=box), el.rcut))
+    return tot
+
+
+def kernel_work(ctx, el, nk, ne, m, pairs=None):
     """Algorithmic work per launch of the per-step kernels (flops or bytes), see the design doc."""
     n = el.n
-    return {
+    w = {
         "sf": ("flop", 8.0 * ne * nk * m),            # one complex multiply-add per (charge, k)
         "site": ("flop", 8.0 * n * nk * m),           # one complex multiply-add per (site, k)
-        "gemv": ("byte", 4.0 * n * n),               # S streamed once (FP32) per launch
+        "gemv": ("byte", 4.0 * n * n * ((m + 7) // 8)),   # S streamed once (FP32) per 8 replicas
     }
+    if pairs is not None:
+        w["real"] = ("flop", 16.0 * pairs)            # tabulated pair function per pair inside rcut
+    return w
 
 
 def cpu_baseline(el, ely, psi, frac=8):
@@ -384,7 +402,8 @@ def main():
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
-    work = kernel_work(mixed, el, nk, ne, m)
+    pairs = real_pairs(el, xyz, Q, ne, m, W)
+    work = kernel_work(mixed, el, nk, ne, m, pairs)
     top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
     avg_ms = prof[top][0] / prof[top][1]
     kind, amount = work.get(top, ("flop", float("nan")))
@@ -400,6 +419,12 @@ def main():
         roof = {"kernel": f"k_{top}", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
     roof["share_of_step"] = prof[top][0] / ms
+    roof["all_kernels"] = {kk: {"ms_per_launch": prof[kk][0] / max(1, prof[kk][1]),
+                                "achieved": (work[kk][1] / (prof[kk][0] / max(1, prof[kk][1]) / 1e3)
+                                             / (1e12 if work[kk][0] == "flop" else 1e9)),
+                                "unit": "TFLOP/s" if work[kk][0] == "flop" else "GB/s"}
+                           for kk in work if kk in prof and prof[kk][1] > 0}
+    roof["pairs_in_rcut_per_launch"] = pairs
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

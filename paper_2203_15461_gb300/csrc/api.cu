@@ -126,14 +126,12 @@ static void free_geometry(cpm_ctx* c) {
     drop_graph(c);
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
-                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
-                    c->sperm, c->schunk_lo, c->schunk_hi};
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
     c->rtab = nullptr; c->rtab_id = nullptr;
-    c->sperm = nullptr; c->schunk_lo = nullptr; c->schunk_hi = nullptr; c->nschunk = 0;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -247,45 +245,6 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
         std::vector<double> eu = es;
         std::sort(eu.begin(), eu.end());
         eu.erase(std::unique(eu.begin(), eu.end()), eu.end());
-        // sites sorted by real-space cell, in chunks of 128 with their cell bounding boxes
-        {
-            CellGrid cg = make_grid(c->g);
-            std::vector<int64_t> key(n);
-            std::vector<int> cx(n), cy(n), cz(n);
-            for (int64_t i = 0; i < n; ++i) {
-                int cc[3];
-                for (int d = 0; d < 3; ++d) {
-                    double x = hx[d * n + i];
-                    double w = x - c->g.boxL[d] * std::floor(x * c->g.inv[d]);
-                    if (w >= c->g.boxL[d]) w -= c->g.boxL[d];
-                    if (w < 0) w = 0;
-                    cc[d] = std::min(cg.nc[d] - 1, (int)(w / cg.h[d]));
-                }
-                cx[i] = cc[0]; cy[i] = cc[1]; cz[i] = cc[2];
-                key[i] = ((int64_t)cc[2] * cg.nc[1] + cc[1]) * cg.nc[0] + cc[0];
-            }
-            std::vector<int> perm(n);
-            for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
-            std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
-            const int nch = (int)((n + 127) / 128);
-            std::vector<int4> lo(nch), hi(nch);
-            for (int ch = 0; ch < nch; ++ch) {
-                int4 l = make_int4(1 << 30, 1 << 30, 1 << 30, 0), h = make_int4(-(1 << 30), -(1 << 30), -(1 << 30), 0);
-                for (int64_t k = (int64_t)ch * 128; k < std::min<int64_t>(n, (int64_t)(ch + 1) * 128); ++k) {
-                    int i = perm[k];
-                    l.x = std::min(l.x, cx[i]); l.y = std::min(l.y, cy[i]); l.z = std::min(l.z, cz[i]);
-                    h.x = std::max(h.x, cx[i]); h.y = std::max(h.y, cy[i]); h.z = std::max(h.z, cz[i]);
-                }
-                lo[ch] = l; hi[ch] = h;
-            }
-            c->nschunk = nch;
-            CPM_TRY(dev_alloc(c, (void**)&c->sperm, sizeof(int) * n));
-            CPM_TRY(dev_alloc(c, &c->schunk_lo, sizeof(int4) * nch));
-            CPM_TRY(dev_alloc(c, &c->schunk_hi, sizeof(int4) * nch));
-            CPM_CUDA(c, cudaMemcpyAsync(c->sperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-            CPM_CUDA(c, cudaMemcpyAsync(c->schunk_lo, lo.data(), sizeof(int4) * nch, cudaMemcpyHostToDevice, st));
-            CPM_CUDA(c, cudaMemcpyAsync(c->schunk_hi, hi.data(), sizeof(int4) * nch, cudaMemcpyHostToDevice, st));
-        }
         if (eu.size() <= 16) {
             std::vector<int> em(n);
             for (int64_t i = 0; i < n; ++i) em[i] = (int)(std::lower_bound(eu.begin(), eu.end(), es[i]) - eu.begin());

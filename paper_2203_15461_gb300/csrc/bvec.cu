@@ -253,72 +253,68 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     if (lane == 0) out[(int64_t)r * n + i] = acc64;
 }
 
-// Real space, single precision, site tiles: the sites are pre-sorted by cell into chunks of
-// RS_TILE (one thread each); a block streams the charges of every cell in the chunk's stencil
-// box through shared memory, so each charge is read once per chunk instead of once per site.
-constexpr int RS_TILE = 128;
-
-__global__ void __launch_bounds__(RS_TILE) k_real_tiled(const float* __restrict__ s32, const int* __restrict__ perm,
-                                                        const int4* __restrict__ chunk_lo, const int4* __restrict__ chunk_hi,
-                                                        int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
-                                                        const float4* __restrict__ sorted, const float4* __restrict__ tab,
-                                                        const int* __restrict__ tabid, double* __restrict__ out) {
-    __shared__ float4 sh[RS_TILE];
-    const int ch = blockIdx.x, r = blockIdx.y;
-    const int64_t slot = (int64_t)ch * RS_TILE + threadIdx.x;
-    const int i = slot < n ? perm[slot] : -1;
-    float px = 0.f, py = 0.f, pz = 0.f;
-    const float4* tb = tab;
-    if (i >= 0) {
-        px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
-        tb = tab + (int64_t)tabid[i] * RT_N;
-    }
+// Real space, single precision: one warp per (replica, site); the warp walks the site's stencil
+// cells together (cells whose box is farther than rcut from the site are skipped), and its lanes
+// split each cell's charges, so every load of the sorted charges is coalesced.  The pair function
+// comes from the site's table.
+__global__ void __launch_bounds__(256) k_real_lanes(const float* __restrict__ s32, int64_t n, int m, Geometry g,
+                                                    CellGrid cg, const int* __restrict__ start,
+                                                    const float4* __restrict__ sorted, const float4* __restrict__ tab,
+                                                    const int* __restrict__ tabid, double* __restrict__ out) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)m * n) return;
+    const int r = (int)(wid / n);
+    const int64_t i = wid % n;
+    const float px = s32[i], py = s32[n + i], pz = s32[2 * n + i];
+    const float4* tb = tab + (int64_t)tabid[i] * RT_N;
+    const float hx = (float)cg.h[0], hy = (float)cg.h[1], hz = (float)cg.h[2];
+    const int cix = min(cg.nc[0] - 1, (int)(px / hx)), ciy = min(cg.nc[1] - 1, (int)(py / hy)),
+              ciz = min(cg.nc[2] - 1, (int)(pz / hz));
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
-    const int4 lo = chunk_lo[ch], hi = chunk_hi[ch];
     float acc = 0.f;
-    for (int uz = lo.z - cg.S[2]; uz <= hi.z + cg.S[2]; ++uz) {
+    for (int dz = -cg.S[2]; dz <= cg.S[2]; ++dz) {
+        const int uz = ciz + dz;
+        const float gz = fmaxf(0.f, fmaxf(uz * hz - pz, pz - (uz + 1) * hz));
+        if (gz * gz >= rc2) continue;
         const int fz = floordiv(uz, cg.nc[2]);
         const int cz = uz - fz * cg.nc[2];
         const float shz = (float)(fz * g.boxL[2]);
-        for (int uy = lo.y - cg.S[1]; uy <= hi.y + cg.S[1]; ++uy) {
+        for (int dy = -cg.S[1]; dy <= cg.S[1]; ++dy) {
+            const int uy = ciy + dy;
+            const float gy = fmaxf(0.f, fmaxf(uy * hy - py, py - (uy + 1) * hy));
+            if (gz * gz + gy * gy >= rc2) continue;
             const int fy = floordiv(uy, cg.nc[1]);
             const int cy = uy - fy * cg.nc[1];
             const float shy = (float)(fy * g.boxL[1]);
-            for (int ux = lo.x - cg.S[0]; ux <= hi.x + cg.S[0]; ++ux) {
+            for (int dx = -cg.S[0]; dx <= cg.S[0]; ++dx) {
+                const int ux = cix + dx;
+                const float gx = fmaxf(0.f, fmaxf(ux * hx - px, px - (ux + 1) * hx));
+                if (gz * gz + gy * gy + gx * gx >= rc2) continue;
                 const int fx = floordiv(ux, cg.nc[0]);
                 const int cx = ux - fx * cg.nc[0];
                 const float shx = (float)(fx * g.boxL[0]);
                 const int cell = r * cg.ncells + (cz * cg.nc[1] + cy) * cg.nc[0] + cx;
                 const int b = start[cell], e = start[cell + 1];
-                for (int p0 = b; p0 < e; p0 += RS_TILE) {
-                    const int cnt = min(RS_TILE, e - p0);
-                    if ((int)threadIdx.x < cnt) {
-                        float4 q = sorted[p0 + threadIdx.x];
-                        q.x += shx; q.y += shy; q.z += shz;
-                        sh[threadIdx.x] = q;
+                for (int p = b + lane; p < e; p += 32) {
+                    const float4 q = sorted[p];
+                    const float ddx = px - (q.x + shx), ddy = py - (q.y + shy), ddz = pz - (q.z + shz);
+                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (r2 < rc2) {
+                        const float u = sqrtf(r2) * inv_h;
+                        const int kk = min((int)u, RT_N - 1);
+                        const float t = u - (float)kk;
+                        const float4 cf = tb[kk];
+                        acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
                     }
-                    __syncthreads();
-                    if (i >= 0) {
-                        for (int k = 0; k < cnt; ++k) {
-                            const float4 q = sh[k];
-                            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < rc2) {
-                                const float u = sqrtf(r2) * inv_h;
-                                const int kk = min((int)u, RT_N - 1);
-                                const float t = u - (float)kk;
-                                const float4 cf = tb[kk];
-                                acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
-                            }
-                        }
-                    }
-                    __syncthreads();
                 }
             }
         }
     }
-    if (i >= 0) out[(int64_t)r * n + i] = (double)acc;
+    double a64 = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) a64 += __shfl_down_sync(0xffffffffu, a64, o);
+    if (lane == 0) out[(int64_t)r * n + i] = a64;
 }
 
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
@@ -979,11 +975,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
-    if (std::is_same<T, float>::value && c->rtab && c->sperm) {
-        k_real_tiled<<<dim3((unsigned)c->nschunk, m), RS_TILE, 0, st>>>(c->s32, c->sperm, (const int4*)c->schunk_lo,
-                                                                        (const int4*)c->schunk_hi, n, c->g, p.cg, start,
-                                                                        (const float4*)sorted, (const float4*)c->rtab,
-                                                                        c->rtab_id, real);
+    if (std::is_same<T, float>::value && c->rtab) {
+        k_real_lanes<<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(
+            c->s32, n, m, c->g, p.cg, start, (const float4*)sorted, (const float4*)c->rtab, c->rtab_id, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,

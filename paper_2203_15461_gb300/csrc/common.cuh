@@ -103,10 +103,6 @@ struct cpm_ctx {
     int* zmap = nullptr;         // [n] index of each site's height in zuniq
     double* zuniq = nullptr;     // distinct site heights (exact values)
     int nzu = 0;
-    int* sperm = nullptr;        // sites sorted by real-space cell (chunks of 128)
-    void* schunk_lo = nullptr;   // int4 per chunk: lowest cell coordinates of its sites
-    void* schunk_hi = nullptr;   // int4 per chunk: highest cell coordinates
-    int nschunk = 0;
     void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
     int* rtab_id = nullptr;      // [n] table of each site
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
