@@ -126,12 +126,14 @@ static void free_geometry(cpm_ctx* c) {
     drop_graph(c);
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
-                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id};
+                    c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
+                    c->sperm, c->schunks};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
     c->rtab = nullptr; c->rtab_id = nullptr;
+    c->sperm = nullptr; c->schunks = nullptr; c->nschunk = 0;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -245,6 +247,40 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
         std::vector<double> eu = es;
         std::sort(eu.begin(), eu.end());
         eu.erase(std::unique(eu.begin(), eu.end()), eu.end());
+        // sites grouped by real-space cell, in chunks of at most 32 (one warp each)
+        {
+            const CellGrid cg = make_grid(c->g);
+            std::vector<int> cell(n);
+            for (int64_t i = 0; i < n; ++i) {
+                int cc[3];
+                for (int d = 0; d < 3; ++d) {
+                    const double x = hx[d * n + i];
+                    double w = x - c->g.boxL[d] * std::floor(x * c->g.inv[d]);
+                    if (w >= c->g.boxL[d]) w -= c->g.boxL[d];
+                    if (w < 0) w = 0;
+                    cc[d] = std::min(cg.nc[d] - 1, (int)((float)w / (float)cg.h[d]));
+                }
+                cell[i] = (cc[2] * cg.nc[1] + cc[1]) * cg.nc[0] + cc[0];
+            }
+            std::vector<int> perm(n);
+            for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
+            std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cell[a] < cell[b]; });
+            std::vector<int4> chunks;
+            for (int64_t k = 0; k < n;) {
+                int64_t e = k;
+                while (e < n && cell[perm[e]] == cell[perm[k]]) ++e;
+                for (int64_t f = k; f < e; f += 32)
+                    chunks.push_back(make_int4((int)f, (int)std::min<int64_t>(32, e - f), cell[perm[k]], 0));
+                k = e;
+            }
+            c->nschunk = (int)chunks.size();
+            CPM_TRY(dev_alloc(c, (void**)&c->sperm, sizeof(int) * n));
+            CPM_TRY(dev_alloc(c, &c->schunks, sizeof(int4) * chunks.size()));
+            CPM_CUDA(c, cudaMemcpyAsync(c->sperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+            CPM_CUDA(c, cudaMemcpyAsync(c->schunks, chunks.data(), sizeof(int4) * chunks.size(),
+                                        cudaMemcpyHostToDevice, st));
+            CPM_CUDA(c, cudaStreamSynchronize(st));
+        }
         if (eu.size() <= 16) {
             std::vector<int> em(n);
             for (int64_t i = 0; i < n; ++i) em[i] = (int)(std::lower_bound(eu.begin(), eu.end(), es[i]) - eu.begin());

@@ -25,7 +25,7 @@ template <> struct V4<double> { using t = double4_32a; };
 CellGrid make_grid(const Geometry& g) {
     CellGrid cg;
     for (int d = 0; d < 3; ++d) {
-        int nc = (int)floor(g.boxL[d] / (0.5 * g.rcut));
+        int nc = (int)floor(g.boxL[d] / (g.rcut / 3.0));
         nc = std::max(1, std::min(nc, 256));
         cg.nc[d] = nc;
         cg.h[d] = g.boxL[d] / nc;
@@ -253,68 +253,81 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     if (lane == 0) out[(int64_t)r * n + i] = acc64;
 }
 
-// Real space, single precision: one warp per (replica, site); the warp walks the site's stencil
-// cells together (cells whose box is farther than rcut from the site are skipped), and its lanes
-// split each cell's charges, so every load of the sorted charges is coalesced.  The pair function
-// comes from the site's table.
-__global__ void __launch_bounds__(256) k_real_lanes(const float* __restrict__ s32, int64_t n, int m, Geometry g,
-                                                    CellGrid cg, const int* __restrict__ start,
-                                                    const float4* __restrict__ sorted, const float4* __restrict__ tab,
-                                                    const int* __restrict__ tabid, double* __restrict__ out) {
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= (int64_t)m * n) return;
-    const int r = (int)(wid / n);
-    const int64_t i = wid % n;
-    const float px = s32[i], py = s32[n + i], pz = s32[2 * n + i];
-    const float4* tb = tab + (int64_t)tabid[i] * RT_N;
-    const float hx = (float)cg.h[0], hy = (float)cg.h[1], hz = (float)cg.h[2];
-    const int cix = min(cg.nc[0] - 1, (int)(px / hx)), ciy = min(cg.nc[1] - 1, (int)(py / hy)),
-              ciz = min(cg.nc[2] - 1, (int)(pz / hz));
+// Real space, single precision, cell pairs: the sites are grouped by real-space cell into chunks
+// of at most 32 (one warp each, assembled once); the warp walks the rows (dy, dz) of its cell's
+// stencil, and since the cells of a row are consecutive in the sorted charge array each row is one
+// or two contiguous ranges, streamed 32 charges at a time through the warp's shared buffer and
+// evaluated by all its sites.
+constexpr int RC_WARPS = 4;   // warps (site chunks) per block
+
+__global__ void __launch_bounds__(32 * RC_WARPS, 4) k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm,
+                                                             const int4* __restrict__ chunks, int nchunks, int64_t n,
+                                                             Geometry g, CellGrid cg, const int* __restrict__ start,
+                                                             const float4* __restrict__ sorted,
+                                                             const float4* __restrict__ tab,
+                                                             const int* __restrict__ tabid, double* __restrict__ out) {
+    __shared__ float4 sh[RC_WARPS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * RC_WARPS + warp, r = blockIdx.y;
+    if (ch >= nchunks) return;
+    const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
+    const int i = lane < cinfo.y ? perm[cinfo.x + lane] : -1;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    const float4* tb = tab;
+    if (i >= 0) {
+        px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
+        tb = tab + (int64_t)tabid[i] * RT_N;
+    }
+    const int cx = cinfo.z % cg.nc[0], cy = (cinfo.z / cg.nc[0]) % cg.nc[1], cz = cinfo.z / (cg.nc[0] * cg.nc[1]);
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
     float acc = 0.f;
+    float4* buf = sh[warp];
     for (int dz = -cg.S[2]; dz <= cg.S[2]; ++dz) {
-        const int uz = ciz + dz;
-        const float gz = fmaxf(0.f, fmaxf(uz * hz - pz, pz - (uz + 1) * hz));
-        if (gz * gz >= rc2) continue;
-        const int fz = floordiv(uz, cg.nc[2]);
-        const int cz = uz - fz * cg.nc[2];
+        const int uz = cz + dz, fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
         const float shz = (float)(fz * g.boxL[2]);
         for (int dy = -cg.S[1]; dy <= cg.S[1]; ++dy) {
-            const int uy = ciy + dy;
-            const float gy = fmaxf(0.f, fmaxf(uy * hy - py, py - (uy + 1) * hy));
-            if (gz * gz + gy * gy >= rc2) continue;
-            const int fy = floordiv(uy, cg.nc[1]);
-            const int cy = uy - fy * cg.nc[1];
+            const int uy = cy + dy, fy = floordiv(uy, cg.nc[1]), wy = uy - fy * cg.nc[1];
             const float shy = (float)(fy * g.boxL[1]);
-            for (int dx = -cg.S[0]; dx <= cg.S[0]; ++dx) {
-                const int ux = cix + dx;
-                const float gx = fmaxf(0.f, fmaxf(ux * hx - px, px - (ux + 1) * hx));
-                if (gz * gz + gy * gy + gx * gx >= rc2) continue;
+            const int rowbase = r * cg.ncells + (wz * cg.nc[1] + wy) * cg.nc[0];
+            int ux = cx - cg.S[0];
+            const int uxe = cx + cg.S[0];
+            while (ux <= uxe) {
+                // a run of unwrapped cells with the same image shift: consecutive wrapped cells
                 const int fx = floordiv(ux, cg.nc[0]);
-                const int cx = ux - fx * cg.nc[0];
+                const int wx0 = ux - fx * cg.nc[0];
+                const int wx1 = min(cg.nc[0] - 1, wx0 + (uxe - ux));
                 const float shx = (float)(fx * g.boxL[0]);
-                const int cell = r * cg.ncells + (cz * cg.nc[1] + cy) * cg.nc[0] + cx;
-                const int b = start[cell], e = start[cell + 1];
-                for (int p = b + lane; p < e; p += 32) {
-                    const float4 q = sorted[p];
-                    const float ddx = px - (q.x + shx), ddy = py - (q.y + shy), ddz = pz - (q.z + shz);
-                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < rc2) {
-                        const float u = sqrtf(r2) * inv_h;
-                        const int kk = min((int)u, RT_N - 1);
-                        const float t = u - (float)kk;
-                        const float4 cf = tb[kk];
-                        acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
+                const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
+                ux += wx1 - wx0 + 1;
+                for (int p0 = b; p0 < e; p0 += 32) {
+                    const int cnt = min(32, e - p0);
+                    if (lane < cnt) {
+                        float4 q = sorted[p0 + lane];
+                        q.x += shx; q.y += shy; q.z += shz;
+                        buf[lane] = q;
                     }
+                    __syncwarp();
+                    if (i >= 0) {
+                        for (int k = 0; k < cnt; ++k) {
+                            const float4 q = buf[k];
+                            const float ddx = px - q.x, ddy = py - q.y, ddz = pz - q.z;
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            if (r2 < rc2) {
+                                const float u = sqrtf(r2) * inv_h;
+                                const int kk = min((int)u, RT_N - 1);
+                                const float t = u - (float)kk;
+                                const float4 cf = tb[kk];
+                                acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
+                            }
+                        }
+                    }
+                    __syncwarp();
                 }
             }
         }
     }
-    double a64 = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) a64 += __shfl_down_sync(0xffffffffu, a64, o);
-    if (lane == 0) out[(int64_t)r * n + i] = a64;
+    if (i >= 0) out[(int64_t)r * n + i] = (double)acc;
 }
 
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
@@ -428,7 +441,7 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
 // tile's columns is formed once per chunk of charges and shared by all 128 harmonics.
 constexpr int S2_BM = 64, S2_BZ = 128, S2_BK = 16;
 
-__global__ void __launch_bounds__(256, 2) k_sf32(const int2* __restrict__ cols, const int* __restrict__ colext,
+__global__ void __launch_bounds__(256, 1) k_sf32(const int2* __restrict__ cols, const int* __restrict__ colext,
                                                  int ncols, int NY, int NZ, int nzw, const float2* __restrict__ EX,
                                                  const float2* __restrict__ EY, const float2* __restrict__ EZ,
                                                  const float* __restrict__ Qv, int64_t ptot, int64_t ne, int splits,
@@ -453,28 +466,53 @@ __global__ void __launch_bounds__(256, 2) k_sf32(const int2* __restrict__ cols, 
         for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
     const int64_t jb = (int64_t)r * ne + (int64_t)s * chunk;
     const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
-    if (block_any) {
-        for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
-            for (int e = threadIdx.x; e < S2_BK * S2_BM; e += 256) {
-                const int kk = e % S2_BK, mm = e / S2_BK;
-                const int64_t j = j0 + kk;
-                const int c = c0 + mm;
-                float2 v = make_float2(0.f, 0.f);
-                if (j < je && c < ncols) {
-                    const int2 cn = cols[c];
-                    const float2 xy = cmul(EX[(int64_t)cn.x * ptot + j], EY[(int64_t)(cn.y + NY) * ptot + j]);
-                    const float qj = Qv[j];
-                    v = make_float2(qj * xy.x, qj * xy.y);
-                }
-                Ps[kk][mm] = v;
+    // each thread stages 4 entries of the charge operand and 8 of Z per chunk; the next chunk's
+    // values are fetched into registers while the current chunk is contracted
+    int2 pcol[4];
+    int pkk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        pkk[u] = e % S2_BK;
+        const int c = c0 + e / S2_BK;
+        pcol[u] = c < ncols ? cols[c] : make_int2(-1, 0);
+    }
+    float2 nP[4], nZ[8];
+    auto fetch = [&](int64_t j0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = j0 + pkk[u];
+            float2 v = make_float2(0.f, 0.f);
+            if (j < je && pcol[u].x >= 0) {
+                const float2 xy = cmul(EX[(int64_t)pcol[u].x * ptot + j], EY[(int64_t)(pcol[u].y + NY) * ptot + j]);
+                const float qj = Qv[j];
+                v = make_float2(qj * xy.x, qj * xy.y);
             }
-            for (int e = threadIdx.x; e < S2_BK * S2_BZ; e += 256) {
-                const int kk = e % S2_BK, zz = e / S2_BK;
-                const int64_t j = j0 + kk;
-                const int z = zbase + zz;
-                Zs[kk][zz] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
+            nP[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int64_t j = j0 + e % S2_BK;
+            const int z = zbase + e / S2_BK;
+            nZ[u] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
+        }
+    };
+    if (block_any) {
+        fetch(jb);
+        for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                Ps[e % S2_BK][e / S2_BK] = nP[u];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                Zs[e % S2_BK][e / S2_BK] = nZ[u];
             }
             __syncthreads();
+            if (j0 + S2_BK < je) fetch(j0 + S2_BK);
             if (active) {
 #pragma unroll 2
                 for (int kk = 0; kk < S2_BK; ++kk) {
@@ -764,7 +802,7 @@ __global__ void k_col0_site(const double* __restrict__ zu, int nzu, int m, doubl
 // 16 column groups of a half warp with shuffles.
 constexpr int T2_BC = 64, T2_BS = 128, T2_BK = 16;
 
-__global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols, const int* __restrict__ colext,
+__global__ void __launch_bounds__(256, 1) k_site32(const int2* __restrict__ cols, const int* __restrict__ colext,
                                                    int ncols, int NY, int NZ, int nzw, const float2* __restrict__ wrho,
                                                    const float2* __restrict__ SX, const float2* __restrict__ SY,
                                                    const float2* __restrict__ SZ, int64_t n, int nctiles,
@@ -785,19 +823,36 @@ __global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols
         for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
     if (mx >= 0) {
         const int zb = NZ - mx, ze = NZ + mx + 1;
-        for (int z0 = zb; z0 < ze; z0 += T2_BK) {
-            for (int e = threadIdx.x; e < T2_BK * T2_BC; e += 256) {
-                const int kk = e % T2_BK, cc = e / T2_BK;
-                const int z = z0 + kk, c = c0 + cc;
-                As[kk][cc] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : make_float2(0.f, 0.f);
+        float2 nA[4], nB[8];
+        auto fetch = [&](int z0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                const int z = z0 + e % T2_BK, c = c0 + e / T2_BK;
+                nA[u] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : make_float2(0.f, 0.f);
             }
-            for (int e = threadIdx.x; e < T2_BK * T2_BS; e += 256) {
-                const int ss = e % T2_BS, kk = e / T2_BS;
-                const int z = z0 + kk;
-                const int64_t i = i0 + ss;
-                Bs[kk][ss] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                const int z = z0 + e / T2_BS;
+                const int64_t i = i0 + e % T2_BS;
+                nB[u] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : make_float2(0.f, 0.f);
+            }
+        };
+        fetch(zb);
+        for (int z0 = zb; z0 < ze; z0 += T2_BK) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                As[e % T2_BK][e / T2_BK] = nA[u];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                Bs[e / T2_BS][e % T2_BS] = nB[u];
             }
             __syncthreads();
+            if (z0 + T2_BK < ze) fetch(z0 + T2_BK);
 #pragma unroll 2
             for (int kk = 0; kk < T2_BK; ++kk) {
                 float2 av[4], bv[8];
@@ -975,9 +1030,10 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
-    if (std::is_same<T, float>::value && c->rtab) {
-        k_real_lanes<<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(
-            c->s32, n, m, c->g, p.cg, start, (const float4*)sorted, (const float4*)c->rtab, c->rtab_id, real);
+    if (std::is_same<T, float>::value && c->rtab && c->schunks) {
+        k_real_cells<<<dim3((unsigned)((c->nschunk + RC_WARPS - 1) / RC_WARPS), m), 32 * RC_WARPS, 0, st>>>(
+            c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
+            (const float4*)c->rtab, c->rtab_id, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,

@@ -103,6 +103,9 @@ struct cpm_ctx {
     int* zmap = nullptr;         // [n] index of each site's height in zuniq
     double* zuniq = nullptr;     // distinct site heights (exact values)
     int nzu = 0;
+    int* sperm = nullptr;        // sites ordered by real-space cell
+    void* schunks = nullptr;     // int4 (first, count, cell, 0): chunks of at most 32 sites of one cell
+    int nschunk = 0;
     void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
     int* rtab_id = nullptr;      // [n] table of each site
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
