@@ -132,7 +132,7 @@ static void free_geometry(cpm_ctx* c) {
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
-    c->rtab = nullptr; c->rtab_id = nullptr;
+    c->rtab = nullptr; c->rtab_id = nullptr; c->nrtab = 0;
     c->sperm = nullptr; c->schunks = nullptr; c->nschunk = 0;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
@@ -287,6 +287,7 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
             CPM_TRY(dev_alloc(c, (void**)&c->rtab_id, sizeof(int) * n));
             CPM_CUDA(c, cudaMemcpyAsync(c->rtab_id, em.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
             CPM_TRY(build_pair_tables(c, eu));
+            c->nrtab = (int)eu.size();
         }
         CPM_TRY(dev_alloc(c, (void**)&c->zmap, sizeof(int) * n));
         CPM_TRY(dev_alloc(c, (void**)&c->zuniq, sizeof(double) * zu.size()));

@@ -254,80 +254,92 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
 }
 
 // Real space, single precision, cell pairs: the sites are grouped by real-space cell into chunks
-// of at most 32 (one warp each, assembled once); the warp walks the rows (dy, dz) of its cell's
-// stencil, and since the cells of a row are consecutive in the sorted charge array each row is one
-// or two contiguous ranges, streamed 32 charges at a time through the warp's shared buffer and
-// evaluated by all its sites.
-constexpr int RC_WARPS = 4;   // warps (site chunks) per block
+// of at most 32 (assembled once).  A block of RC_WARPS warps takes one chunk; its warps split the
+// rows (dy, dz) of the cell's stencil, and since the cells of a row are consecutive in the sorted
+// charge array each row is one or two contiguous ranges, streamed 32 charges at a time through the
+// warp's shared buffer and evaluated by all the chunk's sites.  The warps' partial sums are added
+// in a fixed order.  The pair-function tables of up to two widths are staged in shared memory.
+constexpr int RC_WARPS = 4;
+constexpr int RC_SMEM_TABS = 2;
 
 __global__ void __launch_bounds__(32 * RC_WARPS, 4) k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm,
                                                              const int4* __restrict__ chunks, int nchunks, int64_t n,
                                                              Geometry g, CellGrid cg, const int* __restrict__ start,
                                                              const float4* __restrict__ sorted,
-                                                             const float4* __restrict__ tab,
+                                                             const float4* __restrict__ tab, int ntab,
                                                              const int* __restrict__ tabid, double* __restrict__ out) {
     __shared__ float4 sh[RC_WARPS][32];
+    __shared__ float4 stab[RC_SMEM_TABS * RT_N];
+    __shared__ float part[RC_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x * RC_WARPS + warp, r = blockIdx.y;
-    if (ch >= nchunks) return;
+    const int ch = blockIdx.x, r = blockIdx.y;
+    const bool smem_tab = ntab <= RC_SMEM_TABS;
+    if (smem_tab)
+        for (int e = threadIdx.x; e < ntab * RT_N; e += blockDim.x) stab[e] = tab[e];
+    __syncthreads();
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
     const int i = lane < cinfo.y ? perm[cinfo.x + lane] : -1;
     float px = 0.f, py = 0.f, pz = 0.f;
-    const float4* tb = tab;
+    const float4* tb = smem_tab ? stab : tab;
     if (i >= 0) {
         px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
-        tb = tab + (int64_t)tabid[i] * RT_N;
+        tb += tabid[i] * RT_N;
     }
     const int cx = cinfo.z % cg.nc[0], cy = (cinfo.z / cg.nc[0]) % cg.nc[1], cz = cinfo.z / (cg.nc[0] * cg.nc[1]);
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
     float acc = 0.f;
     float4* buf = sh[warp];
-    for (int dz = -cg.S[2]; dz <= cg.S[2]; ++dz) {
+    const int wy = 2 * cg.S[1] + 1, nrows = wy * (2 * cg.S[2] + 1);
+    for (int row = warp; row < nrows; row += RC_WARPS) {
+        const int dy = row % wy - cg.S[1], dz = row / wy - cg.S[2];
         const int uz = cz + dz, fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
-        const float shz = (float)(fz * g.boxL[2]);
-        for (int dy = -cg.S[1]; dy <= cg.S[1]; ++dy) {
-            const int uy = cy + dy, fy = floordiv(uy, cg.nc[1]), wy = uy - fy * cg.nc[1];
-            const float shy = (float)(fy * g.boxL[1]);
-            const int rowbase = r * cg.ncells + (wz * cg.nc[1] + wy) * cg.nc[0];
-            int ux = cx - cg.S[0];
-            const int uxe = cx + cg.S[0];
-            while (ux <= uxe) {
-                // a run of unwrapped cells with the same image shift: consecutive wrapped cells
-                const int fx = floordiv(ux, cg.nc[0]);
-                const int wx0 = ux - fx * cg.nc[0];
-                const int wx1 = min(cg.nc[0] - 1, wx0 + (uxe - ux));
-                const float shx = (float)(fx * g.boxL[0]);
-                const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
-                ux += wx1 - wx0 + 1;
-                for (int p0 = b; p0 < e; p0 += 32) {
-                    const int cnt = min(32, e - p0);
-                    if (lane < cnt) {
-                        float4 q = sorted[p0 + lane];
-                        q.x += shx; q.y += shy; q.z += shz;
-                        buf[lane] = q;
-                    }
-                    __syncwarp();
-                    if (i >= 0) {
-                        for (int k = 0; k < cnt; ++k) {
-                            const float4 q = buf[k];
-                            const float ddx = px - q.x, ddy = py - q.y, ddz = pz - q.z;
-                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (r2 < rc2) {
-                                const float u = sqrtf(r2) * inv_h;
-                                const int kk = min((int)u, RT_N - 1);
-                                const float t = u - (float)kk;
-                                const float4 cf = tb[kk];
-                                acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
-                            }
+        const int uy = cy + dy, fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
+        const float shz = (float)(fz * g.boxL[2]), shy = (float)(fy * g.boxL[1]);
+        const int rowbase = r * cg.ncells + (wz * cg.nc[1] + wyy) * cg.nc[0];
+        int ux = cx - cg.S[0];
+        const int uxe = cx + cg.S[0];
+        while (ux <= uxe) {
+            // a run of unwrapped cells with the same image shift: consecutive wrapped cells
+            const int fx = floordiv(ux, cg.nc[0]);
+            const int wx0 = ux - fx * cg.nc[0];
+            const int wx1 = min(cg.nc[0] - 1, wx0 + (uxe - ux));
+            const float shx = (float)(fx * g.boxL[0]);
+            const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
+            ux += wx1 - wx0 + 1;
+            for (int p0 = b; p0 < e; p0 += 32) {
+                const int cnt = min(32, e - p0);
+                if (lane < cnt) {
+                    float4 q = sorted[p0 + lane];
+                    q.x += shx; q.y += shy; q.z += shz;
+                    buf[lane] = q;
+                }
+                __syncwarp();
+                if (i >= 0) {
+                    for (int k = 0; k < cnt; ++k) {
+                        const float4 q = buf[k];
+                        const float ddx = px - q.x, ddy = py - q.y, ddz = pz - q.z;
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (r2 < rc2) {
+                            const float u = sqrtf(r2) * inv_h;
+                            const int kk = min((int)u, RT_N - 1);
+                            const float t = u - (float)kk;
+                            const float4 cf = tb[kk];
+                            acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
                         }
                     }
-                    __syncwarp();
                 }
+                __syncwarp();
             }
         }
     }
-    if (i >= 0) out[(int64_t)r * n + i] = (double)acc;
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i >= 0) {
+        double a = 0.0;
+        for (int w = 0; w < RC_WARPS; ++w) a += (double)part[w][lane];
+        out[(int64_t)r * n + i] = a;
+    }
 }
 
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
@@ -434,31 +446,28 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
     }
 }
 
-// Single-precision structure factor with a 64-column x 128-harmonic accumulator tile per block:
-// warp w owns harmonics [16w, 16w + 16) of the tile's z range and skips the contraction when that
-// slab lies outside the largest |nz| of the tile's columns (columns are sorted by k_perp, so the
-// slab test removes most of the padding of the dense grid); the charge operand Q_j X_j Y_j of the
-// tile's columns is formed once per chunk of charges and shared by all 128 harmonics.
-constexpr int S2_BM = 64, S2_BZ = 128, S2_BK = 16;
+// Single-precision structure factor: a work item is a 64-column tile and a chunk of 64 harmonics
+// that meets the tile's ball (columns are sorted by k_perp; the item list is built once per
+// geometry), one 4-warp block per item and charge split.  Each thread accumulates 4 columns x 8
+// harmonics; the charge operand Q_j X_j Y_j of the tile's columns is formed once per chunk of 16
+// charges and shared by the block, and the next chunk is fetched into registers while the
+// current one is contracted.
+constexpr int S2_BM = 64, S2_BZ = 64, S2_BK = 16, S2_THREADS = 128;
 
-__global__ void __launch_bounds__(256, 1) k_sf32(const int2* __restrict__ cols, const int* __restrict__ colext,
-                                                 int ncols, int NY, int NZ, int nzw, const float2* __restrict__ EX,
-                                                 const float2* __restrict__ EY, const float2* __restrict__ EZ,
-                                                 const float* __restrict__ Qv, int64_t ptot, int64_t ne, int splits,
-                                                 int64_t chunk, int m, int nsup, float2* __restrict__ rho_part) {
+__global__ void __launch_bounds__(S2_THREADS, 2) k_sf32(const int2* __restrict__ cols, int ncols, int NY, int nzw,
+                                                        const int2* __restrict__ items, const float2* __restrict__ EX,
+                                                        const float2* __restrict__ EY, const float2* __restrict__ EZ,
+                                                        const float* __restrict__ Qv, int64_t ptot, int64_t ne,
+                                                        int splits, int64_t chunk, int m,
+                                                        float2* __restrict__ rho_part) {
     __shared__ float2 Ps[S2_BK][S2_BM + 1];
     __shared__ float2 Zs[S2_BK][S2_BZ + 1];
-    const int c0 = blockIdx.x * S2_BM;
-    const int zbase = NZ - S2_BZ / 2 - S2_BZ * (nsup / 2) + S2_BZ * (int)blockIdx.y;   // grid index of row 0
-    const int r = blockIdx.z / splits, s = blockIdx.z % splits;
+    const int2 item = items[blockIdx.x];          // (column tile, first harmonic index of the chunk)
+    const int c0 = item.x * S2_BM, zbase = item.y;
+    const int r = blockIdx.y / splits, s = blockIdx.y % splits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = lane & 15, zh = lane >> 4;
     float2* outp = rho_part + ((int64_t)s * m + r) * ncols * nzw;
-    const int mx = tile_maxext<float>(colext, c0, ncols);
-    // harmonics of this warp: zbase + 16 warp + zh + 2 q, q = 0..7  (nz = index - NZ)
-    const int wz0 = zbase + 16 * warp - NZ, wz1 = wz0 + 15;
-    const bool active = mx >= 0 && !(wz0 > mx || wz1 < -mx);
-    const bool block_any = mx >= 0 && !(zbase - NZ > mx || zbase + S2_BZ - 1 - NZ < -mx);
     float2 acc[4][8];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -466,21 +475,19 @@ __global__ void __launch_bounds__(256, 1) k_sf32(const int2* __restrict__ cols, 
         for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
     const int64_t jb = (int64_t)r * ne + (int64_t)s * chunk;
     const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
-    // each thread stages 4 entries of the charge operand and 8 of Z per chunk; the next chunk's
-    // values are fetched into registers while the current chunk is contracted
-    int2 pcol[4];
-    int pkk[4];
+    int2 pcol[8];
+    int pkk[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int e = threadIdx.x + 256 * u;
+    for (int u = 0; u < 8; ++u) {
+        const int e = threadIdx.x + S2_THREADS * u;
         pkk[u] = e % S2_BK;
         const int c = c0 + e / S2_BK;
         pcol[u] = c < ncols ? cols[c] : make_int2(-1, 0);
     }
-    float2 nP[4], nZ[8];
+    float2 nP[8], nZ[8];
     auto fetch = [&](int64_t j0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const int64_t j = j0 + pkk[u];
             float2 v = make_float2(0.f, 0.f);
             if (j < je && pcol[u].x >= 0) {
@@ -492,46 +499,38 @@ __global__ void __launch_bounds__(256, 1) k_sf32(const int2* __restrict__ cols, 
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = threadIdx.x + 256 * u;
+            const int e = threadIdx.x + S2_THREADS * u;
             const int64_t j = j0 + e % S2_BK;
             const int z = zbase + e / S2_BK;
             nZ[u] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
         }
     };
-    if (block_any) {
-        fetch(jb);
-        for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
+    fetch(jb);
+    for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                Ps[e % S2_BK][e / S2_BK] = nP[u];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                Zs[e % S2_BK][e / S2_BK] = nZ[u];
-            }
-            __syncthreads();
-            if (j0 + S2_BK < je) fetch(j0 + S2_BK);
-            if (active) {
-#pragma unroll 2
-                for (int kk = 0; kk < S2_BK; ++kk) {
-                    float2 av[4], bv[8];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) av[p] = Ps[kk][cg + 16 * p];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) bv[q] = Zs[kk][16 * warp + zh + 2 * q];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
-                            acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
-                        }
-                }
-            }
-            __syncthreads();
+        for (int u = 0; u < 8; ++u) {
+            const int e = threadIdx.x + S2_THREADS * u;
+            Ps[e % S2_BK][e / S2_BK] = nP[u];
+            Zs[e % S2_BK][e / S2_BK] = nZ[u];
         }
+        __syncthreads();
+        if (j0 + S2_BK < je) fetch(j0 + S2_BK);
+#pragma unroll 2
+        for (int kk = 0; kk < S2_BK; ++kk) {
+            float2 av[4], bv[8];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) av[p] = Ps[kk][cg + 16 * p];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) bv[q] = Zs[kk][16 * warp + zh + 2 * q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
+                    acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
+                }
+        }
+        __syncthreads();
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -934,10 +933,8 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
-    // the single-precision structure factor uses 128-harmonic super-tiles (k_sf32)
-    const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
-    const int yt = std::is_same<T, float>::value ? 2 * zh2 + 1 : p.ztiles;
-    const int64_t base = (int64_t)p.ctiles * yt * m;
+    // the single-precision structure factor runs one block per work item (k_sf32)
+    const int64_t base = (int64_t)(std::is_same<T, float>::value ? std::max(k.nsfwork, 1) : p.ctiles * p.ztiles) * m;
     int64_t want = (4 * 152 + base - 1) / std::max<int64_t>(base, 1);
     int64_t maxs = std::max<int64_t>(1, (ne + 127) / 128);
     p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(maxs, 64)));
@@ -1031,9 +1028,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
     if (std::is_same<T, float>::value && c->rtab && c->schunks) {
-        k_real_cells<<<dim3((unsigned)((c->nschunk + RC_WARPS - 1) / RC_WARPS), m), 32 * RC_WARPS, 0, st>>>(
+        k_real_cells<<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
             c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
-            (const float4*)c->rtab, c->rtab_id, real);
+            (const float4*)c->rtab, c->nrtab, c->rtab_id, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,
@@ -1048,12 +1045,12 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_end(c, CPM_K_PHASES);
         prof_begin(c, CPM_K_SF);
         if (std::is_same<T, float>::value) {
-            const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
-            const int nsup = 2 * zh2 + 1;
-            dim3 gsf(p.ctiles, nsup, m * p.splits);
-            k_sf32<<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)EX,
-                                        (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne, p.splits,
-                                        p.chunk, m, nsup, (float2*)rp);
+            // entries of the dense grid that no work item covers stay zero
+            CPM_CUDA(c, cudaMemsetAsync(rp, 0, sizeof(c2<T>) * (size_t)k.ncols * k.nzw * m * p.splits, st));
+            dim3 gsf((unsigned)k.nsfwork, m * p.splits);
+            k_sf32<<<gsf, S2_THREADS, 0, st>>>(k.cols, k.ncols, k.NY, k.nzw, k.sfwork, (const float2*)EX,
+                                               (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne,
+                                               p.splits, p.chunk, m, (float2*)rp);
         } else {
             dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
             k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne,

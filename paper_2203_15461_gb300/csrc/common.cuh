@@ -55,6 +55,8 @@ struct KTable {
     double* w = nullptr;            // [ncols * nzw] dense weights (8 pi / V) e^{-k^2/4a^2} / k^2
     float* w32 = nullptr;
     int4* klist = nullptr;          // [nk] compact list: (column, nz, nx, ny)
+    int2* sfwork = nullptr;         // structure-factor work items: (64-column tile, first grid row of 64 harmonics)
+    int nsfwork = 0;
     double* kw = nullptr;           // [nk] weight of each compact entry
 };
 
@@ -108,6 +110,7 @@ struct cpm_ctx {
     int nschunk = 0;
     void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
     int* rtab_id = nullptr;      // [n] table of each site
+    int nrtab = 0;
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
     cpm::KTable kt;
     cpm::Phases<double> site64;

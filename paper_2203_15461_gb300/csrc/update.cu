@@ -75,7 +75,19 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv_t(const TS* __restrict__ S, co
         __syncthreads();
         const int jn = (int)min((int64_t)GT_JT, je - j0);
         if (i < n) {
-            for (int jj = 0; jj < jn; ++jj) {
+            // eight loads of S in flight before they are used
+            int jj = 0;
+            for (; jj + 8 <= jn; jj += 8) {
+                TS sv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sv[u] = S[(j0 + jj + u) * n + i];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int t = 0; t < GT_MR; ++t)
+                        if (t < mm) acc[t].add(sv[u] * (TS)centred(bs[t][jj + u], bi[t]));
+            }
+            for (; jj < jn; ++jj) {
                 const TS sv = S[(j0 + jj) * n + i];
 #pragma unroll
                 for (int t = 0; t < GT_MR; ++t)
