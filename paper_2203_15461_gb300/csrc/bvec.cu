@@ -446,28 +446,31 @@ __global__ void __launch_bounds__(256) k_sf(const int2* __restrict__ cols, const
     }
 }
 
-// Single-precision structure factor: a work item is a 64-column tile and a chunk of 64 harmonics
-// that meets the tile's ball (columns are sorted by k_perp; the item list is built once per
-// geometry), one 4-warp block per item and charge split.  Each thread accumulates 4 columns x 8
-// harmonics; the charge operand Q_j X_j Y_j of the tile's columns is formed once per chunk of 16
-// charges and shared by the block, and the next chunk is fetched into registers while the
-// current one is contracted.
-constexpr int S2_BM = 64, S2_BZ = 64, S2_BK = 16, S2_THREADS = 128;
+// Single-precision structure factor with a 64-column x 128-harmonic accumulator tile per block:
+// warp w owns harmonics [16w, 16w + 16) of the tile's z range and skips the contraction when that
+// slab lies outside the largest |nz| of the tile's columns (columns are sorted by k_perp, so the
+// slab test removes most of the padding of the dense grid); the charge operand Q_j X_j Y_j of the
+// tile's columns is formed once per chunk of charges and shared by all 128 harmonics.
+constexpr int S2_BM = 64, S2_BZ = 128, S2_BK = 16;
 
-__global__ void __launch_bounds__(S2_THREADS, 2) k_sf32(const int2* __restrict__ cols, int ncols, int NY, int nzw,
-                                                        const int2* __restrict__ items, const float2* __restrict__ EX,
-                                                        const float2* __restrict__ EY, const float2* __restrict__ EZ,
-                                                        const float* __restrict__ Qv, int64_t ptot, int64_t ne,
-                                                        int splits, int64_t chunk, int m,
-                                                        float2* __restrict__ rho_part) {
+__global__ void __launch_bounds__(256, 2) k_sf32(const int2* __restrict__ cols, const int* __restrict__ colext,
+                                                 int ncols, int NY, int NZ, int nzw, const float2* __restrict__ EX,
+                                                 const float2* __restrict__ EY, const float2* __restrict__ EZ,
+                                                 const float* __restrict__ Qv, int64_t ptot, int64_t ne, int splits,
+                                                 int64_t chunk, int m, int nsup, float2* __restrict__ rho_part) {
     __shared__ float2 Ps[S2_BK][S2_BM + 1];
     __shared__ float2 Zs[S2_BK][S2_BZ + 1];
-    const int2 item = items[blockIdx.x];          // (column tile, first harmonic index of the chunk)
-    const int c0 = item.x * S2_BM, zbase = item.y;
-    const int r = blockIdx.y / splits, s = blockIdx.y % splits;
+    const int c0 = blockIdx.x * S2_BM;
+    const int zbase = NZ - S2_BZ / 2 - S2_BZ * (nsup / 2) + S2_BZ * (int)blockIdx.y;   // grid index of row 0
+    const int r = blockIdx.z / splits, s = blockIdx.z % splits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = lane & 15, zh = lane >> 4;
     float2* outp = rho_part + ((int64_t)s * m + r) * ncols * nzw;
+    const int mx = tile_maxext<float>(colext, c0, ncols);
+    // harmonics of this warp: zbase + 16 warp + zh + 2 q, q = 0..7  (nz = index - NZ)
+    const int wz0 = zbase + 16 * warp - NZ, wz1 = wz0 + 15;
+    const bool active = mx >= 0 && !(wz0 > mx || wz1 < -mx);
+    const bool block_any = mx >= 0 && !(zbase - NZ > mx || zbase + S2_BZ - 1 - NZ < -mx);
     float2 acc[4][8];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -475,62 +478,47 @@ __global__ void __launch_bounds__(S2_THREADS, 2) k_sf32(const int2* __restrict__
         for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
     const int64_t jb = (int64_t)r * ne + (int64_t)s * chunk;
     const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
-    int2 pcol[8];
-    int pkk[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int e = threadIdx.x + S2_THREADS * u;
-        pkk[u] = e % S2_BK;
-        const int c = c0 + e / S2_BK;
-        pcol[u] = c < ncols ? cols[c] : make_int2(-1, 0);
-    }
-    float2 nP[8], nZ[8];
-    auto fetch = [&](int64_t j0) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int64_t j = j0 + pkk[u];
-            float2 v = make_float2(0.f, 0.f);
-            if (j < je && pcol[u].x >= 0) {
-                const float2 xy = cmul(EX[(int64_t)pcol[u].x * ptot + j], EY[(int64_t)(pcol[u].y + NY) * ptot + j]);
-                const float qj = Qv[j];
-                v = make_float2(qj * xy.x, qj * xy.y);
-            }
-            nP[u] = v;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = threadIdx.x + S2_THREADS * u;
-            const int64_t j = j0 + e % S2_BK;
-            const int z = zbase + e / S2_BK;
-            nZ[u] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
-        }
-    };
-    fetch(jb);
-    for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = threadIdx.x + S2_THREADS * u;
-            Ps[e % S2_BK][e / S2_BK] = nP[u];
-            Zs[e % S2_BK][e / S2_BK] = nZ[u];
-        }
-        __syncthreads();
-        if (j0 + S2_BK < je) fetch(j0 + S2_BK);
-#pragma unroll 2
-        for (int kk = 0; kk < S2_BK; ++kk) {
-            float2 av[4], bv[8];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) av[p] = Ps[kk][cg + 16 * p];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) bv[q] = Zs[kk][16 * warp + zh + 2 * q];
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
-                    acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
+    if (block_any) {
+        for (int64_t j0 = jb; j0 < je; j0 += S2_BK) {
+            for (int e = threadIdx.x; e < S2_BK * S2_BM; e += 256) {
+                const int kk = e % S2_BK, mm = e / S2_BK;
+                const int64_t j = j0 + kk;
+                const int c = c0 + mm;
+                float2 v = make_float2(0.f, 0.f);
+                if (j < je && c < ncols) {
+                    const int2 cn = cols[c];
+                    const float2 xy = cmul(EX[(int64_t)cn.x * ptot + j], EY[(int64_t)(cn.y + NY) * ptot + j]);
+                    const float qj = Qv[j];
+                    v = make_float2(qj * xy.x, qj * xy.y);
                 }
+                Ps[kk][mm] = v;
+            }
+            for (int e = threadIdx.x; e < S2_BK * S2_BZ; e += 256) {
+                const int kk = e % S2_BK, zz = e / S2_BK;
+                const int64_t j = j0 + kk;
+                const int z = zbase + zz;
+                Zs[kk][zz] = (j < je && z >= 0 && z < nzw) ? EZ[(int64_t)z * ptot + j] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll 2
+                for (int kk = 0; kk < S2_BK; ++kk) {
+                    float2 av[4], bv[8];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) av[p] = Ps[kk][cg + 16 * p];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) bv[q] = Zs[kk][16 * warp + zh + 2 * q];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            acc[p][q].x += av[p].x * bv[q].x - av[p].y * bv[q].y;
+                            acc[p][q].y += av[p].x * bv[q].y + av[p].y * bv[q].x;
+                        }
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -801,7 +789,7 @@ __global__ void k_col0_site(const double* __restrict__ zu, int nzu, int m, doubl
 // 16 column groups of a half warp with shuffles.
 constexpr int T2_BC = 64, T2_BS = 128, T2_BK = 16;
 
-__global__ void __launch_bounds__(256, 1) k_site32(const int2* __restrict__ cols, const int* __restrict__ colext,
+__global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols, const int* __restrict__ colext,
                                                    int ncols, int NY, int NZ, int nzw, const float2* __restrict__ wrho,
                                                    const float2* __restrict__ SX, const float2* __restrict__ SY,
                                                    const float2* __restrict__ SZ, int64_t n, int nctiles,
@@ -822,36 +810,19 @@ __global__ void __launch_bounds__(256, 1) k_site32(const int2* __restrict__ cols
         for (int q = 0; q < 8; ++q) acc[p][q] = make_float2(0.f, 0.f);
     if (mx >= 0) {
         const int zb = NZ - mx, ze = NZ + mx + 1;
-        float2 nA[4], nB[8];
-        auto fetch = [&](int z0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                const int z = z0 + e % T2_BK, c = c0 + e / T2_BK;
-                nA[u] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                const int z = z0 + e / T2_BS;
-                const int64_t i = i0 + e % T2_BS;
-                nB[u] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : make_float2(0.f, 0.f);
-            }
-        };
-        fetch(zb);
         for (int z0 = zb; z0 < ze; z0 += T2_BK) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                As[e % T2_BK][e / T2_BK] = nA[u];
+            for (int e = threadIdx.x; e < T2_BK * T2_BC; e += 256) {
+                const int kk = e % T2_BK, cc = e / T2_BK;
+                const int z = z0 + kk, c = c0 + cc;
+                As[kk][cc] = (z < ze && c < ncols) ? rho[(int64_t)c * nzw + z] : make_float2(0.f, 0.f);
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                Bs[e / T2_BS][e % T2_BS] = nB[u];
+            for (int e = threadIdx.x; e < T2_BK * T2_BS; e += 256) {
+                const int ss = e % T2_BS, kk = e / T2_BS;
+                const int z = z0 + kk;
+                const int64_t i = i0 + ss;
+                Bs[kk][ss] = (z < ze && i < n) ? SZ[(int64_t)z * n + i] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            if (z0 + T2_BK < ze) fetch(z0 + T2_BK);
 #pragma unroll 2
             for (int kk = 0; kk < T2_BK; ++kk) {
                 float2 av[4], bv[8];
@@ -933,8 +904,10 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
-    // the single-precision structure factor runs one block per work item (k_sf32)
-    const int64_t base = (int64_t)(std::is_same<T, float>::value ? std::max(k.nsfwork, 1) : p.ctiles * p.ztiles) * m;
+    // the single-precision structure factor uses 128-harmonic super-tiles (k_sf32)
+    const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
+    const int yt = std::is_same<T, float>::value ? 2 * zh2 + 1 : p.ztiles;
+    const int64_t base = (int64_t)p.ctiles * yt * m;
     int64_t want = (4 * 152 + base - 1) / std::max<int64_t>(base, 1);
     int64_t maxs = std::max<int64_t>(1, (ne + 127) / 128);
     p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(maxs, 64)));
@@ -1045,12 +1018,12 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_end(c, CPM_K_PHASES);
         prof_begin(c, CPM_K_SF);
         if (std::is_same<T, float>::value) {
-            // entries of the dense grid that no work item covers stay zero
-            CPM_CUDA(c, cudaMemsetAsync(rp, 0, sizeof(c2<T>) * (size_t)k.ncols * k.nzw * m * p.splits, st));
-            dim3 gsf((unsigned)k.nsfwork, m * p.splits);
-            k_sf32<<<gsf, S2_THREADS, 0, st>>>(k.cols, k.ncols, k.NY, k.nzw, k.sfwork, (const float2*)EX,
-                                               (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne,
-                                               p.splits, p.chunk, m, (float2*)rp);
+            const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
+            const int nsup = 2 * zh2 + 1;
+            dim3 gsf(p.ctiles, nsup, m * p.splits);
+            k_sf32<<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)EX,
+                                        (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne, p.splits,
+                                        p.chunk, m, nsup, (float2*)rp);
         } else {
             dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
             k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne,

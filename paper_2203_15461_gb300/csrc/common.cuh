@@ -55,8 +55,6 @@ struct KTable {
     double* w = nullptr;            // [ncols * nzw] dense weights (8 pi / V) e^{-k^2/4a^2} / k^2
     float* w32 = nullptr;
     int4* klist = nullptr;          // [nk] compact list: (column, nz, nx, ny)
-    int2* sfwork = nullptr;         // structure-factor work items: (64-column tile, first grid row of 64 harmonics)
-    int nsfwork = 0;
     double* kw = nullptr;           // [nk] weight of each compact entry
 };
 

@@ -127,7 +127,7 @@ __global__ void k_compact(const int2* cols, const int* colext, const int64_t* co
 void free_ktable(cpm_ctx* c) {
     KTable& k = c->kt;
     dev_free(c, k.cols); dev_free(c, k.colext); dev_free(c, k.coloff); dev_free(c, k.w);
-    dev_free(c, k.w32); dev_free(c, k.klist); dev_free(c, k.kw); dev_free(c, k.sfwork);
+    dev_free(c, k.w32); dev_free(c, k.klist); dev_free(c, k.kw);
     k = KTable{};
 }
 
@@ -165,24 +165,6 @@ cpm_status build_ktable(cpm_ctx* c) {
                                                                     inv4a2, k.w, k.w32, k.colext);
     CPM_LAUNCH(c, "k_weights");
     CPM_CUDA(c, cudaMemcpyAsync(&k.ext0, k.colext, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    {
-        // work items of the single-precision structure factor: for every 64-column tile, the
-        // 64-harmonic chunks that meet [-ext, ext] of its widest column
-        std::vector<int> ext(k.ncols);
-        CPM_CUDA(c, cudaMemcpyAsync(ext.data(), k.colext, sizeof(int) * k.ncols, cudaMemcpyDeviceToHost, c->stream));
-        CPM_CUDA(c, cudaStreamSynchronize(c->stream));
-        std::vector<int2> items;
-        for (int c0 = 0; c0 < k.ncols; c0 += 64) {
-            int mx = -1;
-            for (int cc = c0; cc < std::min(k.ncols, c0 + 64); ++cc) mx = std::max(mx, ext[cc]);
-            if (mx < 0) continue;
-            for (int z = k.NZ - mx; z <= k.NZ + mx; z += 64) items.push_back(make_int2(c0 / 64, z));
-        }
-        k.nsfwork = (int)items.size();
-        CPM_TRY(dev_alloc(c, (void**)&k.sfwork, sizeof(int2) * std::max<size_t>(1, items.size())));
-        CPM_CUDA(c, cudaMemcpyAsync(k.sfwork, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
-                                    c->stream));
-    }
     int64_t* cnt = nullptr;
     CPM_TRY(dev_alloc(c, (void**)&cnt, k.ncols * sizeof(int64_t)));
     k_colcounts<<<(k.ncols + 255) / 256, 256, 0, c->stream>>>(k.cols, k.colext, k.ncols, cnt);

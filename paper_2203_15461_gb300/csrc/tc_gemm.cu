@@ -321,7 +321,8 @@ static cpm_status launch_tc(cpm_ctx* c, const TcMaps& maps, int n, int m, int64_
     typedef TcCfg<BN> C;
     const int mt = (n + TC_BM - 1) / TC_BM, nt = (m + BN - 1) / BN;
     const int ksteps = (int)(ld / TC_BK);
-    int splits = std::max(1, std::min(ksteps, (2 * 152 + mt * nt - 1) / (mt * nt)));
+    // about one wave of CTAs (one per SM): longer K ranges per CTA keep the TMA/MMA pipeline full
+    int splits = std::max(1, std::min(ksteps, 152 / (mt * nt)));
     const int kchunk_steps = (ksteps + splits - 1) / splits;
     splits = (ksteps + kchunk_steps - 1) / kchunk_steps;
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sb<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));

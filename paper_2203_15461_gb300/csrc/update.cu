@@ -103,6 +103,60 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv_t(const TS* __restrict__ S, co
     }
 }
 
+// Single-precision variant of k_gemv_t: the hi/lo pairs of b are staged jj-major in shared memory so
+// one 16-byte load serves two replicas, and eight loads of S are in flight before use.
+__global__ void __launch_bounds__(GT_COLS) k_gemv32(const float* __restrict__ S, const float2* __restrict__ bv,
+                                                   int64_t n, int m, int64_t jchunk, double* __restrict__ part) {
+    __shared__ __align__(16) float2 bs[GT_JT][GT_MR];
+    const int64_t i = (int64_t)blockIdx.x * GT_COLS + threadIdx.x;
+    const int split = blockIdx.y;
+    const int r0 = blockIdx.z * GT_MR;
+    const int mm = min(GT_MR, m - r0);
+    const int64_t jb = (int64_t)split * jchunk, je = min(n, jb + jchunk);
+    float2 bi[GT_MR];
+    LaneSum<float> acc[GT_MR];
+#pragma unroll
+    for (int t = 0; t < GT_MR; ++t) bi[t] = (t < mm && i < n) ? bv[(int64_t)(r0 + t) * n + i] : make_float2(0.f, 0.f);
+    for (int64_t j0 = jb; j0 < je; j0 += GT_JT) {
+        for (int e = threadIdx.x; e < GT_MR * GT_JT; e += GT_COLS) {
+            const int t = e / GT_JT, jj = e % GT_JT;
+            const int64_t j = j0 + jj;
+            bs[jj][t] = (t < mm && j < je) ? bv[(int64_t)(r0 + t) * n + j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int jn = (int)min((int64_t)GT_JT, je - j0);
+        if (i < n) {
+            int jj = 0;
+            for (; jj + 8 <= jn; jj += 8) {
+                float sv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sv[u] = S[(j0 + jj + u) * n + i];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4* row = reinterpret_cast<const float4*>(bs[jj + u]);
+#pragma unroll
+                    for (int tp = 0; tp < GT_MR / 2; ++tp) {
+                        const float4 v = row[tp];
+                        acc[2 * tp].add(sv[u] * ((v.x - bi[2 * tp].x) + (v.y - bi[2 * tp].y)));
+                        acc[2 * tp + 1].add(sv[u] * ((v.z - bi[2 * tp + 1].x) + (v.w - bi[2 * tp + 1].y)));
+                    }
+                }
+            }
+            for (; jj < jn; ++jj) {
+                const float sv = S[(j0 + jj) * n + i];
+#pragma unroll
+                for (int t = 0; t < GT_MR; ++t) acc[t].add(sv * ((bs[jj][t].x - bi[t].x) + (bs[jj][t].y - bi[t].y)));
+            }
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+#pragma unroll
+        for (int t = 0; t < GT_MR; ++t)
+            if (t < mm) part[((int64_t)split * m + r0 + t) * n + i] = acc[t].value();
+    }
+}
+
 // q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
 __global__ void k_gemv_reduce(const double* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
                               const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
@@ -214,7 +268,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
         k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
-        k_gemv_t<float><<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
+        k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
     } else {
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
     }
