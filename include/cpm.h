@@ -62,8 +62,12 @@ typedef enum {
 typedef enum {
     CPM_PREC_FP64 = 0,  /* IEEE double throughout */
     CPM_PREC_FP32 = 1,  /* single precision products and accumulation, FP64 neutrality and totals */
-    CPM_PREC_BF16X3 = 2 /* s_prec only: S and b each split into three bf16 terms, six products per
+    CPM_PREC_BF16X3 = 2, /* s_prec only: S and b each split into three bf16 terms, six products per
                            step on the tensor cores (tcgen05), FP32 accumulation, FP64 split sums */
+    CPM_PREC_F16X2 = 3  /* k_prec only: as CPM_PREC_FP32, with the two reciprocal-space contractions
+                           (structure factor, site potentials) on the tensor cores (tcgen05): operands
+                           scaled by powers of two and split into two fp16 terms, three products,
+                           FP32 accumulation */
 } cpm_precision;
 
 typedef struct {

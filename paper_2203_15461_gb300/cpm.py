@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libcpm_gb300.so")
 STATUS = {0: "CPM_OK", 1: "CPM_E_ARG", 2: "CPM_E_OOM", 3: "CPM_E_BUDGET", 4: "CPM_E_NOT_SPD", 5: "CPM_E_STATE",
           6: "CPM_E_CUDA", 7: "CPM_E_TIMEOUT", 8: "CPM_E_NONFINITE"}
 BOUNDARY = {"3d": 0, "slab": 1, "wire": 2}
-PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2, "f16x2": 3}
 MATRIX = {"A": 0, "S": 1, "SG": 2, "u": 3}
 
 

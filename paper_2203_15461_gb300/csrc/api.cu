@@ -127,13 +127,14 @@ static void free_geometry(cpm_ctx* c) {
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
-                    c->sperm, c->schunks};
+                    c->sperm, c->schunks, c->tcz, c->tcxy};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
     c->rtab = nullptr; c->rtab_id = nullptr; c->nrtab = 0;
     c->sperm = nullptr; c->schunks = nullptr; c->nschunk = 0;
+    c->tcz = nullptr; c->tcxy = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -161,7 +162,7 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
     if (!(p->alpha > 0.0) || !(p->rcut > 0.0) || !(p->kcut > 0.0)) return CPM_E_ARG;
     if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_WIRE) return CPM_E_ARG;
     if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32 && p->s_prec != CPM_PREC_BF16X3) ||
-        (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32))
+        (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32 && p->k_prec != CPM_PREC_F16X2))
         return CPM_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -314,6 +315,7 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
     CPM_TRY(launch_phases<double>(st, c->g, k, c->sxyz, n, c->site64.X, c->site64.Y, c->site64.Z));
     CPM_TRY(launch_phases<float>(st, c->g, k, c->sxyz, n, c->site32.X, c->site32.Y, c->site32.Z));
     CPM_LAUNCH(c, "k_phases(sites)");
+    if (c->p.k_prec == CPM_PREC_F16X2) CPM_TRY(tc_recip_prepare(c));
     const size_t nn = (size_t)n * n;
     CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));
     CPM_TRY(dev_alloc(c, (void**)&c->W, sizeof(double) * nn));

@@ -39,10 +39,11 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 
 // ----------------------------------------------------------------------------- per-replica totals
 // stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates; one block per replica.
-__global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* stats) {
-    __shared__ double sh[4][256];
+// With qabs, also (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).
+__global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* stats, float2* qabs) {
+    __shared__ double sh[6][256];
     const int r = blockIdx.x;
-    double a[4] = {0, 0, 0, 0};
+    double a[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
         int64_t p = (int64_t)r * ne + j;
         double q = Q[p];
@@ -50,15 +51,21 @@ __global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* 
         a[1] += q * xyz[3 * p];
         a[2] += q * xyz[3 * p + 1];
         a[3] += q * xyz[3 * p + 2];
+        a[4] = fmax(a[4], fabs(q));
+        a[5] += fabs(q);
     }
-    for (int t = 0; t < 4; ++t) sh[t][threadIdx.x] = a[t];
+    for (int t = 0; t < 6; ++t) sh[t][threadIdx.x] = a[t];
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
+        if ((int)threadIdx.x < o) {
             for (int t = 0; t < 4; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + o];
+            sh[4][threadIdx.x] = fmax(sh[4][threadIdx.x], sh[4][threadIdx.x + o]);
+            sh[5][threadIdx.x] += sh[5][threadIdx.x + o];
+        }
         __syncthreads();
     }
     if (threadIdx.x < 4) stats[4 * r + threadIdx.x] = sh[threadIdx.x][0];
+    if (qabs && threadIdx.x == 0) qabs[r] = make_float2((float)sh[4][0], (float)sh[5][0]);
 }
 
 // ----------------------------------------------------------------------------- cell list
@@ -892,6 +899,8 @@ struct BvecPlan {
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
         off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
     int c0chunks;
+    bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
+    size_t off_qabs, off_tcpart, off_w16;
 };
 
 template <typename T>
@@ -904,6 +913,12 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
+    p.tc = std::is_same<T, float>::value && c->p.k_prec == CPM_PREC_F16X2 && k.nk > 0;
+    TcRecipDims td{};
+    if (p.tc) {
+        td = tc_recip_dims(c, m, ne);
+        p.nctiles = td.ncb;
+    }
     // the single-precision structure factor uses 128-harmonic super-tiles (k_sf32)
     const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
     const int yt = std::is_same<T, float>::value ? 2 * zh2 + 1 : p.ztiles;
@@ -922,8 +937,12 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_EY = o; o += al(sizeof(c2<T>) * tabY);
     p.off_EZ = o; o += al(sizeof(c2<T>) * (pe - tabX - tabY));
     p.off_Q = o; o += al(sizeof(T) * ptot);
-    p.off_rp = o; o += al(sizeof(c2<T>) * grid * m * p.splits);
-    p.off_wr = o; o += al(sizeof(c2<T>) * grid * m);
+    if (p.tc) {   // the CUDA-core structure-factor buffers are not used
+        p.off_rp = p.off_wr = o;
+    } else {
+        p.off_rp = o; o += al(sizeof(c2<T>) * grid * m * p.splits);
+        p.off_wr = o; o += al(sizeof(c2<T>) * grid * m);
+    }
     p.off_part = o; o += al(sizeof(T) * (size_t)m * p.nctiles * c->n);
     p.off_real = o; o += al(sizeof(double) * (size_t)m * c->n);
     p.off_stats = o; o += al(sizeof(double) * 4 * m);
@@ -941,6 +960,12 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
     p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
     p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
+    p.off_qabs = o; o += al(sizeof(float2) * m);
+    p.off_tcpart = p.off_w16 = o;
+    if (p.tc) {
+        p.off_tcpart = o; o += al(tc_recip_part_bytes(td, m, k.nzw));
+        p.off_w16 = o; o += al(tc_recip_w16_bytes(td));
+    }
     p.total = o;
     return p;
 }
@@ -979,7 +1004,8 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     c->launches += 4 + (ptot > 0 ? 3 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
 
     prof_begin(c, CPM_K_STATS);
-    k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats);
+    float2* qabs = (float2*)(scr + p.off_qabs);
+    k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats, p.tc ? qabs : nullptr);
     prof_end(c, CPM_K_STATS);
     CPM_LAUNCH(c, "k_stats");
     prof_begin(c, CPM_K_CELLS);
@@ -1016,6 +1042,10 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_begin(c, CPM_K_PHASES);
         CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ));
         prof_end(c, CPM_K_PHASES);
+        if (p.tc) {
+            CPM_TRY(tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const float2*)EZ, (const float*)Qv,
+                                 qabs, scr + p.off_tcpart, scr + p.off_w16, (float*)part));
+        } else {
         prof_begin(c, CPM_K_SF);
         if (std::is_same<T, float>::value) {
             const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
@@ -1051,6 +1081,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         }
         prof_end(c, CPM_K_SITE);
         CPM_LAUNCH(c, "k_site");
+        }
     } else {
         CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, st));
     }
@@ -1083,12 +1114,12 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
 }
 
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
-    const bool f32 = c->p.k_prec == CPM_PREC_FP32;
+    const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }
 
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out) {
-    const bool f32 = c->p.k_prec == CPM_PREC_FP32;
+    const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     const size_t need = f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne);
     CPM_TRY(ensure_scratch(c, need));
     char* scr = (char*)c->scratch;

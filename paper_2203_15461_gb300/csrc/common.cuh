@@ -153,6 +153,9 @@ struct cpm_ctx {
     bool tc_use_z = false;
     void* tbuf = nullptr;        // tensor-core update scratch (K-split partials, b planes)
     size_t tbuf_bytes = 0;
+    void* tcz = nullptr;         // tensor-core reciprocal space: site phase planes [2][npad][KZ] (fp16)
+    float2* tcxy = nullptr;      // [ncols][n] column factors X_i Y_i of the sites
+    float tc_wmax = 0.f;         // bound on the k-space weights
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 
@@ -232,5 +235,20 @@ cpm_status reserve_update(cpm_ctx* c, int m);
 cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);
 cpm_status tc_reserve(cpm_ctx* c, int m);
 cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms);
+
+// tc_recip.cu: reciprocal-space sums of b on the tensor cores (k_prec = CPM_PREC_F16X2)
+struct TcRecipDims {
+    int mtiles, ntiles, cpad, splits;   // stage 1: column tiles, harmonic tiles, padded columns, charge splits
+    int64_t chunk;                      // charges per split
+    int mr, nrb, CT, ncb, NB, ngroups;  // stage 2: replicas per block, blocks, columns per group, ...
+    int KZ;                             // padded K extent (2 x harmonics)
+    int64_t npad;                       // padded site count
+};
+TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne);
+size_t tc_recip_part_bytes(const TcRecipDims& d, int m, int nzw);
+size_t tc_recip_w16_bytes(const TcRecipDims& d);
+cpm_status tc_recip_prepare(cpm_ctx* c);
+cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const float2* EZ,
+                        const float* Qv, const float2* qabs, void* part, void* w16, float* site_partial);
 
 }  // namespace cpm

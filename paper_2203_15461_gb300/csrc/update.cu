@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv_t(const TS* __restrict__ S, co
 }
 
 // Single-precision variant of k_gemv_t: the hi/lo pairs of b are staged jj-major in shared memory so
-// one 16-byte load serves two replicas, and eight loads of S are in flight before use.
+// one 16-byte load serves two replicas, and eight loads of S are in flight before use.  Each tile
+// of GT_JT terms is summed plainly in FP32 as S_ij (hi_j - hi_i) + S_ij lo_j (the hi difference
+// is exact; centring the tiny lo part would change nothing), and the tile sums are added with
+// compensation.
 __global__ void __launch_bounds__(GT_COLS) k_gemv32(const float* __restrict__ S, const float2* __restrict__ bv,
                                                    int64_t n, int m, int64_t jchunk, double* __restrict__ part) {
     __shared__ __align__(16) float2 bs[GT_JT][GT_MR];
@@ -126,6 +129,9 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv32(const float* __restrict__ S,
         __syncthreads();
         const int jn = (int)min((int64_t)GT_JT, je - j0);
         if (i < n) {
+            float tile[GT_MR];
+#pragma unroll
+            for (int t = 0; t < GT_MR; ++t) tile[t] = 0.f;
             int jj = 0;
             for (; jj + 8 <= jn; jj += 8) {
                 float sv[8];
@@ -137,16 +143,23 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv32(const float* __restrict__ S,
 #pragma unroll
                     for (int tp = 0; tp < GT_MR / 2; ++tp) {
                         const float4 v = row[tp];
-                        acc[2 * tp].add(sv[u] * ((v.x - bi[2 * tp].x) + (v.y - bi[2 * tp].y)));
-                        acc[2 * tp + 1].add(sv[u] * ((v.z - bi[2 * tp + 1].x) + (v.w - bi[2 * tp + 1].y)));
+                        tile[2 * tp] = fmaf(sv[u], v.x - bi[2 * tp].x, tile[2 * tp]);
+                        tile[2 * tp] = fmaf(sv[u], v.y, tile[2 * tp]);
+                        tile[2 * tp + 1] = fmaf(sv[u], v.z - bi[2 * tp + 1].x, tile[2 * tp + 1]);
+                        tile[2 * tp + 1] = fmaf(sv[u], v.w, tile[2 * tp + 1]);
                     }
                 }
             }
             for (; jj < jn; ++jj) {
                 const float sv = S[(j0 + jj) * n + i];
 #pragma unroll
-                for (int t = 0; t < GT_MR; ++t) acc[t].add(sv * ((bs[jj][t].x - bi[t].x) + (bs[jj][t].y - bi[t].y)));
+                for (int t = 0; t < GT_MR; ++t) {
+                    tile[t] = fmaf(sv, bs[jj][t].x - bi[t].x, tile[t]);
+                    tile[t] = fmaf(sv, bs[jj][t].y, tile[t]);
+                }
             }
+#pragma unroll
+            for (int t = 0; t < GT_MR; ++t) acc[t].add(tile[t]);
         }
         __syncthreads();
     }
