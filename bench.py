@@ -1,14 +1,15 @@
 """Benchmark of the CPM charge update (b-vector + S (v - b)) on one GB300 per rank.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--replicas M]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--replicas M] [--k-prec P]
 
 Workload: the 4,320-site graphene-like EDL capacitor (3 layers per electrode, 60 A gap,
 1,800 rigid 3-site waters + 150 Na+ + 150 Cl-, slab correction).  One step updates
 M independent replicas of that system (each its own seeded electrolyte, positions
 random-walked by N(0, 0.05 A) per step): b for every replica, then q = S (v - b) and
 the FP64 neutrality fix.  ``value`` is updates per second (replica-updates) of the
-mixed path (FP32 b and S, FP64 neutrality and totals); the plain FP64 path is timed
-beside it.  Inputs are resident in HBM; L2 is flushed (256 MB write) before every
+mixed path (FP32 b and S, FP64 neutrality and totals; by default the two reciprocal-space
+contractions of b run on the tensor cores as two-term fp16 products, ``--k-prec fp32``
+keeps them on the CUDA cores); the plain FP64 path is timed beside it.  Inputs are resident in HBM; L2 is flushed (256 MB write) before every
 timed step and only the step itself is inside the CUDA events.
 """
 from __future__ import annotations
@@ -170,12 +171,16 @@ def real_pairs(el, xyz_steps, Q, ne, m, step):
     return tot
 
 
-def kernel_work(ctx, el, nk, ne, m, pairs=None):
-    """Algorithmic work per launch of the per-step kernels (flops or bytes), see the design doc."""
+def kernel_work(ctx, el, nk, ne, m, pairs=None, tensor=False):
+    """Algorithmic work per launch of the per-step kernels (flops or bytes), see the design doc.
+
+    With ``tensor`` the two reciprocal contractions run on the tensor cores ("tflop": the same
+    algorithmic flops, measured against the tensor-core peak of the emulated FP32 product)."""
     n = el.n
+    fk = "tflop" if tensor else "flop"
     w = {
-        "sf": ("flop", 8.0 * ne * nk * m),            # one complex multiply-add per (charge, k)
-        "site": ("flop", 8.0 * n * nk * m),           # one complex multiply-add per (site, k)
+        "sf": (fk, 8.0 * ne * nk * m),                # one complex multiply-add per (charge, k)
+        "site": (fk, 8.0 * n * nk * m),               # one complex multiply-add per (site, k)
         "gemv": ("byte", 4.0 * n * n * ((m + 7) // 8)),   # S streamed once (FP32) per 8 replicas
     }
     if pairs is not None:
@@ -214,15 +219,15 @@ def cpu_baseline(el, ely, psi, frac=8):
             "sample_seconds": t5 - t0}
 
 
-def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256):
+def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256, k_prec="fp32"):
     """256 replicas of the 216-site Au(111) capacitor per step (one shared S), graph-captured."""
     el, _, psi = s.workload_tiny_slab(seed=1)
     xyz, Q, ne = make_trajectories(el, lambda sd: s.ions_in_gap(el, 100, seed=sd), m, K + W, 5000)
-    out = {"workload": "au111_tiny_216 x 256 replicas", "replicas_per_step": m}
+    out = {"workload": "au111_tiny_216 x 256 replicas", "replicas_per_step": m, "k_prec": k_prec}
     for s_prec in ("fp32", "bf16x3"):
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
-            ctx = CPM.for_electrodes(el, s_prec=s_prec, k_prec="fp32", stream=st).setup(el)
+            ctx = CPM.for_electrodes(el, s_prec=s_prec, k_prec=k_prec, stream=st).setup(el)
             dx = torch.as_tensor(xyz[0], device="cuda").clone()
             dQ = torch.as_tensor(Q, device="cuda")
             dp = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
@@ -251,12 +256,12 @@ def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256):
     return out
 
 
-def bench_serving(torch, s, n_req=600, rate=4000.0):
+def bench_serving(torch, s, n_req=600, rate=4000.0, k_prec="fp32"):
     """Poisson stream of charge-update requests over three slab geometries (216, 512 and 2,048 sites)."""
     from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
     geoms = {"au111_216": s.workload_tiny_slab(seed=1)[0], "graphene_512": s.workload_serving_geometry(512)[0],
              "graphene_2048": s.workload_serving_geometry(2048)[0]}
-    be = GpuBackend(s_prec="fp32", k_prec="fp32", max_batch=16)
+    be = GpuBackend(s_prec="fp32", k_prec=k_prec, max_batch=16)
     sch = Scheduler(be, hbm_budget=4 << 30, max_batch=16)
     for k, el in geoms.items():
         sch.add_geometry(k, el, context_bytes(el.n, 2 * el.n, 16))
@@ -278,7 +283,8 @@ def bench_serving(torch, s, n_req=600, rate=4000.0):
     wall = run_stream(reqs, sch, arrivals=arrivals)
     st = latency_stats(sch.finished)
     st.update({"requests": n_req, "offered_rate_per_s": rate, "updates_per_s": n_req / wall,
-               "geometries": {k: el.n for k, el in geoms.items()}, "max_batch": 16, "path": "mixed"})
+               "geometries": {k: el.n for k, el in geoms.items()}, "max_batch": 16, "path": "mixed",
+               "k_prec": k_prec})
     return st
 
 
@@ -316,6 +322,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--replicas", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k-prec", default="f16x2", choices=["fp32", "f16x2"],
+                    help="b-vector arithmetic of the mixed path (f16x2: reciprocal sums on the tensor cores)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     args.steps = max(1, args.steps)
@@ -345,7 +353,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     t_setup = time.perf_counter()
-    mixed = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32").setup(el)
+    mixed = CPM.for_electrodes(el, s_prec="fp32", k_prec=args.k_prec).setup(el)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     plain = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64").setup(el)
@@ -396,18 +404,25 @@ def main():
            "d2h_bytes_per_step": int(8 * (m * el.n + m))}
 
     # batched replicas of the tiny capacitor: 256 electrolytes sharing one S, one CUDA graph per step
-    batched = bench_batched_tiny(torch, CPM, s, flush, K, W)
+    batched = bench_batched_tiny(torch, CPM, s, flush, K, W, k_prec=args.k_prec)
     # serving stream: Poisson arrivals over three geometries, continuous batching
-    serving = bench_serving(torch, s)
+    serving = bench_serving(torch, s, k_prec=args.k_prec)
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
     pairs = real_pairs(el, xyz, Q, ne, m, W)
-    work = kernel_work(mixed, el, nk, ne, m, pairs)
+    work = kernel_work(mixed, el, nk, ne, m, pairs, tensor=args.k_prec == "f16x2")
     top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
     avg_ms = prof[top][0] / prof[top][1]
     kind, amount = work.get(top, ("flop", float("nan")))
-    if kind == "flop":
+    if kind == "tflop":
+        # fp16 tensor rate = the measured bf16 rate (same nominal peak); three fp16 products per FP32 product
+        peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
+        achieved = amount / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": f"k_tc_{top}", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"bf16_tflops ({src}) / 3: two-term fp16 operands, three products per FP32 product"}
+    elif kind == "flop":
         peak = _fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         achieved = amount / (avg_ms / 1e3) / 1e12
         roof = {"kernel": f"k_{top}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -421,8 +436,8 @@ def main():
     roof["share_of_step"] = prof[top][0] / ms
     roof["all_kernels"] = {kk: {"ms_per_launch": prof[kk][0] / max(1, prof[kk][1]),
                                 "achieved": (work[kk][1] / (prof[kk][0] / max(1, prof[kk][1]) / 1e3)
-                                             / (1e12 if work[kk][0] == "flop" else 1e9)),
-                                "unit": "TFLOP/s" if work[kk][0] == "flop" else "GB/s"}
+                                             / (1e9 if work[kk][0] == "byte" else 1e12)),
+                                "unit": "GB/s" if work[kk][0] == "byte" else "TFLOP/s"}
                            for kk in work if kk in prof and prof[kk][1] > 0}
     roof["pairs_in_rcut_per_launch"] = pairs
 
@@ -430,7 +445,10 @@ def main():
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_sites": el.n, "n_charges": ne, "n_kvectors": nk,
-                       "replicas_per_step": m, "path": "mixed: FP32 b and S, FP64 neutrality and totals",
+                       "replicas_per_step": m, "k_prec": args.k_prec,
+                       "path": ("mixed: FP32 b (reciprocal sums as fp16x2 tensor-core products) and S, FP64 "
+                                "neutrality and totals" if args.k_prec == "f16x2" else
+                                "mixed: FP32 b and S, FP64 neutrality and totals"),
                        "boundary": "slab EW3DC", "alpha": el.alpha, "rcut": el.rcut,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,

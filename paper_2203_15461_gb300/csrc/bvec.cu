@@ -913,7 +913,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
     p.nctiles = p.ctiles;
-    p.tc = std::is_same<T, float>::value && c->p.k_prec == CPM_PREC_F16X2 && k.nk > 0;
+    p.tc = std::is_same<T, float>::value && c->p.k_prec == CPM_PREC_F16X2 && tc_recip_supported(k);
     TcRecipDims td{};
     if (p.tc) {
         td = tc_recip_dims(c, m, ne);

@@ -244,6 +244,7 @@ struct TcRecipDims {
     int KZ;                             // padded K extent (2 x harmonics)
     int64_t npad;                       // padded site count
 };
+bool tc_recip_supported(const KTable& k);   // phase-table rows fit the staging buffer
 TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne);
 size_t tc_recip_part_bytes(const TcRecipDims& d, int m, int nzw);
 size_t tc_recip_w16_bytes(const TcRecipDims& d);

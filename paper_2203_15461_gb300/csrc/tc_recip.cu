@@ -45,7 +45,9 @@ constexpr int RF_A = RF_BM * 128;              // one fp16 term of the P tile (1
 constexpr int RF_B = 2 * RF_ZT * 128;          // one fp16 term of the Z tile (32 KB)
 constexpr int RF_STAGE = 2 * RF_A + 2 * RF_B;  // 96 KB
 constexpr int RF_STAGES = 2;
-constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048;
+constexpr int RF_XYROWS = 60;                 // staged phase-table rows: (NX + 1) + (2 NY + 1) at most
+constexpr int RF_STAGE_XY = (RF_XYROWS + 1) * RF_KC * 8;   // X, Y rows and Q of one K step
+constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048 + RF_STAGE_XY;
 constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14
 
 // stage 2 (site potentials)
@@ -57,6 +59,8 @@ constexpr int RS_STAGE = 2 * RS_A + 2 * RS_BMAX;
 constexpr int RS_STAGES = 2;
 constexpr int RS_SMEM = 1024 + RS_STAGES * RS_STAGE + 256;
 constexpr int RS_ZEXP = 14;                    // site phases scaled by 2^14
+constexpr int RS_CT = 16;                      // columns per group (N = 2 x 16 x replicas of the group)
+constexpr int RS_MR = 8;                       // replicas per group
 
 // 2^e with bound * 2^e < 2^top; 1 for a zero or non-finite bound
 __device__ __forceinline__ float pow2_below(float bound, int top) {
@@ -77,6 +81,21 @@ __device__ __forceinline__ void split2(float2 v, uint32_t& hi, uint32_t& lo) {
 __device__ __forceinline__ uint32_t neg_hi(uint32_t h) { return h ^ 0x80000000u; }            // (a, b) -> (a, -b)
 __device__ __forceinline__ uint32_t swap_h(uint32_t h) { return __byte_perm(h, 0u, 0x1032); }  // (a, b) -> (b, a)
 
+// barrier 1 over the 256 operand-building threads; returns the AND of every thread's flag
+__device__ __forceinline__ bool gen_bar_and(bool flag) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(out)
+        : "r"((uint32_t)flag)
+        : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -87,7 +106,7 @@ __device__ __forceinline__ uint32_t sw128(int r, int ch) { return (uint32_t)(r *
 // part[s][r][zi][c] = 2^14 sA_r sum over the charges of split s of P_r[c][j] Z_j[zi]   (zi = nz + NZ)
 // grid (column tiles, harmonic tiles, m * splits); sA_r = 2^e with |Q| sA_r < 2^14.
 __global__ void __launch_bounds__(RF_THREADS, 1)
-    k_tc_sf(const int2* __restrict__ cols, const int* __restrict__ colext, int ncols, int NY, int NZ, int nzw,
+    k_tc_sf(const int2* __restrict__ cols, const int* __restrict__ colext, int ncols, int NX, int NY, int NZ, int nzw,
             const float2* __restrict__ EX, const float2* __restrict__ EY, const float2* __restrict__ EZ,
             const float* __restrict__ Qv, const float2* __restrict__ qabs, int64_t ptot, int64_t ne, int splits,
             int64_t chunk, int m, int cpad, float2* __restrict__ part, unsigned* __restrict__ status,
@@ -144,30 +163,77 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp < RF_GEN / 32) {
-        // operand builders: P tile (128 columns x 32 charges) and Z tile (2 x zcount rows x 32 charges)
+        // Operand builders.  Thread g owns 16-byte chunk ch = g % 8 (charges 4 ch .. 4 ch + 3 of the
+        // step) of P rows g / 8 + 32 k and of Z row pairs g / 8 + 32 k.  The X and Y table rows and
+        // the charges of a step are staged in shared memory; the loads of step t + 1 (staging
+        // entries and Z values) are issued before the tiles of step t are built.
         const float sA = pow2_below(qabs[r].x, 14);
-        const int g = threadIdx.x;
-        for (int t = 0; t < nsteps; ++t) {
-            const int s = t % RF_STAGES;
-            if (t >= RF_STAGES && !mbar_wait(&empty[s], ((t / RF_STAGES) - 1) & 1, abort, wait_ns)) break;
-            const uint32_t sa = su32(smem + s * RF_STAGE);
-            const uint32_t sb = sa + 2 * RF_A;
+        const int g = threadIdx.x, ch = g & 7, rbase = g >> 3;
+        const int xyrows = (NX + 1) + (2 * NY + 1);
+        const int nst = (xyrows + 1) * RF_KC;
+        float2* sxy = (float2*)(aux + 2048);
+        float2 px[8], pz[4][4];
+        auto prefetch = [&](int t) {
             const int64_t j0 = jb + (int64_t)t * RF_KC;
-#pragma unroll 2
-            for (int e = g; e < RF_BM * 8; e += RF_GEN) {
-                const int row = e >> 3, ch = e & 7;
-                const int2 cn = s_cols[row];
-                const bool live = c0 + row < ncols;
-                const float2* xr = EX + (int64_t)cn.x * ptot;
-                const float2* yr = EY + (int64_t)(cn.y + NY) * ptot;
-                uint32_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = g + RF_GEN * k;
+                float2 v = make_float2(0.f, 0.f);
+                if (e < nst) {
+                    const int row = e >> 5;
+                    const int64_t j = j0 + (e & 31);
+                    if (j < je) {
+                        if (row <= NX) v = EX[(int64_t)row * ptot + j];
+                        else if (row < xyrows) v = EY[(int64_t)(row - NX - 1) * ptot + j];
+                        else v = make_float2(Qv[j] * sA, 0.f);
+                    }
+                }
+                px[k] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int zr = rbase + 32 * k;
+                const float2* zrow = EZ + (int64_t)(z_lo + min(zr, zcount - 1)) * ptot;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t j = j0 + 4 * ch + u;
+                    pz[k][u] = (zr < zcount && j < je) ? zrow[j] : make_float2(0.f, 0.f);
+                }
+            }
+        };
+        if (nsteps > 0) prefetch(0);
+        for (int t = 0; t < nsteps; ++t) {
+            const int s = t % RF_STAGES;
+            bool ok = true;
+            if (t >= RF_STAGES) ok = mbar_wait(&empty[s], ((t / RF_STAGES) - 1) & 1, abort, wait_ns);
+            if (!gen_bar_and(ok)) break;   // uniform; also: everyone is done reading the staged step t - 1
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (g + RF_GEN * k < nst) sxy[g + RF_GEN * k] = px[k];
+            float2 cz[4][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cz[k][u] = pz[k][u];
+            gen_bar();
+            if (t + 1 < nsteps) prefetch(t + 1);
+            const uint32_t sa = su32(smem + s * RF_STAGE);
+            const uint32_t sb = sa + 2 * RF_A;
+            const float2* sq = sxy + xyrows * RF_KC + 4 * ch;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int row = rbase + 32 * k;
+                const int2 cn = s_cols[row];
+                const bool live = c0 + row < ncols;
+                const float2* xr = sxy + cn.x * RF_KC + 4 * ch;
+                const float2* yr = sxy + (NX + 1 + cn.y + NY) * RF_KC + 4 * ch;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
                     float2 p = make_float2(0.f, 0.f);
-                    if (live && j < je) {
-                        const float2 x = xr[j], y = yr[j];
-                        const float q = Qv[j] * sA;
+                    if (live) {
+                        const float2 x = xr[u], y = yr[u];
+                        const float q = sq[u].x;
                         p = make_float2((x.x * y.x - x.y * y.y) * q, (x.x * y.y + x.y * y.x) * q);
                     }
                     split2(p, h[u], l[u]);
@@ -176,17 +242,14 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 sts128(sa + off, h[0], h[1], h[2], h[3]);
                 sts128(sa + RF_A + off, l[0], l[1], l[2], l[3]);
             }
-#pragma unroll 2
-            for (int e = g; e < zcount * 8; e += RF_GEN) {
-                const int zr = e >> 3, ch = e & 7;
-                const float2* zrow = EZ + (int64_t)(z_lo + zr) * ptot;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int zr = rbase + 32 * k;
+                if (zr >= zcount) continue;
                 uint32_t h[4], l[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t j = j0 + 4 * ch + u;
-                    const float2 z = j < je ? zrow[j] : make_float2(0.f, 0.f);
-                    split2(make_float2(z.x * RF_ZSCALE, z.y * RF_ZSCALE), h[u], l[u]);
-                }
+                for (int u = 0; u < 4; ++u)
+                    split2(make_float2(cz[k][u].x * RF_ZSCALE, cz[k][u].y * RF_ZSCALE), h[u], l[u]);
                 const uint32_t o0 = sw128(2 * zr, ch), o1 = sw128(2 * zr + 1, ch);
                 sts128(sb + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
                 sts128(sb + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
@@ -255,7 +318,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
 // row (group g, pair p, re) = (Wr, Wi) and row (.., im) = (Wi, -Wr) at K = 2 zi, 2 zi + 1.
 // Groups hold CT columns x mr replicas: g = (r / mr) ncb + c / CT, p = (r % mr) CT + c % CT.
 // One block transposes a 32-harmonic x 32-column tile of one replica slot.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     k_tc_wsplit(const float2* __restrict__ part, int splits, int m, int cpad, int nzw, int NZ,
                 const int* __restrict__ colext, const float* __restrict__ w32, int ncols,
                 const float2* __restrict__ qabs, float wmax, int CT, int mr, int ncb, int NB, int KZ,
@@ -264,44 +327,42 @@ __global__ void __launch_bounds__(256)
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int zb = blockIdx.x * 32, cb0 = blockIdx.y * 32, rp = blockIdx.z;
     const bool rlive = rp < m;
-    float f = 0.f;
-    if (rlive) {
-        const float2 qa = qabs[rp];
-        f = pow2_below(wmax * qa.y, 14) / (pow2_below(qa.x, 14) * RF_ZSCALE);
-    }
-    for (int zl = ty; zl < 32; zl += 8) {
-        const int zi = zb + zl, c = cb0 + tx;
+    {
+        const int zi = zb + ty, c = cb0 + tx;
         float2 W = make_float2(0.f, 0.f);
         if (rlive && c < ncols && zi < nzw) {
             const int ext = colext[c], nz = zi - NZ;
             const float wt = w32[(int64_t)c * nzw + zi];
             if (nz >= -ext && nz <= ext && wt != 0.f) {
+                const float2 qa = qabs[rp];
+                const float f = pow2_below(wmax * qa.y, 14) / (pow2_below(qa.x, 14) * RF_ZSCALE);
                 float sx = 0.f, sy = 0.f;
+                const float2* pp = part + ((int64_t)rp * nzw + zi) * cpad + c;
+                const int64_t sstride = (int64_t)m * nzw * cpad;
+#pragma unroll 4
                 for (int s = 0; s < splits; ++s) {
-                    const float2 v = part[(((int64_t)s * m + rp) * nzw + zi) * cpad + c];
+                    const float2 v = pp[s * sstride];
                     sx += v.x;
                     sy += v.y;
                 }
                 W = make_float2(sx * wt * f, sy * wt * f);
             }
         }
-        tile[zl][tx] = W;
+        tile[ty][tx] = W;
     }
     __syncthreads();
     const int rb = rp / mr, rr = rp % mr;
     const int kw = KZ / 2;
-    for (int cl = ty; cl < 32; cl += 8) {
-        const int c = cb0 + cl, zi = zb + tx;
-        if (c >= ncb * CT || zi >= kw) continue;
-        const int64_t row = (int64_t)(rb * ncb + c / CT) * NB + 2 * (rr * CT + c % CT);
-        uint32_t h, l;
-        split2(tile[tx][cl], h, l);
-        const int64_t w0 = row * kw + zi;
-        w16[w0] = h;
-        w16[w0 + kw] = neg_hi(swap_h(h));
-        w16[plane_words + w0] = l;
-        w16[plane_words + w0 + kw] = neg_hi(swap_h(l));
-    }
+    const int c = cb0 + ty, zi = zb + tx;
+    if (c >= ncb * CT || zi >= kw) return;
+    const int64_t row = (int64_t)(rb * ncb + c / CT) * NB + 2 * (rr * CT + c % CT);
+    uint32_t h, l;
+    split2(tile[tx][ty], h, l);
+    const int64_t w0 = row * kw + zi;
+    w16[w0] = h;
+    w16[w0 + kw] = neg_hi(swap_h(h));
+    w16[plane_words + w0] = l;
+    w16[plane_words + w0 + kw] = neg_hi(swap_h(l));
 }
 
 // ----------------------------------------------------------------------------- stage 2
@@ -310,10 +371,11 @@ struct SiteMaps {
     CUtensorMap b[2];
 };
 
-// partial[r][cb][i] = sum over the CT columns of block cb of Re[conj(X_i Y_i) T_r[c][i]]
-// grid (site tiles, replica blocks x column blocks)
+// partial[r][cb][i] = sum over the 16 columns of block cb of Re[conj(X_i Y_i) T_r[c][i]]
+// grid (site tiles, replica blocks x column blocks); group g holds mr <= 8 replicas x 16 columns,
+// TMEM columns 32 rr + 2 cc + {re, im}.
 __global__ void __launch_bounds__(RS_THREADS, 1)
-    k_tc_site(const __grid_constant__ SiteMaps maps, const int* __restrict__ colext, int ncols, int NZ, int CT,
+    k_tc_site(const __grid_constant__ SiteMaps maps, const int* __restrict__ colext, int ncols, int NZ,
               int mr, int ncb, int NB, int m, const float2* __restrict__ XY, int64_t n,
               const float2* __restrict__ qabs, float wmax, float* __restrict__ partial,
               unsigned* __restrict__ status, uint64_t wait_ns) {
@@ -328,7 +390,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.y, rb = g / ncb, cb = g % ncb;
-    const int cfirst = cb * CT, clast = min(ncols, cfirst + CT);
+    const int cfirst = cb * RS_CT, clast = min(ncols, cfirst + RS_CT);
     if (warp == 0) {
         int mx = -1;
         for (int c = cfirst + lane; c < clast; c += 32) mx = max(mx, colext[c]);
@@ -399,40 +461,37 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         umma_commit(done);
     }
     if (warp < 4) {
+        // the column factors of this thread's site, loaded while the products run
+        const int64_t i = (int64_t)blockIdx.x * RS_BM + warp * 32 + lane;
+        float2 xy[RS_CT];
+#pragma unroll
+        for (int u = 0; u < RS_CT; ++u) {
+            const int c = cfirst + u;
+            xy[u] = (c < clast && i < n) ? XY[(int64_t)c * n + i] : make_float2(0.f, 0.f);
+        }
         const bool ok = mbar_wait(done, 0, abort, wait_ns);
         tc_fence_after();
         const bool good = __all_sync(0xffffffffu, ok && !*abort) != 0;
         if (good) {
-            const int64_t i = (int64_t)blockIdx.x * RS_BM + warp * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
             const float zinv = ldexpf(1.f, -RS_ZEXP);
-            int rr = 0, cc = 0;
-            float acc = 0.f;
-            for (int q0 = 0; q0 < NB; q0 += 16) {
-                float v[16];
+            for (int rr = 0; rr < mr; ++rr) {
+                float v[2 * RS_CT];
                 if (nsteps > 0) {
-                    tmem_ld16(trow + q0, v);
+                    tmem_ld32(trow + 2 * RS_CT * rr, v);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) v[k] = 0.f;
+                    for (int k = 0; k < 2 * RS_CT; ++k) v[k] = 0.f;
                 }
+                float acc = 0.f;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int c = cfirst + cc;
-                    if (rr < mr && c < clast && i < n) {
-                        const float2 xy = XY[(int64_t)c * n + i];
-                        acc = fmaf(xy.x, v[2 * u], acc);
-                        acc = fmaf(xy.y, v[2 * u + 1], acc);
-                    }
-                    if (++cc == CT) {
-                        const int r = rb * mr + rr;
-                        if (rr < mr && r < m && i < n)
-                            partial[((int64_t)r * ncb + cb) * n + i] = acc * (zinv / pow2_below(wmax * qabs[r].y, 14));
-                        acc = 0.f;
-                        cc = 0;
-                        ++rr;
-                    }
+                for (int u = 0; u < RS_CT; ++u) {
+                    acc = fmaf(xy[u].x, v[2 * u], acc);
+                    acc = fmaf(xy[u].y, v[2 * u + 1], acc);
                 }
+                const int r = rb * mr + rr;
+                if (r < m && i < n)
+                    partial[((int64_t)r * ncb + cb) * n + i] = acc * (zinv / pow2_below(wmax * qabs[r].y, 14));
             }
         } else if (lane == 0) {
             atomicOr(status, ST_TIMEOUT);
@@ -476,6 +535,8 @@ __global__ void k_tc_site_xy(const double2* __restrict__ SX, const double2* __re
 }
 
 // ----------------------------------------------------------------------------- host side
+bool tc_recip_supported(const KTable& k) { return k.nk > 0 && (k.NX + 1) + (2 * k.NY + 1) <= RF_XYROWS; }
+
 TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne) {
     const KTable& k = c->kt;
     TcRecipDims d;
@@ -487,11 +548,11 @@ TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne) {
     d.splits = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, 152 / base), maxs));
     d.chunk = (ne + d.splits - 1) / d.splits;
     d.chunk = ((d.chunk + RF_KC - 1) / RF_KC) * RF_KC;
-    d.mr = std::min(m, 128);
+    d.mr = std::min(m, RS_MR);
     d.nrb = (m + d.mr - 1) / d.mr;
-    d.CT = std::max(1, 128 / d.mr);
+    d.CT = RS_CT;
     d.ncb = (k.ncols + d.CT - 1) / d.CT;
-    d.NB = ((2 * d.CT * d.mr + 15) / 16) * 16;
+    d.NB = 2 * d.CT * d.mr;
     d.ngroups = d.nrb * d.ncb;
     d.KZ = ((2 * k.nzw + 63) / 64) * 64;
     d.npad = ((c->n + RS_BM - 1) / RS_BM) * RS_BM;
@@ -510,7 +571,7 @@ cpm_status tc_recip_prepare(cpm_ctx* c) {
     dev_free(c, c->tcxy);
     c->tcz = nullptr;
     c->tcxy = nullptr;
-    if (k.nk == 0 || k.ncols == 0) return CPM_OK;
+    if (!tc_recip_supported(k)) return CPM_OK;
     const TcRecipDims d = tc_recip_dims(c, 1, 0);
     const int64_t n = c->n;
     CPM_TRY(dev_alloc(c, &c->tcz, sizeof(uint16_t) * 2 * (size_t)d.npad * d.KZ));
@@ -544,7 +605,7 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
     prof_begin(c, CPM_K_SF);
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, RF_SMEM));
     k_tc_sf<<<dim3(d.mtiles, d.ntiles, m * d.splits), RF_THREADS, RF_SMEM, st>>>(
-        k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, qabs, ptot, ne, d.splits, d.chunk, m, d.cpad,
+        k.cols, k.colext, k.ncols, k.NX, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, qabs, ptot, ne, d.splits, d.chunk, m, d.cpad,
         (float2*)part, c->status, RT_WAIT_NS);
     prof_end(c, CPM_K_SF);
     CPM_LAUNCH(c, "k_tc_sf");
@@ -553,7 +614,7 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
     const int64_t plane_words = (int64_t)d.ngroups * d.NB * (d.KZ / 2);
     if (d.NB != 2 * d.CT * d.mr) CPM_CUDA(c, cudaMemsetAsync(w16, 0, tc_recip_w16_bytes(d), st));
     dim3 gw((unsigned)((d.KZ / 2 + 31) / 32), (unsigned)((d.ncb * d.CT + 31) / 32), (unsigned)(d.nrb * d.mr));
-    k_tc_wsplit<<<gw, 256, 0, st>>>((const float2*)part, d.splits, m, d.cpad, k.nzw, k.NZ, k.colext, k.w32, k.ncols,
+    k_tc_wsplit<<<gw, 1024, 0, st>>>((const float2*)part, d.splits, m, d.cpad, k.nzw, k.NZ, k.colext, k.w32, k.ncols,
                                     qabs, c->tc_wmax, d.CT, d.mr, d.ncb, d.NB, d.KZ, (uint32_t*)w16, plane_words);
     prof_end(c, CPM_K_SFRED);
     CPM_LAUNCH(c, "k_tc_wsplit");
@@ -570,7 +631,7 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
     }
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_site, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM));
     k_tc_site<<<dim3((unsigned)(d.npad / RS_BM), (unsigned)d.ngroups), RS_THREADS, RS_SMEM, st>>>(
-        maps, k.colext, k.ncols, k.NZ, d.CT, d.mr, d.ncb, d.NB, m, c->tcxy, n, qabs, c->tc_wmax, site_partial,
+        maps, k.colext, k.ncols, k.NZ, d.mr, d.ncb, d.NB, m, c->tcxy, n, qabs, c->tc_wmax, site_partial,
         c->status, RT_WAIT_NS);
     prof_end(c, CPM_K_SITE);
     CPM_LAUNCH(c, "k_tc_site");
