@@ -38,15 +38,18 @@ CellGrid make_grid(const Geometry& g) {
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // ----------------------------------------------------------------------------- per-replica totals
-// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates; one block per replica.
+// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates; one block of 1,024
+// threads per replica, warp shuffles then one pass over the warps (fixed order).
 // With qabs, also (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).
-__global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* stats, float2* qabs) {
-    __shared__ double sh[6][256];
-    const int r = blockIdx.x;
+constexpr int ST_THREADS = 1024;
+__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const double* Q, int64_t ne, double* stats,
+                                                     float2* qabs) {
+    __shared__ double sh[6][ST_THREADS / 32];
+    const int r = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double a[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
-        int64_t p = (int64_t)r * ne + j;
-        double q = Q[p];
+    for (int64_t j = threadIdx.x; j < ne; j += ST_THREADS) {
+        const int64_t p = (int64_t)r * ne + j;
+        const double q = Q[p];
         a[0] += q;
         a[1] += q * xyz[3 * p];
         a[2] += q * xyz[3 * p + 1];
@@ -54,18 +57,25 @@ __global__ void k_stats(const double* xyz, const double* Q, int64_t ne, double* 
         a[4] = fmax(a[4], fabs(q));
         a[5] += fabs(q);
     }
-    for (int t = 0; t < 6; ++t) sh[t][threadIdx.x] = a[t];
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            for (int t = 0; t < 4; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + o];
-            sh[4][threadIdx.x] = fmax(sh[4][threadIdx.x], sh[4][threadIdx.x + o]);
-            sh[5][threadIdx.x] += sh[5][threadIdx.x + o];
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int t = 0; t < 6; ++t) {
+            const double v = __shfl_down_sync(0xffffffffu, a[t], o);
+            a[t] = t == 4 ? fmax(a[t], v) : a[t] + v;
         }
-        __syncthreads();
     }
-    if (threadIdx.x < 4) stats[4 * r + threadIdx.x] = sh[threadIdx.x][0];
-    if (qabs && threadIdx.x == 0) qabs[r] = make_float2((float)sh[4][0], (float)sh[5][0]);
+    if (lane == 0)
+        for (int t = 0; t < 6; ++t) sh[t][warp] = a[t];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int t = threadIdx.x;
+        double v = sh[t][0];
+        for (int w = 1; w < ST_THREADS / 32; ++w) v = t == 4 ? fmax(v, sh[t][w]) : v + sh[t][w];
+        if (t < 4) stats[4 * r + t] = v;
+        else if (qabs) {
+            if (t == 4) qabs[r].x = (float)v;
+            else qabs[r].y = (float)v;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------- cell list
@@ -1005,7 +1015,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
 
     prof_begin(c, CPM_K_STATS);
     float2* qabs = (float2*)(scr + p.off_qabs);
-    k_stats<<<m, 256, 0, st>>>(xyz, Q, ne, stats, p.tc ? qabs : nullptr);
+    k_stats<<<m, ST_THREADS, 0, st>>>(xyz, Q, ne, stats, p.tc ? qabs : nullptr);
     prof_end(c, CPM_K_STATS);
     CPM_LAUNCH(c, "k_stats");
     prof_begin(c, CPM_K_CELLS);

@@ -170,6 +170,88 @@ __global__ void __launch_bounds__(GT_COLS) k_gemv32(const float* __restrict__ S,
     }
 }
 
+// k_gemv32 with two output columns per thread (8-byte loads of S, n even) and sixteen rows of S
+// in flight, so that enough bytes are outstanding to stream S at HBM speed.
+constexpr int G2_T = 256;
+__global__ void __launch_bounds__(G2_T, 2) k_gemv32x2(const float* __restrict__ S, const float2* __restrict__ bv,
+                                                      int64_t n, int m, int64_t jchunk, double* __restrict__ part) {
+    __shared__ __align__(16) float2 bs[GT_JT][GT_MR];
+    const int64_t i0 = ((int64_t)blockIdx.x * G2_T + threadIdx.x) * 2;
+    const int split = blockIdx.y;
+    const int r0 = blockIdx.z * GT_MR;
+    const int mm = min(GT_MR, m - r0);
+    const int64_t jb = (int64_t)split * jchunk, je = min(n, jb + jchunk);
+    const bool live = i0 < n;
+    float bh[2][GT_MR];
+    LaneSum<float> acc[2][GT_MR];
+#pragma unroll
+    for (int t = 0; t < GT_MR; ++t) {
+        bh[0][t] = (t < mm && live) ? bv[(int64_t)(r0 + t) * n + i0].x : 0.f;
+        bh[1][t] = (t < mm && live) ? bv[(int64_t)(r0 + t) * n + i0 + 1].x : 0.f;
+    }
+    for (int64_t j0 = jb; j0 < je; j0 += GT_JT) {
+        for (int e = threadIdx.x; e < GT_MR * GT_JT; e += G2_T) {
+            const int t = e / GT_JT, jj = e % GT_JT;
+            const int64_t j = j0 + jj;
+            bs[jj][t] = (t < mm && j < je) ? bv[(int64_t)(r0 + t) * n + j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int jn = (int)min((int64_t)GT_JT, je - j0);
+        if (live) {
+            float tile[2][GT_MR];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int t = 0; t < GT_MR; ++t) tile[c][t] = 0.f;
+            int jj = 0;
+            for (; jj + 16 <= jn; jj += 16) {
+                float2 sv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) sv[u] = *reinterpret_cast<const float2*>(S + (j0 + jj + u) * n + i0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float4* row = reinterpret_cast<const float4*>(bs[jj + u]);
+#pragma unroll
+                    for (int tp = 0; tp < GT_MR / 2; ++tp) {
+                        const float4 v = row[tp];   // (hi, lo) of replicas 2 tp and 2 tp + 1
+                        tile[0][2 * tp] = fmaf(sv[u].x, v.x - bh[0][2 * tp], tile[0][2 * tp]);
+                        tile[0][2 * tp] = fmaf(sv[u].x, v.y, tile[0][2 * tp]);
+                        tile[1][2 * tp] = fmaf(sv[u].y, v.x - bh[1][2 * tp], tile[1][2 * tp]);
+                        tile[1][2 * tp] = fmaf(sv[u].y, v.y, tile[1][2 * tp]);
+                        tile[0][2 * tp + 1] = fmaf(sv[u].x, v.z - bh[0][2 * tp + 1], tile[0][2 * tp + 1]);
+                        tile[0][2 * tp + 1] = fmaf(sv[u].x, v.w, tile[0][2 * tp + 1]);
+                        tile[1][2 * tp + 1] = fmaf(sv[u].y, v.z - bh[1][2 * tp + 1], tile[1][2 * tp + 1]);
+                        tile[1][2 * tp + 1] = fmaf(sv[u].y, v.w, tile[1][2 * tp + 1]);
+                    }
+                }
+            }
+            for (; jj < jn; ++jj) {
+                const float2 sv = *reinterpret_cast<const float2*>(S + (j0 + jj) * n + i0);
+#pragma unroll
+                for (int t = 0; t < GT_MR; ++t) {
+                    tile[0][t] = fmaf(sv.x, bs[jj][t].x - bh[0][t], tile[0][t]);
+                    tile[0][t] = fmaf(sv.x, bs[jj][t].y, tile[0][t]);
+                    tile[1][t] = fmaf(sv.y, bs[jj][t].x - bh[1][t], tile[1][t]);
+                    tile[1][t] = fmaf(sv.y, bs[jj][t].y, tile[1][t]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int t = 0; t < GT_MR; ++t) acc[c][t].add(tile[c][t]);
+        }
+        __syncthreads();
+    }
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < GT_MR; ++t)
+            if (t < mm) {
+                part[((int64_t)split * m + r0 + t) * n + i0] = acc[0][t].value();
+                part[((int64_t)split * m + r0 + t) * n + i0 + 1] = acc[1][t].value();
+            }
+    }
+}
+
 // q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
 __global__ void k_gemv_reduce(const double* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
                               const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
@@ -185,53 +267,60 @@ __global__ void k_gemv_reduce(const double* __restrict__ part, int splits, const
 }
 
 // One block per replica: s = e^T q; q <- q - u s (symm); qtot = e^T q with Neumaier compensation.
-__global__ void k_neutral(double* q, const double* u, int64_t n, int symm, double* qtot) {
-    __shared__ double sh[1024];
-    __shared__ double shc[1024];
-    const int r = blockIdx.x;
+__device__ __forceinline__ void neumaier_add(double& a, double& comp, double v) {
+    const double t = a + v;
+    comp += fabs(a) >= fabs(v) ? (a - t) + v : (v - t) + a;
+    a = t;
+}
+
+__global__ void __launch_bounds__(1024) k_neutral(double* q, const double* u, int64_t n, int symm, double* qtot) {
+    __shared__ double sh[32], shc[32];
+    const int r = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* qr = q + (int64_t)r * n;
-    double s = 0.0;
     if (symm) {
+        double s = 0.0;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += qr[i];
-        sh[threadIdx.x] = s;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[warp] = s;
         __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+            sh[0] = t;
         }
+        __syncthreads();
         s = sh[0];
         __syncthreads();
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) qr[i] -= u[i] * s;
     }
     double a = 0.0, comp = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        double v = qr[i];
-        double t = a + v;
-        comp += fabs(a) >= fabs(v) ? (a - t) + v : (v - t) + a;
-        a = t;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) neumaier_add(a, comp, qr[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, a, o), yc = __shfl_down_sync(0xffffffffu, comp, o);
+        comp += yc;
+        neumaier_add(a, comp, y);
     }
-    sh[threadIdx.x] = a;
-    shc[threadIdx.x] = comp;
+    if (lane == 0) { sh[warp] = a; shc[warp] = comp; }
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            double x = sh[threadIdx.x], y = sh[threadIdx.x + o];
-            double t = x + y;
-            double e = fabs(x) >= fabs(y) ? (x - t) + y : (y - t) + x;
-            sh[threadIdx.x] = t;
-            shc[threadIdx.x] += shc[threadIdx.x + o] + e;
-        }
-        __syncthreads();
+    if (threadIdx.x == 0 && qtot) {
+        double t = 0.0, tc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tc += shc[w]; neumaier_add(t, tc, sh[w]); }
+        qtot[r] = t + tc;
     }
-    if (threadIdx.x == 0 && qtot) qtot[r] = sh[0] + shc[0];
 }
 
 // split count and row chunk of the centred product; grows the scratch when needed
+static bool gemv_pairs(const cpm_ctx* c) { return c->p.s_prec == CPM_PREC_FP32 && c->n % 2 == 0; }
+static int64_t gemv_colblocks(const cpm_ctx* c) {
+    return gemv_pairs(c) ? (c->n + 2 * G2_T - 1) / (2 * G2_T) : (c->n + GT_COLS - 1) / GT_COLS;
+}
+
 static cpm_status reserve_update_plan(cpm_ctx* c, int m, int64_t* splits_out, int64_t* jchunk_out) {
     const int64_t n = c->n;
-    const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
+    const int64_t colblocks = gemv_colblocks(c);
     const int rchunks = (m + GT_MR - 1) / GT_MR;
-    int64_t splits = (4 * 152 + colblocks * rchunks - 1) / (colblocks * rchunks);
+    const int64_t want = gemv_pairs(c) ? 2 * 152 : 4 * 152;   // resident blocks: about one wave
+    int64_t splits = (want + colblocks * rchunks - 1) / (colblocks * rchunks);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n + GT_JT - 1) / GT_JT));
     const int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
     splits = (n + jchunk - 1) / jchunk;
@@ -272,7 +361,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     const bool f32 = c->p.s_prec == CPM_PREC_FP32;
     int64_t splits = 0, jchunk = 0;
     CPM_TRY(reserve_update_plan(c, m, &splits, &jchunk));
-    const int64_t colblocks = (n + GT_COLS - 1) / GT_COLS;
+    const int64_t colblocks = gemv_colblocks(c);
     const int rchunks = (m + GT_MR - 1) / GT_MR;
     double* part = (double*)c->ubuf;
     float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
@@ -281,7 +370,8 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
         k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
-        k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
+        if (gemv_pairs(c)) k_gemv32x2<<<grid, G2_T, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
+        else k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
     } else {
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
     }
