@@ -82,6 +82,19 @@ void prof_end(cpm_ctx* c, int k) {
     c->prof_open[k] = nullptr;
 }
 
+cpm_status ensure_tickets(cpm_ctx* c, int m) {
+    if (c->tickets_n >= m) return CPM_OK;
+    c->graph_valid = false;
+    dev_free(c, c->tickets);
+    c->tickets = nullptr;
+    c->tickets_n = 0;
+    const int cap = ((m + 255) / 256) * 256;
+    CPM_TRY(dev_alloc(c, (void**)&c->tickets, sizeof(int) * cap));
+    CPM_CUDA(c, cudaMemsetAsync(c->tickets, 0, sizeof(int) * cap, c->stream));
+    c->tickets_n = cap;
+    return CPM_OK;
+}
+
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes) {
     if (c->scratch_bytes >= bytes) return CPM_OK;
     c->graph_valid = false;
@@ -127,14 +140,14 @@ static void free_geometry(cpm_ctx* c) {
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
-                    c->sperm, c->schunks, c->tcz, c->tcxy};
+                    c->sperm, c->schunks, c->tcz, c->tcxy, c->c0e};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
     c->rtab = nullptr; c->rtab_id = nullptr; c->nrtab = 0;
     c->sperm = nullptr; c->schunks = nullptr; c->nschunk = 0;
-    c->tcz = nullptr; c->tcxy = nullptr;
+    c->tcz = nullptr; c->tcxy = nullptr; c->c0e = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -316,6 +329,7 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
     CPM_TRY(launch_phases<float>(st, c->g, k, c->sxyz, n, c->site32.X, c->site32.Y, c->site32.Z));
     CPM_LAUNCH(c, "k_phases(sites)");
     if (c->p.k_prec == CPM_PREC_F16X2) CPM_TRY(tc_recip_prepare(c));
+    CPM_TRY(build_col0_sites(c));
     const size_t nn = (size_t)n * n;
     CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));
     CPM_TRY(dev_alloc(c, (void**)&c->W, sizeof(double) * nn));

@@ -38,16 +38,19 @@ CellGrid make_grid(const Geometry& g) {
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // ----------------------------------------------------------------------------- per-replica totals
-// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates; one block of 1,024
-// threads per replica, warp shuffles then one pass over the warps (fixed order).
-// With qabs, also (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).
-constexpr int ST_THREADS = 1024;
-__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const double* Q, int64_t ne, double* stats,
-                                                     float2* qabs) {
+// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates, and with qabs also
+// (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).  Grid (SB, m):
+// block b sums its slice of the charges into part[r][b][6]; the last block of the replica adds
+// the slices in order.
+constexpr int ST_THREADS = 256, ST_BLOCKS = 16;
+__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const double* Q, int64_t ne, double* part,
+                                                     int* tickets, double* stats, float2* qabs) {
     __shared__ double sh[6][ST_THREADS / 32];
-    const int r = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t chunk = (ne + nb - 1) / nb, jb = (int64_t)b * chunk, je = min(ne, jb + chunk);
     double a[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t j = threadIdx.x; j < ne; j += ST_THREADS) {
+    for (int64_t j = jb + threadIdx.x; j < je; j += ST_THREADS) {
         const int64_t p = (int64_t)r * ne + j;
         const double q = Q[p];
         a[0] += q;
@@ -66,10 +69,19 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const d
     if (lane == 0)
         for (int t = 0; t < 6; ++t) sh[t][warp] = a[t];
     __syncthreads();
+    double* pr = part + ((int64_t)r * nb + b) * 6;
     if (threadIdx.x < 6) {
         const int t = threadIdx.x;
         double v = sh[t][0];
         for (int w = 1; w < ST_THREADS / 32; ++w) v = t == 4 ? fmax(v, sh[t][w]) : v + sh[t][w];
+        pr[t] = v;
+    }
+    if (!last_block_of(&tickets[r], nb)) return;
+    if (threadIdx.x < 6) {
+        const int t = threadIdx.x;
+        const volatile double* pv = part + (int64_t)r * nb * 6;
+        double v = pv[t];
+        for (int k = 1; k < nb; ++k) v = t == 4 ? fmax(v, pv[k * 6 + t]) : v + pv[k * 6 + t];
         if (t < 4) stats[4 * r + t] = v;
         else if (qabs) {
             if (t == 4) qabs[r].x = (float)v;
@@ -272,50 +284,90 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
 
 // Real space, single precision, cell pairs: the sites are grouped by real-space cell into chunks
 // of at most 32 (assembled once).  A block of RC_WARPS warps takes one chunk; its warps split the
-// rows (dy, dz) of the cell's stencil, and since the cells of a row are consecutive in the sorted
-// charge array each row is one or two contiguous ranges, streamed 32 charges at a time through the
-// warp's shared buffer and evaluated by all the chunk's sites.  The warps' partial sums are added
-// in a fixed order.  The pair-function tables of up to two widths are staged in shared memory.
+// rows (dy, dz) of the cell's stencil.  Rows whose cells lie farther than r_c from the bounding box
+// of the chunk's sites are skipped and the x range of each row is trimmed the same way; since the
+// cells of a row are consecutive in the sorted charge array, a row is one or two contiguous
+// ranges.  The lanes of a warp take 32 charges of a range at a time and every lane runs over all
+// sites of the chunk, keeping one partial sum per site; the partial sums of all lanes and warps
+// are added per site in a fixed order at the end.  The pair-function tables of up to two widths
+// are staged in shared memory.
 constexpr int RC_WARPS = 4;
 constexpr int RC_SMEM_TABS = 2;
 
-__global__ void __launch_bounds__(32 * RC_WARPS, 4) k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm,
-                                                             const int4* __restrict__ chunks, int nchunks, int64_t n,
-                                                             Geometry g, CellGrid cg, const int* __restrict__ start,
-                                                             const float4* __restrict__ sorted,
-                                                             const float4* __restrict__ tab, int ntab,
-                                                             const int* __restrict__ tabid, double* __restrict__ out) {
-    __shared__ float4 sh[RC_WARPS][32];
+__device__ __forceinline__ float4 lds128(const float4* p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * RC_WARPS, 4)
+    k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm, const int4* __restrict__ chunks,
+                 int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
+                 const float4* __restrict__ sorted, const float4* __restrict__ tab, int ntab,
+                 const int* __restrict__ tabid, double* __restrict__ out) {
     __shared__ float4 stab[RC_SMEM_TABS * RT_N];
-    __shared__ float part[RC_WARPS][32];
+    __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
+    __shared__ float red[RC_WARPS][32][33];         // [warp][site][lane]
+    __shared__ float sbox[6];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x, r = blockIdx.y;
     const bool smem_tab = ntab <= RC_SMEM_TABS;
     if (smem_tab)
         for (int e = threadIdx.x; e < ntab * RT_N; e += blockDim.x) stab[e] = tab[e];
-    __syncthreads();
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
-    const int i = lane < cinfo.y ? perm[cinfo.x + lane] : -1;
-    float px = 0.f, py = 0.f, pz = 0.f;
-    const float4* tb = smem_tab ? stab : tab;
-    if (i >= 0) {
-        px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
-        tb += tabid[i] * RT_N;
+    const int nsites = cinfo.y;
+    if (warp == 0) {
+        float px = 0.f, py = 0.f, pz = 0.f;
+        int toff = 0;
+        if (lane < nsites) {
+            const int i = perm[cinfo.x + lane];
+            px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
+            toff = tabid[i] * RT_N;
+        }
+        ssite[lane] = make_float4(px, py, pz, __int_as_float(toff));
+        float lo[3] = {px, py, pz}, hi[3] = {px, py, pz};
+        if (lane >= nsites) {
+            lo[0] = lo[1] = lo[2] = 3.0e38f;
+            hi[0] = hi[1] = hi[2] = -3.0e38f;
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+        if (lane == 0) {
+            sbox[0] = lo[0]; sbox[1] = lo[1]; sbox[2] = lo[2];
+            sbox[3] = hi[0]; sbox[4] = hi[1]; sbox[5] = hi[2];
+        }
     }
+    __syncthreads();
+    const float4* tb = smem_tab ? stab : tab;
     const int cx = cinfo.z % cg.nc[0], cy = (cinfo.z / cg.nc[0]) % cg.nc[1], cz = cinfo.z / (cg.nc[0] * cg.nc[1]);
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
-    float acc = 0.f;
-    float4* buf = sh[warp];
+    const float hx = (float)cg.h[0], hy = (float)cg.h[1], hz = (float)cg.h[2];
+    const float bx0 = sbox[0], by0 = sbox[1], bz0 = sbox[2], bx1 = sbox[3], by1 = sbox[4], bz1 = sbox[5];
+    float acc[32];
+#pragma unroll
+    for (int s = 0; s < 32; ++s) acc[s] = 0.f;
     const int wy = 2 * cg.S[1] + 1, nrows = wy * (2 * cg.S[2] + 1);
     for (int row = warp; row < nrows; row += RC_WARPS) {
         const int dy = row % wy - cg.S[1], dz = row / wy - cg.S[2];
-        const int uz = cz + dz, fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
-        const int uy = cy + dy, fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
+        const int uz = cz + dz, uy = cy + dy;
+        // distance from the sites' box to the row's slab of cells
+        const float dyd = fmaxf(0.f, fmaxf((float)uy * hy - by1, by0 - (float)(uy + 1) * hy));
+        const float dzd = fmaxf(0.f, fmaxf((float)uz * hz - bz1, bz0 - (float)(uz + 1) * hz));
+        const float rx2 = rc2 - dyd * dyd - dzd * dzd;
+        if (rx2 <= 0.f) continue;
+        const float rx = sqrtf(rx2) * 1.0001f + 1e-3f;
+        int ux = max(cx - cg.S[0], (int)floorf((bx0 - rx) / hx));
+        const int uxe = min(cx + cg.S[0], (int)floorf((bx1 + rx) / hx));
+        const int fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
+        const int fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
         const float shz = (float)(fz * g.boxL[2]), shy = (float)(fy * g.boxL[1]);
         const int rowbase = r * cg.ncells + (wz * cg.nc[1] + wyy) * cg.nc[0];
-        int ux = cx - cg.S[0];
-        const int uxe = cx + cg.S[0];
         while (ux <= uxe) {
             // a run of unwrapped cells with the same image shift: consecutive wrapped cells
             const int fx = floordiv(ux, cg.nc[0]);
@@ -325,37 +377,41 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4) k_real_cells(const float* __
             const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
             ux += wx1 - wx0 + 1;
             for (int p0 = b; p0 < e; p0 += 32) {
-                const int cnt = min(32, e - p0);
-                if (lane < cnt) {
-                    float4 q = sorted[p0 + lane];
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool live = p0 + lane < e;
+                if (live) {
+                    q = sorted[p0 + lane];
                     q.x += shx; q.y += shy; q.z += shz;
-                    buf[lane] = q;
                 }
-                __syncwarp();
-                if (i >= 0) {
-                    for (int k = 0; k < cnt; ++k) {
-                        const float4 q = buf[k];
-                        const float ddx = px - q.x, ddy = py - q.y, ddz = pz - q.z;
+#pragma unroll
+                for (int s = 0; s < 32; ++s) {
+                    if (s < nsites) {
+                        const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
+                        const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
                         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (r2 < rc2) {
+                        if (live && r2 < rc2) {
                             const float u = sqrtf(r2) * inv_h;
                             const int kk = min((int)u, RT_N - 1);
                             const float t = u - (float)kk;
-                            const float4 cf = tb[kk];
-                            acc += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
+                            const float4 cf = tb[__float_as_int(st.w) + kk];
+                            acc[s] += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
                         }
                     }
                 }
-                __syncwarp();
             }
         }
     }
-    part[warp][lane] = acc;
+#pragma unroll
+    for (int s = 0; s < 32; ++s) red[warp][s][lane] = acc[s];
     __syncthreads();
-    if (warp == 0 && i >= 0) {
+    if (warp == 0 && lane < nsites) {
         double a = 0.0;
-        for (int w = 0; w < RC_WARPS; ++w) a += (double)part[w][lane];
-        out[(int64_t)r * n + i] = a;
+        for (int w = 0; w < RC_WARPS; ++w) {
+            float fs = 0.f;
+            for (int l = 0; l < 32; ++l) fs += red[w][lane][l];
+            a += (double)fs;
+        }
+        out[(int64_t)r * n + perm[cinfo.x + lane]] = a;
     }
 }
 
@@ -654,15 +710,17 @@ __global__ void __launch_bounds__(256) k_site(const int2* __restrict__ cols, con
 // are the largest of the whole set (they carry the laterally averaged charge profile), so
 // its terms dominate the rounding of a single-precision sum.  Phases by an FP64 recurrence
 // in nz from an exactly reduced first harmonic.
-__device__ __forceinline__ double2 z_phase1(double z, double invLz) {
+__device__ __forceinline__ double2 z_phase_n(double z, double invLz, int nz) {
     double s = z * invLz;
     s -= floor(s);
     double t = s * 18446744073709551616.0;
     uint64_t u = t >= 18446744073709551616.0 ? 0ull : (uint64_t)t;
+    u *= (uint64_t)nz;   // fraction of nz z / Lz, reduced exactly (mod 2^64)
     double sn, cs;
     sincospi((double)(int64_t)u * 0x1p-63, &sn, &cs);
     return make_double2(cs, sn);
 }
+__device__ __forceinline__ double2 z_phase1(double z, double invLz) { return z_phase_n(z, invLz, 1); }
 
 // Double-float arithmetic (pairs of floats, about 48 significant bits; Dekker 1971, Knuth TAOCP
 // vol. 2): the k_perp = 0 column needs better than FP32 accuracy, and FP32 pairs run far faster
@@ -709,10 +767,10 @@ __global__ void k_col0_phase1(const double* __restrict__ xyz, int64_t ptot, doub
     e1[p] = make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-// part[r][chunk][nz - 1] for nz in one block of 8 harmonics: each thread takes 8 charges of the
-// chunk (1,024 charges per block), raises exp(i theta) to the block's first harmonic and steps
+// part[r][chunk][nz - 1] for nz in one block of 12 harmonics: each thread takes 2 charges of the
+// chunk (256 charges per block), raises exp(i theta) to the block's first harmonic and steps
 // through the block by a double-float recurrence; the block sums its threads in a fixed order.
-constexpr int C0_THREADS = 128, C0_PER_THREAD = 8, C0_NB = 8;
+constexpr int C0_THREADS = 128, C0_PER_THREAD = 2, C0_NB = 12;
 
 __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restrict__ e1s, const double* __restrict__ Q,
                                                        int64_t ne, int nz0, double2* __restrict__ part) {
@@ -746,14 +804,15 @@ __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restric
         }
     }
 #pragma unroll
-    for (int k = 0; k < C0_NB; ++k) {
-        double re = (double)acc[k].re.hi + (double)acc[k].re.lo;
-        double im = (double)acc[k].im.hi + (double)acc[k].im.lo;
+    for (int k = 0; k < C0_NB; ++k) {   // warp sums in double-float, one FP64 value per warp
+        dfl re = acc[k].re, im = acc[k].im;
         for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
+            const dfl ore = {__shfl_down_sync(0xffffffffu, re.hi, o), __shfl_down_sync(0xffffffffu, re.lo, o)};
+            const dfl oim = {__shfl_down_sync(0xffffffffu, im.hi, o), __shfl_down_sync(0xffffffffu, im.lo, o)};
+            re = df_add(re, ore);
+            im = df_add(im, oim);
         }
-        if (lane == 0) red[warp][k] = make_double2(re, im);
+        if (lane == 0) red[warp][k] = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
     }
     __syncthreads();
     if (threadIdx.x < C0_NB) {
@@ -782,22 +841,28 @@ __global__ void k_col0_reduce(const double2* __restrict__ part, int nchunks, int
     wrho0[t] = make_double2(wt * a.x, wt * a.y);
 }
 
-// b0[r][u] = sum_nz Re[exp(-i kz z_u) wrho0[r][nz]] for each distinct site height z_u
-__global__ void k_col0_site(const double* __restrict__ zu, int nzu, int m, double invLz, int nz0,
-                            const double2* __restrict__ wrho0, double* __restrict__ b0) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m * nzu) return;
-    const int r = t / nzu, iu = t % nzu;
-    const double2 e1 = z_phase1(zu[iu], invLz);
-    double2 e = e1;
+// e0[u][nz - 1] = exp(i kz z_u) for each distinct site height z_u (fixed with the geometry), one
+// exactly reduced FP64 sincospi per entry
+__global__ void k_col0_e0(const double* __restrict__ zu, int nzu, double invLz, int nz0, double2* __restrict__ e0) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nzu * nz0) return;
+    const int iu = t / nz0, nz = t % nz0 + 1;
+    e0[t] = z_phase_n(zu[iu], invLz, nz);
+}
+
+// b0[r][u] = sum_nz Re[conj(e0[u][nz]) wrho0[r][nz]]: one warp per (r, u), lanes over nz
+__global__ void k_col0_site(const double2* __restrict__ e0, int nzu, int m, int nz0, const double2* __restrict__ wrho0,
+                            double* __restrict__ b0) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= m * nzu) return;
+    const int r = w / nzu, iu = w % nzu;
     double acc = 0.0;
-    const double2* wr = wrho0 + (int64_t)r * nz0;
-    for (int nz = 1; nz <= nz0; ++nz) {
-        double2 v = wr[nz - 1];
+    for (int k = lane; k < nz0; k += 32) {
+        const double2 e = e0[(int64_t)iu * nz0 + k], v = wrho0[(int64_t)r * nz0 + k];
         acc += e.x * v.x + e.y * v.y;
-        e = cmul(e, e1);
     }
-    b0[t] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) b0[w] = acc;
 }
 
 // Single-precision site potential with a 64-column x 128-site tile per block (4 columns x 8 sites
@@ -910,7 +975,7 @@ struct BvecPlan {
         off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
     int c0chunks;
     bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
-    size_t off_qabs, off_tcpart, off_w16;
+    size_t off_qabs, off_tcpart, off_w16, off_spart;
 };
 
 template <typename T>
@@ -971,6 +1036,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
     p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
     p.off_qabs = o; o += al(sizeof(float2) * m);
+    p.off_spart = o; o += al(sizeof(double) * 6 * ST_BLOCKS * m);
     p.off_tcpart = p.off_w16 = o;
     if (p.tc) {
         p.off_tcpart = o; o += al(tc_recip_part_bytes(td, m, k.nzw));
@@ -1015,7 +1081,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
 
     prof_begin(c, CPM_K_STATS);
     float2* qabs = (float2*)(scr + p.off_qabs);
-    k_stats<<<m, ST_THREADS, 0, st>>>(xyz, Q, ne, stats, p.tc ? qabs : nullptr);
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ST_BLOCKS, (ne + 511) / 512));
+    k_stats<<<dim3(sblocks, m), ST_THREADS, 0, st>>>(xyz, Q, ne, (double*)(scr + p.off_spart), c->tickets, stats,
+                                                    p.tc ? qabs : nullptr);
     prof_end(c, CPM_K_STATS);
     CPM_LAUNCH(c, "k_stats");
     prof_begin(c, CPM_K_CELLS);
@@ -1110,7 +1178,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         CPM_LAUNCH(c, "k_col0_rho");
         k_col0_reduce<<<(m * k.ext0 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
         CPM_LAUNCH(c, "k_col0_reduce");
-        k_col0_site<<<(m * c->nzu + 127) / 128, 128, 0, st>>>(c->zuniq, c->nzu, m, c->g.inv[2], k.ext0, c0w, b0);
+        k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, k.ext0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
         c->launches += 4;
@@ -1123,8 +1191,21 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     return CPM_OK;
 }
 
+// phase factors of the k_perp = 0 column at the distinct site heights (after the k table)
+cpm_status build_col0_sites(cpm_ctx* c) {
+    dev_free(c, c->c0e);
+    c->c0e = nullptr;
+    const int nz0 = c->kt.ext0;
+    if (nz0 <= 0 || c->nzu == 0) return CPM_OK;
+    CPM_TRY(dev_alloc(c, (void**)&c->c0e, sizeof(double2) * (size_t)c->nzu * nz0));
+    k_col0_e0<<<(c->nzu * nz0 + 255) / 256, 256, 0, c->stream>>>(c->zuniq, c->nzu, c->g.inv[2], nz0, c->c0e);
+    CPM_LAUNCH(c, "k_col0_e0");
+    return CPM_OK;
+}
+
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
+    CPM_TRY(ensure_tickets(c, m));
     return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }
 
@@ -1132,6 +1213,7 @@ cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* 
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     const size_t need = f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne);
     CPM_TRY(ensure_scratch(c, need));
+    CPM_TRY(ensure_tickets(c, m));
     char* scr = (char*)c->scratch;
     return f32 ? bvec_run<float>(c, m, ne, xyz, Q, b_out, scr) : bvec_run<double>(c, m, ne, xyz, Q, b_out, scr);
 }

@@ -125,6 +125,11 @@ struct cpm_ctx {
     double* dvec = nullptr;      // [n] scratch
     double* red = nullptr;       // [64] scratch scalars
     unsigned* status = nullptr;  // device status word
+    int* tickets = nullptr;      // [tickets_n] per-replica arrival counters, zero between launches
+    int tickets_n = 0;
+    double2* c0e = nullptr;      // [nzu][ext0] exp(i kz z_u) of the k_perp = 0 column at the site heights
+    double* nbuf = nullptr;      // neutrality fix: per-block partial sums of q
+    size_t nbuf_bytes = 0;
     bool assembled = false, inverted = false;
 
     // per-step scratch, grown on demand
@@ -209,6 +214,23 @@ cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, 
 
 // api.cu
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes);
+cpm_status ensure_tickets(cpm_ctx* c, int m);
+
+// Last-block reduction: every block of a replica stores its partial, then takes a ticket; the
+// block that draws the last ticket sums the partials in block order (a fixed order, so the result
+// does not depend on scheduling) and resets the counter for the next launch.
+__device__ __forceinline__ bool last_block_of(int* ticket, int nblocks) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1) == nblocks - 1;
+        if (s_last) atomicExch(ticket, 0);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
 
 // assemble.cu
 cpm_status assemble_A(cpm_ctx* c);
@@ -224,6 +246,7 @@ struct Geometry;
 CellGrid make_grid(const Geometry& g);
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
+cpm_status build_col0_sites(cpm_ctx* c);
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
 
 // update.cu

@@ -273,28 +273,49 @@ __device__ __forceinline__ void neumaier_add(double& a, double& comp, double v) 
     a = t;
 }
 
-__global__ void __launch_bounds__(1024) k_neutral(double* q, const double* u, int64_t n, int symm, double* qtot) {
-    __shared__ double sh[32], shc[32];
-    const int r = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double* qr = q + (int64_t)r * n;
-    if (symm) {
-        double s = 0.0;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += qr[i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-            sh[0] = t;
-        }
-        __syncthreads();
-        s = sh[0];
-        __syncthreads();
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) qr[i] -= u[i] * s;
+// Neutrality fix and total charge, Sec. II.B (q <- q - u e^T q with u = A^-1 e / (e^T A^-1 e), then
+// the FP64 total): grid (NB_BLOCKS slices of the sites, m); two launches because the fix needs
+// the replica's whole sum first.
+constexpr int NB_T = 256;
+
+// p1[r][b] = sum of q[r][i] over slice b
+__global__ void __launch_bounds__(NB_T) k_qsum(const double* __restrict__ q, int64_t n, double* __restrict__ p1) {
+    __shared__ double sh[NB_T / 32];
+    const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t chunk = (n + nb - 1) / nb, ib = (int64_t)b * chunk, ie = min(n, ib + chunk);
+    double s = 0.0;
+    for (int64_t i = ib + threadIdx.x; i < ie; i += NB_T) s += q[(int64_t)r * n + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = sh[0];
+        for (int w = 1; w < NB_T / 32; ++w) t += sh[w];
+        p1[(int64_t)r * nb + b] = t;
     }
+}
+
+// with symm: q[r][i] -= u[i] * sum_b p1[r][b]; then p2[r][b] = compensated sum of the new q over
+// slice b, and the replica's last block writes qtot[r] = sum of p2 in slice order
+__global__ void __launch_bounds__(NB_T) k_neutral_fix(double* __restrict__ q, const double* __restrict__ u, int64_t n,
+                                                      int symm, const double* __restrict__ p1, double* __restrict__ p2,
+                                                      int* __restrict__ tickets, double* __restrict__ qtot) {
+    __shared__ double sh[NB_T / 32], shc[NB_T / 32];
+    const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t chunk = (n + nb - 1) / nb, ib = (int64_t)b * chunk, ie = min(n, ib + chunk);
+    double* qr = q + (int64_t)r * n;
+    double s = 0.0;
+    if (symm)
+        for (int k = 0; k < nb; ++k) s += p1[(int64_t)r * nb + k];
     double a = 0.0, comp = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) neumaier_add(a, comp, qr[i]);
+    for (int64_t i = ib + threadIdx.x; i < ie; i += NB_T) {
+        double v = qr[i];
+        if (symm) {
+            v -= u[i] * s;
+            qr[i] = v;
+        }
+        neumaier_add(a, comp, v);
+    }
     for (int o = 16; o > 0; o >>= 1) {
         const double y = __shfl_down_sync(0xffffffffu, a, o), yc = __shfl_down_sync(0xffffffffu, comp, o);
         comp += yc;
@@ -302,11 +323,48 @@ __global__ void __launch_bounds__(1024) k_neutral(double* q, const double* u, in
     }
     if (lane == 0) { sh[warp] = a; shc[warp] = comp; }
     __syncthreads();
-    if (threadIdx.x == 0 && qtot) {
+    if (threadIdx.x == 0) {
         double t = 0.0, tc = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tc += shc[w]; neumaier_add(t, tc, sh[w]); }
+        for (int w = 0; w < NB_T / 32; ++w) { tc += shc[w]; neumaier_add(t, tc, sh[w]); }
+        p2[2 * ((int64_t)r * nb + b)] = t;
+        p2[2 * ((int64_t)r * nb + b) + 1] = tc;
+    }
+    if (!last_block_of(&tickets[r], nb)) return;
+    if (threadIdx.x == 0 && qtot) {
+        const volatile double* pv = p2 + 2 * (int64_t)r * nb;
+        double t = 0.0, tc = 0.0;
+        for (int k = 0; k < nb; ++k) { tc += pv[2 * k + 1]; neumaier_add(t, tc, pv[2 * k]); }
         qtot[r] = t + tc;
     }
+}
+
+static int neutral_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 1023) / 1024)); }
+
+static cpm_status reserve_neutral(cpm_ctx* c, int m) {
+    CPM_TRY(ensure_tickets(c, m));
+    const size_t need = sizeof(double) * 3 * (size_t)m * neutral_blocks(c->n);
+    if (c->nbuf_bytes >= need) return CPM_OK;
+    c->graph_valid = false;
+    dev_free(c, c->nbuf);
+    c->nbuf = nullptr;
+    c->nbuf_bytes = 0;
+    CPM_TRY(dev_alloc(c, (void**)&c->nbuf, need));
+    c->nbuf_bytes = need;
+    return CPM_OK;
+}
+
+static cpm_status launch_neutral(cpm_ctx* c, int m, double* q, double* qtot) {
+    CPM_TRY(reserve_neutral(c, m));
+    const int nb = neutral_blocks(c->n);
+    double* p1 = c->nbuf;
+    double* p2 = c->nbuf + (size_t)m * nb;
+    prof_begin(c, CPM_K_NEUTRAL);
+    if (c->p.symm) k_qsum<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->n, p1);
+    k_neutral_fix<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->u, c->n, c->p.symm, p1, p2, c->tickets, qtot);
+    prof_end(c, CPM_K_NEUTRAL);
+    CPM_LAUNCH(c, "k_neutral_fix");
+    c->launches += c->p.symm ? 2 : 1;
+    return CPM_OK;
 }
 
 // split count and row chunk of the centred product; grows the scratch when needed
@@ -339,6 +397,7 @@ static cpm_status reserve_update_plan(cpm_ctx* c, int m, int64_t* splits_out, in
 }
 
 cpm_status reserve_update(cpm_ctx* c, int m) {
+    CPM_TRY(reserve_neutral(c, m));
     if (c->p.s_prec == CPM_PREC_BF16X3) return tc_reserve(c, m);
     int64_t s, j;
     return reserve_update_plan(c, m, &s, &j);
@@ -351,12 +410,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
         prof_begin(c, CPM_K_GEMV);
         CPM_TRY(tc_update(c, m, psi, b, q));
         prof_end(c, CPM_K_GEMV);
-        c->launches += 1;
-        prof_begin(c, CPM_K_NEUTRAL);
-        k_neutral<<<m, 1024, 0, st>>>(q, c->u, n, c->p.symm, qtot);
-        prof_end(c, CPM_K_NEUTRAL);
-        CPM_LAUNCH(c, "k_neutral");
-        return CPM_OK;
+        return launch_neutral(c, m, q, qtot);
     }
     const bool f32 = c->p.s_prec == CPM_PREC_FP32;
     int64_t splits = 0, jchunk = 0;
@@ -365,7 +419,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     const int rchunks = (m + GT_MR - 1) / GT_MR;
     double* part = (double*)c->ubuf;
     float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
-    c->launches += f32 ? 4 : 3;
+    c->launches += f32 ? 3 : 2;
     prof_begin(c, CPM_K_GEMV);
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
@@ -378,11 +432,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     k_gemv_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q);
     prof_end(c, CPM_K_GEMV);
     CPM_LAUNCH(c, "k_gemv");
-    prof_begin(c, CPM_K_NEUTRAL);
-    k_neutral<<<m, 1024, 0, st>>>(q, c->u, n, c->p.symm, qtot);
-    prof_end(c, CPM_K_NEUTRAL);
-    CPM_LAUNCH(c, "k_neutral");
-    return CPM_OK;
+    return launch_neutral(c, m, q, qtot);
 }
 
 }  // namespace cpm
