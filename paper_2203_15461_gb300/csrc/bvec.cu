@@ -286,13 +286,14 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
 // of at most 32 (assembled once).  A block of RC_WARPS warps takes one chunk; its warps split the
 // rows (dy, dz) of the cell's stencil.  Rows whose cells lie farther than r_c from the bounding box
 // of the chunk's sites are skipped and the x range of each row is trimmed the same way; since the
-// cells of a row are consecutive in the sorted charge array, a row is one or two contiguous
-// ranges.  The lanes of a warp take 32 charges of a range at a time and every lane runs over all
-// sites of the chunk, keeping one partial sum per site; the partial sums of all lanes and warps
-// are added per site in a fixed order at the end.  The pair-function tables of up to two widths
+// cells of a row are consecutive in the sorted charge array, a row is one contiguous range per
+// image shift.  The lanes of a warp take 32 charges of its concatenated ranges at a time and
+// every lane runs over all sites of the chunk, keeping one partial sum per site; the partial sums
+// of all lanes and warps are added per site in a fixed order at the end.  The pair-function tables of up to two widths
 // are staged in shared memory.
 constexpr int RC_WARPS = 4;
 constexpr int RC_SMEM_TABS = 2;
+constexpr int RC_LIST = 64;                         // charge ranges listed per warp at a time
 
 __device__ __forceinline__ float4 lds128(const float4* p) {
     float4 v;
@@ -311,6 +312,9 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
     __shared__ float red[RC_WARPS][32][33];         // [warp][site][lane]
     __shared__ float sbox[6];
+    __shared__ int lbeg[RC_WARPS][RC_LIST];         // per warp: charge ranges of a group of rows
+    __shared__ int lpre[RC_WARPS][RC_LIST + 1];
+    __shared__ float4 lsh[RC_WARPS][RC_LIST];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x, r = blockIdx.y;
     const bool smem_tab = ntab <= RC_SMEM_TABS;
@@ -352,54 +356,105 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     float acc[32];
 #pragma unroll
     for (int s = 0; s < 32; ++s) acc[s] = 0.f;
+    // The warp's rows are taken in groups; the charge ranges (runs of cells with one image shift)
+    // of a group are listed in shared memory and streamed as one concatenated sequence, 32 charges
+    // per step, so that the lanes stay busy across the ends of the ranges.
+    int* rbeg = lbeg[warp];
+    int* rpre = lpre[warp];
+    float4* rsh = lsh[warp];
     const int wy = 2 * cg.S[1] + 1, nrows = wy * (2 * cg.S[2] + 1);
-    for (int row = warp; row < nrows; row += RC_WARPS) {
-        const int dy = row % wy - cg.S[1], dz = row / wy - cg.S[2];
-        const int uz = cz + dz, uy = cy + dy;
-        // distance from the sites' box to the row's slab of cells
-        const float dyd = fmaxf(0.f, fmaxf((float)uy * hy - by1, by0 - (float)(uy + 1) * hy));
-        const float dzd = fmaxf(0.f, fmaxf((float)uz * hz - bz1, bz0 - (float)(uz + 1) * hz));
-        const float rx2 = rc2 - dyd * dyd - dzd * dzd;
-        if (rx2 <= 0.f) continue;
-        const float rx = sqrtf(rx2) * 1.0001f + 1e-3f;
-        int ux = max(cx - cg.S[0], (int)floorf((bx0 - rx) / hx));
-        const int uxe = min(cx + cg.S[0], (int)floorf((bx1 + rx) / hx));
-        const int fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
-        const int fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
-        const float shz = (float)(fz * g.boxL[2]), shy = (float)(fy * g.boxL[1]);
-        const int rowbase = r * cg.ncells + (wz * cg.nc[1] + wyy) * cg.nc[0];
-        while (ux <= uxe) {
-            // a run of unwrapped cells with the same image shift: consecutive wrapped cells
-            const int fx = floordiv(ux, cg.nc[0]);
-            const int wx0 = ux - fx * cg.nc[0];
-            const int wx1 = min(cg.nc[0] - 1, wx0 + (uxe - ux));
-            const float shx = (float)(fx * g.boxL[0]);
-            const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
-            ux += wx1 - wx0 + 1;
-            for (int p0 = b; p0 < e; p0 += 32) {
-                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                const bool live = p0 + lane < e;
-                if (live) {
-                    q = sorted[p0 + lane];
-                    q.x += shx; q.y += shy; q.z += shz;
+    const int maxruns = (2 * cg.S[0] + 1 + cg.nc[0] - 1) / cg.nc[0] + 1;
+    const int group = max(1, min(32, RC_LIST / maxruns));
+    for (int g0 = warp; g0 < nrows; g0 += RC_WARPS * group) {
+        // lane l takes row g0 + RC_WARPS l of the group
+        const int row = g0 + RC_WARPS * lane;
+        int nrun = 0, ux = 0, uxe = -1, fx0 = 0, rowbase = 0;
+        float shy = 0.f, shz = 0.f;
+        if (lane < group && row < nrows) {
+            const int dy = row % wy - cg.S[1], dz = row / wy - cg.S[2];
+            const int uz = cz + dz, uy = cy + dy;
+            const float dyd = fmaxf(0.f, fmaxf((float)uy * hy - by1, by0 - (float)(uy + 1) * hy));
+            const float dzd = fmaxf(0.f, fmaxf((float)uz * hz - bz1, bz0 - (float)(uz + 1) * hz));
+            const float rx2 = rc2 - dyd * dyd - dzd * dzd;
+            if (rx2 > 0.f) {
+                const float rx = sqrtf(rx2) * 1.0001f + 1e-3f;
+                ux = max(cx - cg.S[0], (int)floorf((bx0 - rx) / hx));
+                uxe = min(cx + cg.S[0], (int)floorf((bx1 + rx) / hx));
+                if (ux <= uxe) {
+                    fx0 = floordiv(ux, cg.nc[0]);
+                    nrun = floordiv(uxe, cg.nc[0]) - fx0 + 1;
+                    const int fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
+                    const int fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
+                    shz = (float)(fz * g.boxL[2]);
+                    shy = (float)(fy * g.boxL[1]);
+                    rowbase = r * cg.ncells + (wz * cg.nc[1] + wyy) * cg.nc[0];
                 }
+            }
+        }
+        // place this lane's runs after those of the lanes before it
+        int off = nrun;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += v;
+        }
+        const int nent = __shfl_sync(0xffffffffu, off, 31);
+        off -= nrun;
+        for (int k = 0; k < nrun; ++k) {
+            const int fx = fx0 + k;
+            const int a = max(ux, fx * cg.nc[0]), bnd = min(uxe, fx * cg.nc[0] + cg.nc[0] - 1);
+            const int wx0 = a - fx * cg.nc[0], wx1 = bnd - fx * cg.nc[0];
+            const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
+            rbeg[off + k] = b;
+            rpre[off + k] = e - b;
+            rsh[off + k] = make_float4((float)(fx * g.boxL[0]), shy, shz, 0.f);
+        }
+        __syncwarp();
+        // exclusive prefix of the range lengths (nent <= RC_LIST)
+        int total = 0;
+        for (int e0 = 0; e0 < nent; e0 += 32) {
+            const int e = e0 + lane;
+            int len = e < nent ? rpre[e] : 0, inc = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            __syncwarp();
+            if (e < nent) rpre[e] = total + inc - len;
+            total += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) rpre[nent] = total;
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int v = base + lane;
+            const bool live = v < total;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live) {
+                int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= v
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (rpre[mid] <= v) lo = mid; else hi = mid - 1;
+                }
+                q = sorted[rbeg[lo] + (v - rpre[lo])];
+                const float4 sh = rsh[lo];
+                q.x += sh.x; q.y += sh.y; q.z += sh.z;
+            }
 #pragma unroll
-                for (int s = 0; s < 32; ++s) {
-                    if (s < nsites) {
-                        const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
-                        const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
-                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (live && r2 < rc2) {
-                            const float u = sqrtf(r2) * inv_h;
-                            const int kk = min((int)u, RT_N - 1);
-                            const float t = u - (float)kk;
-                            const float4 cf = tb[__float_as_int(st.w) + kk];
-                            acc[s] += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
-                        }
+            for (int s = 0; s < 32; ++s) {
+                if (s < nsites) {
+                    const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
+                    const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
+                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (live && r2 < rc2) {
+                        const float u = sqrtf(r2) * inv_h;
+                        const int kk = min((int)u, RT_N - 1);
+                        const float t = u - (float)kk;
+                        const float4 cf = tb[__float_as_int(st.w) + kk];
+                        acc[s] += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
                     }
                 }
             }
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int s = 0; s < 32; ++s) red[warp][s][lane] = acc[s];
