@@ -295,6 +295,12 @@ constexpr int RC_WARPS = 4;
 constexpr int RC_SMEM_TABS = 2;
 constexpr int RC_LIST = 64;                         // charge ranges listed per warp at a time
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float4 lds128(const float4* p) {
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -303,6 +309,7 @@ __device__ __forceinline__ float4 lds128(const float4* p) {
     return v;
 }
 
+template <bool SMEM_TAB>
 __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm, const int4* __restrict__ chunks,
                  int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
@@ -317,8 +324,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     __shared__ float4 lsh[RC_WARPS][RC_LIST];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x, r = blockIdx.y;
-    const bool smem_tab = ntab <= RC_SMEM_TABS;
-    if (smem_tab)
+    if (SMEM_TAB)
         for (int e = threadIdx.x; e < ntab * RT_N; e += blockDim.x) stab[e] = tab[e];
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
     const int nsites = cinfo.y;
@@ -330,8 +336,9 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
             px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
             toff = tabid[i] * RT_N;
         }
+        if (lane >= nsites) px = py = pz = 1.0e6f;   // dummy sites, beyond any cutoff
         ssite[lane] = make_float4(px, py, pz, __int_as_float(toff));
-        float lo[3] = {px, py, pz}, hi[3] = {px, py, pz};
+        float lo[3] = {px, py, pz}, hi[3] = {px, py, pz};   // (dummies excluded below)
         if (lane >= nsites) {
             lo[0] = lo[1] = lo[2] = 3.0e38f;
             hi[0] = hi[1] = hi[2] = -3.0e38f;
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
     }
     __syncthreads();
-    const float4* tb = smem_tab ? stab : tab;
+    const float4* tb = SMEM_TAB ? stab : tab;
     const int cx = cinfo.z % cg.nc[0], cy = (cinfo.z / cg.nc[0]) % cg.nc[1], cz = cinfo.z / (cg.nc[0] * cg.nc[1]);
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
@@ -438,19 +445,26 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                 const float4 sh = rsh[lo];
                 q.x += sh.x; q.y += sh.y; q.z += sh.z;
             }
+            const float qw = live ? q.w : 0.f;
 #pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                if (s < nsites) {
+            for (int sg = 0; sg < 32; sg += 8) {
+                if (sg >= nsites) break;   // uniform; sites past nsites are far-away dummies
+#pragma unroll
+                for (int s = sg; s < sg + 8; ++s) {
+                    // branch-free pair term: the table index is clamped and the weight is zero
+                    // outside the cutoff, so the eight sites of a group interleave
                     const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
                     const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
                     const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (live && r2 < rc2) {
-                        const float u = sqrtf(r2) * inv_h;
-                        const int kk = min((int)u, RT_N - 1);
-                        const float t = u - (float)kk;
-                        const float4 cf = tb[__float_as_int(st.w) + kk];
-                        acc[s] += q.w * (cf.x + t * (cf.y + t * (cf.z + t * cf.w)));
-                    }
+                    const float u = sqrt_approx(r2) * inv_h;
+                    // floor(u) by the 1.5 * 2^23 rounding trick (u >= 0; a tie rounds either way and
+                    // the cubic pieces join continuously)
+                    const float ur = (u - 0.5f) + 12582912.0f;
+                    const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N - 1);
+                    const float t = u - (ur - 12582912.0f);
+                    const float4 cf = tb[__float_as_int(st.w) + kk];
+                    const float w = r2 < rc2 ? qw : 0.f;
+                    acc[s] = fmaf(w, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
                 }
             }
         }
@@ -813,13 +827,16 @@ __device__ __forceinline__ dcx dcx_mul(dcx a, dcx b) {
     return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
 
-// e1[p] = exp(i 2 pi z_p / Lz) as a double-float pair, one FP64 sincospi per charge
-__global__ void k_col0_phase1(const double* __restrict__ xyz, int64_t ptot, double invLz, float4* __restrict__ e1) {
+// e1[p] = exp(i 2 pi z_p / Lz) as a double-float pair (one FP64 sincospi per charge) and q[p] = Q_p
+// as a double-float pair
+__global__ void k_col0_phase1(const double* __restrict__ xyz, const double* __restrict__ Q, int64_t ptot,
+                              double invLz, float4* __restrict__ e1, float2* __restrict__ q) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ptot) return;
     const double2 e = z_phase1(xyz[3 * p + 2], invLz);
-    const dfl re = df_of(e.x), im = df_of(e.y);
+    const dfl re = df_of(e.x), im = df_of(e.y), qq = df_of(Q[p]);
     e1[p] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    q[p] = make_float2(qq.hi, qq.lo);
 }
 
 // part[r][chunk][nz - 1] for nz in one block of 12 harmonics: each thread takes 2 charges of the
@@ -827,7 +844,7 @@ __global__ void k_col0_phase1(const double* __restrict__ xyz, int64_t ptot, doub
 // through the block by a double-float recurrence; the block sums its threads in a fixed order.
 constexpr int C0_THREADS = 128, C0_PER_THREAD = 2, C0_NB = 12;
 
-__global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restrict__ e1s, const double* __restrict__ Q,
+__global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restrict__ e1s, const float2* __restrict__ Qd,
                                                        int64_t ne, int nz0, double2* __restrict__ part) {
     __shared__ double2 red[C0_THREADS / 32][C0_NB];
     const int chunk = blockIdx.x, nb = blockIdx.y, r = blockIdx.z;
@@ -840,9 +857,9 @@ __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restric
         const int64_t j = (int64_t)chunk * C0_THREADS * C0_PER_THREAD + (int64_t)t * C0_THREADS + threadIdx.x;
         if (j >= ne) break;
         const int64_t p = (int64_t)r * ne + j;
-        const double qd = Q[p];
-        if (qd == 0.0) continue;
-        const dfl q = df_of(qd);
+        const float2 qf = Qd[p];
+        if (qf.x == 0.f) continue;
+        const dfl q = {qf.x, qf.y};
         const float4 f = e1s[p];
         const dcx e1 = {{f.x, f.y}, {f.z, f.w}};
         // e = e1^nzs by binary powering
@@ -880,20 +897,27 @@ __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restric
     }
 }
 
-// wrho0[r][nz - 1] = w(0, 0, nz) * sum over chunks of part
+// wrho0[r][nz - 1] = w(0, 0, nz) * sum over chunks of part: one warp per (r, nz), lanes over the
+// chunks, combined in a fixed order
 __global__ void k_col0_reduce(const double2* __restrict__ part, int nchunks, int nz0, const double* __restrict__ w,
                               int NZ, int m, double2* __restrict__ wrho0) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (t >= m * nz0) return;
     const int r = t / nz0, k = t % nz0;
     double2 a = make_double2(0.0, 0.0);
-    for (int ch = 0; ch < nchunks; ++ch) {
-        double2 v = part[((int64_t)r * nchunks + ch) * nz0 + k];
+    for (int ch = lane; ch < nchunks; ch += 32) {
+        const double2 v = part[((int64_t)r * nchunks + ch) * nz0 + k];
         a.x += v.x;
         a.y += v.y;
     }
-    const double wt = w[NZ + k + 1];   // column 0 occupies the first row of the dense grid
-    wrho0[t] = make_double2(wt * a.x, wt * a.y);
+    for (int o = 16; o > 0; o >>= 1) {
+        a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+        a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+    }
+    if (lane == 0) {
+        const double wt = w[NZ + k + 1];   // column 0 occupies the first row of the dense grid
+        wrho0[t] = make_double2(wt * a.x, wt * a.y);
+    }
 }
 
 // e0[u][nz - 1] = exp(i kz z_u) for each distinct site height z_u (fixed with the geometry), one
@@ -1030,7 +1054,7 @@ struct BvecPlan {
         off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
     int c0chunks;
     bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
-    size_t off_qabs, off_tcpart, off_w16, off_spart;
+    size_t off_qabs, off_tcpart, off_w16, off_spart, off_c0q;
 };
 
 template <typename T>
@@ -1090,6 +1114,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
     p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
     p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
+    p.off_c0q = o; o += al(sizeof(float2) * ptot);
     p.off_qabs = o; o += al(sizeof(float2) * m);
     p.off_spart = o; o += al(sizeof(double) * 6 * ST_BLOCKS * m);
     p.off_tcpart = p.off_w16 = o;
@@ -1160,7 +1185,12 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
     if (std::is_same<T, float>::value && c->rtab && c->schunks) {
-        k_real_cells<<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
+        if (c->nrtab <= RC_SMEM_TABS)
+            k_real_cells<true><<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
+            c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
+            (const float4*)c->rtab, c->nrtab, c->rtab_id, real);
+        else
+            k_real_cells<false><<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
             c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
             (const float4*)c->rtab, c->nrtab, c->rtab_id, real);
     } else {
@@ -1227,11 +1257,12 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_begin(c, CPM_K_COL0);
         const int nblk = (k.ext0 + C0_NB - 1) / C0_NB;
         float4* e1s = (float4*)(scr + p.off_c0e1);
-        k_col0_phase1<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, ptot, c->g.inv[2], e1s);
+        float2* q0 = (float2*)(scr + p.off_c0q);
+        k_col0_phase1<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, Q, ptot, c->g.inv[2], e1s, q0);
         CPM_LAUNCH(c, "k_col0_phase1");
-        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, Q, ne, k.ext0, c0part);
+        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, q0, ne, k.ext0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
-        k_col0_reduce<<<(m * k.ext0 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
+        k_col0_reduce<<<(m * k.ext0 * 32 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
         CPM_LAUNCH(c, "k_col0_reduce");
         k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, k.ext0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");

@@ -259,6 +259,11 @@ cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, doub
 cpm_status tc_reserve(cpm_ctx* c, int m);
 cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms);
 
+// gemv_tma.cu: single-precision S streaming with TMA (n a multiple of 4)
+bool gemv_tma_supported(const cpm_ctx* c);
+void gemv_tma_plan(int64_t n, int m, int64_t* colblocks, int64_t* splits, int64_t* jchunk);
+cpm_status gemv_tma(cpm_ctx* c, int m, const float2* bhl, double* part, int64_t splits, int64_t jchunk);
+
 // tc_recip.cu: reciprocal-space sums of b on the tensor cores (k_prec = CPM_PREC_F16X2)
 struct TcRecipDims {
     int mtiles, ntiles, cpad, splits;   // stage 1: column tiles, harmonic tiles, padded columns, charge splits

@@ -380,8 +380,12 @@ static cpm_status reserve_update_plan(cpm_ctx* c, int m, int64_t* splits_out, in
     const int64_t want = gemv_pairs(c) ? 2 * 152 : 4 * 152;   // resident blocks: about one wave
     int64_t splits = (want + colblocks * rchunks - 1) / (colblocks * rchunks);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n + GT_JT - 1) / GT_JT));
-    const int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
+    int64_t jchunk = (((n + splits - 1) / splits + GT_JT - 1) / GT_JT) * GT_JT;
     splits = (n + jchunk - 1) / jchunk;
+    if (gemv_tma_supported(c)) {
+        int64_t cb;
+        gemv_tma_plan(n, m, &cb, &splits, &jchunk);
+    }
     const size_t need = ((sizeof(double) * splits * m * n + 255) & ~(size_t)255) + sizeof(float2) * m * n;
     if (c->ubuf_bytes < need) {
         dev_free(c, c->ubuf);
@@ -424,7 +428,8 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
         k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
-        if (gemv_pairs(c)) k_gemv32x2<<<grid, G2_T, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
+        if (gemv_tma_supported(c)) CPM_TRY(gemv_tma(c, m, bhl, part, splits, jchunk));
+        else if (gemv_pairs(c)) k_gemv32x2<<<grid, G2_T, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
         else k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
     } else {
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
