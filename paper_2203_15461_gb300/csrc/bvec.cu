@@ -774,11 +774,11 @@ __global__ void __launch_bounds__(256) k_site(const int2* __restrict__ cols, con
     }
 }
 
-// ----------------------------------------------------------------------------- k_perp = 0 column in FP64
-// The single-precision path sums the column (0, 0, nz), nz = 1..ext0, in FP64: its weights
-// are the largest of the whole set (they carry the laterally averaged charge profile), so
-// its terms dominate the rounding of a single-precision sum.  Phases by an FP64 recurrence
-// in nz from an exactly reduced first harmonic.
+// ----------------------------------------------------------------------------- k_perp = 0 column, double-float
+// The single-precision paths sum the first harmonics of the column (0, 0, nz), nz = 1..COL0_NZ,
+// in double-float: their weights are the largest of the whole set (they carry the laterally
+// averaged charge profile), so their terms would dominate the rounding of a single-precision sum.
+// Phases by a double-float recurrence in nz from an exactly reduced first harmonic.
 __device__ __forceinline__ double2 z_phase_n(double z, double invLz, int nz) {
     double s = z * invLz;
     s -= floor(s);
@@ -920,8 +920,8 @@ __global__ void k_col0_reduce(const double2* __restrict__ part, int nchunks, int
     }
 }
 
-// e0[u][nz - 1] = exp(i kz z_u) for each distinct site height z_u (fixed with the geometry), one
-// exactly reduced FP64 sincospi per entry
+// e0[u][nz - 1] = exp(i kz z_u) for each distinct site height z_u and nz = 1 .. COL0_NZ (fixed with
+// the geometry), one exactly reduced FP64 sincospi per entry
 __global__ void k_col0_e0(const double* __restrict__ zu, int nzu, double invLz, int nz0, double2* __restrict__ e0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nzu * nz0) return;
@@ -1108,7 +1108,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_order = o; o += al(sizeof(int) * ptot);
     p.c0chunks = (int)std::max<int64_t>(1, (ne + C0_THREADS * C0_PER_THREAD - 1) / (C0_THREADS * C0_PER_THREAD));
-    const int nz0 = std::max(k.ext0, 1);
+    const int nz0 = std::max(std::min(k.ext0, COL0_NZ), 1);
     p.off_c0part = o; o += al(sizeof(double2) * (size_t)m * p.c0chunks * nz0);
     p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
@@ -1255,16 +1255,17 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         double2* c0w = (double2*)(scr + p.off_c0w);
         b0 = (double*)(scr + p.off_b0);
         prof_begin(c, CPM_K_COL0);
-        const int nblk = (k.ext0 + C0_NB - 1) / C0_NB;
+        const int nz0 = std::min(k.ext0, COL0_NZ);
+        const int nblk = (nz0 + C0_NB - 1) / C0_NB;
         float4* e1s = (float4*)(scr + p.off_c0e1);
         float2* q0 = (float2*)(scr + p.off_c0q);
         k_col0_phase1<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, Q, ptot, c->g.inv[2], e1s, q0);
         CPM_LAUNCH(c, "k_col0_phase1");
-        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, q0, ne, k.ext0, c0part);
+        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, q0, ne, nz0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
-        k_col0_reduce<<<(m * k.ext0 * 32 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, k.ext0, k.w, k.NZ, m, c0w);
+        k_col0_reduce<<<(m * nz0 * 32 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, nz0, k.w, k.NZ, m, c0w);
         CPM_LAUNCH(c, "k_col0_reduce");
-        k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, k.ext0, c0w, b0);
+        k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, nz0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
         c->launches += 4;
@@ -1281,7 +1282,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
 cpm_status build_col0_sites(cpm_ctx* c) {
     dev_free(c, c->c0e);
     c->c0e = nullptr;
-    const int nz0 = c->kt.ext0;
+    const int nz0 = std::min(c->kt.ext0, COL0_NZ);
     if (nz0 <= 0 || c->nzu == 0) return CPM_OK;
     CPM_TRY(dev_alloc(c, (void**)&c->c0e, sizeof(double2) * (size_t)c->nzu * nz0));
     k_col0_e0<<<(c->nzu * nz0 + 255) / 256, 256, 0, c->stream>>>(c->zuniq, c->nzu, c->g.inv[2], nz0, c->c0e);

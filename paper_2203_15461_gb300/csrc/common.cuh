@@ -44,6 +44,11 @@ enum : unsigned { ST_NOT_SPD = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
 // width nzw = 2 NZ + 1.  The Ewald weight of an entry is zero outside the
 // half-space ball 0 < |k| <= kcut, so the dense grid and the compact list hold
 // the same set of vectors.
+// Harmonics of the k_perp = 0 column that the single-precision paths sum in double-float; its
+// higher harmonics (weights below ~1e-3 of the first for the usual splittings) go through the
+// single-precision sums with the rest of the k set.
+constexpr int COL0_NZ = 12;
+
 struct KTable {
     int NX = 0, NY = 0, NZ = 0;
     int ncols = 0, nzw = 0;
@@ -127,7 +132,7 @@ struct cpm_ctx {
     unsigned* status = nullptr;  // device status word
     int* tickets = nullptr;      // [tickets_n] per-replica arrival counters, zero between launches
     int tickets_n = 0;
-    double2* c0e = nullptr;      // [nzu][ext0] exp(i kz z_u) of the k_perp = 0 column at the site heights
+    double2* c0e = nullptr;      // [nzu][min(ext0, COL0_NZ)] exp(i kz z_u) of the k_perp = 0 column at the sites
     double* nbuf = nullptr;      // neutrality fix: per-block partial sums of q
     size_t nbuf_bytes = 0;
     bool assembled = false, inverted = false;

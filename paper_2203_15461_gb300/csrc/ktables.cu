@@ -95,8 +95,9 @@ __global__ void k_weights(const int2* cols, int ncols, int NZ, double tx, double
     }
     w[i] = wt;
     // The k_perp = 0 column carries the largest weights (the laterally averaged charge
-    // profile); the single-precision path leaves it to an FP64 kernel.
-    w32[i] = (cn.x == 0 && cn.y == 0) ? 0.0f : (float)wt;
+    // profile); the single-precision path leaves its first COL0_NZ harmonics to a double-float
+    // kernel.
+    w32[i] = (cn.x == 0 && cn.y == 0 && nz <= COL0_NZ) ? 0.0f : (float)wt;
 }
 
 __global__ void k_colcounts(const int2* cols, const int* colext, int ncols, int64_t* cnt) {
