@@ -183,8 +183,10 @@ template <> __device__ __forceinline__ double erfc_t<double>(double x) { return 
 // Pair function f(r) = (erfc(alpha r) - erfc(eta r)) / r of a site's Gaussian width eta, tabulated
 // for the single-precision path: cubic Hermite pieces on RT_N equal intervals of [0, rcut], built
 // in FP64 from f and f' (f is even and smooth, f(0) = 2 (eta - alpha) / sqrt(pi)); the
-// interpolation error is below 1e-8 of f(0) for the widths and cut-offs used here.
+// interpolation error is below 1e-8 of f(0) for the widths and cut-offs used here.  Each table has
+// one more, all-zero row (index RT_N) for distances at or past the cut-off.
 constexpr int RT_N = 1024;
+constexpr int RT_S = RT_N + 1;   // rows per table
 
 __device__ inline void pair_f_df(double r, double a, double e, double* f, double* df) {
     if (r == 0.0) {
@@ -200,8 +202,12 @@ __device__ inline void pair_f_df(double r, double a, double e, double* f, double
 __global__ void k_pair_tables(const double* __restrict__ etas, int ntab, double alpha, double rcut,
                               float4* __restrict__ tab) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntab * RT_N) return;
-    const int id = t / RT_N, k = t % RT_N;
+    if (t >= ntab * RT_S) return;
+    const int id = t / RT_S, k = t % RT_S;
+    if (k == RT_N) {
+        tab[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const double h = rcut / RT_N, e = etas[id];
     double f0, d0, f1, d1;
     pair_f_df(k * h, alpha, e, &f0, &d0);
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
     const T a = (T)g.alpha;
     const T rc2 = (T)(g.rcut * g.rcut);
     const T px = (T)sw[0], py = (T)sw[1], pz = (T)sw[2];
-    const float4* tb = (tab && tabid) ? tab + (int64_t)tabid[i] * RT_N : nullptr;
+    const float4* tb = (tab && tabid) ? tab + (int64_t)tabid[i] * RT_S : nullptr;
     const float inv_h = (float)(RT_N / g.rcut);
     const float hf[3] = {(float)cg.h[0], (float)cg.h[1], (float)cg.h[2]};
     const float swf[3] = {(float)sw[0], (float)sw[1], (float)sw[2]};
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                  int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
                  const float4* __restrict__ sorted, const float4* __restrict__ tab, int ntab,
                  const int* __restrict__ tabid, double* __restrict__ out) {
-    __shared__ float4 stab[RC_SMEM_TABS * RT_N];
+    __shared__ float4 stab[RC_SMEM_TABS * RT_S];
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
     __shared__ float red[RC_WARPS][32][33];         // [warp][site][lane]
     __shared__ float sbox[6];
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x, r = blockIdx.y;
     if (SMEM_TAB)
-        for (int e = threadIdx.x; e < ntab * RT_N; e += blockDim.x) stab[e] = tab[e];
+        for (int e = threadIdx.x; e < ntab * RT_S; e += blockDim.x) stab[e] = tab[e];
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
     const int nsites = cinfo.y;
     if (warp == 0) {
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         if (lane < nsites) {
             const int i = perm[cinfo.x + lane];
             px = s32[i]; py = s32[n + i]; pz = s32[2 * n + i];
-            toff = tabid[i] * RT_N;
+            toff = tabid[i] * RT_S;
         }
         if (lane >= nsites) px = py = pz = 1.0e6f;   // dummy sites, beyond any cutoff
         ssite[lane] = make_float4(px, py, pz, __int_as_float(toff));
@@ -359,6 +365,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     const float rc2 = (float)(g.rcut * g.rcut);
     const float inv_h = (float)(RT_N / g.rcut);
     const float hx = (float)cg.h[0], hy = (float)cg.h[1], hz = (float)cg.h[2];
+    const float lx = (float)g.boxL[0], ly = (float)g.boxL[1], lz = (float)g.boxL[2];
     const float bx0 = sbox[0], by0 = sbox[1], bz0 = sbox[2], bx1 = sbox[3], by1 = sbox[4], bz1 = sbox[5];
     float acc[32];
 #pragma unroll
@@ -392,8 +399,8 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                     nrun = floordiv(uxe, cg.nc[0]) - fx0 + 1;
                     const int fz = floordiv(uz, cg.nc[2]), wz = uz - fz * cg.nc[2];
                     const int fy = floordiv(uy, cg.nc[1]), wyy = uy - fy * cg.nc[1];
-                    shz = (float)(fz * g.boxL[2]);
-                    shy = (float)(fy * g.boxL[1]);
+                    shz = (float)fz * lz;
+                    shy = (float)fy * ly;
                     rowbase = r * cg.ncells + (wz * cg.nc[1] + wyy) * cg.nc[0];
                 }
             }
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
             const int b = start[rowbase + wx0], e = start[rowbase + wx1 + 1];
             rbeg[off + k] = b;
             rpre[off + k] = e - b;
-            rsh[off + k] = make_float4((float)(fx * g.boxL[0]), shy, shz, 0.f);
+            rsh[off + k] = make_float4((float)fx * lx, shy, shz, 0.f);
         }
         __syncwarp();
         // exclusive prefix of the range lengths (nent <= RC_LIST)
@@ -457,14 +464,13 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                     const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
                     const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                     const float u = sqrt_approx(r2) * inv_h;
-                    // floor(u) by the 1.5 * 2^23 rounding trick (u >= 0; a tie rounds either way and
-                    // the cubic pieces join continuously)
-                    const float ur = (u - 0.5f) + 12582912.0f;
-                    const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N - 1);
+                    // floor(u) from the bits of u + 1.5 * 2^23 rounded toward zero (u >= 0); at and
+                    // past the cutoff the index clamps to the table's zero row
+                    const float ur = __fadd_rz(u, 12582912.0f);
+                    const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N);
                     const float t = u - (ur - 12582912.0f);
                     const float4 cf = tb[__float_as_int(st.w) + kk];
-                    const float w = r2 < rc2 ? qw : 0.f;
-                    acc[s] = fmaf(w, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
+                    acc[s] = fmaf(qw, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
                 }
             }
         }
@@ -487,11 +493,11 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
     dev_free(c, c->rtab);
     c->rtab = nullptr;
-    CPM_TRY(dev_alloc(c, (void**)&c->rtab, sizeof(float4) * RT_N * etas.size()));
+    CPM_TRY(dev_alloc(c, (void**)&c->rtab, sizeof(float4) * RT_S * etas.size()));
     double* de = nullptr;
     CPM_TRY(dev_alloc(c, (void**)&de, sizeof(double) * etas.size()));
     CPM_CUDA(c, cudaMemcpyAsync(de, etas.data(), sizeof(double) * etas.size(), cudaMemcpyHostToDevice, c->stream));
-    const int tot = (int)etas.size() * RT_N;
+    const int tot = (int)etas.size() * RT_S;
     k_pair_tables<<<(tot + 127) / 128, 128, 0, c->stream>>>(de, (int)etas.size(), c->g.alpha, c->g.rcut,
                                                              (float4*)c->rtab);
     CPM_LAUNCH(c, "k_pair_tables");

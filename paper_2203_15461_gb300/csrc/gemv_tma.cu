@@ -192,7 +192,8 @@ bool gemv_tma_supported(const cpm_ctx* c) { return c->p.s_prec == CPM_PREC_FP32 
 void gemv_tma_plan(int64_t n, int m, int64_t* colblocks, int64_t* splits, int64_t* jchunk) {
     *colblocks = (n + GV_BC - 1) / GV_BC;
     const int64_t rchunks = (m + GV_MR - 1) / GV_MR;
-    int64_t sp = std::max<int64_t>(1, (152 + *colblocks * rchunks - 1) / (*colblocks * rchunks));
+    // one wave: at most one block per SM (the ring takes most of the shared memory)
+    int64_t sp = std::max<int64_t>(1, 152 / (*colblocks * rchunks));
     sp = std::max<int64_t>(sp, (n + GV_JMAX - 1) / GV_JMAX);
     int64_t jc = (n + sp - 1) / sp;
     jc = ((jc + GV_RJ - 1) / GV_RJ) * GV_RJ;
