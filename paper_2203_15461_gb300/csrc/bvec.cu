@@ -42,7 +42,7 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 // (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).  Grid (SB, m):
 // block b sums its slice of the charges into part[r][b][6]; the last block of the replica adds
 // the slices in order.
-constexpr int ST_THREADS = 256, ST_BLOCKS = 32;
+constexpr int ST_THREADS = 256, ST_BLOCKS = 16;
 __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const double* Q, int64_t ne, double* part,
                                                      int* tickets, double* stats, float2* qabs) {
     __shared__ double sh[6][ST_THREADS / 32];
@@ -1167,7 +1167,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
 
     prof_begin(c, CPM_K_STATS);
     float2* qabs = (float2*)(scr + p.off_qabs);
-    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ST_BLOCKS, (ne + 255) / 256));
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ST_BLOCKS, (ne + 511) / 512));
     k_stats<<<dim3(sblocks, m), ST_THREADS, 0, st>>>(xyz, Q, ne, (double*)(scr + p.off_spart), c->tickets, stats,
                                                     p.tc ? qabs : nullptr);
     prof_end(c, CPM_K_STATS);

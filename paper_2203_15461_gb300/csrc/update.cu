@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NB_T) k_neutral_fix(double* __restrict__ q, co
     }
 }
 
-static int neutral_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 255) / 256)); }
+static int neutral_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 1023) / 1024)); }
 
 static cpm_status reserve_neutral(cpm_ctx* c, int m) {
     CPM_TRY(ensure_tickets(c, m));
