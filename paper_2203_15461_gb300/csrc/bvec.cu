@@ -1,6 +1,5 @@
 // Electrolyte vector b: the potential of the electrolyte point charges at every electrode
-// site (Sec. II.A: "the main computational burden" of each MD step), for m electrolyte
-// configurations at once.
+// site (Sec. II.A: the dominant cost of each MD step), for m electrolyte configurations at once.
 //
 //   b_i = K_E [ sum_j Q_j sum'_n (erfc(alpha r) - erfc(eta_i r)) / r     real space, cell list
 //             + sum_k w_k Re[exp(-i k.R_i) rho(k)]                      reciprocal space
@@ -10,7 +9,8 @@
 // (column c = (nx, ny), harmonic nz):
 //   structure factor  rho[c][nz] = sum_j (Q_j X_j[nx_c] Y_j[ny_c]) Z_j[nz]
 //   site potential    b_i      += sum_c Re[ conj(X_i[nx_c] Y_i[ny_c]) sum_nz w[c][nz] rho[c][nz] conj(Z_i[nz]) ]
-// both register-tiled on the CUDA cores (complex products of phase-table entries).
+// register-tiled on the CUDA cores here (k_prec FP64 and FP32), or as tensor-core products
+// (k_prec F16X2, tc_recip.cu).
 #include <algorithm>
 
 #include "common.cuh"
