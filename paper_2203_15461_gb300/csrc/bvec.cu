@@ -293,9 +293,10 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
 // rows (dy, dz) of the cell's stencil.  Rows whose cells lie farther than r_c from the bounding box
 // of the chunk's sites are skipped and the x range of each row is trimmed the same way; since the
 // cells of a row are consecutive in the sorted charge array, a row is one contiguous range per
-// image shift.  The lanes of a warp take 32 charges of its concatenated ranges at a time and
-// every lane runs over all sites of the chunk, keeping one partial sum per site; the partial sums
-// of all lanes and warps are added per site in a fixed order at the end.  The pair-function tables of up to two widths
+// image shift.  The lanes of a warp read 32 charges of its concatenated ranges at a time; those
+// within r_c of the sites' box are compacted into a per-warp ring, and whenever 32 are there every
+// lane takes one and runs over all sites of the chunk, keeping one partial sum per site; the
+// partial sums of all lanes and warps are added per site in a fixed order at the end.  The pair-function tables of up to two widths
 // are staged in shared memory.
 constexpr int RC_WARPS = 4;
 constexpr int RC_SMEM_TABS = 2;
@@ -323,11 +324,24 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                  const int* __restrict__ tabid, double* __restrict__ out) {
     __shared__ float4 stab[RC_SMEM_TABS * RT_S];
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
-    __shared__ float red[RC_WARPS][32][33];         // [warp][site][lane]
     __shared__ float sbox[6];
-    __shared__ int lbeg[RC_WARPS][RC_LIST];         // per warp: charge ranges of a group of rows
-    __shared__ int lpre[RC_WARPS][RC_LIST + 1];
-    __shared__ float4 lsh[RC_WARPS][RC_LIST];
+    // per warp while streaming: the charge ranges of a group of rows and the ring of charges that
+    // passed the box test; at the end the same bytes hold the per-site partial sums
+    struct Lists {
+        int beg[RC_WARPS][RC_LIST];
+        int pre[RC_WARPS][RC_LIST + 1];
+        float4 sh[RC_WARPS][RC_LIST];
+        float4 ring[RC_WARPS][64];
+    };
+    union Shared {
+        Lists l;
+        float red[RC_WARPS][32][33];   // [warp][site][lane]
+    };
+    __shared__ Shared u_;
+    auto& lbeg = u_.l.beg;
+    auto& lpre = u_.l.pre;
+    auto& lsh = u_.l.sh;
+    auto& red = u_.red;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x, r = blockIdx.y;
     if (SMEM_TAB)
@@ -370,6 +384,32 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     float acc[32];
 #pragma unroll
     for (int s = 0; s < 32; ++s) acc[s] = 0.f;
+    // every lane holds one charge (weight qw, zero for an empty lane) and runs over the chunk's sites
+    auto eval_sites = [&](const float4 q, const float qw) {
+#pragma unroll
+        for (int sg = 0; sg < 32; sg += 8) {
+            if (sg >= nsites) break;   // uniform; sites past nsites are far-away dummies
+#pragma unroll
+            for (int s = sg; s < sg + 8; ++s) {
+                // branch-free pair term: the table index is clamped and the weight is zero
+                // outside the cutoff, so the eight sites of a group interleave
+                const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
+                const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
+                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const float u = sqrt_approx(r2) * inv_h;
+                // floor(u) from the bits of u + 1.5 * 2^23 rounded toward zero (u >= 0); at and
+                // past the cutoff the index clamps to the table's zero row
+                const float ur = __fadd_rz(u, 12582912.0f);
+                const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N);
+                const float t = u - (ur - 12582912.0f);
+                const float4 cf = tb[__float_as_int(st.w) + kk];
+                acc[s] = fmaf(qw, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
+            }
+        }
+    };
+    // charges that pass the box test wait in a per-warp ring until 32 are there
+    float4* ring = u_.l.ring[warp];
+    int rhead = 0, rcount = 0;   // warp-uniform
     // The warp's rows are taken in groups; the charge ranges (runs of cells with one image shift)
     // of a group are listed in shared memory and streamed as one concatenated sequence, 32 charges
     // per step, so that the lanes stay busy across the ends of the ranges.
@@ -440,9 +480,9 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         __syncwarp();
         for (int base = 0; base < total; base += 32) {
             const int v = base + lane;
-            const bool live = v < total;
+            bool keep = v < total;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (live) {
+            if (keep) {
                 int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= v
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -451,31 +491,31 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                 q = sorted[rbeg[lo] + (v - rpre[lo])];
                 const float4 sh = rsh[lo];
                 q.x += sh.x; q.y += sh.y; q.z += sh.z;
+                // only charges within r_c of the sites' box can reach a site
+                const float ex = fmaxf(0.f, fmaxf(bx0 - q.x, q.x - bx1));
+                const float ey = fmaxf(0.f, fmaxf(by0 - q.y, q.y - by1));
+                const float ez = fmaxf(0.f, fmaxf(bz0 - q.z, q.z - bz1));
+                keep = ex * ex + ey * ey + ez * ez < rc2;
             }
-            const float qw = live ? q.w : 0.f;
-#pragma unroll
-            for (int sg = 0; sg < 32; sg += 8) {
-                if (sg >= nsites) break;   // uniform; sites past nsites are far-away dummies
-#pragma unroll
-                for (int s = sg; s < sg + 8; ++s) {
-                    // branch-free pair term: the table index is clamped and the weight is zero
-                    // outside the cutoff, so the eight sites of a group interleave
-                    const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
-                    const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
-                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    const float u = sqrt_approx(r2) * inv_h;
-                    // floor(u) from the bits of u + 1.5 * 2^23 rounded toward zero (u >= 0); at and
-                    // past the cutoff the index clamps to the table's zero row
-                    const float ur = __fadd_rz(u, 12582912.0f);
-                    const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N);
-                    const float t = u - (ur - 12582912.0f);
-                    const float4 cf = tb[__float_as_int(st.w) + kk];
-                    acc[s] = fmaf(qw, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
-                }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) ring[(rhead + rcount + __popc(bal & ((1u << lane) - 1u))) & 63] = q;
+            rcount += __popc(bal);
+            __syncwarp();
+            if (rcount >= 32) {
+                const float4 qq = ring[(rhead + lane) & 63];
+                __syncwarp();
+                rhead = (rhead + 32) & 63;
+                rcount -= 32;
+                eval_sites(qq, qq.w);
             }
         }
         __syncwarp();
     }
+    if (rcount > 0) {   // the rest of the ring
+        const float4 qq = lane < rcount ? ring[(rhead + lane) & 63] : make_float4(0.f, 0.f, 0.f, 0.f);
+        eval_sites(qq, lane < rcount ? qq.w : 0.f);
+    }
+    __syncthreads();   // the lists and rings are done: their bytes now take the partial sums
 #pragma unroll
     for (int s = 0; s < 32; ++s) red[warp][s][lane] = acc[s];
     __syncthreads();
