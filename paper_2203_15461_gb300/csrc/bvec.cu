@@ -1135,8 +1135,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     const int64_t tabX = (int64_t)(k.NX + 1) * ptot, tabY = (int64_t)(2 * k.NY + 1) * ptot;
     p.off_EX = o; o += al(sizeof(c2<T>) * tabX);
     p.off_EY = o; o += al(sizeof(c2<T>) * tabY);
-    p.off_EZ = o;
-    o += al(p.tc ? tc_recip_zp_bytes(td, m, k.nzw) : sizeof(c2<T>) * (pe - tabX - tabY));   // Z table or fp16 planes
+    p.off_EZ = o; o += al(sizeof(c2<T>) * (pe - tabX - tabY));
     p.off_Q = o; o += al(sizeof(T) * ptot);
     if (p.tc) {   // the CUDA-core structure-factor buffers are not used
         p.off_rp = p.off_wr = o;
@@ -1250,17 +1249,11 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     // reciprocal space
     if (k.nk > 0 && ptot > 0) {
         prof_begin(c, CPM_K_PHASES);
-        if (p.tc) {
-            const TcRecipDims td = tc_recip_dims(c, m, ne);
-            CPM_TRY(launch_phases_tc(st, c->g, k, xyz, ptot, ne, td.ne_pad, m, (uint64_t*)(scr + p.off_u),
-                                     (float2*)EX, (float2*)EY, (uint32_t*)EZ));
-        } else {
-            CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ));
-        }
+        CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ));
         prof_end(c, CPM_K_PHASES);
         if (p.tc) {
-            CPM_TRY(tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const uint32_t*)EZ,
-                                 (const float*)Qv, qabs, scr + p.off_tcpart, scr + p.off_w16, (float*)part));
+            CPM_TRY(tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const float2*)EZ, (const float*)Qv,
+                                 qabs, scr + p.off_tcpart, scr + p.off_w16, (float*)part));
         } else {
         prof_begin(c, CPM_K_SF);
         if (std::is_same<T, float>::value) {

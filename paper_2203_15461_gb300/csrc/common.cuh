@@ -213,8 +213,6 @@ template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
                          c2<T>* X, c2<T>* Y, c2<T>* Z);
 size_t phase_elems(const KTable& k, int64_t P);
-cpm_status launch_phases_tc(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                            int64_t ne, int64_t ne_pad, int m, uint64_t* u, float2* X, float2* Y, uint32_t* zp);
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
                            uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z);
@@ -278,15 +276,13 @@ struct TcRecipDims {
     int mr, nrb, CT, ncb, NB, ngroups;  // stage 2: replicas per block, blocks, columns per group, ...
     int KZ;                             // padded K extent (2 x harmonics)
     int64_t npad;                       // padded site count
-    int64_t ne_pad;                     // charges per replica in the Z planes (multiple of 32)
 };
 bool tc_recip_supported(const KTable& k);   // phase-table rows fit the staging buffer
 TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne);
 size_t tc_recip_part_bytes(const TcRecipDims& d, int m, int nzw);
 size_t tc_recip_w16_bytes(const TcRecipDims& d);
 cpm_status tc_recip_prepare(cpm_ctx* c);
-size_t tc_recip_zp_bytes(const TcRecipDims& d, int m, int nzw);
-cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const uint32_t* zp,
+cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const float2* EZ,
                         const float* Qv, const float2* qabs, void* part, void* w16, float* site_partial);
 
 }  // namespace cpm

@@ -6,8 +6,6 @@
 // the factor 2 standing for the mirror vector -k.  Membership is decided with
 // correctly rounded multiplies and adds in a fixed order so that the set does
 // not depend on FMA contraction.
-#include <cuda_fp16.h>
-
 #include "common.cuh"
 
 namespace cpm {
@@ -270,42 +268,6 @@ cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, 
     k_phases_u<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X, Y, Z);
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
 }
-// Charge phases along z for the tensor-core structure factor: zp[q][zi][jp] = term q of
-// 2^14 (Re, Im) Z_j[zi] as a packed fp16 pair (q = 0: fp16 of the value, q = 1: fp16 of the
-// remainder), jp = r ne_pad + l for charge l < ne of replica r; padding slots hold zeros.
-__global__ void k_zplanes(const uint64_t* __restrict__ u, int64_t P, int64_t ne, int64_t ne_pad, int m, int NZ,
-                          uint32_t* __restrict__ zp) {
-    const int64_t kw = (int64_t)m * ne_pad, nzw = 2 * NZ + 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nzw * kw) return;
-    const int zi = (int)(t / kw);
-    const int64_t jp = t % kw, r = jp / ne_pad, l = jp % ne_pad;
-    uint32_t hi = 0u, lo = 0u;
-    if (l < ne) {
-        const float2 z = phase_of<float>(u[2 * P + r * ne + l], zi - NZ);
-        const float zr = z.x * 16384.f, zm = z.y * 16384.f;
-        const __half2 h = __floats2half2_rn(zr, zm);
-        const float2 f = __half22float2(h);
-        const __half2 q = __floats2half2_rn(zr - f.x, zm - f.y);
-        hi = *reinterpret_cast<const uint32_t*>(&h);
-        lo = *reinterpret_cast<const uint32_t*>(&q);
-    }
-    zp[t] = hi;
-    zp[nzw * kw + t] = lo;
-}
-
-// X and Y tables as for the CUDA-core path, Z as the fp16 planes above
-cpm_status launch_phases_tc(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                            int64_t ne, int64_t ne_pad, int m, uint64_t* u, float2* X, float2* Y, uint32_t* zp) {
-    if (P == 0) return CPM_OK;
-    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u);
-    const int64_t txy = P * ((k.NX + 1) + (2 * k.NY + 1));   // the X and Y slots only
-    k_phases_u<float><<<(unsigned)((txy + 255) / 256), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X, Y, nullptr);
-    const int64_t tz = (int64_t)k.nzw * m * ne_pad;
-    k_zplanes<<<(unsigned)((tz + 255) / 256), 256, 0, st>>>(u, P, ne, ne_pad, m, k.NZ, zp);
-    return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
-}
-
 template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
                                            uint64_t*, float2*, float2*, float2*);
 template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,

@@ -10,7 +10,7 @@
 //
 // Both stages are dense complex contractions (over the charges j, then over the harmonics nz),
 // so they run as real matrix products with (re, im) interleaved along K and N:
-//   stage 1: A rows (c, re) = (Pr, -Pi), (c, im) = (Pi, Pr) (K = (j, re/im)), B rows nz = (Zr, Zi)
+//   stage 1: A = P (rows c, K = (j, re/im)), B rows (nz, re) = (Zr, -Zi), (nz, im) = (Zi, Zr)
 //   stage 2: A = site phases (rows i, K = (nz, re/im)), B rows (c, r, re) = (Wr, Wi),
 //            (c, r, im) = (Wi, -Wr); the epilogue contracts over c with conj(X_i Y_i).
 //
@@ -19,9 +19,9 @@
 // are accumulated in FP32 in tensor memory and the scales are removed exactly afterwards.  The
 // k_perp = 0 column keeps its double-float treatment (its single-precision weight is zero here).
 //
-// Stage 1 builds its P tile in shared memory from the phase tables (64 columns x 32 charges per K
-// step, two rows per column, 128-byte swizzle) and copies the charge phases Z, written as fp16
-// planes by k_zplanes, into the same layout; stage 2 streams both operands with TMA.  One thread issues the tcgen05.mma instructions; every
+// Stage 1 builds both operand tiles in shared memory from the phase tables (128 columns x 32
+// charges of P, 2 x 128 harmonic rows x 32 charges of Z per K step, 128-byte swizzle); stage 2
+// streams its operands with TMA.  One thread issues the tcgen05.mma instructions; every
 // mbarrier wait is bounded by wall time and on expiry the CTA records ST_TIMEOUT, frees its
 // tensor memory and returns.
 #include <cuda_fp16.h>
@@ -36,20 +36,19 @@ namespace cpm {
 constexpr uint64_t RT_WAIT_NS = 2000000000ull;   // bound on any single mbarrier wait: 2 s
 
 // stage 1 (structure factor)
-constexpr int RF_CM = 64;                      // columns per tile: two MMA rows each (M = 128)
-constexpr int RF_BM = 2 * RF_CM;
-constexpr int RF_ZT = 128;                     // harmonics per tile (MMA N <= 128)
+constexpr int RF_BM = 128;                     // columns per tile (MMA M)
+constexpr int RF_ZT = 128;                     // harmonics per tile (MMA N = 2 x 128)
 constexpr int RF_KC = 32;                      // charges per K step (64 fp16 = 128 bytes per row)
 constexpr int RF_GEN = 256;                    // operand-building threads (warps 0-7)
 constexpr int RF_THREADS = RF_GEN + 32;        // + the MMA warp
 constexpr int RF_A = RF_BM * 128;              // one fp16 term of the P tile (16 KB)
-constexpr int RF_B = RF_ZT * 128;              // one fp16 term of the Z tile (16 KB)
-constexpr int RF_STAGE = 2 * RF_A + 2 * RF_B;  // 64 KB
-constexpr int RF_STAGES = 3;
-constexpr int RF_XYROWS = 60;                  // staged phase-table rows: (NX + 1) + (2 NY + 1) at most
+constexpr int RF_B = 2 * RF_ZT * 128;          // one fp16 term of the Z tile (32 KB)
+constexpr int RF_STAGE = 2 * RF_A + 2 * RF_B;  // 96 KB
+constexpr int RF_STAGES = 2;
+constexpr int RF_XYROWS = 60;                 // staged phase-table rows: (NX + 1) + (2 NY + 1) at most
 constexpr int RF_STAGE_XY = (RF_XYROWS + 1) * RF_KC * 8;   // X, Y rows and Q of one K step
 constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048 + RF_STAGE_XY;
-constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14 (k_zplanes)
+constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14
 
 // stage 2 (site potentials)
 constexpr int RS_BM = 128;                     // sites per tile (MMA M)
@@ -105,15 +104,13 @@ __device__ __forceinline__ uint32_t sw128(int r, int ch) { return (uint32_t)(r *
 
 // ----------------------------------------------------------------------------- stage 1
 // part[s][r][zi][c] = 2^14 sA_r sum over the charges of split s of P_r[c][j] Z_j[zi]   (zi = nz + NZ)
-// grid (column tiles of 64, harmonic tiles of 128, m * splits); sA_r = 2^e with |Q| sA_r < 2^14.
-// zp: the fp16 charge-phase planes of k_zplanes, [2][nzw][kw] words (kw = m ne_pad), read as 16-byte
-// chunks of four charges.
+// grid (column tiles, harmonic tiles, m * splits); sA_r = 2^e with |Q| sA_r < 2^14.
 __global__ void __launch_bounds__(RF_THREADS, 1)
-    k_tc_sf(const uint4* __restrict__ zp, const int2* __restrict__ cols, const int* __restrict__ colext,
-            int ncols, int NX, int NY, int NZ, int nzw, const float2* __restrict__ EX, const float2* __restrict__ EY,
-            const float* __restrict__ Qv, const float2* __restrict__ qabs, int64_t ptot, int64_t ne,
-            int64_t ne_pad, int splits, int64_t chunk, int m, int cpad, float2* __restrict__ part,
-            unsigned* __restrict__ status, uint64_t wait_ns) {
+    k_tc_sf(const int2* __restrict__ cols, const int* __restrict__ colext, int ncols, int NX, int NY, int NZ, int nzw,
+            const float2* __restrict__ EX, const float2* __restrict__ EY, const float2* __restrict__ EZ,
+            const float* __restrict__ Qv, const float2* __restrict__ qabs, int64_t ptot, int64_t ne, int splits,
+            int64_t chunk, int m, int cpad, float2* __restrict__ part, unsigned* __restrict__ status,
+            uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* aux = smem + RF_STAGES * RF_STAGE;
@@ -123,20 +120,20 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     int* s_mx = (int*)(tmem_slot + 2);
-    int2* s_cols = (int2*)(aux + 128);
+    int2* s_cols = (int2*)(aux + 64);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * RF_CM;
+    const int c0 = blockIdx.x * RF_BM;
     const int r = blockIdx.z / splits, sp = blockIdx.z % splits;
 
     if (warp == 0) {
         int mx = -1;
-        for (int t = lane; t < RF_CM; t += 32)
+        for (int t = lane; t < RF_BM; t += 32)
             if (c0 + t < ncols) mx = max(mx, colext[c0 + t]);
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) *s_mx = mx;
     }
-    if (threadIdx.x < RF_CM) s_cols[threadIdx.x] = c0 + (int)threadIdx.x < ncols ? cols[c0 + threadIdx.x] : make_int2(0, 0);
+    if (threadIdx.x < RF_BM) s_cols[threadIdx.x] = c0 + (int)threadIdx.x < ncols ? cols[c0 + threadIdx.x] : make_int2(0, 0);
     if (threadIdx.x == 0) {
         for (int s = 0; s < RF_STAGES; ++s) { mbar_init(&full[s], RF_GEN); mbar_init(&empty[s], 1); }
         mbar_init(done, 1);
@@ -149,15 +146,14 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     const int zcount = min(RF_ZT, 2 * mx + 1 - zoff);
     if (mx < 0 || zcount <= 0) return;   // block-uniform; nothing allocated yet
     const int z_lo = NZ - mx + zoff;     // grid index of the tile's first harmonic
-    const int nused = ((zcount + 15) / 16) * 16;
-    const int64_t lb = (int64_t)sp * chunk;                     // first charge of the split (replica-local)
-    const int64_t le = min(ne, lb + chunk);
-    const int64_t jb = (int64_t)r * ne + lb, je = (int64_t)r * ne + le;
-    const int nsteps = le > lb ? (int)((le - lb + RF_KC - 1) / RF_KC) : 0;
+    const int nused = ((2 * zcount + 15) / 16) * 16;
+    const int64_t jb = (int64_t)r * ne + (int64_t)sp * chunk;
+    const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
+    const int nsteps = je > jb ? (int)((je - jb + RF_KC - 1) / RF_KC) : 0;
 
     if (warp == RF_GEN / 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(128u)
+                     "r"(256u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -168,17 +164,15 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
 
     if (warp < RF_GEN / 32) {
         // Operand builders.  Thread g owns 16-byte chunk ch = g % 8 (charges 4 ch .. 4 ch + 3 of the
-        // step) of columns g / 8 and g / 8 + 32 (P tile) and of harmonic rows g / 8 + 32 k of both
-        // fp16 planes (Z tile, copied as is).  The X and Y table rows and the charges of a step are
-        // staged in shared memory; the loads of step t + 1 are issued before step t is built.
+        // step) of P rows g / 8 + 32 k and of Z row pairs g / 8 + 32 k.  The X and Y table rows and
+        // the charges of a step are staged in shared memory; the loads of step t + 1 (staging
+        // entries and Z values) are issued before the tiles of step t are built.
         const float sA = pow2_below(qabs[r].x, 14);
-        const int g = threadIdx.x, ch = g & 7, cbase = g >> 3;
+        const int g = threadIdx.x, ch = g & 7, rbase = g >> 3;
         const int xyrows = (NX + 1) + (2 * NY + 1);
         const int nst = (xyrows + 1) * RF_KC;
-        const int64_t kw4 = (int64_t)m * ne_pad / 4;   // 16-byte chunks per plane row
         float2* sxy = (float2*)(aux + 2048);
-        float2 px[8];
-        uint4 pz[8];
+        float2 px[8], pz[4][4];
         auto prefetch = [&](int t) {
             const int64_t j0 = jb + (int64_t)t * RF_KC;
 #pragma unroll
@@ -196,13 +190,15 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 }
                 px[k] = v;
             }
-            // Z chunks: planes q = k / 4, rows cbase + 32 (k % 4); the 32 charges of the step are
-            // jp = r ne_pad + lb + 32 t .. + 31, inside the replica's padded segment
-            const int64_t c4 = ((int64_t)r * ne_pad + lb + (int64_t)t * RF_KC) / 4 + ch;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int q = k >> 2, zr = cbase + 32 * (k & 3);
-                pz[k] = zr < zcount ? zp[((int64_t)q * nzw + z_lo + zr) * kw4 + c4] : make_uint4(0u, 0u, 0u, 0u);
+            for (int k = 0; k < 4; ++k) {
+                const int zr = rbase + 32 * k;
+                const float2* zrow = EZ + (int64_t)(z_lo + min(zr, zcount - 1)) * ptot;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t j = j0 + 4 * ch + u;
+                    pz[k][u] = (zr < zcount && j < je) ? zrow[j] : make_float2(0.f, 0.f);
+                }
             }
         };
         if (nsteps > 0) prefetch(0);
@@ -214,21 +210,21 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (g + RF_GEN * k < nst) sxy[g + RF_GEN * k] = px[k];
-            const uint32_t sa = su32(smem + s * RF_STAGE);
-            const uint32_t sb = sa + 2 * RF_A;
+            float2 cz[4][4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int q = k >> 2, zr = cbase + 32 * (k & 3);
-                sts128(sb + q * RF_B + sw128(zr, ch), pz[k].x, pz[k].y, pz[k].z, pz[k].w);
-            }
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cz[k][u] = pz[k][u];
             gen_bar();
             if (t + 1 < nsteps) prefetch(t + 1);
+            const uint32_t sa = su32(smem + s * RF_STAGE);
+            const uint32_t sb = sa + 2 * RF_A;
             const float2* sq = sxy + xyrows * RF_KC + 4 * ch;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int cl = cbase + 32 * k;
-                const int2 cn = s_cols[cl];
-                const bool live = c0 + cl < ncols;
+            for (int k = 0; k < 4; ++k) {
+                const int row = rbase + 32 * k;
+                const int2 cn = s_cols[row];
+                const bool live = c0 + row < ncols;
                 const float2* xr = sxy + cn.x * RF_KC + 4 * ch;
                 const float2* yr = sxy + (NX + 1 + cn.y + NY) * RF_KC + 4 * ch;
                 uint32_t h[4], l[4];
@@ -242,12 +238,23 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     }
                     split2(p, h[u], l[u]);
                 }
-                // row 2 cl gives Re(P Z) with Z row (Zr, Zi): (Pr, -Pi); row 2 cl + 1 gives Im: (Pi, Pr)
-                const uint32_t o0 = sw128(2 * cl, ch), o1 = sw128(2 * cl + 1, ch);
-                sts128(sa + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
-                sts128(sa + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
-                sts128(sa + RF_A + o0, neg_hi(l[0]), neg_hi(l[1]), neg_hi(l[2]), neg_hi(l[3]));
-                sts128(sa + RF_A + o1, swap_h(l[0]), swap_h(l[1]), swap_h(l[2]), swap_h(l[3]));
+                const uint32_t off = sw128(row, ch);
+                sts128(sa + off, h[0], h[1], h[2], h[3]);
+                sts128(sa + RF_A + off, l[0], l[1], l[2], l[3]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int zr = rbase + 32 * k;
+                if (zr >= zcount) continue;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    split2(make_float2(cz[k][u].x * RF_ZSCALE, cz[k][u].y * RF_ZSCALE), h[u], l[u]);
+                const uint32_t o0 = sw128(2 * zr, ch), o1 = sw128(2 * zr + 1, ch);
+                sts128(sb + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
+                sts128(sb + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
+                sts128(sb + RF_B + o0, neg_hi(l[0]), neg_hi(l[1]), neg_hi(l[2]), neg_hi(l[3]));
+                sts128(sb + RF_B + o1, swap_h(l[0]), swap_h(l[1]), swap_h(l[2]), swap_h(l[3]));
             }
             fence_async_smem();
             mbar_arrive(&full[s]);
@@ -273,13 +280,12 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         umma_commit(done);   // also after an abort: the epilogue then waits for the MMAs in flight
     }
     if (warp < 4) {
-        // rows 2 cl (real parts) and 2 cl + 1 (imaginary parts) sit in neighbouring lanes
         const bool ok = mbar_wait(done, 0, abort, wait_ns);
         tc_fence_after();
         const bool good = __all_sync(0xffffffffu, ok && !*abort) != 0;
         if (good) {
-            const int cl = (warp * 32 + lane) >> 1;
-            float2* out = part + ((int64_t)sp * m + r) * nzw * cpad + c0 + cl;
+            const int c = c0 + warp * 32 + lane;
+            float2* out = part + ((int64_t)sp * m + r) * nzw * cpad + c;
             const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
             for (int q0 = 0; q0 < nused; q0 += 16) {
                 float v[16];
@@ -290,9 +296,9 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     for (int k = 0; k < 16; ++k) v[k] = 0.f;
                 }
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const float im = __shfl_xor_sync(0xffffffffu, v[u], 1);
-                    if (!(lane & 1) && q0 + u < zcount) out[(int64_t)(z_lo + q0 + u) * cpad] = make_float2(v[u], im);
+                for (int u = 0; u < 8; ++u) {
+                    const int zz = q0 / 2 + u;
+                    if (zz < zcount) out[(int64_t)(z_lo + zz) * cpad] = make_float2(v[2 * u], v[2 * u + 1]);
                 }
             }
         } else if (lane == 0) {
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == RF_GEN / 32) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
     }
 }
 
@@ -534,15 +540,14 @@ bool tc_recip_supported(const KTable& k) { return k.nk > 0 && (k.NX + 1) + (2 * 
 TcRecipDims tc_recip_dims(const cpm_ctx* c, int m, int64_t ne) {
     const KTable& k = c->kt;
     TcRecipDims d;
-    d.mtiles = (k.ncols + RF_CM - 1) / RF_CM;
-    d.cpad = d.mtiles * RF_CM;
+    d.mtiles = (k.ncols + RF_BM - 1) / RF_BM;
+    d.cpad = d.mtiles * RF_BM;
     d.ntiles = (k.nzw + RF_ZT - 1) / RF_ZT;
     const int base = std::max(1, d.mtiles * d.ntiles * m);
     const int64_t maxs = std::max<int64_t>(1, (ne + 4 * RF_KC - 1) / (4 * RF_KC));   // >= 4 K steps per CTA
     d.splits = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, 152 / base), maxs));
     d.chunk = (ne + d.splits - 1) / d.splits;
     d.chunk = ((d.chunk + RF_KC - 1) / RF_KC) * RF_KC;
-    d.ne_pad = ((ne + RF_KC - 1) / RF_KC) * RF_KC;
     d.mr = std::min(m, RS_MR);
     d.nrb = (m + d.mr - 1) / d.mr;
     d.CT = RS_CT;
@@ -589,11 +594,7 @@ cpm_status tc_recip_prepare(cpm_ctx* c) {
     return CPM_OK;
 }
 
-size_t tc_recip_zp_bytes(const TcRecipDims& d, int m, int nzw) {
-    return 2 * sizeof(uint32_t) * (size_t)nzw * m * d.ne_pad;
-}
-
-cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const uint32_t* zp,
+cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const float2* EZ,
                         const float* Qv, const float2* qabs, void* part, void* w16, float* site_partial) {
     const KTable& k = c->kt;
     const TcRecipDims d = tc_recip_dims(c, m, ne);
@@ -604,8 +605,8 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
     prof_begin(c, CPM_K_SF);
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, RF_SMEM));
     k_tc_sf<<<dim3(d.mtiles, d.ntiles, m * d.splits), RF_THREADS, RF_SMEM, st>>>(
-        (const uint4*)zp, k.cols, k.colext, k.ncols, k.NX, k.NY, k.NZ, k.nzw, EX, EY, Qv, qabs, ptot, ne, d.ne_pad,
-        d.splits, d.chunk, m, d.cpad, (float2*)part, c->status, RT_WAIT_NS);
+        k.cols, k.colext, k.ncols, k.NX, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, qabs, ptot, ne, d.splits, d.chunk, m, d.cpad,
+        (float2*)part, c->status, RT_WAIT_NS);
     prof_end(c, CPM_K_SF);
     CPM_LAUNCH(c, "k_tc_sf");
 
