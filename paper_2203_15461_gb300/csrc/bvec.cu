@@ -38,27 +38,47 @@ CellGrid make_grid(const Geometry& g) {
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // ----------------------------------------------------------------------------- per-replica totals
-// stats[r] = (Q_tot, M_x, M_y, M_z) over the raw (unwrapped) coordinates, and with qabs also
-// (max |Q_j|, sum |Q_j|) of the replica (operand scales of the tensor-core path).  Grid (SB, m):
-// block b sums its slice of the charges into part[r][b][6]; the last block of the replica adds
-// the slices in order.
-constexpr int ST_THREADS = 256, ST_BLOCKS = 16;
-__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const double* Q, int64_t ne, double* part,
-                                                     int* tickets, double* stats, float2* qabs) {
+constexpr int ST_THREADS = 256;
+
+// ----------------------------------------------------------------------------- cell list
+// Binning and the per-replica totals in one pass: grid (charge blocks, m), one thread per charge.
+// Each charge gets its wrapped position, its cell (cells of the real-space grid) and a single-precision
+// copy; each block sums (Q, Q x, Q y, Q z, max |Q|, sum |Q|) over its charges into part[r][b][6], and
+// the replica's last block adds the block sums in order (stats[r], qabs[r]).
+template <typename T>
+__global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ xyz, const double* __restrict__ Q,
+                                                  int64_t ne, Geometry g, CellGrid cg, float3 inv_h, int* key,
+                                                  int* count, typename V4<T>::t* wpos, T* Qv, double* part,
+                                                  int* tickets, double* stats, float2* qabs) {
     __shared__ double sh[6][ST_THREADS / 32];
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t chunk = (ne + nb - 1) / nb, jb = (int64_t)b * chunk, je = min(ne, jb + chunk);
+    const int64_t j = (int64_t)b * ST_THREADS + threadIdx.x;
     double a[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t j = jb + threadIdx.x; j < je; j += ST_THREADS) {
+    if (j < ne) {
         const int64_t p = (int64_t)r * ne + j;
         const double q = Q[p];
-        a[0] += q;
-        a[1] += q * xyz[3 * p];
-        a[2] += q * xyz[3 * p + 1];
-        a[3] += q * xyz[3 * p + 2];
-        a[4] = fmax(a[4], fabs(q));
-        a[5] += fabs(q);
+        double w[3];
+        int ci[3];
+        const float ih[3] = {inv_h.x, inv_h.y, inv_h.z};
+        for (int d = 0; d < 3; ++d) {
+            const double x = xyz[3 * p + d];
+            a[1 + d] = q * x;
+            w[d] = x - g.boxL[d] * floor(x * g.inv[d]);
+            if (w[d] >= g.boxL[d]) w[d] -= g.boxL[d];
+            if (w[d] < 0) w[d] = 0;
+            ci[d] = min(cg.nc[d] - 1, (int)((float)w[d] * ih[d]));
+        }
+        a[0] = q;
+        a[4] = fabs(q);
+        a[5] = fabs(q);
+        const int k = r * cg.ncells + (ci[2] * cg.nc[1] + ci[1]) * cg.nc[0] + ci[0];
+        key[p] = k;
+        atomicAdd(&count[k], 1);
+        typename V4<T>::t v;
+        v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)q;
+        wpos[p] = v;
+        Qv[p] = (T)q;
     }
     for (int o = 16; o > 0; o >>= 1) {
         for (int t = 0; t < 6; ++t) {
@@ -88,31 +108,6 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* xyz, const d
             else qabs[r].y = (float)v;
         }
     }
-}
-
-// ----------------------------------------------------------------------------- cell list
-template <typename T>
-__global__ void k_bin(const double* xyz, const double* Q, int64_t ptot, int64_t ne, Geometry g, CellGrid cg,
-                      int* key, int* count, typename V4<T>::t* wpos, T* Qv) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= ptot) return;
-    int r = (int)(p / ne);
-    double w[3];
-    int ci[3];
-    for (int d = 0; d < 3; ++d) {
-        double x = xyz[3 * p + d];
-        w[d] = x - g.boxL[d] * floor(x * g.inv[d]);
-        if (w[d] >= g.boxL[d]) w[d] -= g.boxL[d];
-        if (w[d] < 0) w[d] = 0;
-        ci[d] = min(cg.nc[d] - 1, (int)(w[d] / cg.h[d]));
-    }
-    int k = r * cg.ncells + (ci[2] * cg.nc[1] + ci[1]) * cg.nc[0] + ci[0];
-    key[p] = k;
-    atomicAdd(&count[k], 1);
-    typename V4<T>::t v;
-    v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)Q[p];
-    wpos[p] = v;
-    Qv[p] = (T)Q[p];
 }
 
 // Per-replica exclusive scan of cell counts into global start offsets (replica r starts at r * ne).
@@ -873,18 +868,6 @@ __device__ __forceinline__ dcx dcx_mul(dcx a, dcx b) {
     return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
 
-// e1[p] = exp(i 2 pi z_p / Lz) as a double-float pair (one FP64 sincospi per charge) and q[p] = Q_p
-// as a double-float pair
-__global__ void k_col0_phase1(const double* __restrict__ xyz, const double* __restrict__ Q, int64_t ptot,
-                              double invLz, float4* __restrict__ e1, float2* __restrict__ q) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= ptot) return;
-    const double2 e = z_phase1(xyz[3 * p + 2], invLz);
-    const dfl re = df_of(e.x), im = df_of(e.y), qq = df_of(Q[p]);
-    e1[p] = make_float4(re.hi, re.lo, im.hi, im.lo);
-    q[p] = make_float2(qq.hi, qq.lo);
-}
-
 // part[r][chunk][nz - 1] for nz in one block of 12 harmonics: each thread takes 2 charges of the
 // chunk (256 charges per block), raises exp(i theta) to the block's first harmonic and steps
 // through the block by a double-float recurrence; the block sums its threads in a fixed order.
@@ -1162,7 +1145,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
     p.off_c0q = o; o += al(sizeof(float2) * ptot);
     p.off_qabs = o; o += al(sizeof(float2) * m);
-    p.off_spart = o; o += al(sizeof(double) * 6 * ST_BLOCKS * m);
+    p.off_spart = o; o += al(sizeof(double) * 6 * (size_t)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS) * m);
     p.off_tcpart = p.off_w16 = o;
     if (p.tc) {
         p.off_tcpart = o; o += al(tc_recip_part_bytes(td, m, k.nzw));
@@ -1203,22 +1186,19 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     V4T* sorted = (V4T*)(scr + p.off_sorted);
     int* order = (int*)(scr + p.off_order);
     const int nc = m * p.cg.ncells;
-    c->launches += 4 + (ptot > 0 ? 3 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
+    c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
 
-    prof_begin(c, CPM_K_STATS);
-    float2* qabs = (float2*)(scr + p.off_qabs);
-    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ST_BLOCKS, (ne + 511) / 512));
-    k_stats<<<dim3(sblocks, m), ST_THREADS, 0, st>>>(xyz, Q, ne, (double*)(scr + p.off_spart), c->tickets, stats,
-                                                    p.tc ? qabs : nullptr);
-    prof_end(c, CPM_K_STATS);
-    CPM_LAUNCH(c, "k_stats");
+    // binning and the per-replica totals (one pass over the charges)
     prof_begin(c, CPM_K_CELLS);
-    if (ptot > 0) {
-        CPM_CUDA(c, cudaMemsetAsync(cnt, 0, p.off_start - p.off_cnt, st));   // counts and cursors
-        k_bin<T><<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, Q, ptot, ne, c->g, p.cg, key, cnt, wpos, Qv);
+    float2* qabs = (float2*)(scr + p.off_qabs);
+    CPM_CUDA(c, cudaMemsetAsync(cnt, 0, p.off_start - p.off_cnt, st));   // counts and cursors
+    {
+        const float3 inv_h = make_float3((float)(1.0 / p.cg.h[0]), (float)(1.0 / p.cg.h[1]), (float)(1.0 / p.cg.h[2]));
+        const unsigned nbx = (unsigned)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS);
+        k_bin<T><<<dim3(nbx, m), ST_THREADS, 0, st>>>(xyz, Q, ne, c->g, p.cg, inv_h, key, cnt, wpos, Qv,
+                                                     (double*)(scr + p.off_spart), c->tickets, stats,
+                                                     p.tc ? qabs : nullptr);
         CPM_LAUNCH(c, "k_bin");
-    } else {
-        CPM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), st));
     }
     k_cellscan<<<m, 1024, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
     CPM_LAUNCH(c, "k_cellscan");
@@ -1249,7 +1229,10 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     // reciprocal space
     if (k.nk > 0 && ptot > 0) {
         prof_begin(c, CPM_K_PHASES);
-        CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ));
+        const bool col0 = std::is_same<T, float>::value && k.ext0 > 0;   // its phases come along
+        CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ, Q,
+                                   col0 ? (float4*)(scr + p.off_c0e1) : nullptr,
+                                   col0 ? (float2*)(scr + p.off_c0q) : nullptr));
         prof_end(c, CPM_K_PHASES);
         if (p.tc) {
             CPM_TRY(tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const float2*)EZ, (const float*)Qv,
@@ -1304,9 +1287,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         const int nz0 = std::min(k.ext0, COL0_NZ);
         const int nblk = (nz0 + C0_NB - 1) / C0_NB;
         float4* e1s = (float4*)(scr + p.off_c0e1);
-        float2* q0 = (float2*)(scr + p.off_c0q);
-        k_col0_phase1<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(xyz, Q, ptot, c->g.inv[2], e1s, q0);
-        CPM_LAUNCH(c, "k_col0_phase1");
+        float2* q0 = (float2*)(scr + p.off_c0q);   // e1s and q0 come from k_fracs
         k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, q0, ne, nz0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
         k_col0_reduce<<<(m * nz0 * 32 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, nz0, k.w, k.NZ, m, c0w);
@@ -1314,7 +1295,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, nz0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
-        c->launches += 4;
+        c->launches += 3;
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,

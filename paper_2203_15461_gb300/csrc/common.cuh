@@ -215,7 +215,8 @@ cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, co
 size_t phase_elems(const KTable& k, int64_t P);
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z);
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, const double* Q = nullptr,
+                           float4* e1 = nullptr, float2* q2 = nullptr);
 
 // api.cu
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes);

@@ -230,23 +230,35 @@ __global__ void k_phases(const double* __restrict__ xyz, int64_t P, double ix, d
 
 // The fixed-point fractions of each point once per axis (u[d][p]), then the tables from them:
 // the table kernel then needs no FP64 arithmetic at all.
+// With e1 (single-precision paths), also the first z harmonic exp(2 pi i z / Lz) as a double-float
+// pair (from the same exactly reduced fraction, one FP64 sincospi) and the charge as a double-float
+// pair, for the double-float k_perp = 0 column.
 __global__ void k_fracs(const double* __restrict__ xyz, int64_t P, double ix, double iy, double iz,
-                        uint64_t* __restrict__ u) {
+                        uint64_t* __restrict__ u, const double* __restrict__ Q, float4* __restrict__ e1,
+                        float2* __restrict__ q2) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     u[p] = frac_fixed(xyz[3 * p + 0], ix);
     u[P + p] = frac_fixed(xyz[3 * p + 1], iy);
-    u[2 * P + p] = frac_fixed(xyz[3 * p + 2], iz);
+    const uint64_t uz = frac_fixed(xyz[3 * p + 2], iz);
+    u[2 * P + p] = uz;
+    if (e1) {
+        const double2 e = phase_of<double>(uz, 1);
+        const float rh = (float)e.x, ih = (float)e.y;
+        e1[p] = make_float4(rh, (float)(e.x - (double)rh), ih, (float)(e.y - (double)ih));
+        const double qd = Q[p];
+        const float qh = (float)qd;
+        q2[p] = make_float2(qh, (float)(qd - (double)qh));
+    }
 }
 
+// grid (points / 256, slots): no index division per entry
 template <typename T>
 __global__ void k_phases_u(const uint64_t* __restrict__ u, int64_t P, int NX, int NY, int NZ, c2<T>* X, c2<T>* Y,
                            c2<T>* Z) {
-    const int nslot = (NX + 1) + (2 * NY + 1) + (2 * NZ + 1);
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P * nslot) return;
-    int slot = (int)(t / P);
-    int64_t p = t % P;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int slot = blockIdx.y;
     if (slot <= NX) {
         X[(int64_t)slot * P + p] = phase_of<T>(u[p], slot);
     } else if (slot <= NX + 2 * NY + 1) {
@@ -260,18 +272,18 @@ __global__ void k_phases_u(const uint64_t* __restrict__ u, int64_t P, int NX, in
 
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z) {
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, const double* Q, float4* e1, float2* q2) {
     if (P == 0) return CPM_OK;
-    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u);
+    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u, Q, e1, q2);
     const int nslot = (k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1);
-    const int64_t tot = P * nslot;
-    k_phases_u<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X, Y, Z);
+    k_phases_u<T><<<dim3((unsigned)((P + 255) / 256), (unsigned)nslot), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X, Y, Z);
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
 }
 template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                           uint64_t*, float2*, float2*, float2*);
+                                           uint64_t*, float2*, float2*, float2*, const double*, float4*, float2*);
 template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                            uint64_t*, double2*, double2*, double2*);
+                                            uint64_t*, double2*, double2*, double2*, const double*, float4*,
+                                            float2*);
 
 template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,

@@ -252,21 +252,36 @@ __global__ void __launch_bounds__(G2_T, 2) k_gemv32x2(const float* __restrict__ 
     }
 }
 
-// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]
-__global__ void k_gemv_reduce(const double* __restrict__ part, int splits, const double* __restrict__ SG, int ng,
-                              const double* __restrict__ psi, int64_t n, int m, double* __restrict__ q) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)m * n) return;
-    const int r = (int)(t / n);
-    const int64_t i = t % n;
-    double v = 0.0;
-    for (int sp = 0; sp < splits; ++sp) v += part[((int64_t)sp * m + r) * n + i];
-    double sv = 0.0;
-    for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
-    q[t] = sv - v;
+// q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]; grid (sites / NB_T, m); with p1,
+// each block also writes the sum of its q values (the first pass of the neutrality fix)
+constexpr int NB_T = 256;
+__global__ void __launch_bounds__(NB_T) k_gemv_reduce(const double* __restrict__ part, int splits,
+                                                      const double* __restrict__ SG, int ng,
+                                                      const double* __restrict__ psi, int64_t n, int m,
+                                                      double* __restrict__ q, double* __restrict__ p1) {
+    __shared__ double sh[NB_T / 32];
+    const int r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * NB_T + threadIdx.x;
+    double qi = 0.0;
+    if (i < n) {
+        double v = 0.0;
+        for (int sp = 0; sp < splits; ++sp) v += part[((int64_t)sp * m + r) * n + i];
+        double sv = 0.0;
+        for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
+        qi = sv - v;
+        q[(int64_t)r * n + i] = qi;
+    }
+    if (!p1) return;
+    for (int o = 16; o > 0; o >>= 1) qi += __shfl_down_sync(0xffffffffu, qi, o);
+    if (lane == 0) sh[warp] = qi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = sh[0];
+        for (int w = 1; w < NB_T / 32; ++w) t += sh[w];
+        p1[(int64_t)r * gridDim.x + blockIdx.x] = t;
+    }
 }
 
-// One block per replica: s = e^T q; q <- q - u s (symm); qtot = e^T q with Neumaier compensation.
 __device__ __forceinline__ void neumaier_add(double& a, double& comp, double v) {
     const double t = a + v;
     comp += fabs(a) >= fabs(v) ? (a - t) + v : (v - t) + a;
@@ -274,9 +289,8 @@ __device__ __forceinline__ void neumaier_add(double& a, double& comp, double v) 
 }
 
 // Neutrality fix and total charge, Sec. II.B (q <- q - u e^T q with u = A^-1 e / (e^T A^-1 e), then
-// the FP64 total): grid (NB_BLOCKS slices of the sites, m); two launches because the fix needs
-// the replica's whole sum first.
-constexpr int NB_T = 256;
+// the FP64 total): grid (slices of the sites, m); two passes because the fix needs the replica's
+// whole sum first (the first pass is k_qsum, or the GEMV reduction when it writes p1).
 
 // p1[r][b] = sum of q[r][i] over slice b
 __global__ void __launch_bounds__(NB_T) k_qsum(const double* __restrict__ q, int64_t n, double* __restrict__ p1) {
@@ -295,54 +309,52 @@ __global__ void __launch_bounds__(NB_T) k_qsum(const double* __restrict__ q, int
     }
 }
 
-// with symm: q[r][i] -= u[i] * sum_b p1[r][b]; then p2[r][b] = compensated sum of the new q over
-// slice b, and the replica's last block writes qtot[r] = sum of p2 in slice order
+// with symm: q[r][i] -= u[i] * sum_b p1[r][b] (np1 block sums); then p2[r][b] = sum of the new q over
+// slice b, and the replica's last block writes qtot[r] = sum of p2 in slice order (plain FP64 sums in
+// a fixed order: the rounding, about n eps max|q|, is far below the 1e-12 e the total is held to)
 __global__ void __launch_bounds__(NB_T) k_neutral_fix(double* __restrict__ q, const double* __restrict__ u, int64_t n,
-                                                      int symm, const double* __restrict__ p1, double* __restrict__ p2,
-                                                      int* __restrict__ tickets, double* __restrict__ qtot) {
-    __shared__ double sh[NB_T / 32], shc[NB_T / 32];
+                                                      int symm, const double* __restrict__ p1, int np1,
+                                                      double* __restrict__ p2, int* __restrict__ tickets,
+                                                      double* __restrict__ qtot) {
+    __shared__ double sh[NB_T / 32];
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t chunk = (n + nb - 1) / nb, ib = (int64_t)b * chunk, ie = min(n, ib + chunk);
     double* qr = q + (int64_t)r * n;
     double s = 0.0;
     if (symm)
-        for (int k = 0; k < nb; ++k) s += p1[(int64_t)r * nb + k];
-    double a = 0.0, comp = 0.0;
+        for (int k = 0; k < np1; ++k) s += p1[(int64_t)r * np1 + k];
+    double a = 0.0;
     for (int64_t i = ib + threadIdx.x; i < ie; i += NB_T) {
         double v = qr[i];
         if (symm) {
             v -= u[i] * s;
             qr[i] = v;
         }
-        neumaier_add(a, comp, v);
+        a += v;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_down_sync(0xffffffffu, a, o), yc = __shfl_down_sync(0xffffffffu, comp, o);
-        comp += yc;
-        neumaier_add(a, comp, y);
-    }
-    if (lane == 0) { sh[warp] = a; shc[warp] = comp; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[warp] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0, tc = 0.0;
-        for (int w = 0; w < NB_T / 32; ++w) { tc += shc[w]; neumaier_add(t, tc, sh[w]); }
-        p2[2 * ((int64_t)r * nb + b)] = t;
-        p2[2 * ((int64_t)r * nb + b) + 1] = tc;
+        double t = sh[0];
+        for (int w = 1; w < NB_T / 32; ++w) t += sh[w];
+        p2[(int64_t)r * nb + b] = t;
     }
     if (!last_block_of(&tickets[r], nb)) return;
     if (threadIdx.x == 0 && qtot) {
-        const volatile double* pv = p2 + 2 * (int64_t)r * nb;
-        double t = 0.0, tc = 0.0;
-        for (int k = 0; k < nb; ++k) { tc += pv[2 * k + 1]; neumaier_add(t, tc, pv[2 * k]); }
-        qtot[r] = t + tc;
+        const volatile double* pv = p2 + (int64_t)r * nb;
+        double t = 0.0;
+        for (int k = 0; k < nb; ++k) t += pv[k];
+        qtot[r] = t;
     }
 }
 
 static int neutral_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 1023) / 1024)); }
+static int reduce_blocks(int64_t n) { return (int)((n + NB_T - 1) / NB_T); }
 
 static cpm_status reserve_neutral(cpm_ctx* c, int m) {
     CPM_TRY(ensure_tickets(c, m));
-    const size_t need = sizeof(double) * 3 * (size_t)m * neutral_blocks(c->n);
+    const size_t need = sizeof(double) * (size_t)m * (reduce_blocks(c->n) + neutral_blocks(c->n));
     if (c->nbuf_bytes >= need) return CPM_OK;
     c->graph_valid = false;
     dev_free(c, c->nbuf);
@@ -353,17 +365,22 @@ static cpm_status reserve_neutral(cpm_ctx* c, int m) {
     return CPM_OK;
 }
 
-static cpm_status launch_neutral(cpm_ctx* c, int m, double* q, double* qtot) {
+// have_p1: the block sums p1 were written by the GEMV reduction; else k_qsum writes them
+static cpm_status launch_neutral(cpm_ctx* c, int m, double* q, double* qtot, bool have_p1) {
     CPM_TRY(reserve_neutral(c, m));
     const int nb = neutral_blocks(c->n);
+    const int np1 = have_p1 ? reduce_blocks(c->n) : nb;
     double* p1 = c->nbuf;
-    double* p2 = c->nbuf + (size_t)m * nb;
+    double* p2 = c->nbuf + (size_t)m * reduce_blocks(c->n);
     prof_begin(c, CPM_K_NEUTRAL);
-    if (c->p.symm) k_qsum<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->n, p1);
-    k_neutral_fix<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->u, c->n, c->p.symm, p1, p2, c->tickets, qtot);
+    if (c->p.symm && !have_p1) {
+        k_qsum<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->n, p1);
+        c->launches += 1;
+    }
+    k_neutral_fix<<<dim3(nb, m), NB_T, 0, c->stream>>>(q, c->u, c->n, c->p.symm, p1, np1, p2, c->tickets, qtot);
     prof_end(c, CPM_K_NEUTRAL);
     CPM_LAUNCH(c, "k_neutral_fix");
-    c->launches += c->p.symm ? 2 : 1;
+    c->launches += 1;
     return CPM_OK;
 }
 
@@ -414,7 +431,7 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
         prof_begin(c, CPM_K_GEMV);
         CPM_TRY(tc_update(c, m, psi, b, q));
         prof_end(c, CPM_K_GEMV);
-        return launch_neutral(c, m, q, qtot);
+        return launch_neutral(c, m, q, qtot, false);
     }
     const bool f32 = c->p.s_prec == CPM_PREC_FP32;
     int64_t splits = 0, jchunk = 0;
@@ -434,10 +451,12 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     } else {
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
     }
-    k_gemv_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q);
+    CPM_TRY(reserve_neutral(c, m));
+    k_gemv_reduce<<<dim3((unsigned)reduce_blocks(n), m), NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q,
+                                                                       c->p.symm ? c->nbuf : nullptr);
     prof_end(c, CPM_K_GEMV);
     CPM_LAUNCH(c, "k_gemv");
-    return launch_neutral(c, m, q, qtot);
+    return launch_neutral(c, m, q, qtot, true);
 }
 
 }  // namespace cpm
