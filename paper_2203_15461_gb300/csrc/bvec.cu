@@ -473,18 +473,25 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
         if (lane == 0) rpre[nent] = total;
         __syncwarp();
+        // charge v of the concatenated ranges (its image shift applied later), loaded one batch ahead
+        auto fetch = [&](int v, float4& q, float4& sh) {
+            int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= v
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rpre[mid] <= v) lo = mid; else hi = mid - 1;
+            }
+            q = sorted[rbeg[lo] + (v - rpre[lo])];
+            sh = rsh[lo];
+        };
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f), shn = qn;
+        if (lane < total) fetch(lane, qn, shn);
         for (int base = 0; base < total; base += 32) {
             const int v = base + lane;
             bool keep = v < total;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 q = qn;
+            const float4 sh = shn;
+            if (v + 32 < total) fetch(v + 32, qn, shn);
             if (keep) {
-                int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= v
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (rpre[mid] <= v) lo = mid; else hi = mid - 1;
-                }
-                q = sorted[rbeg[lo] + (v - rpre[lo])];
-                const float4 sh = rsh[lo];
                 q.x += sh.x; q.y += sh.y; q.z += sh.z;
                 // only charges within r_c of the sites' box can reach a site
                 const float ex = fmaxf(0.f, fmaxf(bx0 - q.x, q.x - bx1));

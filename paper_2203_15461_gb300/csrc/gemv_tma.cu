@@ -7,7 +7,8 @@
 // zero, Eq. S; it keeps the large common part of b out of the single-precision sums).
 //
 // A block owns 512 consecutive columns i and a range of rows j.  One producer thread streams S
-// through a four-stage shared-memory ring with TMA (16 rows x 512 columns per stage, 32 KB); the
+// through a two-stage shared-memory ring with TMA (16 rows x 512 columns per stage, 32 KB; two blocks
+// per SM); the
 // 256 consumer threads take two columns each and evaluate the eight replicas as four packed pairs
 // (fma.rn.f32x2), summing each stage plainly in FP32 and adding the stage sums with compensation.
 // Every mbarrier wait is bounded by wall time; on expiry the block records ST_TIMEOUT, lets its
@@ -22,9 +23,9 @@ namespace cpm {
 constexpr int GV_T = 256;                      // consumer threads (two columns each)
 constexpr int GV_BC = 2 * GV_T;                // columns per block
 constexpr int GV_RJ = 16;                      // rows of S per stage
-constexpr int GV_STAGES = 4;
+constexpr int GV_STAGES = 2;                   // per block; two blocks per SM
 constexpr int GV_STAGE_BYTES = GV_RJ * GV_BC * 4;
-constexpr int GV_JMAX = 512;                   // rows of b staged per block
+constexpr int GV_JMAX = 256;                   // rows of b staged per block
 constexpr int GV_MR = 8;                       // replicas per block
 constexpr int GV_SMEM = 1024 + GV_STAGES * GV_STAGE_BYTES + GV_JMAX * 2 * GV_MR * 4 + 256;
 constexpr uint64_t GV_WAIT_NS = 2000000000ull;
@@ -60,7 +61,7 @@ struct Kahan {
 };
 
 // grid (column blocks, splits, replica chunks of eight)
-__global__ void __launch_bounds__(GV_T + 32, 1)
+__global__ void __launch_bounds__(GV_T + 32, 2)
     k_gemv_tma(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ bv, int64_t n, int m,
                int64_t jchunk, double* __restrict__ part, unsigned* __restrict__ status, uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
@@ -192,8 +193,8 @@ bool gemv_tma_supported(const cpm_ctx* c) { return c->p.s_prec == CPM_PREC_FP32 
 void gemv_tma_plan(int64_t n, int m, int64_t* colblocks, int64_t* splits, int64_t* jchunk) {
     *colblocks = (n + GV_BC - 1) / GV_BC;
     const int64_t rchunks = (m + GV_MR - 1) / GV_MR;
-    // one wave: at most one block per SM (the ring takes most of the shared memory)
-    int64_t sp = std::max<int64_t>(1, 152 / (*colblocks * rchunks));
+    // one wave: two blocks per SM
+    int64_t sp = std::max<int64_t>(1, 2 * 152 / (*colblocks * rchunks));
     sp = std::max<int64_t>(sp, (n + GV_JMAX - 1) / GV_JMAX);
     int64_t jc = (n + sp - 1) / sp;
     jc = ((jc + GV_RJ - 1) / GV_RJ) * GV_RJ;
