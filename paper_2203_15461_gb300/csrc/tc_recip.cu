@@ -39,14 +39,18 @@ constexpr uint64_t RT_WAIT_NS = 2000000000ull;   // bound on any single mbarrier
 constexpr int RF_BM = 128;                     // columns per tile (MMA M)
 constexpr int RF_ZT = 128;                     // harmonics per tile (MMA N = 2 x 128)
 constexpr int RF_KC = 32;                      // charges per K step (64 fp16 = 128 bytes per row)
-constexpr int RF_GEN = 256;                    // operand-building threads (warps 0-7)
+constexpr int RF_GEN = 512;                    // operand-building threads (warps 0-15)
 constexpr int RF_THREADS = RF_GEN + 32;        // + the MMA warp
+constexpr int RF_ROWSTEP = RF_GEN / 8;         // tile rows covered by one pass of the builders
+constexpr int RF_PK = RF_BM / RF_ROWSTEP;      // P rows per builder
+constexpr int RF_ZK = RF_ZT / RF_ROWSTEP;      // Z row pairs per builder
 constexpr int RF_A = RF_BM * 128;              // one fp16 term of the P tile (16 KB)
 constexpr int RF_B = 2 * RF_ZT * 128;          // one fp16 term of the Z tile (32 KB)
 constexpr int RF_STAGE = 2 * RF_A + 2 * RF_B;  // 96 KB
 constexpr int RF_STAGES = 2;
 constexpr int RF_XYROWS = 60;                 // staged phase-table rows: (NX + 1) + (2 NY + 1) at most
 constexpr int RF_STAGE_XY = (RF_XYROWS + 1) * RF_KC * 8;   // X, Y rows and Q of one K step
+constexpr int RF_PX = ((RF_XYROWS + 1) * RF_KC + RF_GEN - 1) / RF_GEN;   // staging entries per builder
 constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048 + RF_STAGE_XY;
 constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14
 
@@ -81,20 +85,20 @@ __device__ __forceinline__ void split2(float2 v, uint32_t& hi, uint32_t& lo) {
 __device__ __forceinline__ uint32_t neg_hi(uint32_t h) { return h ^ 0x80000000u; }            // (a, b) -> (a, -b)
 __device__ __forceinline__ uint32_t swap_h(uint32_t h) { return __byte_perm(h, 0u, 0x1032); }  // (a, b) -> (b, a)
 
-// barrier 1 over the 256 operand-building threads; returns the AND of every thread's flag
+// barrier 1 over the RF_GEN operand-building threads; returns the AND of every thread's flag
 __device__ __forceinline__ bool gen_bar_and(bool flag) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 256, p;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(out)
-        : "r"((uint32_t)flag)
+        : "r"((uint32_t)flag), "n"(RF_GEN)
         : "memory");
     return out != 0;
 }
-__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(RF_GEN) : "memory"); }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -164,19 +168,23 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
 
     if (warp < RF_GEN / 32) {
         // Operand builders.  Thread g owns 16-byte chunk ch = g % 8 (charges 4 ch .. 4 ch + 3 of the
-        // step) of P rows g / 8 + 32 k and of Z row pairs g / 8 + 32 k.  The X and Y table rows and
+        // step) of P rows g / 8 + 64 k and of Z row pairs g / 8 + 64 k.  The X and Y table rows and
         // the charges of a step are staged in shared memory; the loads of step t + 1 (staging
-        // entries and Z values) are issued before the tiles of step t are built.
+        // entries and Z values) are issued before the tiles of step t are built.  Within a staged
+        // table row, charge 4 ch + u sits at 16 (u / 2) + 2 ch + u % 2, so that the eight threads
+        // of a quarter warp (one P row) read two 128-byte runs with two 16-byte loads each; the
+        // charges are a row of 32 floats in natural order.
         const float sA = pow2_below(qabs[r].x, 14);
         const int g = threadIdx.x, ch = g & 7, rbase = g >> 3;
         const int xyrows = (NX + 1) + (2 * NY + 1);
         const int nst = (xyrows + 1) * RF_KC;
         float2* sxy = (float2*)(aux + 2048);
-        float2 px[8], pz[4][4];
+        float* sqf = (float*)(sxy + xyrows * RF_KC);
+        float2 px[RF_PX], pz[RF_ZK][4];
         auto prefetch = [&](int t) {
             const int64_t j0 = jb + (int64_t)t * RF_KC;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < RF_PX; ++k) {
                 const int e = g + RF_GEN * k;
                 float2 v = make_float2(0.f, 0.f);
                 if (e < nst) {
@@ -191,8 +199,8 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 px[k] = v;
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int zr = rbase + 32 * k;
+            for (int k = 0; k < RF_ZK; ++k) {
+                const int zr = rbase + RF_ROWSTEP * k;
                 const float2* zrow = EZ + (int64_t)(z_lo + min(zr, zcount - 1)) * ptot;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -208,34 +216,47 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
             if (t >= RF_STAGES) ok = mbar_wait(&empty[s], ((t / RF_STAGES) - 1) & 1, abort, wait_ns);
             if (!gen_bar_and(ok)) break;   // uniform; also: everyone is done reading the staged step t - 1
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (g + RF_GEN * k < nst) sxy[g + RF_GEN * k] = px[k];
-            float2 cz[4][4];
+            for (int k = 0; k < RF_PX; ++k) {
+                const int e = g + RF_GEN * k;
+                if (e < nst) {
+                    const int row = e >> 5, jj = e & 31;
+                    if (row < xyrows) sxy[row * RF_KC + (((jj & 2) << 3) | ((jj >> 2) << 1) | (jj & 1))] = px[k];
+                    else sqf[jj] = px[k].x;
+                }
+            }
+            float2 cz[RF_ZK][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < RF_ZK; ++k)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) cz[k][u] = pz[k][u];
             gen_bar();
             if (t + 1 < nsteps) prefetch(t + 1);
             const uint32_t sa = su32(smem + s * RF_STAGE);
             const uint32_t sb = sa + 2 * RF_A;
-            const float2* sq = sxy + xyrows * RF_KC + 4 * ch;
+            const float4 q4 = reinterpret_cast<const float4*>(sqf)[ch];
+            const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int row = rbase + 32 * k;
+            for (int k = 0; k < RF_PK; ++k) {
+                const int row = rbase + RF_ROWSTEP * k;
                 const int2 cn = s_cols[row];
                 const bool live = c0 + row < ncols;
-                const float2* xr = sxy + cn.x * RF_KC + 4 * ch;
-                const float2* yr = sxy + (NX + 1 + cn.y + NY) * RF_KC + 4 * ch;
+                float2 x[4], y[4];
+                if (live) {
+                    const float4* xr = reinterpret_cast<const float4*>(sxy + cn.x * RF_KC);
+                    const float4* yr = reinterpret_cast<const float4*>(sxy + (NX + 1 + cn.y + NY) * RF_KC);
+                    const float4 x01 = xr[ch], x23 = xr[8 + ch], y01 = yr[ch], y23 = yr[8 + ch];
+                    x[0] = make_float2(x01.x, x01.y); x[1] = make_float2(x01.z, x01.w);
+                    x[2] = make_float2(x23.x, x23.y); x[3] = make_float2(x23.z, x23.w);
+                    y[0] = make_float2(y01.x, y01.y); y[1] = make_float2(y01.z, y01.w);
+                    y[2] = make_float2(y23.x, y23.y); y[3] = make_float2(y23.z, y23.w);
+                }
                 uint32_t h[4], l[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float2 p = make_float2(0.f, 0.f);
-                    if (live) {
-                        const float2 x = xr[u], y = yr[u];
-                        const float q = sq[u].x;
-                        p = make_float2((x.x * y.x - x.y * y.y) * q, (x.x * y.y + x.y * y.x) * q);
-                    }
+                    if (live)
+                        p = make_float2((x[u].x * y[u].x - x[u].y * y[u].y) * qv[u],
+                                        (x[u].x * y[u].y + x[u].y * y[u].x) * qv[u]);
                     split2(p, h[u], l[u]);
                 }
                 const uint32_t off = sw128(row, ch);
@@ -243,8 +264,8 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 sts128(sa + RF_A + off, l[0], l[1], l[2], l[3]);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int zr = rbase + 32 * k;
+            for (int k = 0; k < RF_ZK; ++k) {
+                const int zr = rbase + RF_ROWSTEP * k;
                 if (zr >= zcount) continue;
                 uint32_t h[4], l[4];
 #pragma unroll
@@ -371,34 +392,43 @@ struct SiteMaps {
     CUtensorMap b[2];
 };
 
+// K steps (64 wide) covering the harmonics zi in [NZ - mx, NZ + mx] of column group g (two K entries
+// per harmonic), mx = the largest harmonic extent of the group's columns; nsteps = 0 for no column
+__device__ __forceinline__ void site_group_steps(const int* __restrict__ colext, int ncols, int NZ, int g, int ncb,
+                                                 int& t0, int& nsteps) {
+    const int cb = g % ncb;
+    const int cfirst = cb * RS_CT, clast = min(ncols, cfirst + RS_CT);
+    int mx = -1;
+    for (int c = cfirst; c < clast; ++c) mx = max(mx, colext[c]);
+    t0 = mx >= 0 ? (2 * (NZ - mx)) / 64 : 0;
+    nsteps = mx >= 0 ? (2 * (NZ + mx + 1) + 63) / 64 - t0 : 0;
+}
+
 // partial[r][cb][i] = sum over the 16 columns of block cb of Re[conj(X_i Y_i) T_r[c][i]]
-// grid (site tiles, replica blocks x column blocks); group g holds mr <= 8 replicas x 16 columns,
-// TMEM columns 32 rr + 2 cc + {re, im}.
+// Persistent: CTA b takes the tiles tau = b, b + gridDim.x, ... of the (site tile, group) grid, in
+// group-major order (groups of low |k_perp| have the most harmonics and come first); group g holds
+// mr <= 8 replicas x 16 columns.  Two accumulators in tensor memory (columns 256 buf + 32 rr + 2 cc
+// + {re, im}): the epilogue warps read tile k from one while the MMA thread fills the other with
+// tile k + 1; tfull[buf] / tempty[buf] hand the buffers over.
 __global__ void __launch_bounds__(RS_THREADS, 1)
     k_tc_site(const __grid_constant__ SiteMaps maps, const int* __restrict__ colext, int ncols, int NZ,
-              int mr, int ncb, int NB, int m, const float2* __restrict__ XY, int64_t n,
+              int mr, int ncb, int NB, int m, int ntx, int ntiles, const float2* __restrict__ XY, int64_t n,
               const float2* __restrict__ qabs, float wmax, float* __restrict__ partial,
               unsigned* __restrict__ status, uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + RS_STAGES * RS_STAGE);
     uint64_t* empty = full + RS_STAGES;
-    uint64_t* done = empty + RS_STAGES;
+    uint64_t* tfull = empty + RS_STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
-    int* s_mx = (int*)(tmem_slot + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.y, rb = g / ncb, cb = g % ncb;
-    const int cfirst = cb * RS_CT, clast = min(ncols, cfirst + RS_CT);
-    if (warp == 0) {
-        int mx = -1;
-        for (int c = cfirst + lane; c < clast; c += 32) mx = max(mx, colext[c]);
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) *s_mx = mx;
-    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
         mbar_init(done, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -406,7 +436,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     }
     if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(256u)
+                     "r"(512u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -414,93 +444,121 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int mx = *s_mx;
-    // K steps covering the group's harmonics zi in [NZ - mx, NZ + mx], two K entries per harmonic
-    const int t0 = mx >= 0 ? (2 * (NZ - mx)) / 64 : 0;
-    const int nsteps = mx >= 0 ? (2 * (NZ + mx + 1) + 63) / 64 - t0 : 0;
     const uint32_t stage_bytes = 2 * RS_A + 2 * NB * 128;
 
     if (warp == 4 && lane == 0) {
-        int issued = 0;
-        for (int t = 0; t < nsteps; ++t) {
-            const int s = t % RS_STAGES;
-            if (t >= RS_STAGES && !mbar_wait(&empty[s], ((t / RS_STAGES) - 1) & 1, abort, wait_ns)) break;
-            uint8_t* st = smem + s * RS_STAGE;
-            mbar_expect_tx(&full[s], stage_bytes);
-            const int kx = (t0 + t) * 64;
-            tma_load_2d(st, &maps.a[0], kx, blockIdx.x * RS_BM, &full[s]);
-            tma_load_2d(st + RS_A, &maps.a[1], kx, blockIdx.x * RS_BM, &full[s]);
-            tma_load_2d(st + 2 * RS_A, &maps.b[0], kx, g * NB, &full[s]);
-            tma_load_2d(st + 2 * RS_A + RS_BMAX, &maps.b[1], kx, g * NB, &full[s]);
-            ++issued;
+        // TMA producer: one ring over the K steps of all this CTA's tiles
+        int it = 0;
+        for (int tau = blockIdx.x; tau < ntiles && !*abort; tau += gridDim.x) {
+            const int g = tau / ntx, tx = tau % ntx;
+            int t0, nsteps;
+            site_group_steps(colext, ncols, NZ, g, ncb, t0, nsteps);
+            for (int t = 0; t < nsteps; ++t, ++it) {
+                const int s = it % RS_STAGES;
+                if (it >= RS_STAGES && !mbar_wait(&empty[s], ((it / RS_STAGES) - 1) & 1, abort, wait_ns)) break;
+                uint8_t* st = smem + s * RS_STAGE;
+                mbar_expect_tx(&full[s], stage_bytes);
+                const int kx = (t0 + t) * 64;
+                tma_load_2d(st, &maps.a[0], kx, tx * RS_BM, &full[s]);
+                tma_load_2d(st + RS_A, &maps.a[1], kx, tx * RS_BM, &full[s]);
+                tma_load_2d(st + 2 * RS_A, &maps.b[0], kx, g * NB, &full[s]);
+                tma_load_2d(st + 2 * RS_A + RS_BMAX, &maps.b[1], kx, g * NB, &full[s]);
+            }
         }
         if (*abort) {
-            for (int t = 0; t < issued; ++t) {   // let the copies already issued land (bounded)
+            // let the copies still in flight land (bounded): only the last RS_STAGES issued steps can be
+            for (int t = max(0, it - RS_STAGES); t < it; ++t) {
                 const int s = t % RS_STAGES;
                 const uint64_t ts = gtimer_ns();
                 while (!mbar_try(&full[s], (t / RS_STAGES) & 1) && gtimer_ns() - ts < wait_ns) {}
             }
         }
     } else if (warp == 5 && lane == 0) {
+        // MMA issuer
         const uint32_t idesc = idesc_f16(RS_BM, NB);
-        for (int t = 0; t < nsteps; ++t) {
-            const int s = t % RS_STAGES;
-            if (!mbar_wait(&full[s], (t / RS_STAGES) & 1, abort, wait_ns)) break;
+        int it = 0, k = 0;
+        for (int tau = blockIdx.x; tau < ntiles; tau += gridDim.x, ++k) {
+            const int g = tau / ntx;
+            int t0, nsteps;
+            site_group_steps(colext, ncols, NZ, g, ncb, t0, nsteps);
+            const int buf = k & 1;
+            if (k >= 2 && !mbar_wait(&tempty[buf], ((k >> 1) - 1) & 1, abort, wait_ns)) break;
             tc_fence_after();
-            const uint32_t sa = su32(smem + s * RS_STAGE), sb = sa + 2 * RS_A;
+            const uint32_t acc = tmem + (uint32_t)(256 * buf);
+            bool ok = true;
+            for (int t = 0; t < nsteps; ++t, ++it) {
+                const int s = it % RS_STAGES;
+                if (!mbar_wait(&full[s], (it / RS_STAGES) & 1, abort, wait_ns)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = su32(smem + s * RS_STAGE), sb = sa + 2 * RS_A;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t a0 = sdesc_sw128(sa + kk * 32), a1 = sdesc_sw128(sa + RS_A + kk * 32);
-                const uint64_t b0 = sdesc_sw128(sb + kk * 32), b1 = sdesc_sw128(sb + RS_BMAX + kk * 32);
-                umma_f16(tmem, a0, b0, idesc, (t > 0 || kk > 0) ? 1u : 0u);
-                umma_f16(tmem, a0, b1, idesc, 1u);
-                umma_f16(tmem, a1, b0, idesc, 1u);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t a0 = sdesc_sw128(sa + kk * 32), a1 = sdesc_sw128(sa + RS_A + kk * 32);
+                    const uint64_t b0 = sdesc_sw128(sb + kk * 32), b1 = sdesc_sw128(sb + RS_BMAX + kk * 32);
+                    umma_f16(acc, a0, b0, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                    umma_f16(acc, a0, b1, idesc, 1u);
+                    umma_f16(acc, a1, b0, idesc, 1u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            if (!ok) break;
+            umma_commit(&tfull[buf]);
         }
-        umma_commit(done);
-    }
-    if (warp < 4) {
-        // the column factors of this thread's site, loaded while the products run
-        const int64_t i = (int64_t)blockIdx.x * RS_BM + warp * 32 + lane;
-        float2 xy[RS_CT];
+        umma_commit(done);   // also after an abort: the MMAs in flight complete before the dealloc
+        const uint64_t ts = gtimer_ns();
+        while (!mbar_try(done, 0) && gtimer_ns() - ts < wait_ns) {}
+    } else if (warp < 4) {
+        // epilogue: thread = site i of the tile, accumulator lane warp * 32 + lane
+        const uint32_t trow = (uint32_t)(warp * 32) << 16;
+        const float zinv = ldexpf(1.f, -RS_ZEXP);
+        int k = 0;
+        for (int tau = blockIdx.x; tau < ntiles; tau += gridDim.x, ++k) {
+            const int g = tau / ntx, tx = tau % ntx;
+            const int rb = g / ncb, cb = g % ncb;
+            const int cfirst = cb * RS_CT, clast = min(ncols, cfirst + RS_CT);
+            int t0, nsteps;
+            site_group_steps(colext, ncols, NZ, g, ncb, t0, nsteps);
+            const int64_t i = (int64_t)tx * RS_BM + warp * 32 + lane;
+            float2 xy[RS_CT];   // the column factors of this thread's site, loaded while the products run
 #pragma unroll
-        for (int u = 0; u < RS_CT; ++u) {
-            const int c = cfirst + u;
-            xy[u] = (c < clast && i < n) ? XY[(int64_t)c * n + i] : make_float2(0.f, 0.f);
-        }
-        const bool ok = mbar_wait(done, 0, abort, wait_ns);
-        tc_fence_after();
-        const bool good = __all_sync(0xffffffffu, ok && !*abort) != 0;
-        if (good) {
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-            const float zinv = ldexpf(1.f, -RS_ZEXP);
+            for (int u = 0; u < RS_CT; ++u) {
+                const int c = cfirst + u;
+                xy[u] = (c < clast && i < n) ? XY[(int64_t)c * n + i] : make_float2(0.f, 0.f);
+            }
+            const int buf = k & 1;
+            const bool ok = mbar_wait(&tfull[buf], (k >> 1) & 1, abort, wait_ns);
+            tc_fence_after();
+            if (__any_sync(0xffffffffu, !ok || *abort)) break;
             for (int rr = 0; rr < mr; ++rr) {
                 float v[2 * RS_CT];
                 if (nsteps > 0) {
-                    tmem_ld32(trow + 2 * RS_CT * rr, v);
+                    tmem_ld32(tmem + trow + (uint32_t)(256 * buf + 2 * RS_CT * rr), v);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 2 * RS_CT; ++k) v[k] = 0.f;
+                    for (int q = 0; q < 2 * RS_CT; ++q) v[q] = 0.f;
                 }
-                float acc = 0.f;
+                float sacc = 0.f;
 #pragma unroll
                 for (int u = 0; u < RS_CT; ++u) {
-                    acc = fmaf(xy[u].x, v[2 * u], acc);
-                    acc = fmaf(xy[u].y, v[2 * u + 1], acc);
+                    sacc = fmaf(xy[u].x, v[2 * u], sacc);
+                    sacc = fmaf(xy[u].y, v[2 * u + 1], sacc);
                 }
                 const int r = rb * mr + rr;
                 if (r < m && i < n)
-                    partial[((int64_t)r * ncb + cb) * n + i] = acc * (zinv / pow2_below(wmax * qabs[r].y, 14));
+                    partial[((int64_t)r * ncb + cb) * n + i] = sacc * (zinv / pow2_below(wmax * qabs[r].y, 14));
             }
-        } else if (lane == 0) {
-            atomicOr(status, ST_TIMEOUT);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
         }
+        if (*abort && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     }
     tc_fence_before();
     __syncthreads();
+    if (*abort && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     if (warp == 5) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
 }
 
@@ -630,8 +688,9 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
             return set_err(c, CPM_E_CUDA, "cuTensorMapEncodeTiled failed");
     }
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_site, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM));
-    k_tc_site<<<dim3((unsigned)(d.npad / RS_BM), (unsigned)d.ngroups), RS_THREADS, RS_SMEM, st>>>(
-        maps, k.colext, k.ncols, k.NZ, d.mr, d.ncb, d.NB, m, c->tcxy, n, qabs, c->tc_wmax, site_partial,
+    const int ntx = (int)(d.npad / RS_BM), ntiles = ntx * d.ngroups;
+    k_tc_site<<<(unsigned)std::min(ntiles, 152), RS_THREADS, RS_SMEM, st>>>(
+        maps, k.colext, k.ncols, k.NZ, d.mr, d.ncb, d.NB, m, ntx, ntiles, c->tcxy, n, qabs, c->tc_wmax, site_partial,
         c->status, RT_WAIT_NS);
     prof_end(c, CPM_K_SITE);
     CPM_LAUNCH(c, "k_tc_site");

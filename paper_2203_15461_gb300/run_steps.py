@@ -1,0 +1,50 @@
+"""Run the graph-captured charge update of the EDL capacitor (4,320 sites, 8 replicas of 5,700
+charges) for a fixed number of steps and exit: a plain driver for an external profiler, which
+times nothing itself.  One step is one replay of cpm_step_graph (electrolyte vector b, S product,
+neutrality), the same step bench.py times.
+
+    python -m paper_2203_15461_gb300.run_steps --steps 4 [--k-prec f16x2|fp32] [--replicas 8]
+"""
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--replicas", type=int, default=8)
+    ap.add_argument("--k-prec", default="f16x2", choices=["fp32", "f16x2"])
+    args = ap.parse_args()
+
+    import torch
+
+    from . import systems as s
+    from .cpm import CPM
+
+    el, _, psi = s.workload_edl_capacitor(seed=1)
+    m = args.replicas
+    reps = [s.workload_edl_capacitor(seed=100 + r)[1] for r in range(m)]
+    ne = max(e.n for e in reps)
+    xyz = np.zeros((m, ne, 3))
+    Q = np.zeros((m, ne))
+    for r, e in enumerate(reps):
+        xyz[r, :e.n] = e.xyz
+        Q[r, :e.n] = e.Q
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec=args.k_prec, stream=st).setup(el)
+        dx = torch.as_tensor(xyz.reshape(-1, 3), device="cuda")
+        dQ = torch.as_tensor(Q.reshape(-1), device="cuda")
+        dp = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
+        b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+        q = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+        qt = torch.empty((m,), dtype=torch.float64, device="cuda")
+        for _ in range(args.steps):
+            ctx.cpm_step_graph(m, ne, dx, dQ, dp, b, q, qt)
+    st.synchronize()
+    print(f"{args.steps} steps, max |sum q| = {float(qt.abs().max()):.3e}")
+
+
+if __name__ == "__main__":
+    main()
