@@ -402,8 +402,9 @@ cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, 
         CPM_CUDA(c, cudaMemcpyAsync(dQ, Q, sizeof(double) * pt, cudaMemcpyHostToDevice, st));
     }
     CPM_CUDA(c, cudaMemcpyAsync(dpsi, psi, sizeof(double) * m * c->ng, cudaMemcpyHostToDevice, st));
-    CPM_TRY(bvec(c, m, n_e, dxyz, dQ, db));
-    CPM_TRY(update(c, m, dpsi, db, dq, dqt));
+    float2* bhl = update_bhl(c, m);   // b's two-float split written by bvec: no separate split pass
+    CPM_TRY(bvec(c, m, n_e, dxyz, dQ, db, bhl));
+    CPM_TRY(update(c, m, dpsi, db, dq, dqt, bhl != nullptr));
     CPM_CUDA(c, cudaMemcpyAsync(q_out, dq, sizeof(double) * m * c->n, cudaMemcpyDeviceToHost, st));
     if (qtot_out) CPM_CUDA(c, cudaMemcpyAsync(qtot_out, dqt, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     CPM_CUDA(c, cudaStreamSynchronize(st));
@@ -428,8 +429,9 @@ cpm_status cpm_step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz,
         c->prof_on = false;
         const int64_t l0 = c->launches;
         CPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out);
-        cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out) : s1;
+        float2* bhl = update_bhl(c, m);
+        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out, bhl);
+        cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out, bhl != nullptr) : s1;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         c->prof_on = prof;

@@ -1060,9 +1060,12 @@ __global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols
 }
 
 // b[r][i] = K_E (recip + real - pi Q_tot / (V alpha^2) + boundary)
+// with bhl also the two-float split of b for the single-precision S product (the same arithmetic as
+// k_split_b, so the update gives bit-identical results either way)
 template <typename T>
 __global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const int* zmap,
-                          int nzu, const double* stats, const double* sx, int64_t n, int m, Geometry g, double* b) {
+                          int nzu, const double* stats, const double* sx, int64_t n, int m, Geometry g, double* b,
+                          float2* bhl) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
@@ -1075,7 +1078,12 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     s += -PI * st[0] / (g.V * g.alpha * g.alpha);
     if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];
     else if (g.bc == CPM_BC_WIRE) s += (2.0 * PI / g.V) * (sx[i] * st[1] + sx[n + i] * st[2]);
-    b[t] = KE * s;
+    const double v = KE * s;
+    b[t] = v;
+    if (bhl) {
+        const float hi = (float)v;
+        bhl[t] = make_float2(hi, (float)(v - (double)hi));
+    }
 }
 
 // ----------------------------------------------------------------------------- driver
@@ -1170,7 +1178,8 @@ template <> const Phases<double>& site_tables<double>(const cpm_ctx* c) { return
 template <> const Phases<float>& site_tables<float>(const cpm_ctx* c) { return c->site32; }
 
 template <typename T>
-cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out, char* scr) {
+cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out, float2* bhl,
+                    char* scr) {
     const BvecPlan<T> p = plan_bvec<T>(c, m, ne);
     const KTable& k = c->kt;
     cudaStream_t st = c->stream;
@@ -1306,7 +1315,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
-                                                                          stats, c->sx, n, m, c->g, b_out);
+                                                                          stats, c->sx, n, m, c->g, b_out, bhl);
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;
@@ -1330,13 +1339,13 @@ cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
     return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }
 
-cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out) {
+cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out, float2* bhl) {
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     const size_t need = f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne);
     CPM_TRY(ensure_scratch(c, need));
     CPM_TRY(ensure_tickets(c, m));
     char* scr = (char*)c->scratch;
-    return f32 ? bvec_run<float>(c, m, ne, xyz, Q, b_out, scr) : bvec_run<double>(c, m, ne, xyz, Q, b_out, scr);
+    return f32 ? bvec_run<float>(c, m, ne, xyz, Q, b_out, bhl, scr) : bvec_run<double>(c, m, ne, xyz, Q, b_out, bhl, scr);
 }
 
 }  // namespace cpm

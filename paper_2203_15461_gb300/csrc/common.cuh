@@ -250,13 +250,19 @@ cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, d
 // bvec.cu
 struct Geometry;
 CellGrid make_grid(const Geometry& g);
-cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out);
+// bhl (optional): also write the two-float split of b that the single-precision update reads
+cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out,
+                float2* bhl = nullptr);
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
 cpm_status build_col0_sites(cpm_ctx* c);
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
 
 // update.cu
-cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot);
+// bhl_ready: the split of b is already in update_bhl(c, m) (written by bvec in the same step)
+cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot,
+                  bool bhl_ready = false);
+// where the single-precision update keeps the two-float split of b (nullptr for other S precisions)
+float2* update_bhl(cpm_ctx* c, int m);
 
 cpm_status reserve_update(cpm_ctx* c, int m);
 
@@ -268,7 +274,7 @@ cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms);
 // gemv_tma.cu: single-precision S streaming with TMA (n a multiple of 4)
 bool gemv_tma_supported(const cpm_ctx* c);
 void gemv_tma_plan(int64_t n, int m, int64_t* colblocks, int64_t* splits, int64_t* jchunk);
-cpm_status gemv_tma(cpm_ctx* c, int m, const float2* bhl, double* part, int64_t splits, int64_t jchunk);
+cpm_status gemv_tma(cpm_ctx* c, int m, const float2* bhl, float2* part, int64_t splits, int64_t jchunk);
 
 // tc_recip.cu: reciprocal-space sums of b on the tensor cores (k_prec = CPM_PREC_F16X2)
 struct TcRecipDims {

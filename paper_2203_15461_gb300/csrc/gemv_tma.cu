@@ -1,16 +1,24 @@
 // Charge update q = S G psi - S b for m replicas with the single-precision capacitance matrix
-// (Sec. II.B), streaming S once per eight replicas:
+// (Sec. II.B), streaming S once per eight replicas.  A block owns 512 consecutive columns i and a
+// range of rows j (a split); every consumer thread owns four adjacent columns i0 .. i0 + 3 and
+// centres b on beta = bh_i0 (b = bh + bl split into two floats):
 //
-//   part[split][r][i] = sum over the split's rows j of S_ij ((bh_j - bh_i) + bl_j)
+//   part[split][r][i] = sum_j S_ij d_j  -  (b_i - beta) sum_j S_ij,   d_j = (bh_j - beta) + bl_j,
 //
-// with b = bh + bl split into two floats (the centred form is exact because the rows of S sum to
-// zero, Eq. S; it keeps the large common part of b out of the single-precision sums).
+// over the split's rows j.  This equals sum_j S_ij (b_j - b_i) for any matrix, and the rows of the
+// exact S sum to zero (Eq. S), so the result is the S b of the method; centring on a site next to
+// i keeps the large common part of b out of the single-precision sums, and the row sums are taken
+// over the stored single-precision S so the identity holds for the stored values too.  d_j is formed
+// once per row and replica and serves the thread's four columns: 1.5 FP32 operations per (i, j, r)
+// plus one row-sum addition per (i, j).
 //
-// A block owns 512 consecutive columns i and a range of rows j.  One producer thread streams S
-// through a two-stage shared-memory ring with TMA (16 rows x 512 columns per stage, 32 KB; two blocks
-// per SM); the
-// 256 consumer threads take two columns each and evaluate the eight replicas as four packed pairs
-// (fma.rn.f32x2), summing each stage plainly in FP32 and adding the stage sums with compensation.
+// One producer thread streams S through a three-stage shared-memory ring with TMA (16 rows x 512
+// columns per stage, 32 KB; two blocks per SM); 128 consumer threads read their four columns of a
+// row with one 16-byte shared load and evaluate the eight replicas as four packed pairs
+// (fma.rn.f32x2), summing each stage plainly in FP32 and adding the stage sums with compensation
+// (packed Kahan).  The (b_i - beta) row-sum term is applied in double-float arithmetic, and the
+// result leaves as an FP32 pair (high, low) per replica and column that the reduction over the
+// splits adds in double-float arithmetic, so no FP64 instruction runs in this kernel.
 // Every mbarrier wait is bounded by wall time; on expiry the block records ST_TIMEOUT, lets its
 // copies in flight land and returns.
 #include <algorithm>
@@ -20,13 +28,15 @@
 
 namespace cpm {
 
-constexpr int GV_T = 256;                      // consumer threads (two columns each)
-constexpr int GV_BC = 2 * GV_T;                // columns per block
+constexpr int GV_T = 128;                      // consumer threads
+constexpr int GV_CPT = 4;                      // adjacent columns per consumer thread
+constexpr int GV_BC = GV_CPT * GV_T;           // columns per block (two TMA boxes of 256)
 constexpr int GV_RJ = 16;                      // rows of S per stage
-constexpr int GV_STAGES = 2;                   // per block; two blocks per SM
+constexpr int GV_STAGES = 3;                   // per block; two blocks per SM
 constexpr int GV_STAGE_BYTES = GV_RJ * GV_BC * 4;
-constexpr int GV_JMAX = 256;                   // rows of b staged per block
+constexpr int GV_JMAX = 192;                   // rows of b staged per block
 constexpr int GV_MR = 8;                       // replicas per block
+constexpr int GV_SPT = (GV_JMAX * GV_MR + GV_T - 1) / GV_T;   // staged entries per consumer thread
 constexpr int GV_SMEM = 1024 + GV_STAGES * GV_STAGE_BYTES + GV_JMAX * 2 * GV_MR * 4 + 256;
 constexpr uint64_t GV_WAIT_NS = 2000000000ull;
 
@@ -45,27 +55,56 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
     uint64_t d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c, t = s + y;
-        c = (t - s) - y;
+// compensated sum of packed pairs (Kahan): the sum is s - c; every step is one rounding
+struct Kahan2 {
+    uint64_t s = 0ull, c = 0ull;
+    __device__ __forceinline__ void add(uint64_t x) {
+        const uint64_t y = sub2(x, c), t = add2(s, y);
+        c = sub2(sub2(t, s), y);
         s = t;
     }
 };
 
+// double-float helpers (value = hi + lo): exact sum and difference (Knuth's two-sum) and a product
+// with the rounding error of the leading term recovered by an FMA
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_norm(float hi, float lo) {
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_norm(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi))));
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+    const DF s = two_sum(a.hi, -b.hi);
+    return df_norm(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+
 // grid (column blocks, splits, replica chunks of eight)
 __global__ void __launch_bounds__(GV_T + 32, 2)
     k_gemv_tma(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ bv, int64_t n, int m,
-               int64_t jchunk, double* __restrict__ part, unsigned* __restrict__ status, uint64_t wait_ns) {
+               int64_t jchunk, float2* __restrict__ part, unsigned* __restrict__ status, uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = align1024(smem_raw);
     float* shi = (float*)(smem + GV_STAGES * GV_STAGE_BYTES);   // [jj][8] high parts of b
     float* slo = shi + GV_JMAX * GV_MR;                          // [jj][8] low parts
     uint64_t* full = (uint64_t*)(slo + GV_JMAX * GV_MR);
@@ -113,41 +152,52 @@ __global__ void __launch_bounds__(GV_T + 32, 2)
         return;
     }
 
-    // consumers: stage b of the block's rows, replica-minor, high and low parts apart
-    for (int e = tid; e < nrow * GV_MR; e += GV_T) {
-        const int jj = e / GV_MR, t = e % GV_MR;
-        const float2 v = t < mm ? bv[(int64_t)(r0 + t) * n + jb + jj] : make_float2(0.f, 0.f);
-        shi[e] = v.x;
-        slo[e] = v.y;
-    }
-    const int64_t ic = i0 + 2 * tid;
-    const bool live0 = ic < n, live1 = ic + 1 < n;
-    uint64_t bh[2][GV_MR / 2];
+    // consumers: stage b of the block's rows, replica-minor, high and low parts apart (coalesced
+    // loads along the rows, all in flight before the first store)
+    const int64_t ic = i0 + GV_CPT * tid;
+    const bool live = ic < n;   // n is a multiple of 4: a thread's columns are all in range or all out
+    {
+        float2 v[GV_SPT];
 #pragma unroll
-    for (int tp = 0; tp < GV_MR / 2; ++tp) {
-        const int ta = 2 * tp, tb = 2 * tp + 1;
-        bh[0][tp] = pk2((ta < mm && live0) ? bv[(int64_t)(r0 + ta) * n + ic].x : 0.f,
-                        (tb < mm && live0) ? bv[(int64_t)(r0 + tb) * n + ic].x : 0.f);
-        bh[1][tp] = pk2((ta < mm && live1) ? bv[(int64_t)(r0 + ta) * n + ic + 1].x : 0.f,
-                        (tb < mm && live1) ? bv[(int64_t)(r0 + tb) * n + ic + 1].x : 0.f);
+        for (int k = 0; k < GV_SPT; ++k) {
+            const int e = tid + GV_T * k, t = e / GV_JMAX, jj = e % GV_JMAX;
+            v[k] = (t < mm && jj < nrow) ? bv[(int64_t)(r0 + t) * n + jb + jj] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < GV_SPT; ++k) {
+            const int e = tid + GV_T * k, t = e / GV_JMAX, jj = e % GV_JMAX;
+            if (t < GV_MR) {
+                shi[jj * GV_MR + t] = v[k].x;
+                slo[jj * GV_MR + t] = v[k].y;
+            }
+        }
+    }
+    // beta_r = bh of this thread's first column, as replica pairs
+    uint64_t beta[GV_MR / 2];
+#pragma unroll
+    for (int h = 0; h < GV_MR / 2; ++h) {
+        const int ta = 2 * h, tb = 2 * h + 1;
+        beta[h] = pk2((ta < mm && live) ? bv[(int64_t)(r0 + ta) * n + ic].x : 0.f,
+                      (tb < mm && live) ? bv[(int64_t)(r0 + tb) * n + ic].x : 0.f);
     }
     asm volatile("bar.sync 1, %0;" ::"n"(GV_T) : "memory");
-    Kahan acc[2][GV_MR];
-    const uint32_t col_off = (uint32_t)((tid / (GV_T / 2)) * (GV_STAGE_BYTES / 2) + (2 * tid % (GV_BC / 2)) * 4);
+    Kahan2 acc[GV_CPT][GV_MR / 2], rsum[GV_CPT / 2];
+    // this thread's 16-byte run of a staged row: box (4 tid) / 256, offset (4 tid) % 256
+    const uint32_t col_off = (uint32_t)((GV_CPT * tid / 256) * (GV_STAGE_BYTES / 2) + (GV_CPT * tid % 256) * 4);
     bool ok = true;
     for (int t = 0; t < nst; ++t) {
         const int s = t % GV_STAGES;
         if (!mbar_wait(&full[s], (t / GV_STAGES) & 1, abort, wait_ns)) { ok = false; break; }
         const uint8_t* st = smem + s * GV_STAGE_BYTES + col_off;
         const int rows = min(GV_RJ, nrow - t * GV_RJ);
-        uint64_t tile[2][GV_MR / 2];
+        uint64_t tile[GV_CPT][GV_MR / 2], rs[GV_CPT / 2] = {0ull, 0ull};
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < GV_CPT; ++c)
 #pragma unroll
-            for (int tp = 0; tp < GV_MR / 2; ++tp) tile[c][tp] = 0ull;
-#pragma unroll 4
+            for (int h = 0; h < GV_MR / 2; ++h) tile[c][h] = 0ull;
+#pragma unroll 2
         for (int u = 0; u < rows; ++u) {
-            const float2 sv = *reinterpret_cast<const float2*>(st + u * (GV_BC / 2) * 4);
+            const float4 s4 = *reinterpret_cast<const float4*>(st + u * 256 * 4);   // S_j,i0 .. S_j,i0+3
             const int jj = t * GV_RJ + u;
             const float4 h0 = *reinterpret_cast<const float4*>(shi + jj * GV_MR);
             const float4 h1 = *reinterpret_cast<const float4*>(shi + jj * GV_MR + 4);
@@ -155,36 +205,61 @@ __global__ void __launch_bounds__(GV_T + 32, 2)
             const float4 l1 = *reinterpret_cast<const float4*>(slo + jj * GV_MR + 4);
             const uint64_t hp[4] = {pk2(h0.x, h0.y), pk2(h0.z, h0.w), pk2(h1.x, h1.y), pk2(h1.z, h1.w)};
             const uint64_t lp[4] = {pk2(l0.x, l0.y), pk2(l0.z, l0.w), pk2(l1.x, l1.y), pk2(l1.z, l1.w)};
-            const uint64_t s0 = pk2(sv.x, sv.x), s1 = pk2(sv.y, sv.y);
+            uint64_t d[GV_MR / 2];
 #pragma unroll
-            for (int tp = 0; tp < GV_MR / 2; ++tp) {
-                tile[0][tp] = fma2(s0, sub2(hp[tp], bh[0][tp]), tile[0][tp]);
-                tile[0][tp] = fma2(s0, lp[tp], tile[0][tp]);
-                tile[1][tp] = fma2(s1, sub2(hp[tp], bh[1][tp]), tile[1][tp]);
-                tile[1][tp] = fma2(s1, lp[tp], tile[1][tp]);
+            for (int h = 0; h < GV_MR / 2; ++h) d[h] = add2(sub2(hp[h], beta[h]), lp[h]);
+            const float sc[GV_CPT] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int c = 0; c < GV_CPT; ++c) {
+                const uint64_t sp = pk2(sc[c], sc[c]);
+#pragma unroll
+                for (int h = 0; h < GV_MR / 2; ++h) tile[c][h] = fma2(sp, d[h], tile[c][h]);
             }
+            rs[0] = add2(rs[0], pk2(s4.x, s4.y));
+            rs[1] = add2(rs[1], pk2(s4.z, s4.w));
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < GV_CPT; ++c)
 #pragma unroll
-            for (int tp = 0; tp < GV_MR / 2; ++tp) {
-                const float2 v = up2(tile[c][tp]);
-                acc[c][2 * tp].add(v.x);
-                acc[c][2 * tp + 1].add(v.y);
-            }
+            for (int h = 0; h < GV_MR / 2; ++h) acc[c][h].add(tile[c][h]);
+        rsum[0].add(rs[0]);
+        rsum[1].add(rs[1]);
     }
     if (!ok) {
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
         return;
     }
+    if (!live) return;
+    // row sums of the four columns and the sums of the products, as double-float values
+    DF rsc[GV_CPT];
+    {
+        const float2 s01 = up2(rsum[0].s), c01 = up2(rsum[0].c), s23 = up2(rsum[1].s), c23 = up2(rsum[1].c);
+        rsc[0] = df_norm(s01.x, -c01.x);
+        rsc[1] = df_norm(s01.y, -c01.y);
+        rsc[2] = df_norm(s23.x, -c23.x);
+        rsc[3] = df_norm(s23.y, -c23.y);
+    }
 #pragma unroll
     for (int t = 0; t < GV_MR; ++t) {
         if (t >= mm) continue;
-        double* pr = part + ((int64_t)split * m + r0 + t) * n;
-        if (live0) pr[ic] = (double)acc[0][t].s - (double)acc[0][t].c;
-        if (live1) pr[ic + 1] = (double)acc[1][t].s - (double)acc[1][t].c;
+        const float2* br = bv + (int64_t)(r0 + t) * n + ic;
+        const float bt = br[0].x;   // beta_t
+        float2 o[GV_CPT];
+#pragma unroll
+        for (int c = 0; c < GV_CPT; ++c) {
+            const float2 as = up2(acc[c][t / 2].s), ac = up2(acc[c][t / 2].c);
+            const DF a = df_norm((t & 1) ? as.y : as.x, -((t & 1) ? ac.y : ac.x));
+            const float2 bi = br[c];
+            const DF e0 = two_sum(bi.x, -bt);                          // bh_i - beta, exactly
+            const DF e = df_norm(e0.hi, __fadd_rn(e0.lo, bi.y));      // (b_i - beta)
+            const DF r = df_sub(a, df_mul(e, rsc[c]));
+            o[c] = make_float2(r.hi, r.lo);
+        }
+        float4* pr = reinterpret_cast<float4*>(part + ((int64_t)split * m + r0 + t) * n + ic);   // 32-byte aligned
+        pr[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        pr[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
     }
 }
 
@@ -202,7 +277,7 @@ void gemv_tma_plan(int64_t n, int m, int64_t* colblocks, int64_t* splits, int64_
     *splits = (n + *jchunk - 1) / *jchunk;
 }
 
-cpm_status gemv_tma(cpm_ctx* c, int m, const float2* bhl, double* part, int64_t splits, int64_t jchunk) {
+cpm_status gemv_tma(cpm_ctx* c, int m, const float2* bhl, float2* part, int64_t splits, int64_t jchunk) {
     const int64_t n = c->n;
     auto enc = encode_fn();
     if (!enc) return set_err(c, CPM_E_CUDA, "cuTensorMapEncodeTiled unavailable");

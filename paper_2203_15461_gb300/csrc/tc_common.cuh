@@ -15,6 +15,10 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
 }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// first 1024-byte aligned byte of a dynamic shared-memory buffer, reached by pointer arithmetic on
+// the buffer itself so that the compiler still knows it is shared memory (a round trip through an
+// integer would turn every access into a generic load or store)
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) { return p + ((1024u - (su32(p) & 1023u)) & 1023u); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
@@ -40,6 +44,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 // bounded wait (wall time, globaltimer); false when the limit expired or another role raised the abort flag
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
+    if (mbar_try(bar, parity)) return true;   // fast path: no timer read
     const uint64_t t0 = gtimer_ns();
     while (true) {
         if (mbar_try(bar, parity)) return true;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_sb(const __grid_constant__
                                                          uint64_t wait_ns) {
     typedef TcCfg<BN> C;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = align1024(smem_raw);
     uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
     uint64_t* empty = full + C::STAGES;
     uint64_t* done = empty + C::STAGES;

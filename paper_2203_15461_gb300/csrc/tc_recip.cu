@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
             int64_t chunk, int m, int cpad, float2* __restrict__ part, unsigned* __restrict__ status,
             uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = align1024(smem_raw);
     uint8_t* aux = smem + RF_STAGES * RF_STAGE;
     uint64_t* full = (uint64_t*)aux;
     uint64_t* empty = full + RF_STAGES;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
               const float2* __restrict__ qabs, float wmax, float* __restrict__ partial,
               unsigned* __restrict__ status, uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = align1024(smem_raw);
     uint64_t* full = (uint64_t*)(smem + RS_STAGES * RS_STAGE);
     uint64_t* empty = full + RS_STAGES;
     uint64_t* tfull = empty + RS_STAGES;

@@ -255,7 +255,32 @@ __global__ void __launch_bounds__(G2_T, 2) k_gemv32x2(const float* __restrict__ 
 // q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]; grid (sites / NB_T, m); with p1,
 // each block also writes the sum of its q values (the first pass of the neutrality fix)
 constexpr int NB_T = 256;
-__global__ void __launch_bounds__(NB_T) k_gemv_reduce(const double* __restrict__ part, int splits,
+// sum of the split partials of one output: FP64 partials added in FP64; FP32 pairs (sum, low part)
+// added in double-float arithmetic (the exact error of each high-part addition, by the two-sum of
+// Knuth, is carried in the low part) and converted to FP64 once
+struct PartSumD {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+struct PartSumF2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float2 x) {
+        const float s = __fadd_rn(hi, x.x);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x.x, bb));
+        lo = __fadd_rn(lo, __fadd_rn(e, x.y));
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <typename P> struct PartSum;
+template <> struct PartSum<double> { using type = PartSumD; };
+template <> struct PartSum<float2> { using type = PartSumF2; };
+
+// q = SG psi - sum of the split partials; with p1 also the block sums of q for the neutrality fix
+template <typename P>
+__global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part, int splits,
                                                       const double* __restrict__ SG, int ng,
                                                       const double* __restrict__ psi, int64_t n, int m,
                                                       double* __restrict__ q, double* __restrict__ p1) {
@@ -264,11 +289,21 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const double* __restrict__
     const int64_t i = (int64_t)blockIdx.x * NB_T + threadIdx.x;
     double qi = 0.0;
     if (i < n) {
-        double v = 0.0;
-        for (int sp = 0; sp < splits; ++sp) v += part[((int64_t)sp * m + r) * n + i];
+        typename PartSum<P>::type v;
+        const P* pi = part + (int64_t)r * n + i;
+        const int64_t stride = (int64_t)m * n;
+        int sp = 0;
+        for (; sp + 8 <= splits; sp += 8) {   // eight loads in flight, added in split order
+            P x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = pi[(int64_t)(sp + k) * stride];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v.add(x[k]);
+        }
+        for (; sp < splits; ++sp) v.add(pi[(int64_t)sp * stride]);
         double sv = 0.0;
         for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
-        qi = sv - v;
+        qi = sv - v.value();
         q[(int64_t)r * n + i] = qi;
     }
     if (!p1) return;
@@ -424,7 +459,14 @@ cpm_status reserve_update(cpm_ctx* c, int m) {
     return reserve_update_plan(c, m, &s, &j);
 }
 
-cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot) {
+float2* update_bhl(cpm_ctx* c, int m) {
+    if (c->p.s_prec != CPM_PREC_FP32) return nullptr;
+    int64_t splits = 0, jchunk = 0;
+    if (reserve_update_plan(c, m, &splits, &jchunk) != CPM_OK) return nullptr;
+    return (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * c->n + 255) & ~(size_t)255));
+}
+
+cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double* q, double* qtot, bool bhl_ready) {
     const int64_t n = c->n;
     cudaStream_t st = c->stream;
     if (c->p.s_prec == CPM_PREC_BF16X3) {
@@ -440,20 +482,25 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     const int rchunks = (m + GT_MR - 1) / GT_MR;
     double* part = (double*)c->ubuf;
     float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
-    c->launches += f32 ? 3 : 2;
+    bhl_ready = bhl_ready && f32;
+    c->launches += (f32 && !bhl_ready) ? 3 : 2;
     prof_begin(c, CPM_K_GEMV);
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
-        k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
-        if (gemv_tma_supported(c)) CPM_TRY(gemv_tma(c, m, bhl, part, splits, jchunk));
+        if (!bhl_ready) k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
+        if (gemv_tma_supported(c)) CPM_TRY(gemv_tma(c, m, bhl, (float2*)part, splits, jchunk));
         else if (gemv_pairs(c)) k_gemv32x2<<<grid, G2_T, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
         else k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
     } else {
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
     }
     CPM_TRY(reserve_neutral(c, m));
-    k_gemv_reduce<<<dim3((unsigned)reduce_blocks(n), m), NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q,
-                                                                       c->p.symm ? c->nbuf : nullptr);
+    const dim3 rgrid((unsigned)reduce_blocks(n), m);
+    double* p1 = c->p.symm ? c->nbuf : nullptr;
+    if (f32 && gemv_tma_supported(c))
+        k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
+    else
+        k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
     prof_end(c, CPM_K_GEMV);
     CPM_LAUNCH(c, "k_gemv");
     return launch_neutral(c, m, q, qtot, true);
