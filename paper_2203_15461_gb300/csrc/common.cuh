@@ -166,6 +166,8 @@ struct cpm_ctx {
     void* tcz = nullptr;         // tensor-core reciprocal space: site phase planes [2][npad][KZ] (fp16)
     float2* tcxy = nullptr;      // [ncols][n] column factors X_i Y_i of the sites
     float tc_wmax = 0.f;         // bound on the k-space weights
+    int tc_mx[32] = {};          // largest harmonic extent of each 128-column structure-factor tile
+    int tc_nmx = 0;              // tiles in tc_mx (0: the kernel finds them)
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 

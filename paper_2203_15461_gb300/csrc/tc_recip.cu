@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -51,6 +52,7 @@ constexpr int RF_STAGES = 2;
 constexpr int RF_XYROWS = 60;                 // staged phase-table rows: (NX + 1) + (2 NY + 1) at most
 constexpr int RF_STAGE_XY = (RF_XYROWS + 1) * RF_KC * 8;   // X, Y rows and Q of one K step
 constexpr int RF_PX = ((RF_XYROWS + 1) * RF_KC + RF_GEN - 1) / RF_GEN;   // staging entries per builder
+constexpr int RF_QSLOT = 1 << 16;              // staging slots at or above this are charges
 constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048 + RF_STAGE_XY;
 constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14
 
@@ -109,12 +111,18 @@ __device__ __forceinline__ uint32_t sw128(int r, int ch) { return (uint32_t)(r *
 // ----------------------------------------------------------------------------- stage 1
 // part[s][r][zi][c] = 2^14 sA_r sum over the charges of split s of P_r[c][j] Z_j[zi]   (zi = nz + NZ)
 // grid (column tiles, harmonic tiles, m * splits); sA_r = 2^e with |Q| sA_r < 2^14.
+// largest harmonic extent of each 128-column tile, known on the host (fixed with the k set)
+struct TileMx {
+    int n;          // number of tiles given; 0: the kernel finds the extents itself
+    int mx[32];
+};
+
 __global__ void __launch_bounds__(RF_THREADS, 1)
     k_tc_sf(const int2* __restrict__ cols, const int* __restrict__ colext, int ncols, int NX, int NY, int NZ, int nzw,
             const float2* __restrict__ EX, const float2* __restrict__ EY, const float2* __restrict__ EZ,
             const float* __restrict__ Qv, const float2* __restrict__ qabs, int64_t ptot, int64_t ne, int splits,
-            int64_t chunk, int m, int cpad, float2* __restrict__ part, unsigned* __restrict__ status,
-            uint64_t wait_ns) {
+            int64_t chunk, int m, int cpad, const __grid_constant__ TileMx tmx, float2* __restrict__ part,
+            unsigned* __restrict__ status, uint64_t wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     uint8_t* aux = smem + RF_STAGES * RF_STAGE;
@@ -130,22 +138,20 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     const int c0 = blockIdx.x * RF_BM;
     const int r = blockIdx.z / splits, sp = blockIdx.z % splits;
 
-    if (warp == 0) {
-        int mx = -1;
-        for (int t = lane; t < RF_BM; t += 32)
-            if (c0 + t < ncols) mx = max(mx, colext[c0 + t]);
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) *s_mx = mx;
+    int mx;
+    if ((int)blockIdx.x < tmx.n) {
+        mx = tmx.mx[blockIdx.x];
+    } else {
+        if (warp == 0) {
+            int v = -1;
+            for (int t = lane; t < RF_BM; t += 32)
+                if (c0 + t < ncols) v = max(v, colext[c0 + t]);
+            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) *s_mx = v;
+        }
+        __syncthreads();
+        mx = *s_mx;
     }
-    if (threadIdx.x < RF_BM) s_cols[threadIdx.x] = c0 + (int)threadIdx.x < ncols ? cols[c0 + threadIdx.x] : make_int2(0, 0);
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < RF_STAGES; ++s) { mbar_init(&full[s], RF_GEN); mbar_init(&empty[s], 1); }
-        mbar_init(done, 1);
-        *abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const int mx = *s_mx;
     const int zoff = blockIdx.y * RF_ZT;
     const int zcount = min(RF_ZT, 2 * mx + 1 - zoff);
     if (mx < 0 || zcount <= 0) return;   // block-uniform; nothing allocated yet
@@ -154,7 +160,86 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     const int64_t jb = (int64_t)r * ne + (int64_t)sp * chunk;
     const int64_t je = min((int64_t)r * ne + ne, jb + chunk);
     const int nsteps = je > jb ? (int)((je - jb + RF_KC - 1) / RF_KC) : 0;
+    const int rem0 = (int)max((int64_t)0, je - jb);   // charges of this split
 
+    // Operand builders.  Thread g owns 16-byte chunk ch = g % 8 (charges 4 ch .. 4 ch + 3 of the step)
+    // of P rows g / 8 + 64 k and of Z row pairs g / 8 + 64 k.  The X and Y table rows and the charges
+    // of a step are staged in shared memory; the loads of step t + 1 (staging entries and Z values)
+    // are issued before the tiles of step t are built.  Within a staged table row, charge 4 ch + u sits
+    // at 16 (u / 2) + 2 ch + u % 2, so that the eight threads of a quarter warp (one P row) read two
+    // 128-byte runs with two 16-byte loads each; the charges are a row of 32 floats in natural order.
+    // Every source address and staging slot of a thread is fixed for the split and advances by one
+    // step (32 charges) at a time, so it is computed once here.
+    const int g = threadIdx.x, ch = g & 7, rbase = g >> 3;
+    const int xyrows = (NX + 1) + (2 * NY + 1);
+    const int nst = (xyrows + 1) * RF_KC;
+    float2* sxy = (float2*)(aux + 2048);
+    float* sqf = (float*)(sxy + xyrows * RF_KC);
+    const bool vec = (ne & 1) == 0;   // then every Z run of a thread starts on a 16-byte boundary
+    // entry k of this thread is charge jj = g % 32 of staged row (g + RF_GEN k) / 32; xdst: its slot
+    // in the staged table rows, or RF_QSLOT + jj for the charge row, or -1 past the last row
+    const int xjj = g & 31;
+    const float2* xsrc[RF_PX];
+    int xdst[RF_PX];
+    const float2* zsrc[RF_ZK];
+    bool zlive[RF_ZK];
+    float sA = 1.f;
+    float2 px[RF_PX], pz[RF_ZK][4];
+    auto prefetch = [&](int t) {
+        const int o = t * RF_KC;
+#pragma unroll
+        for (int k = 0; k < RF_PX; ++k) {
+            float2 v = make_float2(0.f, 0.f);
+            if (xdst[k] >= 0 && xjj + o < rem0)
+                v = xdst[k] < RF_QSLOT ? xsrc[k][o] : make_float2(reinterpret_cast<const float*>(xsrc[k])[o] * sA, 0.f);
+            px[k] = v;
+        }
+        const int jt = o + 4 * ch;   // first charge of this thread's run, relative to the split
+#pragma unroll
+        for (int k = 0; k < RF_ZK; ++k) {
+            if (!zlive[k]) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pz[k][u] = make_float2(0.f, 0.f);
+            } else if (vec && jt + 3 < rem0) {
+                const float4 a01 = *reinterpret_cast<const float4*>(zsrc[k] + o);
+                const float4 a23 = *reinterpret_cast<const float4*>(zsrc[k] + o + 2);
+                pz[k][0] = make_float2(a01.x, a01.y);
+                pz[k][1] = make_float2(a01.z, a01.w);
+                pz[k][2] = make_float2(a23.x, a23.y);
+                pz[k][3] = make_float2(a23.z, a23.w);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pz[k][u] = jt + u < rem0 ? zsrc[k][o + u] : make_float2(0.f, 0.f);
+            }
+        }
+    };
+    if (warp < RF_GEN / 32) {
+        sA = pow2_below(qabs[r].x, 14);
+#pragma unroll
+        for (int k = 0; k < RF_PX; ++k) {
+            const int e = g + RF_GEN * k, row = e >> 5, jj = xjj;
+            xdst[k] = e >= nst ? -1
+                    : row < xyrows ? row * RF_KC + (((jj & 2) << 3) | ((jj >> 2) << 1) | (jj & 1)) : RF_QSLOT + jj;
+            xsrc[k] = row <= NX ? EX + (int64_t)row * ptot + jb + jj
+                    : row < xyrows ? EY + (int64_t)(row - NX - 1) * ptot + jb + jj
+                                   : reinterpret_cast<const float2*>(Qv + jb + jj);
+        }
+#pragma unroll
+        for (int k = 0; k < RF_ZK; ++k) {
+            const int zr = rbase + RF_ROWSTEP * k;
+            zlive[k] = zr < zcount;
+            zsrc[k] = EZ + (int64_t)(z_lo + min(zr, zcount - 1)) * ptot + jb + 4 * ch;
+        }
+        if (nsteps > 0) prefetch(0);   // in flight during the set-up below
+    }
+
+    if (threadIdx.x < RF_BM) s_cols[threadIdx.x] = c0 + (int)threadIdx.x < ncols ? cols[c0 + threadIdx.x] : make_int2(0, 0);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RF_STAGES; ++s) { mbar_init(&full[s], RF_GEN); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     if (warp == RF_GEN / 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(256u)
@@ -167,49 +252,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp < RF_GEN / 32) {
-        // Operand builders.  Thread g owns 16-byte chunk ch = g % 8 (charges 4 ch .. 4 ch + 3 of the
-        // step) of P rows g / 8 + 64 k and of Z row pairs g / 8 + 64 k.  The X and Y table rows and
-        // the charges of a step are staged in shared memory; the loads of step t + 1 (staging
-        // entries and Z values) are issued before the tiles of step t are built.  Within a staged
-        // table row, charge 4 ch + u sits at 16 (u / 2) + 2 ch + u % 2, so that the eight threads
-        // of a quarter warp (one P row) read two 128-byte runs with two 16-byte loads each; the
-        // charges are a row of 32 floats in natural order.
-        const float sA = pow2_below(qabs[r].x, 14);
-        const int g = threadIdx.x, ch = g & 7, rbase = g >> 3;
-        const int xyrows = (NX + 1) + (2 * NY + 1);
-        const int nst = (xyrows + 1) * RF_KC;
-        float2* sxy = (float2*)(aux + 2048);
-        float* sqf = (float*)(sxy + xyrows * RF_KC);
-        float2 px[RF_PX], pz[RF_ZK][4];
-        auto prefetch = [&](int t) {
-            const int64_t j0 = jb + (int64_t)t * RF_KC;
-#pragma unroll
-            for (int k = 0; k < RF_PX; ++k) {
-                const int e = g + RF_GEN * k;
-                float2 v = make_float2(0.f, 0.f);
-                if (e < nst) {
-                    const int row = e >> 5;
-                    const int64_t j = j0 + (e & 31);
-                    if (j < je) {
-                        if (row <= NX) v = EX[(int64_t)row * ptot + j];
-                        else if (row < xyrows) v = EY[(int64_t)(row - NX - 1) * ptot + j];
-                        else v = make_float2(Qv[j] * sA, 0.f);
-                    }
-                }
-                px[k] = v;
-            }
-#pragma unroll
-            for (int k = 0; k < RF_ZK; ++k) {
-                const int zr = rbase + RF_ROWSTEP * k;
-                const float2* zrow = EZ + (int64_t)(z_lo + min(zr, zcount - 1)) * ptot;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t j = j0 + 4 * ch + u;
-                    pz[k][u] = (zr < zcount && j < je) ? zrow[j] : make_float2(0.f, 0.f);
-                }
-            }
-        };
-        if (nsteps > 0) prefetch(0);
         for (int t = 0; t < nsteps; ++t) {
             const int s = t % RF_STAGES;
             bool ok = true;
@@ -217,22 +259,28 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
             if (!gen_bar_and(ok)) break;   // uniform; also: everyone is done reading the staged step t - 1
 #pragma unroll
             for (int k = 0; k < RF_PX; ++k) {
-                const int e = g + RF_GEN * k;
-                if (e < nst) {
-                    const int row = e >> 5, jj = e & 31;
-                    if (row < xyrows) sxy[row * RF_KC + (((jj & 2) << 3) | ((jj >> 2) << 1) | (jj & 1))] = px[k];
-                    else sqf[jj] = px[k].x;
-                }
+                if (xdst[k] >= RF_QSLOT) sqf[xdst[k] - RF_QSLOT] = px[k].x;
+                else if (xdst[k] >= 0) sxy[xdst[k]] = px[k];
             }
-            float2 cz[RF_ZK][4];
-#pragma unroll
-            for (int k = 0; k < RF_ZK; ++k)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) cz[k][u] = pz[k][u];
-            gen_bar();
-            if (t + 1 < nsteps) prefetch(t + 1);
             const uint32_t sa = su32(smem + s * RF_STAGE);
             const uint32_t sb = sa + 2 * RF_A;
+            // the Z tile needs nothing staged: built from registers before they take the next step
+#pragma unroll
+            for (int k = 0; k < RF_ZK; ++k) {
+                const int zr = rbase + RF_ROWSTEP * k;
+                if (zr >= zcount) continue;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    split2(make_float2(pz[k][u].x * RF_ZSCALE, pz[k][u].y * RF_ZSCALE), h[u], l[u]);
+                const uint32_t o0 = sw128(2 * zr, ch), o1 = sw128(2 * zr + 1, ch);
+                sts128(sb + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
+                sts128(sb + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
+                sts128(sb + RF_B + o0, neg_hi(l[0]), neg_hi(l[1]), neg_hi(l[2]), neg_hi(l[3]));
+                sts128(sb + RF_B + o1, swap_h(l[0]), swap_h(l[1]), swap_h(l[2]), swap_h(l[3]));
+            }
+            gen_bar();   // the staged rows of step t are complete
+            if (t + 1 < nsteps) prefetch(t + 1);
             const float4 q4 = reinterpret_cast<const float4*>(sqf)[ch];
             const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
@@ -263,20 +311,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 sts128(sa + off, h[0], h[1], h[2], h[3]);
                 sts128(sa + RF_A + off, l[0], l[1], l[2], l[3]);
             }
-#pragma unroll
-            for (int k = 0; k < RF_ZK; ++k) {
-                const int zr = rbase + RF_ROWSTEP * k;
-                if (zr >= zcount) continue;
-                uint32_t h[4], l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    split2(make_float2(cz[k][u].x * RF_ZSCALE, cz[k][u].y * RF_ZSCALE), h[u], l[u]);
-                const uint32_t o0 = sw128(2 * zr, ch), o1 = sw128(2 * zr + 1, ch);
-                sts128(sb + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
-                sts128(sb + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
-                sts128(sb + RF_B + o0, neg_hi(l[0]), neg_hi(l[1]), neg_hi(l[2]), neg_hi(l[3]));
-                sts128(sb + RF_B + o1, swap_h(l[0]), swap_h(l[1]), swap_h(l[2]), swap_h(l[3]));
-            }
             fence_async_smem();
             mbar_arrive(&full[s]);
         }
@@ -300,15 +334,18 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         }
         umma_commit(done);   // also after an abort: the epilogue then waits for the MMAs in flight
     }
-    if (warp < 4) {
+    if (warp < RF_GEN / 32) {
+        // epilogue on all builder warps: warp w reads accumulator lanes 32 (w % 4) .. + 31 (its columns)
+        // and accumulator columns 16 (w / 4) + 64 i (eight harmonics each)
         const bool ok = mbar_wait(done, 0, abort, wait_ns);
         tc_fence_after();
         const bool good = __all_sync(0xffffffffu, ok && !*abort) != 0;
         if (good) {
-            const int c = c0 + warp * 32 + lane;
+            const int lq = warp & 3, cg = warp >> 2;
+            const int c = c0 + lq * 32 + lane;
             float2* out = part + ((int64_t)sp * m + r) * nzw * cpad + c;
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-            for (int q0 = 0; q0 < nused; q0 += 16) {
+            const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16);
+            for (int q0 = 16 * cg; q0 < nused; q0 += 64) {
                 float v[16];
                 if (nsteps > 0) {
                     tmem_ld16(trow + q0, v);
@@ -649,6 +686,19 @@ cpm_status tc_recip_prepare(cpm_ctx* c) {
         kmin2 = std::min(kmin2, kk * kk);
     }
     c->tc_wmax = (float)(1.01 * 8.0 * PI / c->g.V / kmin2);
+    // largest harmonic extent of each 128-column tile of the structure-factor stage
+    c->tc_nmx = 0;
+    if (d.mtiles <= 32) {
+        std::vector<int> ext(k.ncols);
+        CPM_CUDA(c, cudaMemcpyAsync(ext.data(), k.colext, sizeof(int) * k.ncols, cudaMemcpyDeviceToHost, c->stream));
+        CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int t = 0; t < d.mtiles; ++t) {
+            int mx = -1;
+            for (int cc = t * RF_BM; cc < std::min(k.ncols, (t + 1) * RF_BM); ++cc) mx = std::max(mx, ext[cc]);
+            c->tc_mx[t] = mx;
+        }
+        c->tc_nmx = d.mtiles;
+    }
     return CPM_OK;
 }
 
@@ -662,9 +712,12 @@ cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const f
 
     prof_begin(c, CPM_K_SF);
     CPM_CUDA(c, cudaFuncSetAttribute(k_tc_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, RF_SMEM));
+    TileMx tmx;
+    tmx.n = c->tc_nmx;
+    for (int t = 0; t < 32; ++t) tmx.mx[t] = c->tc_mx[t];
     k_tc_sf<<<dim3(d.mtiles, d.ntiles, m * d.splits), RF_THREADS, RF_SMEM, st>>>(
         k.cols, k.colext, k.ncols, k.NX, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, qabs, ptot, ne, d.splits, d.chunk, m, d.cpad,
-        (float2*)part, c->status, RT_WAIT_NS);
+        tmx, (float2*)part, c->status, RT_WAIT_NS);
     prof_end(c, CPM_K_SF);
     CPM_LAUNCH(c, "k_tc_sf");
 
