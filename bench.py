@@ -217,7 +217,7 @@ def real_pairs(el, xyz_steps, Q, ne, m, step):
 
 
 def kernel_work(ctx, el, nk, ne, m, pairs=None, tensor=False):
-    """Algorithmic work per launch of the per-step kernels (flops or bytes), see the design doc.
+    """Algorithmic work per launch of the per-step kernels (flops or bytes).
 
     With ``tensor`` the two reciprocal contractions run on the tensor cores ("tflop": the same
     algorithmic flops, measured against the tensor-core peak of the emulated FP32 product)."""
@@ -481,6 +481,11 @@ def main():
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
+    # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the full
+    # workload (cold caches: ncu flushes them before each launch); None for a kernel not captured
+    traffic_ncu = {"real": 0.770e6, "sf": 59.35e6, "site": 15.56e6, "gemv": 76.78e6}
+    kname = {"real": "k_real_cells", "sf": "k_tc_sf" if args.k_prec == "f16x2" else "k_sf32",
+             "site": "k_tc_site" if args.k_prec == "f16x2" else "k_site32", "gemv": "k_gemv_tma"}
     pairs = real_pairs(el, xyz, Q, ne, m, W)
     work = kernel_work(mixed, el, nk, ne, m, pairs, tensor=args.k_prec == "f16x2")
     top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
@@ -490,20 +495,20 @@ def main():
         # fp16 tensor rate = the measured bf16 rate (same nominal peak); three fp16 products per FP32 product
         peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
         achieved = amount / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": f"k_tc_{top}", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+        roof = {"kernel": kname.get(top, top), "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_ncu.get(top),
                 "peak_source": f"bf16_tflops ({src}) / 3: two-term fp16 operands, three products per FP32 product"}
     elif kind == "flop":
         peak = _fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         achieved = amount / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": f"k_{top}", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+        roof = {"kernel": kname.get(top, top), "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_ncu.get(top),
                 "peak_source": f"FP32 FMA issue rate 152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
     else:
         peak = float(peaks["hbm_gbs"])
         achieved = amount / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": f"k_{top}", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+        roof = {"kernel": kname.get(top, top), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_ncu.get(top), "peak_source": f"hbm_gbs ({src})"}
     roof["share_of_step"] = prof[top][0] / ms_prof
     roof["all_kernels"] = {kk: {"ms_per_launch": prof[kk][0] / max(1, prof[kk][1]),
                                 "achieved": (work[kk][1] / (prof[kk][0] / max(1, prof[kk][1]) / 1e3)

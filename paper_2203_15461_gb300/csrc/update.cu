@@ -484,24 +484,33 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     float2* bhl = (float2*)((char*)c->ubuf + ((sizeof(double) * splits * m * n + 255) & ~(size_t)255));
     bhl_ready = bhl_ready && f32;
     c->launches += (f32 && !bhl_ready) ? 3 : 2;
-    prof_begin(c, CPM_K_GEMV);
+    // profiled stages: the split of b with the combination of b, the S stream alone, the reduction
+    // of the split partial sums with the neutrality fix
     dim3 grid((unsigned)colblocks, (unsigned)splits, (unsigned)rchunks);
     if (f32) {
-        if (!bhl_ready) k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
+        if (!bhl_ready) {
+            prof_begin(c, CPM_K_COMBINE);
+            k_split_b<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(b, (int64_t)m * n, bhl);
+            prof_end(c, CPM_K_COMBINE);
+        }
+        prof_begin(c, CPM_K_GEMV);
         if (gemv_tma_supported(c)) CPM_TRY(gemv_tma(c, m, bhl, (float2*)part, splits, jchunk));
         else if (gemv_pairs(c)) k_gemv32x2<<<grid, G2_T, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
         else k_gemv32<<<grid, GT_COLS, 0, st>>>(c->S32, bhl, n, m, jchunk, part);
     } else {
+        prof_begin(c, CPM_K_GEMV);
         k_gemv_t<double><<<grid, GT_COLS, 0, st>>>(c->S, b, n, m, jchunk, part);
     }
+    prof_end(c, CPM_K_GEMV);
     CPM_TRY(reserve_neutral(c, m));
+    prof_begin(c, CPM_K_NEUTRAL);
     const dim3 rgrid((unsigned)reduce_blocks(n), m);
     double* p1 = c->p.symm ? c->nbuf : nullptr;
     if (f32 && gemv_tma_supported(c))
         k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
     else
         k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
-    prof_end(c, CPM_K_GEMV);
+    prof_end(c, CPM_K_NEUTRAL);
     CPM_LAUNCH(c, "k_gemv");
     return launch_neutral(c, m, q, qtot, true);
 }
