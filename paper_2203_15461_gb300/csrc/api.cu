@@ -206,6 +206,10 @@ void cpm_destroy(cpm_ctx* c) {
     for (int k = 0; k < CPM_K_COUNT; ++k)
         for (auto& pr : c->prof_pending[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaStream_t s : c->aux)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->fev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 

@@ -97,11 +97,27 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
         pr[t] = v;
     }
     if (!last_block_of(&tickets[r], nb)) return;
+    // the block sums, ST_THREADS blocks at a time, loaded by all threads at once and added by
+    // threads 0..5 in block order
+    __shared__ double buf[6][ST_THREADS];
+    const volatile double* pv = part + (int64_t)r * nb * 6;
+    double v = 0.0;
+    for (int k0 = 0; k0 < nb; k0 += ST_THREADS) {
+        const int k = k0 + threadIdx.x;
+        if (k < nb)
+            for (int t = 0; t < 6; ++t) buf[t][threadIdx.x] = pv[k * 6 + t];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int t = threadIdx.x, cnt = min(ST_THREADS, nb - k0);
+            for (int kk = 0; kk < cnt; ++kk) {
+                const double x = buf[t][kk];
+                v = (k0 == 0 && kk == 0) ? x : (t == 4 ? fmax(v, x) : v + x);
+            }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x < 6) {
         const int t = threadIdx.x;
-        const volatile double* pv = part + (int64_t)r * nb * 6;
-        double v = pv[t];
-        for (int k = 1; k < nb; ++k) v = t == 4 ? fmax(v, pv[k * 6 + t]) : v + pv[k * 6 + t];
         if (t < 4) stats[4 * r + t] = v;
         else if (qabs) {
             if (t == 4) qabs[r].x = (float)v;
@@ -875,10 +891,20 @@ __device__ __forceinline__ dcx dcx_mul(dcx a, dcx b) {
     return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
 
-// part[r][chunk][nz - 1] for nz in one block of 12 harmonics: each thread takes 2 charges of the
-// chunk (256 charges per block), raises exp(i theta) to the block's first harmonic and steps
-// through the block by a double-float recurrence; the block sums its threads in a fixed order.
-constexpr int C0_THREADS = 128, C0_PER_THREAD = 2, C0_NB = 12;
+// part[r][chunk][nz - 1] for nz in one block of C0_NB harmonics: each thread takes 2 charges of the
+// chunk (256 charges per block), raises exp(i theta) of both to the block's first harmonic and steps
+// through the block by a double-float recurrence (the two charges' chains interleaved); the block
+// sums its threads in a fixed order.
+constexpr int C0_THREADS = 128, C0_PER_THREAD = 2, C0_NB = 6;
+
+__device__ __forceinline__ dcx dcx_pow(dcx e1, int pw) {   // e1^pw by binary powering, pw >= 1
+    dcx e = {{1.f, 0.f}, {0.f, 0.f}}, base = e1;
+    for (; pw > 0; pw >>= 1) {
+        if (pw & 1) e = dcx_mul(e, base);
+        base = dcx_mul(base, base);
+    }
+    return e;
+}
 
 __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restrict__ e1s, const float2* __restrict__ Qd,
                                                        int64_t ne, int nz0, double2* __restrict__ part) {
@@ -889,26 +915,30 @@ __global__ void __launch_bounds__(C0_THREADS) k_col0_rho(const float4* __restric
     dcx acc[C0_NB];
 #pragma unroll
     for (int k = 0; k < C0_NB; ++k) acc[k] = {{0.f, 0.f}, {0.f, 0.f}};
+    // the thread's two charges (a zero charge, also past the end, contributes exact zeros)
+    dfl q[C0_PER_THREAD];
+    dcx e1[C0_PER_THREAD], e[C0_PER_THREAD];
+#pragma unroll
     for (int t = 0; t < C0_PER_THREAD; ++t) {
         const int64_t j = (int64_t)chunk * C0_THREADS * C0_PER_THREAD + (int64_t)t * C0_THREADS + threadIdx.x;
-        if (j >= ne) break;
-        const int64_t p = (int64_t)r * ne + j;
-        const float2 qf = Qd[p];
-        if (qf.x == 0.f) continue;
-        const dfl q = {qf.x, qf.y};
-        const float4 f = e1s[p];
-        const dcx e1 = {{f.x, f.y}, {f.z, f.w}};
-        // e = e1^nzs by binary powering
-        dcx e = {{1.f, 0.f}, {0.f, 0.f}}, base = e1;
-        for (int pw = nzs; pw > 0; pw >>= 1) {
-            if (pw & 1) e = dcx_mul(e, base);
-            base = dcx_mul(base, base);
+        float2 qf = make_float2(0.f, 0.f);
+        float4 f = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (j < ne) {
+            const int64_t p = (int64_t)r * ne + j;
+            qf = Qd[p];
+            f = e1s[p];
         }
+        q[t] = {qf.x, qf.y};
+        e1[t] = {{f.x, f.y}, {f.z, f.w}};
+        e[t] = dcx_pow(e1[t], nzs);
+    }
 #pragma unroll
-        for (int k = 0; k < C0_NB; ++k) {
-            acc[k].re = df_add(acc[k].re, df_mul(q, e.re));
-            acc[k].im = df_add(acc[k].im, df_mul(q, e.im));
-            e = dcx_mul(e, e1);
+    for (int k = 0; k < C0_NB; ++k) {
+#pragma unroll
+        for (int t = 0; t < C0_PER_THREAD; ++t) {
+            acc[k].re = df_add(acc[k].re, df_mul(q[t], e[t].re));
+            acc[k].im = df_add(acc[k].im, df_mul(q[t], e[t].im));
+            e[t] = dcx_mul(e[t], e1[t]);
         }
     }
 #pragma unroll
@@ -1071,7 +1101,16 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     const int r = (int)(t / n);
     const int64_t i = t % n;
     double s = 0.0;
-    for (int k = 0; k < nctiles; ++k) s += (double)partial[((int64_t)r * nctiles + k) * n + i];
+    const T* pp = partial + (int64_t)r * nctiles * n + i;
+    int k = 0;
+    for (; k + 8 <= nctiles; k += 8) {   // eight loads in flight, added in tile order
+        T x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = pp[(int64_t)(k + u) * n];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)x[u];
+    }
+    for (; k < nctiles; ++k) s += (double)pp[(int64_t)k * n];
     s += real[t];
     if (b0) s += b0[(int64_t)r * nzu + zmap[i]];
     const double* st = stats + 4 * r;
@@ -1204,6 +1243,53 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     const int nc = m * p.cg.ncells;
     c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
 
+    // Three chains: the origin stream bins the charges (per-replica totals, single-precision charges)
+    // and runs the cell list and the real-space sum; side stream 1 builds the phase tables and, once
+    // the binning is done (it needs the charge scales), the reciprocal sums; side stream 2 sums the
+    // k_perp = 0 column once the phase kernel has written its inputs.  k_combine joins them.  With
+    // per-kernel profiling on, everything runs on the origin stream in the same order.
+    const bool recip = k.nk > 0 && ptot > 0;
+    const bool fork = !c->prof_on;
+    cudaStream_t s0 = st, s1 = st, s2 = st;
+    if (fork) {
+        CPM_TRY(ensure_aux(c));
+        s1 = c->aux[0];
+        s2 = c->aux[1];
+        CPM_CUDA(c, cudaEventRecord(c->fev[0], s0));
+        CPM_CUDA(c, cudaStreamWaitEvent(s1, c->fev[0], 0));
+    }
+    if (recip) {
+        prof_begin(c, CPM_K_PHASES);
+        const bool col0 = std::is_same<T, float>::value && k.ext0 > 0;   // its phases come along
+        CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ, Q,
+                                   col0 ? (float4*)(scr + p.off_c0e1) : nullptr,
+                                   col0 ? (float2*)(scr + p.off_c0q) : nullptr));
+        prof_end(c, CPM_K_PHASES);
+    }
+    if (fork) {
+        CPM_CUDA(c, cudaEventRecord(c->fev[1], s1));
+        CPM_CUDA(c, cudaStreamWaitEvent(s2, c->fev[1], 0));
+    }
+    double* b0 = nullptr;
+    if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0) {
+        // the k_perp = 0 column in FP64 (its single-precision weights are zero)
+        double2* c0part = (double2*)(scr + p.off_c0part);
+        double2* c0w = (double2*)(scr + p.off_c0w);
+        b0 = (double*)(scr + p.off_b0);
+        prof_begin(c, CPM_K_COL0);
+        const int nz0 = std::min(k.ext0, COL0_NZ);
+        const int nblk = (nz0 + C0_NB - 1) / C0_NB;
+        float4* e1s = (float4*)(scr + p.off_c0e1);
+        float2* q0 = (float2*)(scr + p.off_c0q);   // e1s and q0 come from k_fracs
+        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, s2>>>(e1s, q0, ne, nz0, c0part);
+        CPM_LAUNCH(c, "k_col0_rho");
+        k_col0_reduce<<<(m * nz0 * 32 + 255) / 256, 256, 0, s2>>>(c0part, p.c0chunks, nz0, k.w, k.NZ, m, c0w);
+        CPM_LAUNCH(c, "k_col0_reduce");
+        k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, s2>>>(c->c0e, c->nzu, m, nz0, c0w, b0);
+        CPM_LAUNCH(c, "k_col0_site");
+        prof_end(c, CPM_K_COL0);
+        c->launches += 3;
+    }
     // binning and the per-replica totals (one pass over the charges)
     prof_begin(c, CPM_K_CELLS);
     float2* qabs = (float2*)(scr + p.off_qabs);
@@ -1216,6 +1302,60 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
                                                      p.tc ? qabs : nullptr);
         CPM_LAUNCH(c, "k_bin");
     }
+    prof_end(c, CPM_K_CELLS);
+    if (fork) {
+        CPM_CUDA(c, cudaEventRecord(c->fev[2], s0));
+        CPM_CUDA(c, cudaStreamWaitEvent(s1, c->fev[2], 0));
+    }
+    if (recip) {
+        if (p.tc) {
+            c->stream = s1;   // tc_recip_run launches on the context stream
+            const cpm_status rs = tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const float2*)EZ,
+                                               (const float*)Qv, qabs, scr + p.off_tcpart, scr + p.off_w16,
+                                               (float*)part);
+            c->stream = s0;
+            CPM_TRY(rs);
+        } else {
+        prof_begin(c, CPM_K_SF);
+        if (std::is_same<T, float>::value) {
+            const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
+            const int nsup = 2 * zh2 + 1;
+            dim3 gsf(p.ctiles, nsup, m * p.splits);
+            k_sf32<<<gsf, 256, 0, s1>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)EX,
+                                        (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne, p.splits,
+                                        p.chunk, m, nsup, (float2*)rp);
+        } else {
+            dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
+            k_sf<T><<<gsf, 256, 0, s1>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne,
+                                         p.splits, p.chunk, m, rp);
+        }
+        prof_end(c, CPM_K_SF);
+        CPM_LAUNCH(c, "k_sf");
+        prof_begin(c, CPM_K_SFRED);
+        const int64_t per_rep = (int64_t)k.ncols * k.nzw;
+        const T* w = std::is_same<T, float>::value ? (const T*)k.w32 : (const T*)k.w;
+        k_sf_reduce<T><<<(unsigned)((per_rep * m + 255) / 256), 256, 0, s1>>>(rp, w, per_rep, m, p.splits, wr);
+        prof_end(c, CPM_K_SFRED);
+        CPM_LAUNCH(c, "k_sf_reduce");
+        prof_begin(c, CPM_K_SITE);
+        const Phases<T>& sp = site_tables<T>(c);
+        if (std::is_same<T, float>::value) {
+            dim3 gs((unsigned)((n + T2_BS - 1) / T2_BS), p.ctiles, m);
+            k_site32<<<gs, 256, 0, s1>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)wr,
+                                         (const float2*)sp.X, (const float2*)sp.Y, (const float2*)sp.Z, n, p.nctiles,
+                                         (float*)part);
+        } else {
+            dim3 gs((unsigned)((n + SF_BN - 1) / SF_BN), p.ctiles, m);
+            k_site<T><<<gs, 256, 0, s1>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, wr, sp.X, sp.Y, sp.Z, n,
+                                          p.nctiles, part);
+        }
+        prof_end(c, CPM_K_SITE);
+        CPM_LAUNCH(c, "k_site");
+        }
+    } else {
+        CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, s1));
+    }
+    prof_begin(c, CPM_K_CELLS);
     k_cellscan<<<m, 1024, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
     CPM_LAUNCH(c, "k_cellscan");
     if (ptot > 0) {
@@ -1242,76 +1382,11 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_end(c, CPM_K_REAL);
     CPM_LAUNCH(c, "k_real_b");
-    // reciprocal space
-    if (k.nk > 0 && ptot > 0) {
-        prof_begin(c, CPM_K_PHASES);
-        const bool col0 = std::is_same<T, float>::value && k.ext0 > 0;   // its phases come along
-        CPM_TRY(launch_phases_u<T>(st, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ, Q,
-                                   col0 ? (float4*)(scr + p.off_c0e1) : nullptr,
-                                   col0 ? (float2*)(scr + p.off_c0q) : nullptr));
-        prof_end(c, CPM_K_PHASES);
-        if (p.tc) {
-            CPM_TRY(tc_recip_run(c, m, ne, (const float2*)EX, (const float2*)EY, (const float2*)EZ, (const float*)Qv,
-                                 qabs, scr + p.off_tcpart, scr + p.off_w16, (float*)part));
-        } else {
-        prof_begin(c, CPM_K_SF);
-        if (std::is_same<T, float>::value) {
-            const int zh2 = k.NZ + 1 - S2_BZ / 2 > 0 ? (k.NZ + 1 - S2_BZ / 2 + S2_BZ - 1) / S2_BZ : 0;
-            const int nsup = 2 * zh2 + 1;
-            dim3 gsf(p.ctiles, nsup, m * p.splits);
-            k_sf32<<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)EX,
-                                        (const float2*)EY, (const float2*)EZ, (const float*)Qv, ptot, ne, p.splits,
-                                        p.chunk, m, nsup, (float2*)rp);
-        } else {
-            dim3 gsf(p.ctiles, p.ztiles, m * p.splits);
-            k_sf<T><<<gsf, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, EX, EY, EZ, Qv, ptot, ne,
-                                         p.splits, p.chunk, m, rp);
-        }
-        prof_end(c, CPM_K_SF);
-        CPM_LAUNCH(c, "k_sf");
-        prof_begin(c, CPM_K_SFRED);
-        const int64_t per_rep = (int64_t)k.ncols * k.nzw;
-        const T* w = std::is_same<T, float>::value ? (const T*)k.w32 : (const T*)k.w;
-        k_sf_reduce<T><<<(unsigned)((per_rep * m + 255) / 256), 256, 0, st>>>(rp, w, per_rep, m, p.splits, wr);
-        prof_end(c, CPM_K_SFRED);
-        CPM_LAUNCH(c, "k_sf_reduce");
-        prof_begin(c, CPM_K_SITE);
-        const Phases<T>& sp = site_tables<T>(c);
-        if (std::is_same<T, float>::value) {
-            dim3 gs((unsigned)((n + T2_BS - 1) / T2_BS), p.ctiles, m);
-            k_site32<<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, (const float2*)wr,
-                                         (const float2*)sp.X, (const float2*)sp.Y, (const float2*)sp.Z, n, p.nctiles,
-                                         (float*)part);
-        } else {
-            dim3 gs((unsigned)((n + SF_BN - 1) / SF_BN), p.ctiles, m);
-            k_site<T><<<gs, 256, 0, st>>>(k.cols, k.colext, k.ncols, k.NY, k.NZ, k.nzw, wr, sp.X, sp.Y, sp.Z, n,
-                                          p.nctiles, part);
-        }
-        prof_end(c, CPM_K_SITE);
-        CPM_LAUNCH(c, "k_site");
-        }
-    } else {
-        CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, st));
-    }
-    double* b0 = nullptr;
-    if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0) {
-        // the k_perp = 0 column in FP64 (its single-precision weights are zero)
-        double2* c0part = (double2*)(scr + p.off_c0part);
-        double2* c0w = (double2*)(scr + p.off_c0w);
-        b0 = (double*)(scr + p.off_b0);
-        prof_begin(c, CPM_K_COL0);
-        const int nz0 = std::min(k.ext0, COL0_NZ);
-        const int nblk = (nz0 + C0_NB - 1) / C0_NB;
-        float4* e1s = (float4*)(scr + p.off_c0e1);
-        float2* q0 = (float2*)(scr + p.off_c0q);   // e1s and q0 come from k_fracs
-        k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, st>>>(e1s, q0, ne, nz0, c0part);
-        CPM_LAUNCH(c, "k_col0_rho");
-        k_col0_reduce<<<(m * nz0 * 32 + 255) / 256, 256, 0, st>>>(c0part, p.c0chunks, nz0, k.w, k.NZ, m, c0w);
-        CPM_LAUNCH(c, "k_col0_reduce");
-        k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, st>>>(c->c0e, c->nzu, m, nz0, c0w, b0);
-        CPM_LAUNCH(c, "k_col0_site");
-        prof_end(c, CPM_K_COL0);
-        c->launches += 3;
+    if (fork) {
+        CPM_CUDA(c, cudaEventRecord(c->fev[3], s1));
+        CPM_CUDA(c, cudaEventRecord(c->fev[4], s2));
+        CPM_CUDA(c, cudaStreamWaitEvent(s0, c->fev[3], 0));
+        CPM_CUDA(c, cudaStreamWaitEvent(s0, c->fev[4], 0));
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
@@ -1333,8 +1408,17 @@ cpm_status build_col0_sites(cpm_ctx* c) {
     return CPM_OK;
 }
 
+cpm_status ensure_aux(cpm_ctx* c) {
+    for (cudaStream_t& s : c->aux)
+        if (!s) CPM_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->fev)
+        if (!e) CPM_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return CPM_OK;
+}
+
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
+    CPM_TRY(ensure_aux(c));
     CPM_TRY(ensure_tickets(c, m));
     return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }

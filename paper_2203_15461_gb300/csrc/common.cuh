@@ -93,6 +93,10 @@ struct Geometry {
 struct cpm_ctx {
     cpm_params p{};
     cudaStream_t stream = nullptr;
+    // two side streams and fork/join events: the reciprocal-space and k_perp = 0 chains of b run beside
+    // the real-space chain (in an eager call and inside a captured graph alike)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t fev[5] = {};
     int device = 0;
     std::string err;
     size_t bytes = 0;
@@ -256,6 +260,7 @@ CellGrid make_grid(const Geometry& g);
 cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* Q, double* b_out,
                 float2* bhl = nullptr);
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
+cpm_status ensure_aux(cpm_ctx* c);
 cpm_status build_col0_sites(cpm_ctx* c);
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
 

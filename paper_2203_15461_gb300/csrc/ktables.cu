@@ -202,10 +202,14 @@ template <> __device__ __forceinline__ double2 phase_of<double>(uint64_t u, int 
     sincospi((double)p * 0x1p-63, &s, &co);
     return make_double2(co, s);
 }
+// single precision: bits 32..63 of h u (mod 2^64) are a signed 32-bit turn fraction (resolution
+// 2^-31 turn, far below the sincospif error); two 32-bit multiplies and an int32 conversion
 template <> __device__ __forceinline__ float2 phase_of<float>(uint64_t u, int h) {
-    int64_t p = (int64_t)(u * (uint64_t)(int64_t)h);
+    const uint32_t lo = (uint32_t)u, hi = (uint32_t)(u >> 32), hl = (uint32_t)h;
+    uint32_t top = __umulhi(lo, hl) + hi * hl;   // (u * h) >> 32 mod 2^32 for h >= 0
+    if (h < 0) top -= lo;                         // the sign extension of h contributes -lo * 2^32
     float s, co;
-    sincospif((float)p * 0x1p-63f, &s, &co);
+    sincospif((float)(int32_t)top * 0x1p-31f, &s, &co);
     return make_float2(co, s);
 }
 

@@ -352,12 +352,25 @@ __global__ void __launch_bounds__(NB_T) k_neutral_fix(double* __restrict__ q, co
                                                       double* __restrict__ p2, int* __restrict__ tickets,
                                                       double* __restrict__ qtot) {
     __shared__ double sh[NB_T / 32];
+    __shared__ double buf[NB_T];
+    __shared__ double s_sum;
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t chunk = (n + nb - 1) / nb, ib = (int64_t)b * chunk, ie = min(n, ib + chunk);
     double* qr = q + (int64_t)r * n;
     double s = 0.0;
-    if (symm)
-        for (int k = 0; k < np1; ++k) s += p1[(int64_t)r * np1 + k];
+    if (symm) {
+        // sum of the np1 block sums in order: loaded by all threads at once, added by thread 0
+        for (int k0 = 0; k0 < np1; k0 += NB_T) {
+            if (k0 + (int)threadIdx.x < np1) buf[threadIdx.x] = p1[(int64_t)r * np1 + k0 + threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int k = 0; k < min(NB_T, np1 - k0); ++k) s += buf[k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_sum = s;
+        __syncthreads();
+        s = s_sum;
+    }
     double a = 0.0;
     for (int64_t i = ib + threadIdx.x; i < ie; i += NB_T) {
         double v = qr[i];
@@ -376,10 +389,13 @@ __global__ void __launch_bounds__(NB_T) k_neutral_fix(double* __restrict__ q, co
         p2[(int64_t)r * nb + b] = t;
     }
     if (!last_block_of(&tickets[r], nb)) return;
-    if (threadIdx.x == 0 && qtot) {
-        const volatile double* pv = p2 + (int64_t)r * nb;
+    if (!qtot) return;
+    const volatile double* pv = p2 + (int64_t)r * nb;
+    if ((int)threadIdx.x < nb) buf[threadIdx.x] = pv[threadIdx.x];   // nb <= 64 slices
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int k = 0; k < nb; ++k) t += pv[k];
+        for (int k = 0; k < nb; ++k) t += buf[k];
         qtot[r] = t;
     }
 }
