@@ -278,15 +278,24 @@ template <typename P> struct PartSum;
 template <> struct PartSum<double> { using type = PartSumD; };
 template <> struct PartSum<float2> { using type = PartSumF2; };
 
-// q = SG psi - sum of the split partials; with p1 also the block sums of q for the neutrality fix
+// q = SG psi - sum of the split partials, then the neutrality fix of Sec. II.B in the last block of
+// each replica: every block writes its slice of q and the slice's sum p1[r][b]; the replica's last
+// block (ticket) adds the p1 in block order, applies q <- q - u (e^T q) with symm, and writes
+// qtot[r] = e^T q of the result (plain FP64 sums in a fixed order: the rounding, about n eps max|q|,
+// is far below the 1e-12 e the total is held to)
 template <typename P>
 __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part, int splits,
                                                       const double* __restrict__ SG, int ng,
                                                       const double* __restrict__ psi, int64_t n, int m,
-                                                      double* __restrict__ q, double* __restrict__ p1) {
+                                                      double* __restrict__ q, double* __restrict__ p1,
+                                                      const double* __restrict__ u, int symm,
+                                                      int* __restrict__ tickets, double* __restrict__ qtot) {
     __shared__ double sh[NB_T / 32];
-    const int r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double buf[NB_T];
+    __shared__ double s_sum;
+    const int r = blockIdx.y, nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * NB_T + threadIdx.x;
+    double* qr = q + (int64_t)r * n;
     double qi = 0.0;
     if (i < n) {
         typename PartSum<P>::type v;
@@ -304,17 +313,49 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         double sv = 0.0;
         for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
         qi = sv - v.value();
-        q[(int64_t)r * n + i] = qi;
+        qr[i] = qi;
     }
-    if (!p1) return;
-    for (int o = 16; o > 0; o >>= 1) qi += __shfl_down_sync(0xffffffffu, qi, o);
-    if (lane == 0) sh[warp] = qi;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = sh[0];
-        for (int w = 1; w < NB_T / 32; ++w) t += sh[w];
-        p1[(int64_t)r * gridDim.x + blockIdx.x] = t;
+    auto block_sum = [&](double a) {   // fixed order: warp trees, then warps in order
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[warp] = a;
+        __syncthreads();
+        double t = 0.0;
+        if (threadIdx.x == 0) {
+            t = sh[0];
+            for (int w = 1; w < NB_T / 32; ++w) t += sh[w];
+        }
+        __syncthreads();
+        return t;   // valid in thread 0
+    };
+    const double bsum = block_sum(qi);
+    if (threadIdx.x == 0) p1[(int64_t)r * nb + blockIdx.x] = bsum;
+    if (!last_block_of(&tickets[r], nb)) return;
+    double s = 0.0;
+    if (symm) {
+        const volatile double* pv = p1 + (int64_t)r * nb;
+        for (int k0 = 0; k0 < nb; k0 += NB_T) {
+            if (k0 + (int)threadIdx.x < nb) buf[threadIdx.x] = pv[k0 + threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int k = 0; k < min(NB_T, nb - k0); ++k) s += buf[k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_sum = s;
+        __syncthreads();
+        s = s_sum;
     }
+    volatile double* qv = qr;
+    double a = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += NB_T) {
+        double v = qv[k];
+        if (symm) {
+            v -= u[k] * s;
+            qv[k] = v;
+        }
+        a += v;
+    }
+    const double tot = block_sum(a);
+    if (threadIdx.x == 0 && qtot) qtot[r] = tot;
 }
 
 __device__ __forceinline__ void neumaier_add(double& a, double& comp, double v) {
@@ -521,14 +562,15 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     CPM_TRY(reserve_neutral(c, m));
     prof_begin(c, CPM_K_NEUTRAL);
     const dim3 rgrid((unsigned)reduce_blocks(n), m);
-    double* p1 = c->p.symm ? c->nbuf : nullptr;
     if (f32 && gemv_tma_supported(c))
-        k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
+        k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, c->SG, c->ng, psi, n, m, q,
+                                                      c->nbuf, c->u, c->p.symm, c->tickets, qtot);
     else
-        k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q, p1);
+        k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q, c->nbuf, c->u,
+                                                      c->p.symm, c->tickets, qtot);
     prof_end(c, CPM_K_NEUTRAL);
     CPM_LAUNCH(c, "k_gemv");
-    return launch_neutral(c, m, q, qtot, true);
+    return CPM_OK;
 }
 
 }  // namespace cpm
