@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(256) k_real_b(const double* __restrict__ sx, i
 constexpr int RC_WARPS = 4;
 constexpr int RC_SMEM_TABS = 2;
 constexpr int RC_LIST = 64;                         // charge ranges listed per warp at a time
+constexpr int RC_RING = 64;                         // per-warp ring of charges that passed the box test
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm, const int4* __restrict__ chunks,
                  int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
                  const float4* __restrict__ sorted, const float4* __restrict__ tab, int ntab,
-                 const int* __restrict__ tabid, double* __restrict__ out) {
+                 const int* __restrict__ tabid, int m, double* __restrict__ out) {
     __shared__ float4 stab[RC_SMEM_TABS * RT_S];
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
     __shared__ float sbox[6];
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         int beg[RC_WARPS][RC_LIST];
         int pre[RC_WARPS][RC_LIST + 1];
         float4 sh[RC_WARPS][RC_LIST];
-        float4 ring[RC_WARPS][64];
+        float4 ring[RC_WARPS][RC_RING];
     };
     union Shared {
         Lists l;
@@ -354,9 +355,26 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     auto& lsh = u_.l.sh;
     auto& red = u_.red;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x, r = blockIdx.y;
-    if (SMEM_TAB)
-        for (int e = threadIdx.x; e < ntab * RT_S; e += blockDim.x) stab[e] = tab[e];
+    if (SMEM_TAB) {   // staged once per block, eight loads per thread in flight
+        const int tot = ntab * RT_S;
+        for (int e0 = 0; e0 < tot; e0 += 8 * (int)blockDim.x) {
+            float4 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = e0 + k * (int)blockDim.x + (int)threadIdx.x;
+                if (e < tot) v[k] = tab[e];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = e0 + k * (int)blockDim.x + (int)threadIdx.x;
+                if (e < tot) stab[e] = v[k];
+            }
+        }
+    }
+    // persistent: the block takes the (chunk, replica) items blockIdx.x, blockIdx.x + gridDim.x, ...
+    for (int item = blockIdx.x; item < nchunks * m; item += gridDim.x) {
+    const int ch = item % nchunks, r = item / nchunks;
+    __syncthreads();   // the previous item's partial sums have been read
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
     const int nsites = cinfo.y;
     if (warp == 0) {
@@ -396,25 +414,28 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
 #pragma unroll
     for (int s = 0; s < 32; ++s) acc[s] = 0.f;
     // every lane holds one charge (weight qw, zero for an empty lane) and runs over the chunk's sites
+    auto pair_term = [&](const float4 st, const float4 q) {
+        // branch-free pair term: the table index is clamped and the weight is zero outside the
+        // cutoff, so the sites of a group interleave
+        const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const float u = sqrt_approx(r2) * inv_h;
+        // floor(u) from the bits of u + 1.5 * 2^23 rounded toward zero (u >= 0); at and past the
+        // cutoff the index clamps to the table's zero row
+        const float ur = __fadd_rz(u, 12582912.0f);
+        const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N);
+        const float t = u - (ur - 12582912.0f);
+        const float4 cf = tb[__float_as_int(st.w) + kk];
+        return cf.x + t * (cf.y + t * (cf.z + t * cf.w));
+    };
     auto eval_sites = [&](const float4 q, const float qw) {
 #pragma unroll
         for (int sg = 0; sg < 32; sg += 8) {
             if (sg >= nsites) break;   // uniform; sites past nsites are far-away dummies
 #pragma unroll
             for (int s = sg; s < sg + 8; ++s) {
-                // branch-free pair term: the table index is clamped and the weight is zero
-                // outside the cutoff, so the eight sites of a group interleave
                 const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
-                const float ddx = st.x - q.x, ddy = st.y - q.y, ddz = st.z - q.z;
-                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                const float u = sqrt_approx(r2) * inv_h;
-                // floor(u) from the bits of u + 1.5 * 2^23 rounded toward zero (u >= 0); at and
-                // past the cutoff the index clamps to the table's zero row
-                const float ur = __fadd_rz(u, 12582912.0f);
-                const int kk = min(__float_as_int(ur) - 0x4B400000, RT_N);
-                const float t = u - (ur - 12582912.0f);
-                const float4 cf = tb[__float_as_int(st.w) + kk];
-                acc[s] = fmaf(qw, cf.x + t * (cf.y + t * (cf.z + t * cf.w)), acc[s]);
+                acc[s] = fmaf(qw, pair_term(st, q), acc[s]);
             }
         }
     };
@@ -489,15 +510,22 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
         if (lane == 0) rpre[nent] = total;
         __syncwarp();
-        // charge v of the concatenated ranges (its image shift applied later), loaded one batch ahead
-        auto fetch = [&](int v, float4& q, float4& sh) {
-            int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= v
+        // charge v of the concatenated ranges (its image shift applied later), loaded one batch ahead;
+        // each lane keeps the index of the range its next charge falls in and moves it forward (the
+        // charges a lane takes only increase)
+        int ec = 0;
+        {
+            int lo = 0, hi = nent - 1;   // last entry with rpre[e] <= lane
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (rpre[mid] <= v) lo = mid; else hi = mid - 1;
+                if (rpre[mid] <= lane) lo = mid; else hi = mid - 1;
             }
-            q = sorted[rbeg[lo] + (v - rpre[lo])];
-            sh = rsh[lo];
+            ec = lo;
+        }
+        auto fetch = [&](int v, float4& q, float4& sh) {
+            while (ec + 1 < nent && rpre[ec + 1] <= v) ++ec;
+            q = sorted[rbeg[ec] + (v - rpre[ec])];
+            sh = rsh[ec];
         };
         float4 qn = make_float4(0.f, 0.f, 0.f, 0.f), shn = qn;
         if (lane < total) fetch(lane, qn, shn);
@@ -516,13 +544,13 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                 keep = ex * ex + ey * ey + ez * ez < rc2;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) ring[(rhead + rcount + __popc(bal & ((1u << lane) - 1u))) & 63] = q;
+            if (keep) ring[(rhead + rcount + __popc(bal & ((1u << lane) - 1u))) & (RC_RING - 1)] = q;
             rcount += __popc(bal);
             __syncwarp();
             if (rcount >= 32) {
-                const float4 qq = ring[(rhead + lane) & 63];
+                const float4 qq = ring[(rhead + lane) & (RC_RING - 1)];
                 __syncwarp();
-                rhead = (rhead + 32) & 63;
+                rhead = (rhead + 32) & (RC_RING - 1);
                 rcount -= 32;
                 eval_sites(qq, qq.w);
             }
@@ -530,7 +558,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         __syncwarp();
     }
     if (rcount > 0) {   // the rest of the ring
-        const float4 qq = lane < rcount ? ring[(rhead + lane) & 63] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 qq = lane < rcount ? ring[(rhead + lane) & (RC_RING - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
         eval_sites(qq, lane < rcount ? qq.w : 0.f);
     }
     __syncthreads();   // the lists and rings are done: their bytes now take the partial sums
@@ -546,6 +574,12 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
         out[(int64_t)r * n + perm[cinfo.x + lane]] = a;
     }
+    }
+}
+
+// one wave of the persistent real-space kernel: four blocks per SM (its launch bound)
+static unsigned real_grid(int nchunks, int m) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nchunks * m, 4 * 152));
 }
 
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas) {
@@ -1368,13 +1402,13 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_begin(c, CPM_K_REAL);
     if (std::is_same<T, float>::value && c->rtab && c->schunks) {
         if (c->nrtab <= RC_SMEM_TABS)
-            k_real_cells<true><<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
+            k_real_cells<true><<<real_grid(c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
             c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
-            (const float4*)c->rtab, c->nrtab, c->rtab_id, real);
+            (const float4*)c->rtab, c->nrtab, c->rtab_id, m, real);
         else
-            k_real_cells<false><<<dim3((unsigned)c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
+            k_real_cells<false><<<real_grid(c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
             c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
-            (const float4*)c->rtab, c->nrtab, c->rtab_id, real);
+            (const float4*)c->rtab, c->nrtab, c->rtab_id, m, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,
