@@ -1294,16 +1294,14 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     if (recip) {
         prof_begin(c, CPM_K_PHASES);
-        const bool col0 = std::is_same<T, float>::value && k.ext0 > 0;   // its phases come along
-        CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ, Q,
-                                   col0 ? (float4*)(scr + p.off_c0e1) : nullptr,
-                                   col0 ? (float2*)(scr + p.off_c0q) : nullptr));
+        // the k_perp = 0 chain needs only the fractions: it starts after k_fracs
+        CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ,
+                                   fork ? c->fev[1] : nullptr));
         prof_end(c, CPM_K_PHASES);
-    }
-    if (fork) {
+    } else if (fork) {
         CPM_CUDA(c, cudaEventRecord(c->fev[1], s1));
-        CPM_CUDA(c, cudaStreamWaitEvent(s2, c->fev[1], 0));
     }
+    if (fork) CPM_CUDA(c, cudaStreamWaitEvent(s2, c->fev[1], 0));
     double* b0 = nullptr;
     if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0) {
         // the k_perp = 0 column in FP64 (its single-precision weights are zero)
@@ -1314,7 +1312,8 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         const int nz0 = std::min(k.ext0, COL0_NZ);
         const int nblk = (nz0 + C0_NB - 1) / C0_NB;
         float4* e1s = (float4*)(scr + p.off_c0e1);
-        float2* q0 = (float2*)(scr + p.off_c0q);   // e1s and q0 come from k_fracs
+        float2* q0 = (float2*)(scr + p.off_c0q);
+        CPM_TRY(launch_col0_inputs(s2, (const uint64_t*)(scr + p.off_u), Q, ptot, e1s, q0));
         k_col0_rho<<<dim3(p.c0chunks, nblk, m), C0_THREADS, 0, s2>>>(e1s, q0, ne, nz0, c0part);
         CPM_LAUNCH(c, "k_col0_rho");
         k_col0_reduce<<<(m * nz0 * 32 + 255) / 256, 256, 0, s2>>>(c0part, p.c0chunks, nz0, k.w, k.NZ, m, c0w);
@@ -1322,7 +1321,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         k_col0_site<<<(m * c->nzu * 32 + 255) / 256, 256, 0, s2>>>(c->c0e, c->nzu, m, nz0, c0w, b0);
         CPM_LAUNCH(c, "k_col0_site");
         prof_end(c, CPM_K_COL0);
-        c->launches += 3;
+        c->launches += 4;
     }
     // binning and the per-replica totals (one pass over the charges)
     prof_begin(c, CPM_K_CELLS);

@@ -221,8 +221,10 @@ cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, co
 size_t phase_elems(const KTable& k, int64_t P);
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, const double* Q = nullptr,
-                           float4* e1 = nullptr, float2* q2 = nullptr);
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs = nullptr);
+// inputs of the double-float k_perp = 0 column from the z fractions (u as written by the phase kernels)
+cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* Q, int64_t P, float4* e1,
+                              float2* q2);
 
 // api.cu
 cpm_status ensure_scratch(cpm_ctx* c, size_t bytes);

@@ -6,6 +6,8 @@
 // the factor 2 standing for the mirror vector -k.  Membership is decided with
 // correctly rounded multiplies and adds in a fixed order so that the set does
 // not depend on FMA contraction.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cpm {
@@ -234,26 +236,28 @@ __global__ void k_phases(const double* __restrict__ xyz, int64_t P, double ix, d
 
 // The fixed-point fractions of each point once per axis (u[d][p]), then the tables from them:
 // the table kernel then needs no FP64 arithmetic at all.
-// With e1 (single-precision paths), also the first z harmonic exp(2 pi i z / Lz) as a double-float
-// pair (from the same exactly reduced fraction, one FP64 sincospi) and the charge as a double-float
-// pair, for the double-float k_perp = 0 column.
 __global__ void k_fracs(const double* __restrict__ xyz, int64_t P, double ix, double iy, double iz,
-                        uint64_t* __restrict__ u, const double* __restrict__ Q, float4* __restrict__ e1,
-                        float2* __restrict__ q2) {
+                        uint64_t* __restrict__ u) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     u[p] = frac_fixed(xyz[3 * p + 0], ix);
     u[P + p] = frac_fixed(xyz[3 * p + 1], iy);
-    const uint64_t uz = frac_fixed(xyz[3 * p + 2], iz);
-    u[2 * P + p] = uz;
-    if (e1) {
-        const double2 e = phase_of<double>(uz, 1);
-        const float rh = (float)e.x, ih = (float)e.y;
-        e1[p] = make_float4(rh, (float)(e.x - (double)rh), ih, (float)(e.y - (double)ih));
-        const double qd = Q[p];
-        const float qh = (float)qd;
-        q2[p] = make_float2(qh, (float)(qd - (double)qh));
-    }
+    u[2 * P + p] = frac_fixed(xyz[3 * p + 2], iz);
+}
+
+// For the double-float k_perp = 0 column of the single-precision paths: the first z harmonic
+// exp(2 pi i z / Lz) as a double-float pair (from the exactly reduced fraction, one FP64 sincospi)
+// and the charge as a double-float pair.
+__global__ void k_col0_inputs(const uint64_t* __restrict__ uz, const double* __restrict__ Q, int64_t P,
+                              float4* __restrict__ e1, float2* __restrict__ q2) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const double2 e = phase_of<double>(uz[p], 1);
+    const float rh = (float)e.x, ih = (float)e.y;
+    e1[p] = make_float4(rh, (float)(e.x - (double)rh), ih, (float)(e.y - (double)ih));
+    const double qd = Q[p];
+    const float qh = (float)qd;
+    q2[p] = make_float2(qh, (float)(qd - (double)qh));
 }
 
 // grid (points / 256, slots): no index division per entry
@@ -274,20 +278,65 @@ __global__ void k_phases_u(const uint64_t* __restrict__ u, int64_t P, int NX, in
     }
 }
 
+// Single precision, one thread per (point, axis): the harmonics h = 8a + k >= 0 of the axis are
+// products e^{2 pi i 8a f} e^{2 pi i k f} of sixteen exactly reduced phases at most (k = 0..7 and the
+// multiples of 8, each from the fixed-point fraction f), one rounding more than a direct evaluation
+// (below the precision the single-precision sums keep); h < 0 is the conjugate of -h.
+// grid (points / 128, 3 axes)
+__global__ void __launch_bounds__(128) k_phases_rows(const uint64_t* __restrict__ u, int64_t P, int NX, int NY,
+                                                     int NZ, float2* __restrict__ X, float2* __restrict__ Y,
+                                                     float2* __restrict__ Z) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int axis = blockIdx.y;
+    const int H = axis == 0 ? NX : axis == 1 ? NY : NZ;   // largest |h|
+    float2* T = axis == 0 ? X : axis == 1 ? Y : Z;
+    const int64_t h0row = axis == 0 ? 0 : H;              // row of h = 0
+    const uint64_t f = u[(int64_t)axis * P + p];
+    float2 base[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) base[k] = k <= H ? phase_of<float>(f, k) : make_float2(1.f, 0.f);
+    for (int a = 0; 8 * a <= H; ++a) {
+        const float2 g = a == 0 ? make_float2(1.f, 0.f) : phase_of<float>(f, 8 * a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int h = 8 * a + k;
+            if (h > H) break;
+            const float2 b = base[k];
+            const float2 v = a == 0 ? b : make_float2(g.x * b.x - g.y * b.y, g.x * b.y + g.y * b.x);
+            T[(h0row + h) * P + p] = v;
+            if (axis != 0 && h > 0) T[(h0row - h) * P + p] = make_float2(v.x, -v.y);
+        }
+    }
+}
+
+cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* Q, int64_t P, float4* e1,
+                              float2* q2) {
+    if (P == 0) return CPM_OK;
+    k_col0_inputs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(u + 2 * P, Q, P, e1, q2);
+    return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
+}
+
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, const double* Q, float4* e1, float2* q2) {
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs) {
     if (P == 0) return CPM_OK;
-    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u, Q, e1, q2);
-    const int nslot = (k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1);
-    k_phases_u<T><<<dim3((unsigned)((P + 255) / 256), (unsigned)nslot), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X, Y, Z);
+    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u);
+    if (after_fracs && cudaEventRecord(after_fracs, st) != cudaSuccess) return CPM_E_CUDA;
+    if (std::is_same<T, float>::value) {
+        k_phases_rows<<<dim3((unsigned)((P + 127) / 128), 3), 128, 0, st>>>(u, P, k.NX, k.NY, k.NZ, (float2*)X,
+                                                                            (float2*)Y, (float2*)Z);
+    } else {
+        const int nslot = (k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1);
+        k_phases_u<T><<<dim3((unsigned)((P + 255) / 256), (unsigned)nslot), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X,
+                                                                                          Y, Z);
+    }
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
 }
 template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                           uint64_t*, float2*, float2*, float2*, const double*, float4*, float2*);
+                                           uint64_t*, float2*, float2*, float2*, cudaEvent_t);
 template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                            uint64_t*, double2*, double2*, double2*, const double*, float4*,
-                                            float2*);
+                                            uint64_t*, double2*, double2*, double2*, cudaEvent_t);
 
 template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
