@@ -1296,7 +1296,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_begin(c, CPM_K_PHASES);
         // the k_perp = 0 chain needs only the fractions: it starts after k_fracs
         CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ,
-                                   fork ? c->fev[1] : nullptr));
+                                   fork ? c->fev[1] : nullptr, p.tc ? TC_ZSCALE : 1.f));
         prof_end(c, CPM_K_PHASES);
     } else if (fork) {
         CPM_CUDA(c, cudaEventRecord(c->fev[1], s1));

@@ -47,6 +47,8 @@ enum : unsigned { ST_NOT_SPD = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
 // Harmonics of the k_perp = 0 column that the single-precision paths sum in double-float; its
 // higher harmonics (weights below ~1e-3 of the first for the usual splittings) go through the
 // single-precision sums with the rest of the k set.
+// charge phases of the tensor-core structure factor are written scaled by 2^14 (exact)
+constexpr float TC_ZSCALE = 16384.f;
 constexpr int COL0_NZ = 12;
 
 struct KTable {
@@ -221,7 +223,8 @@ cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, co
 size_t phase_elems(const KTable& k, int64_t P);
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs = nullptr);
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs = nullptr,
+                           float zscale = 1.f);
 // inputs of the double-float k_perp = 0 column from the z fractions (u as written by the phase kernels)
 cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* Q, int64_t P, float4* e1,
                               float2* q2);

@@ -281,11 +281,12 @@ __global__ void k_phases_u(const uint64_t* __restrict__ u, int64_t P, int NX, in
 // Single precision, one thread per (point, axis): the harmonics h = 8a + k >= 0 of the axis are
 // products e^{2 pi i 8a f} e^{2 pi i k f} of sixteen exactly reduced phases at most (k = 0..7 and the
 // multiples of 8, each from the fixed-point fraction f), one rounding more than a direct evaluation
-// (below the precision the single-precision sums keep); h < 0 is the conjugate of -h.
+// (below the precision the single-precision sums keep); h < 0 is the conjugate of -h.  The z table
+// is multiplied by zscale (a power of two: exact).
 // grid (points / 128, 3 axes)
 __global__ void __launch_bounds__(128) k_phases_rows(const uint64_t* __restrict__ u, int64_t P, int NX, int NY,
                                                      int NZ, float2* __restrict__ X, float2* __restrict__ Y,
-                                                     float2* __restrict__ Z) {
+                                                     float2* __restrict__ Z, float zscale) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int axis = blockIdx.y;
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(128) k_phases_rows(const uint64_t* __restrict_
     float2* T = axis == 0 ? X : axis == 1 ? Y : Z;
     const int64_t h0row = axis == 0 ? 0 : H;              // row of h = 0
     const uint64_t f = u[(int64_t)axis * P + p];
+    const float sc = axis == 2 ? zscale : 1.f;
     float2 base[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) base[k] = k <= H ? phase_of<float>(f, k) : make_float2(1.f, 0.f);
@@ -303,7 +305,9 @@ __global__ void __launch_bounds__(128) k_phases_rows(const uint64_t* __restrict_
             const int h = 8 * a + k;
             if (h > H) break;
             const float2 b = base[k];
-            const float2 v = a == 0 ? b : make_float2(g.x * b.x - g.y * b.y, g.x * b.y + g.y * b.x);
+            float2 v = a == 0 ? b : make_float2(g.x * b.x - g.y * b.y, g.x * b.y + g.y * b.x);
+            v.x *= sc;
+            v.y *= sc;
             T[(h0row + h) * P + p] = v;
             if (axis != 0 && h > 0) T[(h0row - h) * P + p] = make_float2(v.x, -v.y);
         }
@@ -319,13 +323,13 @@ cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* 
 
 template <typename T>
 cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs) {
+                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs, float zscale) {
     if (P == 0) return CPM_OK;
     k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u);
     if (after_fracs && cudaEventRecord(after_fracs, st) != cudaSuccess) return CPM_E_CUDA;
     if (std::is_same<T, float>::value) {
         k_phases_rows<<<dim3((unsigned)((P + 127) / 128), 3), 128, 0, st>>>(u, P, k.NX, k.NY, k.NZ, (float2*)X,
-                                                                            (float2*)Y, (float2*)Z);
+                                                                            (float2*)Y, (float2*)Z, zscale);
     } else {
         const int nslot = (k.NX + 1) + (2 * k.NY + 1) + (2 * k.NZ + 1);
         k_phases_u<T><<<dim3((unsigned)((P + 255) / 256), (unsigned)nslot), 256, 0, st>>>(u, P, k.NX, k.NY, k.NZ, X,
@@ -334,9 +338,9 @@ cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, 
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
 }
 template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                           uint64_t*, float2*, float2*, float2*, cudaEvent_t);
+                                           uint64_t*, float2*, float2*, float2*, cudaEvent_t, float);
 template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                            uint64_t*, double2*, double2*, double2*, cudaEvent_t);
+                                            uint64_t*, double2*, double2*, double2*, cudaEvent_t, float);
 
 template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,

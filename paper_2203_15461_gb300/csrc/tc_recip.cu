@@ -54,7 +54,7 @@ constexpr int RF_STAGE_XY = (RF_XYROWS + 1) * RF_KC * 8;   // X, Y rows and Q of
 constexpr int RF_PX = ((RF_XYROWS + 1) * RF_KC + RF_GEN - 1) / RF_GEN;   // staging entries per builder
 constexpr int RF_QSLOT = 1 << 16;              // staging slots at or above this are charges
 constexpr int RF_SMEM = 1024 + RF_STAGES * RF_STAGE + 2048 + RF_STAGE_XY;
-constexpr float RF_ZSCALE = 16384.f;           // charge phases scaled by 2^14
+constexpr float RF_ZSCALE = TC_ZSCALE;         // charge phases scaled by 2^14 (in the table)
 
 // stage 2 (site potentials)
 constexpr int RS_BM = 128;                     // sites per tile (MMA M)
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 uint32_t h[4], l[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    split2(make_float2(pz[k][u].x * RF_ZSCALE, pz[k][u].y * RF_ZSCALE), h[u], l[u]);
+                    split2(pz[k][u], h[u], l[u]);   // the table holds 2^14 Z
                 const uint32_t o0 = sw128(2 * zr, ch), o1 = sw128(2 * zr + 1, ch);
                 sts128(sb + o0, neg_hi(h[0]), neg_hi(h[1]), neg_hi(h[2]), neg_hi(h[3]));
                 sts128(sb + o1, swap_h(h[0]), swap_h(h[1]), swap_h(h[2]), swap_h(h[3]));
