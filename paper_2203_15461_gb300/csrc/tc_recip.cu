@@ -58,7 +58,9 @@ constexpr float RF_ZSCALE = TC_ZSCALE;         // charge phases scaled by 2^14 (
 
 // stage 2 (site potentials)
 constexpr int RS_BM = 128;                     // sites per tile (MMA M)
-constexpr int RS_THREADS = 192;                // warps 0-3 epilogue, warp 4 TMA, warp 5 MMA
+constexpr int RS_EPI = 8;                      // epilogue warps (two per TMEM lane quarter)
+constexpr int RS_THREADS = 32 * (RS_EPI + 2);   // warps 0-7 epilogue, warp 8 TMA, warp 9 MMA
+constexpr int RS_TMA_WARP = RS_EPI, RS_MMA_WARP = RS_EPI + 1;
 constexpr int RS_A = RS_BM * 128;              // one fp16 term of the site-phase tile (16 KB)
 constexpr int RS_BMAX = 256 * 128;             // one fp16 term of the W tile, N <= 256 (32 KB)
 constexpr int RS_STAGE = 2 * RS_A + 2 * RS_BMAX;
@@ -465,13 +467,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], RS_EPI); }
         mbar_init(done, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == RS_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(512u)
                      : "memory");
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t stage_bytes = 2 * RS_A + 2 * NB * 128;
 
-    if (warp == 4 && lane == 0) {
+    if (warp == RS_TMA_WARP && lane == 0) {
         // TMA producer: one ring over the K steps of all this CTA's tiles
         int it = 0;
         for (int tau = blockIdx.x; tau < ntiles && !*abort; tau += gridDim.x) {
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 while (!mbar_try(&full[s], (t / RS_STAGES) & 1) && gtimer_ns() - ts < wait_ns) {}
             }
         }
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == RS_MMA_WARP && lane == 0) {
         // MMA issuer
         const uint32_t idesc = idesc_f16(RS_BM, NB);
         int it = 0, k = 0;
@@ -544,9 +546,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         umma_commit(done);   // also after an abort: the MMAs in flight complete before the dealloc
         const uint64_t ts = gtimer_ns();
         while (!mbar_try(done, 0) && gtimer_ns() - ts < wait_ns) {}
-    } else if (warp < 4) {
-        // epilogue: thread = site i of the tile, accumulator lane warp * 32 + lane
-        const uint32_t trow = (uint32_t)(warp * 32) << 16;
+    } else if (warp < RS_EPI) {
+        // epilogue: thread = site i of the tile, accumulator lane (warp % 4) * 32 + lane; warp w takes
+        // the replicas of parity w / 4 of the group
+        const int lq = warp & 3, rpar = warp >> 2;
+        const uint32_t trow = (uint32_t)(lq * 32) << 16;
         const float zinv = ldexpf(1.f, -RS_ZEXP);
         int k = 0;
         for (int tau = blockIdx.x; tau < ntiles; tau += gridDim.x, ++k) {
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             const int cfirst = cb * RS_CT, clast = min(ncols, cfirst + RS_CT);
             int t0, nsteps;
             site_group_steps(colext, ncols, NZ, g, ncb, t0, nsteps);
-            const int64_t i = (int64_t)tx * RS_BM + warp * 32 + lane;
+            const int64_t i = (int64_t)tx * RS_BM + lq * 32 + lane;
             float2 xy[RS_CT];   // the column factors of this thread's site, loaded while the products run
 #pragma unroll
             for (int u = 0; u < RS_CT; ++u) {
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             const bool ok = mbar_wait(&tfull[buf], (k >> 1) & 1, abort, wait_ns);
             tc_fence_after();
             if (__any_sync(0xffffffffu, !ok || *abort)) break;
-            for (int rr = 0; rr < mr; ++rr) {
+            for (int rr = rpar; rr < mr; rr += RS_EPI / 4) {
                 float v[2 * RS_CT];
                 if (nsteps > 0) {
                     tmem_ld32(tmem + trow + (uint32_t)(256 * buf + 2 * RS_CT * rr), v);
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (*abort && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    if (warp == 5) {
+    if (warp == RS_MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
