@@ -50,7 +50,6 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
                                                   int64_t ne, Geometry g, CellGrid cg, float3 inv_h, int* key,
                                                   int* count, typename V4<T>::t* wpos, T* Qv, double* part,
                                                   int* tickets, double* stats, float2* qabs) {
-    __shared__ double sh[6][ST_THREADS / 32];
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t j = (int64_t)b * ST_THREADS + threadIdx.x;
@@ -80,21 +79,21 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
         wpos[p] = v;
         Qv[p] = (T)q;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int t = 0; t < 6; ++t) {
-            const double v = __shfl_down_sync(0xffffffffu, a[t], o);
-            a[t] = t == 4 ? fmax(a[t], v) : a[t] + v;
-        }
-    }
-    if (lane == 0)
-        for (int t = 0; t < 6; ++t) sh[t][warp] = a[t];
+    // block sums in a fixed order: the thread values through shared memory, warp t of the first six
+    // takes quantity t (each lane adds eight threads' values, then a shuffle tree)
+    __shared__ double sv[6][ST_THREADS];
+    for (int t = 0; t < 6; ++t) sv[t][threadIdx.x] = a[t];
     __syncthreads();
     double* pr = part + ((int64_t)r * nb + b) * 6;
-    if (threadIdx.x < 6) {
-        const int t = threadIdx.x;
-        double v = sh[t][0];
-        for (int w = 1; w < ST_THREADS / 32; ++w) v = t == 4 ? fmax(v, sh[t][w]) : v + sh[t][w];
-        pr[t] = v;
+    if (warp < 6) {
+        const int t = warp;
+        double v = sv[t][lane];
+        for (int k = 1; k < ST_THREADS / 32; ++k) v = t == 4 ? fmax(v, sv[t][lane + 32 * k]) : v + sv[t][lane + 32 * k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = t == 4 ? fmax(v, w) : v + w;
+        }
+        if (lane == 0) pr[t] = v;
     }
     if (!last_block_of(&tickets[r], nb)) return;
     // the block sums, ST_THREADS blocks at a time, loaded by all threads at once and added by
@@ -328,7 +327,7 @@ __device__ __forceinline__ float4 lds128(const float4* p) {
     return v;
 }
 
-template <bool SMEM_TAB>
+template <bool SMEM_TAB, bool ONE_TAB>
 __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm, const int4* __restrict__ chunks,
                  int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
@@ -336,6 +335,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
                  const int* __restrict__ tabid, int m, double* __restrict__ out) {
     __shared__ float4 stab[RC_SMEM_TABS * RT_S];
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
+    __shared__ float ssite_x[32], ssite_y[32], ssite_z[32];   // the same coordinates, one array each
     __shared__ float sbox[6];
     // per warp while streaming: the charge ranges of a group of rows and the ring of charges that
     // passed the box test; at the end the same bytes hold the per-site partial sums
@@ -387,6 +387,9 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
         if (lane >= nsites) px = py = pz = 1.0e6f;   // dummy sites, beyond any cutoff
         ssite[lane] = make_float4(px, py, pz, __int_as_float(toff));
+        ssite_x[lane] = px;
+        ssite_y[lane] = py;
+        ssite_z[lane] = pz;
         float lo[3] = {px, py, pz}, hi[3] = {px, py, pz};   // (dummies excluded below)
         if (lane >= nsites) {
             lo[0] = lo[1] = lo[2] = 3.0e38f;
@@ -434,7 +437,9 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
             if (sg >= nsites) break;   // uniform; sites past nsites are far-away dummies
 #pragma unroll
             for (int s = sg; s < sg + 8; ++s) {
-                const float4 st = lds128(&ssite[s]);   // re-read: keeps 32 sites out of registers
+                // re-read: keeps 32 sites out of registers; with one table the offset is zero and
+                // three 4-byte broadcasts cost fewer wavefronts than one 16-byte broadcast
+                const float4 st = ONE_TAB ? make_float4(ssite_x[s], ssite_y[s], ssite_z[s], 0.f) : lds128(&ssite[s]);
                 acc[s] = fmaf(qw, pair_term(st, q), acc[s]);
             }
         }
@@ -1400,14 +1405,21 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
     if (std::is_same<T, float>::value && c->rtab && c->schunks) {
-        if (c->nrtab <= RC_SMEM_TABS)
-            k_real_cells<true><<<real_grid(c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
-            c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
-            (const float4*)c->rtab, c->nrtab, c->rtab_id, m, real);
+        const int4* ch4 = (const int4*)c->schunks;
+        const float4* tab4 = (const float4*)c->rtab;
+        const unsigned rg = real_grid(c->nschunk, m);
+        if (c->nrtab == 1)
+            k_real_cells<true, true><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g, p.cg,
+                                                                  start, (const float4*)sorted, tab4, c->nrtab,
+                                                                  c->rtab_id, m, real);
+        else if (c->nrtab <= RC_SMEM_TABS)
+            k_real_cells<true, false><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g, p.cg,
+                                                                   start, (const float4*)sorted, tab4, c->nrtab,
+                                                                   c->rtab_id, m, real);
         else
-            k_real_cells<false><<<real_grid(c->nschunk, m), 32 * RC_WARPS, 0, st>>>(
-            c->s32, c->sperm, (const int4*)c->schunks, c->nschunk, n, c->g, p.cg, start, (const float4*)sorted,
-            (const float4*)c->rtab, c->nrtab, c->rtab_id, m, real);
+            k_real_cells<false, false><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g,
+                                                                    p.cg, start, (const float4*)sorted, tab4,
+                                                                    c->nrtab, c->rtab_id, m, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,

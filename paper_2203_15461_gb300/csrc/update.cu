@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
         qi = sv - v.value();
         qr[i] = qi;
+        __threadfence();   // this slice of q is visible device-wide before the block takes its ticket
     }
     auto block_sum = [&](double a) {   // fixed order: warp trees, then warps in order
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
@@ -344,15 +345,27 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         __syncthreads();
         s = s_sum;
     }
-    volatile double* qv = qr;
+    // the replica's q, written by the other blocks: loaded past L1 (__ldcg), eight per thread in
+    // flight, fixed and summed in index order per thread
     double a = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += NB_T) {
-        double v = qv[k];
-        if (symm) {
-            v -= u[k] * s;
-            qv[k] = v;
+    for (int64_t k0 = 0; k0 < n; k0 += 8 * NB_T) {
+        double v[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int64_t k = k0 + (int64_t)w * NB_T + threadIdx.x;
+            v[w] = k < n ? __ldcg(qr + k) : 0.0;
         }
-        a += v;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int64_t k = k0 + (int64_t)w * NB_T + threadIdx.x;
+            if (k < n) {
+                if (symm) {
+                    v[w] -= u[k] * s;
+                    qr[k] = v[w];
+                }
+                a += v[w];
+            }
+        }
     }
     const double tot = block_sum(a);
     if (threadIdx.x == 0 && qtot) qtot[r] = tot;
