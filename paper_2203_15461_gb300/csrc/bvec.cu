@@ -1139,19 +1139,29 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
     const int64_t i = t % n;
+    const double rl = real[t];   // issued with the tile loads below
+    const double bz = b0 ? b0[(int64_t)r * nzu + zmap[i]] : 0.0;
     double s = 0.0;
     const T* pp = partial + (int64_t)r * nctiles * n + i;
     int k = 0;
-    for (; k + 8 <= nctiles; k += 8) {   // eight loads in flight, added in tile order
+    for (; k + 16 <= nctiles; k += 16) {   // sixteen loads in flight, added in tile order
+        T x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = pp[(int64_t)(k + u) * n];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s += (double)x[u];
+    }
+    if (k + 8 <= nctiles) {
         T x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = pp[(int64_t)(k + u) * n];
 #pragma unroll
         for (int u = 0; u < 8; ++u) s += (double)x[u];
+        k += 8;
     }
     for (; k < nctiles; ++k) s += (double)pp[(int64_t)k * n];
-    s += real[t];
-    if (b0) s += b0[(int64_t)r * nzu + zmap[i]];
+    s += rl;
+    if (b0) s += bz;
     const double* st = stats + 4 * r;
     s += -PI * st[0] / (g.V * g.alpha * g.alpha);
     if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];

@@ -399,8 +399,18 @@ __global__ void __launch_bounds__(1024)
                 float sx = 0.f, sy = 0.f;
                 const float2* pp = part + ((int64_t)rp * nzw + zi) * cpad + c;
                 const int64_t sstride = (int64_t)m * nzw * cpad;
-#pragma unroll 4
-                for (int s = 0; s < splits; ++s) {
+                int s = 0;
+                for (; s + 8 <= splits; s += 8) {   // eight loads in flight, added in split order
+                    float2 v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = pp[(s + k) * sstride];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        sx += v[k].x;
+                        sy += v[k].y;
+                    }
+                }
+                for (; s < splits; ++s) {
                     const float2 v = pp[s * sstride];
                     sx += v.x;
                     sy += v.y;

@@ -302,12 +302,12 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         const P* pi = part + (int64_t)r * n + i;
         const int64_t stride = (int64_t)m * n;
         int sp = 0;
-        for (; sp + 8 <= splits; sp += 8) {   // eight loads in flight, added in split order
-            P x[8];
+        for (; sp + 16 <= splits; sp += 16) {   // sixteen loads in flight, added in split order
+            P x[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) x[k] = pi[(int64_t)(sp + k) * stride];
+            for (int k = 0; k < 16; ++k) x[k] = pi[(int64_t)(sp + k) * stride];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v.add(x[k]);
+            for (int k = 0; k < 16; ++k) v.add(x[k]);
         }
         for (; sp < splits; ++sp) v.add(pi[(int64_t)sp * stride]);
         double sv = 0.0;
