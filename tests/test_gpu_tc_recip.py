@@ -95,3 +95,23 @@ def test_tc_step_graph_equals_separate_calls():
     q_ref, _ = run_update(ctx, psi, b_ref)
     assert np.array_equal(b.cpu().numpy(), b_ref)
     assert np.array_equal(q.cpu().numpy(), q_ref)
+
+
+@pytest.mark.parametrize("k_prec", ["fp32", "f16x2"])
+def test_three_stream_b_equals_one_stream_order(k_prec):
+    """The electrolyte vector runs as three chains on side streams; with the library's per-kernel
+    profiling on, the same kernels run on the context stream alone.  Both orders give bit-identical
+    b and q (the chains touch disjoint scratch and every reduction has a fixed order)."""
+    need_gpu()
+    el, _, psi = s.workload_tiny_slab(seed=3)
+    elyts = [s.ions_in_gap(el, 90, seed=1300 + r) for r in range(5)]
+    ctx = make_ctx(el, s_prec="fp32", k_prec=k_prec).setup(el)
+    b_fork = run_bvec(ctx, elyts)
+    q_fork, qt_fork = run_update(ctx, psi, b_fork)
+    ctx.cpm_profile(True)
+    b_one = run_bvec(ctx, elyts)
+    q_one, qt_one = run_update(ctx, psi, b_one)
+    ctx.cpm_profile(False)
+    assert np.array_equal(b_fork, b_one)
+    assert np.array_equal(q_fork, q_one)
+    assert np.array_equal(qt_fork, qt_one)
