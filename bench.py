@@ -11,7 +11,9 @@ mixed path (FP32 b and S, FP64 neutrality and totals; by default the two recipro
 contractions of b run on the tensor cores as two-term fp16 products, ``--k-prec fp32``
 keeps them on the CUDA cores); the plain FP64 path is timed beside it.  Inputs are
 resident in HBM; L2 is flushed (a 256 MB write, then a 256 MB read of a second buffer)
-before every timed step and only the step itself is inside the CUDA events.
+before every timed step and only the step itself is inside the CUDA events.  Extra fields:
+256 replicas of the 216-site capacitor per step, a Poisson serving stream, and the
+single-precision S product alone at 16,384 sites (S32 = 1.07 GB) against the HBM peak.
 """
 from __future__ import annotations
 
@@ -301,6 +303,51 @@ def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256, k_prec="fp32"):
     return out
 
 
+def bench_s_stream(torch, CPM, s, flush, peaks, K=10, W=3, m=8):
+    """The single-precision S product alone at the size where S is far larger than L2: two graphene
+    electrodes of two sheets, 16,384 sites (S32 = 1.07 GB), assembled with a small Ewald alpha (0.1,
+    r_c = 35 A: few k-vectors, the assembly stays short; the S product does not depend on the split).
+    b is random; per update the library's profiler times the S stream (k_gemv_tma) on the context
+    stream, with L2 flushed before every update."""
+    import time as _t
+    el = s.graphene_plates(32, 32, 2, 40.0, alpha=0.1, rcut=35.0)
+    n = el.n
+    t0 = _t.perf_counter()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
+    st.synchronize()
+    setup_s = _t.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    with torch.cuda.stream(st):
+        b = torch.as_tensor(rng.normal(0.0, 1.0, (m, n)), device="cuda")
+        psi = torch.as_tensor(np.tile([0.0, 1.0], (m, 1)), device="cuda")
+        q = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        qt = torch.empty(m, dtype=torch.float64, device="cuda")
+    for _ in range(W):
+        with torch.cuda.stream(st):
+            ctx.cpm_update(m, psi, b, q, qt)
+    st.synchronize()
+    ctx.cpm_profile_read(reset=True)
+    ctx.cpm_profile(True)
+    for _ in range(K):
+        with torch.cuda.stream(st):
+            flush()
+            ctx.cpm_update(m, psi, b, q, qt)
+    st.synchronize()
+    ctx.cpm_profile(False)
+    prof = ctx.cpm_profile_read(reset=True)
+    ms = prof["gemv"][0] / max(1, prof["gemv"][1])
+    nbytes = 4.0 * n * n
+    gbs = nbytes / (ms / 1e3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    ctx.close()
+    return {"workload": f"graphene 32x32, 2 sheets per electrode: {n} sites, {m} replicas per pass",
+            "kernel": "k_gemv_tma", "s_bytes": nbytes, "ms_per_launch": ms, "achieved_gbs": gbs,
+            "hbm_peak_gbs": hbm, "frac": gbs / hbm, "max_abs_qtot": float(qt.abs().max()),
+            "setup_seconds": setup_s, "l2": "flushed before every update"}
+
+
 def bench_serving(torch, s, n_req=600, rate=4000.0, k_prec="fp32"):
     """Poisson stream of charge-update requests over three slab geometries (216, 512 and 2,048 sites)."""
     from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
@@ -478,6 +525,7 @@ def main():
     batched = bench_batched_tiny(torch, CPM, s, flush, K, W, k_prec=args.k_prec)
     # serving stream: Poisson arrivals over three geometries, continuous batching
     serving = bench_serving(torch, s, k_prec=args.k_prec)
+    s_stream = bench_s_stream(torch, CPM, s, flush, _peaks()[0])
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
@@ -535,7 +583,7 @@ def main():
             "rel_err_mixed_vs_fp64": err_mixed, "max_abs_qtot": qtot_max, "setup_seconds": t_setup,
             "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items()},
             "ms_per_step_kernel_by_kernel": ms_prof / K,
-            "batched_tiny_256": batched, "serving": serving}
+            "batched_tiny_256": batched, "serving": serving, "s_stream_16384": s_stream}
     clocks = clk.summary()
     line["clocks"] = clocks
     if rank == 0 and not args.no_cpu_baseline:
