@@ -516,7 +516,13 @@ def main():
         t0 = time.perf_counter()
         e2e_step()
         e2e_times.append(time.perf_counter() - t0)
-    e2e = {"value": world * m * K / sum(e2e_times), "unit": "updates/s",
+    e2e_value, _ = aggregate(1e3 * sum(e2e_times), m, K, world, dist if world > 1 else None)   # max over ranks
+    if rank != 0:
+        # only rank 0 reports: the other ranks leave after the timed headline and end-to-end legs
+        dist.barrier()
+        dist.destroy_process_group()
+        return 0
+    e2e = {"value": e2e_value, "unit": "updates/s",
            "h2d_bytes_per_step": int(8 * (m * ne * 4 + m * el.n_groups)),
            "d2h_bytes_per_step": int(8 * (m * el.n + m)),
            "path": "pinned host buffers -> cpm_step_graph -> pinned host buffers, wall clock per step"}
