@@ -1,9 +1,12 @@
 """Run the graph-captured charge update of the EDL capacitor (4,320 sites, 8 replicas of 5,700
 charges) for a fixed number of steps and exit: a plain driver for an external profiler, which
 times nothing itself.  One step is one replay of cpm_step_graph (electrolyte vector b, S product,
-neutrality), the same step bench.py times.
+neutrality), the same step bench.py times.  With --s-product-only the driver instead runs the
+single-precision S product (cpm_update on a random b) of the 16,384-site two-sheet graphene
+capacitor that bench.py measures against the HBM peak.
 
     python -m paper_2203_15461_gb300.run_steps --steps 4 [--k-prec f16x2|fp32] [--replicas 8]
+    python -m paper_2203_15461_gb300.run_steps --steps 4 --s-product-only
 """
 import argparse
 
@@ -15,12 +18,29 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--replicas", type=int, default=8)
     ap.add_argument("--k-prec", default="f16x2", choices=["fp32", "f16x2"])
+    ap.add_argument("--s-product-only", action="store_true")
     args = ap.parse_args()
 
     import torch
 
     from . import systems as s
     from .cpm import CPM
+
+    if args.s_product_only:
+        el = s.graphene_plates(32, 32, 2, 40.0, alpha=0.1, rcut=35.0)
+        m = args.replicas
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
+            b = torch.as_tensor(np.random.default_rng(7).normal(0.0, 1.0, (m, el.n)), device="cuda")
+            psi = torch.as_tensor(np.tile([0.0, 1.0], (m, 1)), device="cuda")
+            q = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+            qt = torch.empty((m,), dtype=torch.float64, device="cuda")
+            for _ in range(args.steps):
+                ctx.cpm_update(m, psi, b, q, qt)
+        st.synchronize()
+        print(f"{args.steps} S products, n = {el.n}, max |sum q| = {float(qt.abs().max()):.3e}")
+        return
 
     el, _, psi = s.workload_edl_capacitor(seed=1)
     m = args.replicas
