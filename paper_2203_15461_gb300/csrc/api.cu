@@ -140,13 +140,13 @@ static void free_geometry(cpm_ctx* c) {
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
-                    c->sperm, c->schunks, c->tcz, c->tcxy, c->c0e};
+                    c->sperm, c->schunks, c->rqueue, c->tcz, c->tcxy, c->c0e};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
     c->Sb = nullptr; c->SZ = nullptr;
     c->rtab = nullptr; c->rtab_id = nullptr; c->nrtab = 0;
-    c->sperm = nullptr; c->schunks = nullptr; c->nschunk = 0;
+    c->sperm = nullptr; c->schunks = nullptr; c->rqueue = nullptr; c->nschunk = 0;
     c->tcz = nullptr; c->tcxy = nullptr; c->c0e = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
@@ -291,9 +291,15 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
                     chunks.push_back(make_int4((int)f, (int)std::min<int64_t>(32, e - f), cell[perm[k]], 0));
                 k = e;
             }
+            // most sites first (padded to the kernel's groups of eight): the real-space kernel takes
+            // chunks from a queue in this order, so the long items start early and the short ones fill in
+            std::stable_sort(chunks.begin(), chunks.end(),
+                             [](const int4& a, const int4& b) { return (a.y + 7) / 8 > (b.y + 7) / 8; });
             c->nschunk = (int)chunks.size();
             CPM_TRY(dev_alloc(c, (void**)&c->sperm, sizeof(int) * n));
             CPM_TRY(dev_alloc(c, &c->schunks, sizeof(int4) * chunks.size()));
+            CPM_TRY(dev_alloc(c, (void**)&c->rqueue, 2 * sizeof(int)));
+            CPM_CUDA(c, cudaMemsetAsync(c->rqueue, 0, 2 * sizeof(int), st));
             CPM_CUDA(c, cudaMemcpyAsync(c->sperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
             CPM_CUDA(c, cudaMemcpyAsync(c->schunks, chunks.data(), sizeof(int4) * chunks.size(),
                                         cudaMemcpyHostToDevice, st));

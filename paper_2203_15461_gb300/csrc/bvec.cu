@@ -42,18 +42,19 @@ constexpr int ST_THREADS = 256;
 
 // ----------------------------------------------------------------------------- cell list
 // Binning and the per-replica totals in one pass: grid (charge blocks, m), one thread per charge.
-// Each charge gets its wrapped position, its cell (cells of the real-space grid) and a single-precision
-// copy; each block sums (Q, Q x, Q y, Q z, max |Q|, sum |Q|) over its charges into part[r][b][6], and
-// the replica's last block adds the block sums in order (stats[r], qabs[r]).
+// Each charge gets its wrapped position and its cell (cells of the real-space grid); each block sums
+// (Q, Q x, Q y, Q z) over its charges into part[r][b][4], and the replica's last block adds the
+// block sums in order (stats[r]).
+constexpr int ST_Q = 4;   // totals per replica
 template <typename T>
 __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ xyz, const double* __restrict__ Q,
                                                   int64_t ne, Geometry g, CellGrid cg, float3 inv_h, int* key,
-                                                  int* count, typename V4<T>::t* wpos, T* Qv, double* part,
-                                                  int* tickets, double* stats, float2* qabs) {
+                                                  int* count, typename V4<T>::t* wpos, double* part,
+                                                  int* tickets, double* stats) {
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t j = (int64_t)b * ST_THREADS + threadIdx.x;
-    double a[6] = {0, 0, 0, 0, 0, 0};
+    double a[ST_Q] = {0, 0, 0, 0};
     if (j < ne) {
         const int64_t p = (int64_t)r * ne + j;
         const double q = Q[p];
@@ -69,93 +70,92 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
             ci[d] = min(cg.nc[d] - 1, (int)((float)w[d] * ih[d]));
         }
         a[0] = q;
-        a[4] = fabs(q);
-        a[5] = fabs(q);
         const int k = r * cg.ncells + (ci[2] * cg.nc[1] + ci[1]) * cg.nc[0] + ci[0];
         key[p] = k;
         atomicAdd(&count[k], 1);
         typename V4<T>::t v;
         v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)q;
         wpos[p] = v;
-        Qv[p] = (T)q;
     }
-    // block sums in a fixed order: the thread values through shared memory, warp t of the first six
+    // block sums in a fixed order: the thread values through shared memory, warp t of the first four
     // takes quantity t (each lane adds eight threads' values, then a shuffle tree)
-    __shared__ double sv[6][ST_THREADS];
-    for (int t = 0; t < 6; ++t) sv[t][threadIdx.x] = a[t];
+    __shared__ double sv[ST_Q][ST_THREADS];
+    for (int t = 0; t < ST_Q; ++t) sv[t][threadIdx.x] = a[t];
     __syncthreads();
-    double* pr = part + ((int64_t)r * nb + b) * 6;
-    if (warp < 6) {
+    double* pr = part + ((int64_t)r * nb + b) * ST_Q;
+    if (warp < ST_Q) {
         const int t = warp;
         double v = sv[t][lane];
-        for (int k = 1; k < ST_THREADS / 32; ++k) v = t == 4 ? fmax(v, sv[t][lane + 32 * k]) : v + sv[t][lane + 32 * k];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_down_sync(0xffffffffu, v, o);
-            v = t == 4 ? fmax(v, w) : v + w;
-        }
+        for (int k = 1; k < ST_THREADS / 32; ++k) v += sv[t][lane + 32 * k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) pr[t] = v;
     }
     if (!last_block_of(&tickets[r], nb)) return;
     // the block sums, ST_THREADS blocks at a time, loaded by all threads at once and added by
-    // threads 0..5 in block order
-    __shared__ double buf[6][ST_THREADS];
-    const volatile double* pv = part + (int64_t)r * nb * 6;
+    // threads 0..3 in block order
+    __shared__ double buf[ST_Q][ST_THREADS];
+    const volatile double* pv = part + (int64_t)r * nb * ST_Q;
     double v = 0.0;
     for (int k0 = 0; k0 < nb; k0 += ST_THREADS) {
         const int k = k0 + threadIdx.x;
         if (k < nb)
-            for (int t = 0; t < 6; ++t) buf[t][threadIdx.x] = pv[k * 6 + t];
+            for (int t = 0; t < ST_Q; ++t) buf[t][threadIdx.x] = pv[k * ST_Q + t];
         __syncthreads();
-        if (threadIdx.x < 6) {
+        if (threadIdx.x < ST_Q) {
             const int t = threadIdx.x, cnt = min(ST_THREADS, nb - k0);
             for (int kk = 0; kk < cnt; ++kk) {
                 const double x = buf[t][kk];
-                v = (k0 == 0 && kk == 0) ? x : (t == 4 ? fmax(v, x) : v + x);
+                v = (k0 == 0 && kk == 0) ? x : v + x;
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x < 6) {
-        const int t = threadIdx.x;
-        if (t < 4) stats[4 * r + t] = v;
-        else if (qabs) {
-            if (t == 4) qabs[r].x = (float)v;
-            else qabs[r].y = (float)v;
-        }
-    }
+    if (threadIdx.x < ST_Q) stats[4 * r + threadIdx.x] = v;
 }
 
-// Per-replica exclusive scan of cell counts into global start offsets (replica r starts at r * ne).
-__global__ void k_cellscan(const int* count, int* start, int ncells, int64_t ne, int m) {
-    __shared__ int warp_tot[32];
+// Per-replica exclusive scan of cell counts into global start offsets (replica r starts at r * ne):
+// one block per replica; each thread takes CS_PER consecutive cells of a tile of CS_THREADS x CS_PER.
+// The block is small enough to run beside a structure-factor CTA on its SM.
+constexpr int CS_THREADS = 256, CS_PER = 8;
+__global__ void __launch_bounds__(CS_THREADS) k_cellscan(const int* count, int* start, int ncells, int64_t ne, int m) {
+    __shared__ int warp_tot[CS_THREADS / 32];
     __shared__ int carry;
     const int r = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = (int)(r * ne);
     __syncthreads();
-    for (int base = 0; base < ncells; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = i < ncells ? count[r * ncells + i] : 0;
-        int x = v;
+    for (int base = 0; base < ncells; base += CS_THREADS * CS_PER) {
+        const int i0 = base + (int)threadIdx.x * CS_PER;
+        int v[CS_PER];
+#pragma unroll
+        for (int k = 0; k < CS_PER; ++k) v[k] = i0 + k < ncells ? count[r * ncells + i0 + k] : 0;
+        int tsum = 0;
+#pragma unroll
+        for (int k = 0; k < CS_PER; ++k) tsum += v[k];
+        int x = tsum;   // inclusive scan of the thread totals within the warp
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_tot[wid] = x;
         __syncthreads();
         if (wid == 0) {
-            int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            int t = lane < CS_THREADS / 32 ? warp_tot[lane] : 0;
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, t, o);
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
                 if (lane >= o) t += y;
             }
-            warp_tot[lane] = t;
+            if (lane < CS_THREADS / 32) warp_tot[lane] = t;
         }
         __syncthreads();
-        int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - v;
-        if (i < ncells) start[r * ncells + i] = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        int run = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - tsum;
+#pragma unroll
+        for (int k = 0; k < CS_PER; ++k) {
+            if (i0 + k < ncells) start[r * ncells + i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();   // carry has been read by every thread
+        if (threadIdx.x == CS_THREADS - 1) carry = run;
         __syncthreads();
     }
     if (r == m - 1 && threadIdx.x == 0) start[m * ncells] = (int)(m * ne);
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     k_real_cells(const float* __restrict__ s32, const int* __restrict__ perm, const int4* __restrict__ chunks,
                  int nchunks, int64_t n, Geometry g, CellGrid cg, const int* __restrict__ start,
                  const float4* __restrict__ sorted, const float4* __restrict__ tab, int ntab,
-                 const int* __restrict__ tabid, int m, double* __restrict__ out) {
+                 const int* __restrict__ tabid, int m, int* __restrict__ rqueue, double* __restrict__ out) {
     __shared__ float4 stab[RC_SMEM_TABS * RT_S];
     __shared__ float4 ssite[32];                    // (x, y, z, table offset as int bits)
     __shared__ float ssite_x[32], ssite_y[32], ssite_z[32];   // the same coordinates, one array each
@@ -355,6 +355,12 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
     auto& lsh = u_.l.sh;
     auto& red = u_.red;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // persistent, items from a queue: item k is chunk k / m (chunks are stored with the most sites
+    // first) of replica k % m; thread 0 takes the next item while the block works on the current one
+    __shared__ int s_item;
+    const int nitems = nchunks * m;
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(&rqueue[0], 1);
     if (SMEM_TAB) {   // staged once per block, eight loads per thread in flight
         const int tot = ntab * RT_S;
         for (int e0 = 0; e0 < tot; e0 += 8 * (int)blockDim.x) {
@@ -371,10 +377,14 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
             }
         }
     }
-    // persistent: the block takes the (chunk, replica) items blockIdx.x, blockIdx.x + gridDim.x, ...
-    for (int item = blockIdx.x; item < nchunks * m; item += gridDim.x) {
-    const int ch = item % nchunks, r = item / nchunks;
-    __syncthreads();   // the previous item's partial sums have been read
+    for (;;) {
+    __syncthreads();   // the previous item's partial sums and s_item have been read
+    if (threadIdx.x == 0) s_item = nxt;
+    __syncthreads();
+    const int item = s_item;
+    if (item >= nitems) break;
+    if (threadIdx.x == 0) nxt = atomicAdd(&rqueue[0], 1);   // used at the next item
+    const int ch = item / m, r = item % m;
     const int4 cinfo = chunks[ch];   // (first, count, cell, 0)
     const int nsites = cinfo.y;
     if (warp == 0) {
@@ -579,6 +589,15 @@ __global__ void __launch_bounds__(32 * RC_WARPS, 4)
         }
         out[(int64_t)r * n + perm[cinfo.x + lane]] = a;
     }
+    }
+    // every take of this block is done; the last block to finish puts the queue back to zero for
+    // the next launch (launches on one context are stream-ordered)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&rqueue[1], 1) == (int)gridDim.x - 1) {
+            atomicExch(&rqueue[0], 0);
+            atomicExch(&rqueue[1], 0);
+        }
     }
 }
 
@@ -1186,7 +1205,7 @@ struct BvecPlan {
         off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
     int c0chunks;
     bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
-    size_t off_qabs, off_tcpart, off_w16, off_spart, off_c0q;
+    size_t off_qabs, off_tcpart, off_w16, off_spart, off_qpart, off_c0q;
 };
 
 template <typename T>
@@ -1248,7 +1267,8 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
     p.off_c0q = o; o += al(sizeof(float2) * ptot);
     p.off_qabs = o; o += al(sizeof(float2) * m);
-    p.off_spart = o; o += al(sizeof(double) * 6 * (size_t)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS) * m);
+    p.off_spart = o; o += al(sizeof(double) * ST_Q * (size_t)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS) * m);
+    p.off_qpart = o; o += al(sizeof(double) * 2 * (size_t)std::max<int64_t>(1, (ne + FR_THREADS - 1) / FR_THREADS) * m);
     p.off_tcpart = p.off_w16 = o;
     if (p.tc) {
         p.off_tcpart = o; o += al(tc_recip_part_bytes(td, m, k.nzw));
@@ -1292,11 +1312,11 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     const int nc = m * p.cg.ncells;
     c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
 
-    // Three chains: the origin stream bins the charges (per-replica totals, single-precision charges)
-    // and runs the cell list and the real-space sum; side stream 1 builds the phase tables and, once
-    // the binning is done (it needs the charge scales), the reciprocal sums; side stream 2 sums the
-    // k_perp = 0 column once the phase kernel has written its inputs.  k_combine joins them.  With
-    // per-kernel profiling on, everything runs on the origin stream in the same order.
+    // Three chains: the origin stream bins the charges (per-replica totals) and runs the cell list and
+    // the real-space sum; side stream 1 takes the fractions, the charges in the working precision and
+    // their scales in one pass, then the phase tables and the reciprocal sums; side stream 2 sums the
+    // k_perp = 0 column once the fractions are written.  k_combine joins them.  With per-kernel
+    // profiling on, everything runs on the origin stream in the same order.
     const bool recip = k.nk > 0 && ptot > 0;
     const bool fork = !c->prof_on;
     cudaStream_t s0 = st, s1 = st, s2 = st;
@@ -1310,7 +1330,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     if (recip) {
         prof_begin(c, CPM_K_PHASES);
         // the k_perp = 0 chain needs only the fractions: it starts after k_fracs
-        CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, ptot, (uint64_t*)(scr + p.off_u), EX, EY, EZ,
+        CPM_TRY(launch_phases_u<T>(s1, c->g, k, xyz, Q, ne, m, (uint64_t*)(scr + p.off_u), Qv,
+                                   (double*)(scr + p.off_qpart), c->tickets + m,
+                                   p.tc ? (float2*)(scr + p.off_qabs) : nullptr, EX, EY, EZ,
                                    fork ? c->fev[1] : nullptr, p.tc ? TC_ZSCALE : 1.f));
         prof_end(c, CPM_K_PHASES);
     } else if (fork) {
@@ -1345,16 +1367,11 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     {
         const float3 inv_h = make_float3((float)(1.0 / p.cg.h[0]), (float)(1.0 / p.cg.h[1]), (float)(1.0 / p.cg.h[2]));
         const unsigned nbx = (unsigned)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS);
-        k_bin<T><<<dim3(nbx, m), ST_THREADS, 0, st>>>(xyz, Q, ne, c->g, p.cg, inv_h, key, cnt, wpos, Qv,
-                                                     (double*)(scr + p.off_spart), c->tickets, stats,
-                                                     p.tc ? qabs : nullptr);
+        k_bin<T><<<dim3(nbx, m), ST_THREADS, 0, st>>>(xyz, Q, ne, c->g, p.cg, inv_h, key, cnt, wpos,
+                                                     (double*)(scr + p.off_spart), c->tickets, stats);
         CPM_LAUNCH(c, "k_bin");
     }
     prof_end(c, CPM_K_CELLS);
-    if (fork) {
-        CPM_CUDA(c, cudaEventRecord(c->fev[2], s0));
-        CPM_CUDA(c, cudaStreamWaitEvent(s1, c->fev[2], 0));
-    }
     if (recip) {
         if (p.tc) {
             c->stream = s1;   // tc_recip_run launches on the context stream
@@ -1404,7 +1421,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, s1));
     }
     prof_begin(c, CPM_K_CELLS);
-    k_cellscan<<<m, 1024, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
+    k_cellscan<<<m, CS_THREADS, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
     CPM_LAUNCH(c, "k_cellscan");
     if (ptot > 0) {
         k_scatter<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, ptot, order);
@@ -1421,15 +1438,15 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         if (c->nrtab == 1)
             k_real_cells<true, true><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g, p.cg,
                                                                   start, (const float4*)sorted, tab4, c->nrtab,
-                                                                  c->rtab_id, m, real);
+                                                                  c->rtab_id, m, c->rqueue, real);
         else if (c->nrtab <= RC_SMEM_TABS)
             k_real_cells<true, false><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g, p.cg,
                                                                    start, (const float4*)sorted, tab4, c->nrtab,
-                                                                   c->rtab_id, m, real);
+                                                                   c->rtab_id, m, c->rqueue, real);
         else
             k_real_cells<false, false><<<rg, 32 * RC_WARPS, 0, st>>>(c->s32, c->sperm, ch4, c->nschunk, n, c->g,
                                                                     p.cg, start, (const float4*)sorted, tab4,
-                                                                    c->nrtab, c->rtab_id, m, real);
+                                                                    c->nrtab, c->rtab_id, m, c->rqueue, real);
     } else {
         k_real_b<T><<<(unsigned)(((int64_t)m * n * 32 + 255) / 256), 256, 0, st>>>(c->sx, n, m, c->g, p.cg, start,
                                                                                     sorted, (const float4*)c->rtab,
@@ -1474,7 +1491,7 @@ cpm_status ensure_aux(cpm_ctx* c) {
 cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne) {
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     CPM_TRY(ensure_aux(c));
-    CPM_TRY(ensure_tickets(c, m));
+    CPM_TRY(ensure_tickets(c, 2 * m));   // k_bin takes [0, m), k_fracs [m, 2m)
     return ensure_scratch(c, f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne));
 }
 
@@ -1482,7 +1499,7 @@ cpm_status bvec(cpm_ctx* c, int m, int64_t ne, const double* xyz, const double* 
     const bool f32 = c->p.k_prec != CPM_PREC_FP64;
     const size_t need = f32 ? bvec_scratch_bytes<float>(c, m, ne) : bvec_scratch_bytes<double>(c, m, ne);
     CPM_TRY(ensure_scratch(c, need));
-    CPM_TRY(ensure_tickets(c, m));
+    CPM_TRY(ensure_tickets(c, 2 * m));   // k_bin takes [0, m), k_fracs [m, 2m)
     char* scr = (char*)c->scratch;
     return f32 ? bvec_run<float>(c, m, ne, xyz, Q, b_out, bhl, scr) : bvec_run<double>(c, m, ne, xyz, Q, b_out, bhl, scr);
 }

@@ -115,7 +115,9 @@ struct cpm_ctx {
     double* zuniq = nullptr;     // distinct site heights (exact values)
     int nzu = 0;
     int* sperm = nullptr;        // sites ordered by real-space cell
-    void* schunks = nullptr;     // int4 (first, count, cell, 0): chunks of at most 32 sites of one cell
+    void* schunks = nullptr;     // int4 (first, count, cell, 0): chunks of at most 32 sites of one cell,
+                                 // the most sites first
+    int* rqueue = nullptr;       // real-space work queue: next item, blocks done (both zero between launches)
     int nschunk = 0;
     void* rtab = nullptr;        // single-precision pair-function tables, one per distinct eta
     int* rtab_id = nullptr;      // [n] table of each site
@@ -221,10 +223,13 @@ template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
                          c2<T>* X, c2<T>* Y, c2<T>* Z);
 size_t phase_elems(const KTable& k, int64_t P);
+constexpr int FR_THREADS = 256;   // threads per block of the fractions kernel (k_fracs)
+// fractions u, charges Qv in T and (qabs non-null) the per-replica max |Q|, sum |Q| (qpart: m x blocks
+// x 2 doubles, tickets: m counters), then the phase tables; after_fracs is recorded after the first kernel
 template <typename T>
-cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs = nullptr,
-                           float zscale = 1.f);
+cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, const double* Q,
+                           int64_t ne, int m, uint64_t* u, T* Qv, double* qpart, int* tickets, float2* qabs,
+                           c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs = nullptr, float zscale = 1.f);
 // inputs of the double-float k_perp = 0 column from the z fractions (u as written by the phase kernels)
 cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* Q, int64_t P, float4* e1,
                               float2* q2);

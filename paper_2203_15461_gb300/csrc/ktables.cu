@@ -235,14 +235,66 @@ __global__ void k_phases(const double* __restrict__ xyz, int64_t P, double ix, d
 }
 
 // The fixed-point fractions of each point once per axis (u[d][p]), then the tables from them:
-// the table kernel then needs no FP64 arithmetic at all.
-__global__ void k_fracs(const double* __restrict__ xyz, int64_t P, double ix, double iy, double iz,
-                        uint64_t* __restrict__ u) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    u[p] = frac_fixed(xyz[3 * p + 0], ix);
-    u[P + p] = frac_fixed(xyz[3 * p + 1], iy);
-    u[2 * P + p] = frac_fixed(xyz[3 * p + 2], iz);
+// the table kernel then needs no FP64 arithmetic at all.  The same pass writes the charges in the
+// working precision (Qv) and, when qabs is given, max |Q| and sum |Q| of each replica (the scales
+// of the tensor-core reciprocal sums), so that the reciprocal chain needs nothing from the binning
+// of the real-space chain: each block reduces its charges into part[r][b][2] (lane l takes threads
+// l, l + 32, ..., then a shuffle tree) and the replica's last block adds the block values in block
+// order.  grid (charge blocks, m); point p = r ne + j.
+template <typename T>
+__global__ void __launch_bounds__(FR_THREADS) k_fracs(const double* __restrict__ xyz, const double* __restrict__ Q,
+                                                    int64_t ne, double ix, double iy, double iz,
+                                                    uint64_t* __restrict__ u, T* __restrict__ Qv,
+                                                    double* __restrict__ part, int* __restrict__ tickets,
+                                                    float2* __restrict__ qabs) {
+    const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)b * FR_THREADS + threadIdx.x;
+    const int64_t P = (int64_t)gridDim.y * ne;
+    double aq = 0.0;
+    if (j < ne) {
+        const int64_t p = (int64_t)r * ne + j;
+        u[p] = frac_fixed(xyz[3 * p + 0], ix);
+        u[P + p] = frac_fixed(xyz[3 * p + 1], iy);
+        u[2 * P + p] = frac_fixed(xyz[3 * p + 2], iz);
+        const double q = Q[p];
+        Qv[p] = (T)q;
+        aq = fabs(q);
+    }
+    if (!qabs) return;   // uniform
+    __shared__ double sv[FR_THREADS];
+    sv[threadIdx.x] = aq;
+    __syncthreads();
+    if (warp < 2) {   // warp 0: max |Q|, warp 1: sum |Q|
+        double v = sv[lane];
+        for (int k = 1; k < FR_THREADS / 32; ++k) v = warp == 0 ? fmax(v, sv[lane + 32 * k]) : v + sv[lane + 32 * k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = warp == 0 ? fmax(v, w) : v + w;
+        }
+        if (lane == 0) part[((int64_t)r * nb + b) * 2 + warp] = v;
+    }
+    if (!last_block_of(&tickets[r], nb)) return;
+    __shared__ double buf[2][FR_THREADS];
+    const volatile double* pv = part + (int64_t)r * nb * 2;
+    double v = 0.0;
+    for (int k0 = 0; k0 < nb; k0 += FR_THREADS) {
+        const int k = k0 + threadIdx.x;
+        if (k < nb) {
+            buf[0][threadIdx.x] = pv[2 * k];
+            buf[1][threadIdx.x] = pv[2 * k + 1];
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int t = threadIdx.x, cnt = min(FR_THREADS, nb - k0);
+            for (int kk = 0; kk < cnt; ++kk) {
+                const double x = buf[t][kk];
+                v = (k0 == 0 && kk == 0) ? x : (t == 0 ? fmax(v, x) : v + x);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) qabs[r].x = (float)v;
+    if (threadIdx.x == 1) qabs[r].y = (float)v;
 }
 
 // For the double-float k_perp = 0 column of the single-precision paths: the first z harmonic
@@ -322,10 +374,13 @@ cpm_status launch_col0_inputs(cudaStream_t st, const uint64_t* u, const double* 
 }
 
 template <typename T>
-cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
-                           uint64_t* u, c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs, float zscale) {
+cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, const double* Q,
+                           int64_t ne, int m, uint64_t* u, T* Qv, double* qpart, int* tickets, float2* qabs,
+                           c2<T>* X, c2<T>* Y, c2<T>* Z, cudaEvent_t after_fracs, float zscale) {
+    const int64_t P = (int64_t)m * ne;
     if (P == 0) return CPM_OK;
-    k_fracs<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(xyz, P, g.inv[0], g.inv[1], g.inv[2], u);
+    k_fracs<T><<<dim3((unsigned)((ne + FR_THREADS - 1) / FR_THREADS), (unsigned)m), FR_THREADS, 0, st>>>(
+        xyz, Q, ne, g.inv[0], g.inv[1], g.inv[2], u, Qv, qpart, tickets, qabs);
     if (after_fracs && cudaEventRecord(after_fracs, st) != cudaSuccess) return CPM_E_CUDA;
     if (std::is_same<T, float>::value) {
         k_phases_rows<<<dim3((unsigned)((P + 127) / 128), 3), 128, 0, st>>>(u, P, k.NX, k.NY, k.NZ, (float2*)X,
@@ -337,10 +392,12 @@ cpm_status launch_phases_u(cudaStream_t st, const Geometry& g, const KTable& k, 
     }
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_E_CUDA;
 }
-template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                           uint64_t*, float2*, float2*, float2*, cudaEvent_t, float);
-template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*, int64_t,
-                                            uint64_t*, double2*, double2*, double2*, cudaEvent_t, float);
+template cpm_status launch_phases_u<float>(cudaStream_t, const Geometry&, const KTable&, const double*, const double*,
+                                           int64_t, int, uint64_t*, float*, double*, int*, float2*, float2*, float2*,
+                                           float2*, cudaEvent_t, float);
+template cpm_status launch_phases_u<double>(cudaStream_t, const Geometry&, const KTable&, const double*,
+                                            const double*, int64_t, int, uint64_t*, double*, double*, int*, float2*,
+                                            double2*, double2*, double2*, cudaEvent_t, float);
 
 template <typename T>
 cpm_status launch_phases(cudaStream_t st, const Geometry& g, const KTable& k, const double* xyz, int64_t P,
