@@ -537,8 +537,7 @@ def main():
     peaks, src = _peaks()
     # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the full
     # workload (cold caches: ncu flushes them before each launch); None for a kernel not captured
-    # since its last change (k_real_cells: work queue)
-    traffic_ncu = {"real": None, "sf": 59.33e6, "site": 15.56e6, "gemv": 76.67e6}
+    traffic_ncu = {"real": 0.75e6, "sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
     kname = {"real": "k_real_cells", "sf": "k_tc_sf" if args.k_prec == "f16x2" else "k_sf32",
              "site": "k_tc_site" if args.k_prec == "f16x2" else "k_site32", "gemv": "k_gemv_tma"}
     pairs = real_pairs(el, xyz, Q, ne, m, W)
