@@ -100,12 +100,53 @@ def _stream_handle(stream) -> int:
     return int(s.cuda_stream)
 
 
+def _check_noalloc_args(site_xyz, site_eta, xyz, Q, b_out) -> None:
+    """Sizes, types and devices of cpm_bvec_noalloc's arguments.
+
+    The C entry point receives bare device pointers and cannot see how long the buffers are, so a
+    short or mistyped tensor would be read or written past its end on the GPU; everything is
+    checked here, before anything is launched (TypeError for a type or device, ValueError for a
+    shape)."""
+    import torch
+    named = {"site_xyz": site_xyz, "site_eta": site_eta, "b_out": b_out}
+    if xyz is not None or Q is not None:
+        named.update(xyz=xyz, Q=Q)
+    for name, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+        if t.dtype != torch.float64:
+            raise TypeError(f"{name}: expected float64, got {t.dtype}")
+    n = int(site_xyz.shape[0]) if site_xyz.dim() == 2 else -1
+    if site_xyz.dim() != 2 or site_xyz.shape[1] != 3 or n < 1:
+        raise ValueError(f"site_xyz: expected shape (n, 3) with n >= 1, got {tuple(site_xyz.shape)}")
+    if site_eta.numel() != n:
+        raise ValueError(f"site_eta: expected {n} values, got {site_eta.numel()}")
+    if b_out.numel() < n:
+        raise ValueError(f"b_out: expected at least {n} values, got {b_out.numel()}")
+    if "xyz" in named:
+        if xyz is None or Q is None:
+            raise ValueError("xyz and Q: give both or neither")
+        if xyz.dim() != 2 or xyz.shape[1] != 3:
+            raise ValueError(f"xyz: expected shape (n_e, 3), got {tuple(xyz.shape)}")
+        if Q.numel() != xyz.shape[0]:
+            raise ValueError(f"Q: expected {xyz.shape[0]} values, got {Q.numel()}")
+    devs = {t.device for t in named.values()}
+    if len(devs) != 1 or not next(iter(devs)).type == "cuda":
+        raise TypeError(f"all tensors must be on one CUDA device, got {sorted(map(str, devs))}")
+    if next(iter(devs)).index not in (None, torch.cuda.current_device()):
+        raise TypeError(f"tensors are on {next(iter(devs))}, the current device is cuda:{torch.cuda.current_device()}")
+    for name, t in named.items():
+        if not t.is_contiguous():
+            raise TypeError(f"{name}: expected a contiguous tensor")
+
+
 def cpm_bvec_noalloc(params: cpm_params, site_xyz, site_eta, xyz, Q, b_out, stream=None) -> None:
     """b for one electrolyte configuration without any device allocation (see include/cpm.h).
 
     For callers that cannot allocate device memory: the library's fixed 4 MiB scratch
     array holds the reciprocal-space grid, shared by all calls (serialise overlapping calls).
     """
+    _check_noalloc_args(site_xyz, site_eta, xyz, Q, b_out)
     lib = load_library()
     n_e = int(xyz.shape[0]) if xyz is not None else 0
     st = lib.cpm_bvec_noalloc(ctypes.byref(params), int(site_xyz.shape[0]), _ptr(site_xyz), _ptr(site_eta), n_e,

@@ -4,7 +4,8 @@
 // Its only scratch is the structure-factor grid below, a file-scope device array that
 // every GPU loading this library holds until the process exits.  Host code must not pass
 // the array's name to a kernel (on the host it is only a stand-in symbol); it passes the
-// device address that cudaGetSymbolAddress returns, looked up once per device.
+// device address that cudaGetSymbolAddress returns, looked up on every call made outside stream
+// capture.
 #include <mutex>
 
 #include "common.cuh"
@@ -131,29 +132,42 @@ extern "C" cpm_status cpm_bvec_noalloc(const cpm_params* p, int64_t n, const dou
     for (int d = 0; d < 3; ++d) { g.boxL[d] = p->box[d]; g.inv[d] = 1.0 / p->box[d]; }
     g.V = p->box[0] * p->box[1] * p->box[2];
     g.alpha = p->alpha; g.rcut = p->rcut; g.kcut = p->kcut; g.bc = p->boundary;
-    const int NX = (int)(g.kcut / ((2.0 * PI) / g.boxL[0])) + 1;
-    const int NY = (int)(g.kcut / ((2.0 * PI) / g.boxL[1])) + 1;
-    const int NZ = (int)(g.kcut / ((2.0 * PI) / g.boxL[2])) + 1;
-    const int64_t G = (int64_t)(NX + 1) * (2 * NY + 1) * (2 * NZ + 1);
-    if (G > NOALLOC_MAX_KGRID) return CPM_E_BUDGET;   // k grid larger than the fixed scratch
+    // harmonics per axis, checked in floating point before any conversion to int: a grid that
+    // cannot fit the scratch is refused without forming (and overflowing) its size
+    double hd[3];
+    for (int d = 0; d < 3; ++d) {
+        hd[d] = g.kcut / ((2.0 * PI) / g.boxL[d]);
+        if (!(hd[d] >= 0.0) || hd[d] > (double)NOALLOC_MAX_KGRID) return CPM_E_BUDGET;
+    }
+    const int NX = (int)hd[0] + 1, NY = (int)hd[1] + 1, NZ = (int)hd[2] + 1;
+    const double Gd = (double)(NX + 1) * (double)(2 * NY + 1) * (double)(2 * NZ + 1);
+    if (!(Gd >= 1.0) || Gd > (double)NOALLOC_MAX_KGRID) return CPM_E_BUDGET;   // larger than the fixed scratch
+    const int64_t G = (int64_t)Gd;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CPM_E_CUDA; }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return CPM_E_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The array's device address is looked up again on every call made outside stream capture, so
+    // a device reset or a new primary context between calls leaves no stale address behind; while
+    // the stream is being captured only the address of an earlier call on this device is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) { cudaGetLastError(); return CPM_E_CUDA; }
     double2* rho = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_rho) != cudaSuccess || !ptr) {
                 cudaGetLastError();
                 return CPM_E_CUDA;
             }
             g_noalloc_addr[dev] = (double2*)ptr;
+        } else if (!g_noalloc_addr[dev]) {
+            return CPM_E_STATE;   // first call on this device inside a capture: no address yet
         }
         rho = g_noalloc_addr[dev];
     }
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     k_noalloc_rho<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(g, NX, NY, NZ, xyz, Q, n_e, rho);
     if (cudaGetLastError() != cudaSuccess) return CPM_E_CUDA;
     k_noalloc_site<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, NX, NY, NZ, site_xyz, site_eta, n, xyz, Q, n_e,

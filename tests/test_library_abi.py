@@ -59,3 +59,28 @@ def test_no_cpu_fallback_without_a_device(lib):
     assert lib.cpm_create(ctypes.byref(p), None, ctypes.byref(h)) == 6   # CPM_E_CUDA
     with pytest.raises(cpm.CPMError, match="CPM_E_CUDA"):
         cpm.CPM((10, 10, 10), "slab", 0.3, 10.0, 2.0)
+
+
+def test_noalloc_binding_refuses_bad_buffers_before_any_launch():
+    """cpm_bvec_noalloc receives bare device pointers; the binding checks types, sizes and devices first."""
+    torch = pytest.importorskip("torch")
+    p = cpm.cpm_params()
+    p.box[:] = [10.0, 10.0, 30.0]
+    p.alpha, p.rcut, p.kcut, p.boundary = 0.3, 9.0, 2.0, 1
+    f64 = torch.float64
+    sx, se, b = torch.zeros((4, 3), dtype=f64), torch.ones(4, dtype=f64), torch.zeros(4, dtype=f64)
+    x, Q = torch.zeros((2, 3), dtype=f64), torch.zeros(2, dtype=f64)
+    with pytest.raises(TypeError, match="float64"):
+        cpm.cpm_bvec_noalloc(p, sx.float(), se, x, Q, b)
+    with pytest.raises(TypeError, match="float64"):
+        cpm.cpm_bvec_noalloc(p, sx, se, x, Q, b.float())
+    with pytest.raises(ValueError, match="b_out"):
+        cpm.cpm_bvec_noalloc(p, sx, se, x, Q, torch.zeros(3, dtype=f64))
+    with pytest.raises(ValueError, match="site_eta"):
+        cpm.cpm_bvec_noalloc(p, sx, se[:3], x, Q, b)
+    with pytest.raises(ValueError, match="Q"):
+        cpm.cpm_bvec_noalloc(p, sx, se, x, Q[:1], b)
+    with pytest.raises(ValueError, match="site_xyz"):
+        cpm.cpm_bvec_noalloc(p, sx.reshape(-1), se, x, Q, b)
+    with pytest.raises(TypeError, match="CUDA"):
+        cpm.cpm_bvec_noalloc(p, sx, se, x, Q, b)     # well formed, but host memory
