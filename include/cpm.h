@@ -155,6 +155,11 @@ cpm_status cpm_update(cpm_ctx* ctx, int32_t m, const double* psi, const double* 
  * and synchronise.  xyz: host, (m * n_e) x 3; Q: host, m * n_e; psi: host,
  * m x n_groups; q_out: host, m x n; qtot_out: host, m (may be NULL).
  * Host buffers may be pageable; page-locked memory gives faster copies.
+ * On a context created with its own (non-default) stream the device part runs as
+ * the CUDA graph of cpm_step_graph, captured once on the context's staging buffers
+ * for each (m, n_e) and replayed; the context keeps one graph, shared with
+ * cpm_step_graph, so alternating the two calls re-captures.  On the default stream,
+ * or while cpm_profile is on, the kernels launch one by one.
  */
 cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
                          const double* psi, double* q_out, double* qtot_out);
@@ -178,6 +183,39 @@ cpm_status cpm_step_graph(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xy
  * status word is cleared).  Needs cpm_invert.
  */
 cpm_status cpm_selftest_timeout(cpm_ctx* ctx, double wait_ms);
+
+/*
+ * Change the arithmetic of the S product (cpm_params.s_prec: CPM_PREC_FP64, CPM_PREC_FP32 or
+ * CPM_PREC_BF16X3) of an inverted context without assembling again: S is kept in FP64 and in
+ * FP32 after cpm_invert, and the three bf16 planes of the tensor-core product are made from the
+ * FP64 S on their first use.  Drops the captured step graph.  Synchronises the stream.
+ * Errors: CPM_E_ARG (not an S precision), CPM_E_STATE (not inverted).
+ */
+cpm_status cpm_set_s_prec(cpm_ctx* ctx, int32_t s_prec);
+
+/*
+ * Tile plan of the tensor-core S product (s_prec = CPM_PREC_BF16X3; the batched product
+ * S [b_1 .. b_m] of Eq. electrode-wise, Sec. II.B, over m replicas sharing one geometry).  The
+ * product runs as a persistent kernel over work items (128 sites x BN replicas x one K split);
+ * the first time m replicas are used on a device with a geometry of n sites (outside stream
+ * capture) every candidate plan - BN in {32, 64, 128}, two or three ring stages, split counts that
+ * give 1 to 8 waves of items - is timed on the context stream and the fastest is kept for the
+ * process per (device, n, m); inside a capture without a tuned plan an untimed default is used.
+ * This call runs that choice when needed and reports it.  plan_out: host, 5 int32 (BN, stages,
+ * K splits, CTAs, candidates timed); ms_out (may be NULL): the plan's time per product in ms
+ * (negative when it was not timed).  Synchronises the stream.
+ * Errors: CPM_E_STATE (not inverted, or the stream is capturing), CPM_E_ARG (other s_prec, m < 1).
+ */
+cpm_status cpm_gemm_plan(cpm_ctx* ctx, int32_t m, int32_t* plan_out, double* ms_out);
+
+/*
+ * Replace the kept tile plan for (this device, n, m) with plan[0..3] = (BN, stages, K splits,
+ * CTAs); the built (BN, stages) pairs are (32, 2), (32, 3), (64, 2), (64, 3), (128, 2).  The
+ * split count is rounded to whole 64-wide K steps per split and capped at 256 MiB of FP32
+ * partial sums.  For tests and for callers that tune offline.  Synchronises the stream.
+ * Errors: CPM_E_ARG (a pair that is not built, splits or CTAs < 1, too many splits), CPM_E_STATE.
+ */
+cpm_status cpm_gemm_set_plan(cpm_ctx* ctx, int32_t m, const int32_t* plan);
 
 /* Wait for all work of the context and report any deferred kernel error. */
 cpm_status cpm_sync(cpm_ctx* ctx);
@@ -241,7 +279,8 @@ typedef enum {
     CPM_K_GEMV = 8,     /* S (G psi - b) */
     CPM_K_NEUTRAL = 9,  /* neutrality fix and total charge */
     CPM_K_COL0 = 10,    /* FP64 k_perp = 0 column of the single-precision path */
-    CPM_K_COUNT = 11
+    CPM_K_TCGEMM = 11,  /* the tensor-core product alone (inside CPM_K_GEMV when s_prec = BF16X3) */
+    CPM_K_COUNT = 12
 } cpm_kernel;
 
 /*
@@ -270,14 +309,20 @@ cpm_status cpm_profile_read(cpm_ctx* ctx, int32_t kernel, double* total_ms, int6
  * library, which every GPU that loads the library holds until the process exits.
  * The reciprocal-space grid, (NX + 1)(2 NY + 1)(2 NZ + 1) entries with
  * N_d = floor(kcut L_d / 2 pi) + 1, must fit in it; a larger grid returns
- * CPM_E_BUDGET and launches nothing.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls share the one array, so
- * calls whose work overlaps on the GPU (other streams, other threads) race and
- * must be serialised by the caller.  Real-space pairs are summed directly over all
- * charges and images (no cell list), so the cost grows as n * n_e.
+ * CPM_E_BUDGET and launches nothing.  Every call made outside stream capture looks
+ * up the array's device address (cudaGetSymbolAddress) with the current device, so a
+ * device reset between calls is harmless; a call made while `cuda_stream` is being
+ * captured reuses the address of the last uncaptured call on that device, so make at
+ * least one call on each device before any stream capture (CPM_E_STATE otherwise).
+ * All calls share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  The device
+ * pointers cannot be checked here: site_eta and b_out must hold n doubles, site_xyz
+ * n x 3, xyz n_e x 3 and Q n_e (the Python binding checks them).  Real-space pairs
+ * are summed directly over all charges and images (no cell list), so the cost grows
+ * as n * n_e.
  * Errors: CPM_E_ARG (bad parameters or pointers), CPM_E_BUDGET (grid too large),
- * CPM_E_CUDA (no device, or a launch failed).
+ * CPM_E_STATE (first call on a device inside a stream capture), CPM_E_CUDA (no device,
+ * or a launch failed).
  */
 cpm_status cpm_bvec_noalloc(const cpm_params* p, int64_t n, const double* site_xyz, const double* site_eta,
                             int64_t n_e, const double* xyz, const double* Q, double* b_out, void* cuda_stream);

@@ -61,10 +61,13 @@ _SIGS = {
     "cpm_device_bytes": ([_P], ctypes.c_size_t),
     "cpm_launch_count": ([_P], _I64),
     "cpm_bvec_noalloc": ([ctypes.POINTER(cpm_params), _I64, _P, _P, _I64, _P, _P, _P, _P], _I32),
+    "cpm_gemm_plan": ([_P, _I32, _P, ctypes.POINTER(_D)], _I32),
+    "cpm_gemm_set_plan": ([_P, _I32, _P], _I32),
+    "cpm_set_s_prec": ([_P, _I32], _I32),
     "cpm_profile": ([_P, _I32], _I32),
     "cpm_profile_read": ([_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32], _I32),
 }
-KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral", "col0"]
+KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral", "col0", "tcgemm"]
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -236,6 +239,22 @@ class CPM:
     def cpm_selftest_timeout(self, wait_ms: float = 50.0) -> str:
         """Run the bounded-wait self test; returns the status name (CPM_E_TIMEOUT when it works)."""
         return STATUS[self.lib.cpm_selftest_timeout(self.handle, float(wait_ms))]
+
+    def cpm_gemm_plan(self, m: int) -> dict:
+        """Tile plan of the tensor-core S product for m replicas (tuned on first use; see include/cpm.h)."""
+        plan = np.zeros(5, dtype=np.int32)
+        ms = _D(0.0)
+        self._check(self.lib.cpm_gemm_plan(self.handle, int(m), plan.ctypes.data, ctypes.byref(ms)))
+        return {"BN": int(plan[0]), "stages": int(plan[1]), "splits": int(plan[2]), "ctas": int(plan[3]),
+                "candidates": int(plan[4]), "ms": float(ms.value)}
+
+    def cpm_set_s_prec(self, s_prec: str):
+        self._check(self.lib.cpm_set_s_prec(self.handle, PRECISION[s_prec]))
+        self.params.s_prec = PRECISION[s_prec]
+
+    def cpm_gemm_set_plan(self, m: int, BN: int, stages: int, splits: int, ctas: int = 152):
+        plan = np.array([BN, stages, splits, ctas], dtype=np.int32)
+        self._check(self.lib.cpm_gemm_set_plan(self.handle, int(m), plan.ctypes.data))
 
     def cpm_sync(self):
         self._check(self.lib.cpm_sync(self.handle))

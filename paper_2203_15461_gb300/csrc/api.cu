@@ -161,6 +161,43 @@ static uint64_t fnv1a(uint64_t h, const void* data, size_t bytes) {
     return h;
 }
 
+// cpm_bvec followed by cpm_update as one CUDA graph on the context stream: captured and
+// instantiated on the first call for given (m, n_e, buffer addresses), replayed afterwards.
+static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q,
+                             const double* psi, double* b_out, double* q_out, double* qtot_out) {
+    const void* ptrs[7] = {xyz, Q, psi, b_out, q_out, qtot_out, nullptr};
+    CPM_TRY(reserve_bvec(c, m, n_e));
+    CPM_TRY(reserve_update(c, m));
+    bool same = c->graph_valid && c->graph_m == m && c->graph_ne == n_e;
+    for (int k = 0; k < 6 && same; ++k) same = c->graph_ptrs[k] == ptrs[k];
+    if (!same) {
+        drop_graph(c);
+        const bool prof = c->prof_on;
+        c->prof_on = false;
+        const int64_t l0 = c->launches;
+        CPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        float2* bhl = update_bhl(c, m);
+        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out, bhl);
+        cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out, bhl != nullptr) : s1;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->prof_on = prof;
+        if (s2 != CPM_OK) { if (g) cudaGraphDestroy(g); return s2; }
+        if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
+        c->graph = g;
+        CPM_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+        c->graph_valid = true;
+        c->graph_m = m;
+        c->graph_ne = n_e;
+        for (int k = 0; k < 7; ++k) c->graph_ptrs[k] = ptrs[k];
+    }
+    CPM_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_launches;
+    return CPM_OK;
+}
+
 }  // namespace cpm
 
 using namespace cpm;
@@ -412,9 +449,14 @@ cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, 
         CPM_CUDA(c, cudaMemcpyAsync(dQ, Q, sizeof(double) * pt, cudaMemcpyHostToDevice, st));
     }
     CPM_CUDA(c, cudaMemcpyAsync(dpsi, psi, sizeof(double) * m * c->ng, cudaMemcpyHostToDevice, st));
-    float2* bhl = update_bhl(c, m);   // b's two-float split written by bvec: no separate split pass
-    CPM_TRY(bvec(c, m, n_e, dxyz, dQ, db, bhl));
-    CPM_TRY(update(c, m, dpsi, db, dq, dqt, bhl != nullptr));
+    if (c->stream && !c->prof_on) {
+        // the captured step, replayed on the staging buffers (addresses stable while dstage is)
+        CPM_TRY(step_graph(c, m, n_e, dxyz, dQ, dpsi, db, dq, dqt));
+    } else {
+        float2* bhl = update_bhl(c, m);   // b's two-float split written by bvec: no separate split pass
+        CPM_TRY(bvec(c, m, n_e, dxyz, dQ, db, bhl));
+        CPM_TRY(update(c, m, dpsi, db, dq, dqt, bhl != nullptr));
+    }
     CPM_CUDA(c, cudaMemcpyAsync(q_out, dq, sizeof(double) * m * c->n, cudaMemcpyDeviceToHost, st));
     if (qtot_out) CPM_CUDA(c, cudaMemcpyAsync(qtot_out, dqt, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     CPM_CUDA(c, cudaStreamSynchronize(st));
@@ -428,37 +470,7 @@ cpm_status cpm_step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz,
     if (m < 1 || n_e < 0 || !psi || !b_out || !q_out || (n_e > 0 && (!xyz || !Q)))
         return set_err(c, CPM_E_ARG, "cpm_step_graph: need m >= 1, n_e >= 0 and non-null buffers");
     if (!c->stream) return set_err(c, CPM_E_ARG, "cpm_step_graph: needs a context created on a non-default stream");
-    const void* ptrs[7] = {xyz, Q, psi, b_out, q_out, qtot_out, nullptr};
-    CPM_TRY(reserve_bvec(c, m, n_e));
-    CPM_TRY(reserve_update(c, m));
-    bool same = c->graph_valid && c->graph_m == m && c->graph_ne == n_e;
-    for (int k = 0; k < 6 && same; ++k) same = c->graph_ptrs[k] == ptrs[k];
-    if (!same) {
-        drop_graph(c);
-        const bool prof = c->prof_on;
-        c->prof_on = false;
-        const int64_t l0 = c->launches;
-        CPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        float2* bhl = update_bhl(c, m);
-        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out, bhl);
-        cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out, bhl != nullptr) : s1;
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        c->prof_on = prof;
-        if (s2 != CPM_OK) { if (g) cudaGraphDestroy(g); return s2; }
-        if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
-        c->graph = g;
-        CPM_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
-        c->graph_launches = c->launches - l0;
-        c->launches = l0;
-        c->graph_valid = true;
-        c->graph_m = m;
-        c->graph_ne = n_e;
-        for (int k = 0; k < 7; ++k) c->graph_ptrs[k] = ptrs[k];
-    }
-    CPM_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += c->graph_launches;
-    return CPM_OK;
+    return step_graph(c, m, n_e, xyz, Q, psi, b_out, q_out, qtot_out);
 }
 
 cpm_status cpm_selftest_timeout(cpm_ctx* c, double wait_ms) {
@@ -471,6 +483,40 @@ cpm_status cpm_selftest_timeout(cpm_ctx* c, double wait_ms) {
     CPM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
     return s;
+}
+
+cpm_status cpm_gemm_plan(cpm_ctx* c, int32_t m, int32_t* plan_out, double* ms_out) {
+    if (!c || m < 1) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_gemm_plan before cpm_invert");
+    if (c->p.s_prec != CPM_PREC_BF16X3) return set_err(c, CPM_E_ARG, "cpm_gemm_plan: s_prec is not CPM_PREC_BF16X3");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CPM_CUDA(c, cudaStreamIsCapturing(c->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return set_err(c, CPM_E_STATE, "cpm_gemm_plan during stream capture");
+    CPM_TRY(tc_plan_query(c, m, plan_out, ms_out));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CPM_OK;
+}
+
+cpm_status cpm_set_s_prec(cpm_ctx* c, int32_t s_prec) {
+    if (!c) return CPM_E_ARG;
+    if (s_prec != CPM_PREC_FP64 && s_prec != CPM_PREC_FP32 && s_prec != CPM_PREC_BF16X3)
+        return set_err(c, CPM_E_ARG, "cpm_set_s_prec: %d is not an S precision", s_prec);
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_set_s_prec before cpm_invert");
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->p.s_prec != s_prec) {
+        c->p.s_prec = s_prec;
+        drop_graph(c);
+    }
+    return CPM_OK;
+}
+
+cpm_status cpm_gemm_set_plan(cpm_ctx* c, int32_t m, const int32_t* plan) {
+    if (!c || m < 1 || !plan) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_gemm_set_plan before cpm_invert");
+    if (c->p.s_prec != CPM_PREC_BF16X3) return set_err(c, CPM_E_ARG, "cpm_gemm_set_plan: s_prec is not CPM_PREC_BF16X3");
+    CPM_TRY(tc_plan_set(c, m, plan));
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CPM_OK;
 }
 
 cpm_status cpm_sync(cpm_ctx* c) {

@@ -171,6 +171,8 @@ struct cpm_ctx {
     bool tc_use_z = false;
     void* tbuf = nullptr;        // tensor-core update scratch (K-split partials, b planes)
     size_t tbuf_bytes = 0;
+    size_t tc_pbytes = 0;        // bytes of tbuf holding the K-split partial sums
+    bool tc_autotune = true;     // time the tile plans of the tensor-core product per (n, m)
     void* tcz = nullptr;         // tensor-core reciprocal space: site phase planes [2][npad][KZ] (fp16)
     float2* tcxy = nullptr;      // [ncols][n] column factors X_i Y_i of the sites
     float tc_wmax = 0.f;         // bound on the k-space weights
@@ -287,6 +289,9 @@ cpm_status reserve_update(cpm_ctx* c, int m);
 cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);
 cpm_status tc_reserve(cpm_ctx* c, int m);
 cpm_status tc_selftest_timeout(cpm_ctx* c, double wait_ms);
+// tile plan of the tensor-core product for m replicas: BN, stages, splits, CTAs, candidates timed
+cpm_status tc_plan_query(cpm_ctx* c, int m, int32_t* plan, double* ms);
+cpm_status tc_plan_set(cpm_ctx* c, int m, const int32_t* plan);
 
 // gemv_tma.cu: single-precision S streaming with TMA (n a multiple of 4)
 bool gemv_tma_supported(const cpm_ctx* c);

@@ -195,3 +195,33 @@ def test_edl_capacitor_one_replica_matches_oracle(edl):
         ctx = make_ctx(el, s_prec="fp32", k_prec=k_prec).setup(el)
         q, qt = _bvec_update(ctx, elyts[:1], psi)
         _check(q, qt, _q_ref(S, el, psi, b[:1]), MIXED_TOL)
+
+
+# ----------------------------------------------------------------------------- tile plans of the tensor-core product
+
+@pytest.mark.parametrize("bn,stages", [(32, 2), (32, 3), (64, 2), (64, 3), (128, 2)])
+def test_every_tile_plan_matches_oracle(serving, bn, stages):
+    """Every built (BN, stages) pair of the persistent tensor-core product, each with one item per CTA,
+    several items per CTA and many items per CTA (both TMEM accumulators reused), against the oracle."""
+    el, S, _, b = serving
+    m = 37 if bn < 128 else 150          # ragged replica tiles
+    bm = np.stack([b[r % len(b)] * (1.0 - 0.003 * r) for r in range(m)])
+    psi = _psi(m)
+    ctx = make_ctx(el, s_prec="bf16x3").setup(el)
+    for splits, ctas in ((1, 152), (3, 7), (5, 2)):
+        ctx.cpm_gemm_set_plan(m, bn, stages, splits, ctas)
+        plan = ctx.cpm_gemm_plan(m)
+        assert (plan["BN"], plan["stages"]) == (bn, stages) and plan["splits"] >= 1
+        q, qt = _update(ctx, bm, psi)
+        _check(q, qt, _q_ref(S, el, psi, bm), MIXED_TOL)
+
+
+def test_autotuned_plan_is_timed_and_kept(serving):
+    el, S, _, b = serving
+    m = 64
+    ctx = make_ctx(el, s_prec="bf16x3").setup(el)
+    plan = ctx.cpm_gemm_plan(m)
+    assert plan["candidates"] > 1 and plan["ms"] > 0
+    assert ctx.cpm_gemm_plan(m) == plan            # kept per (n, m), not tuned again
+    other = make_ctx(el, s_prec="bf16x3").setup(el)
+    assert other.cpm_gemm_plan(m) == plan          # another context of the same n reuses it

@@ -279,3 +279,28 @@ def test_capacitance_by_fp32_factor_and_fp64_refinement(which):
     C, it, res = ctx.cpm_capacitance_ir()
     assert it >= 1 and res < 1e-12
     assert np.abs(C - C64).max() <= 1e-10 * np.abs(C64).max()
+
+
+def test_step_host_on_a_stream_replays_the_graph(tiny):
+    """cpm_step_host on a context with its own stream runs the captured step: the same q as
+    cpm_step_graph on device buffers, bit for bit, and the same on a second call with new inputs."""
+    el, _, psi, _, _ = tiny
+    st = torch.cuda.Stream()
+    ctx = make_ctx(el, s_prec="fp32", k_prec="f16x2", stream=st).setup(el)
+    ref = make_ctx(el, s_prec="fp32", k_prec="f16x2", stream=torch.cuda.Stream()).setup(el)
+    from gpu_util import stack_replicas
+    m = 3
+    for seed in (40, 41):
+        elyts = [s.ions_in_gap(el, 100, seed=10 * seed + r) for r in range(m)]
+        xyz, Q, ne = stack_replicas(elyts)
+        psis = np.tile(psi, (m, 1))
+        q = np.zeros((m, el.n))
+        qt = np.zeros(m)
+        ctx.cpm_step_host(m, ne, np.ascontiguousarray(xyz), np.ascontiguousarray(Q), psis.copy(), q, qt)
+        with torch.cuda.stream(ref.stream):
+            b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+            qd = torch.empty_like(b)
+            qtd = torch.empty(m, dtype=torch.float64, device="cuda")
+            ref.cpm_step_graph(m, ne, dev(xyz), dev(Q), dev(psis), b, qd, qtd)
+        ref.stream.synchronize()
+        assert np.array_equal(q, qd.cpu().numpy()) and np.array_equal(qt, qtd.cpu().numpy())
