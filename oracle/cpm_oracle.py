@@ -30,6 +30,9 @@ What it computes (ELECTRODE paper, arXiv 2203.15461):
 * The electrode-wise potentials of Sec. II.B: v = G psi, q* = S (v - b)
   (Eq. electrode-wise in API sign), and the electrode-wise capacitance
   C~ = G^T S G (Sec. II.C with S in place of A^-1; Sec. III.B uses it for C0).
+* Electrodes at prescribed total charge (Sec. II.C, Eq. ewise-conq), the
+  thermo-potentiostat step (Sec. II.D, Eq. deissenbeck) and the finite-field
+  site potentials (Sec. II.F, Eq. cpm-ffield).
 
 Readings of what the paper leaves open (units, cut-offs, the slab vacuum) are
 fixed by the arguments: positions in Angstrom, charges in e, potentials in V,
@@ -257,3 +260,74 @@ def update(S, el, elyt, psi):
     b = bvec(el, elyt)
     q = charges(S, el, psi, b)
     return b, q, float(q.sum())
+
+
+# --------------------------------------------------------------------------- constant charge method
+
+def indicator(el):
+    """Indicator matrix G of Sec. II.B: G[i, g] = 1 when site i belongs to electrode g."""
+    G = np.zeros((el.n, el.n_groups))
+    G[np.arange(el.n), np.asarray(el.group)] = 1.0
+    return G
+
+
+def ccm_charges(A, el, qtilde, b):
+    """Charges at prescribed electrode-wise totals (Sec. II.C, Eq. ewise-conq).
+
+    With the capacitance matrix A^-1 (not S): the totals are q~ = G^T A^-1 (G v~ - b) in the API
+    sign of b, i.e. q~ = q~_b + C~ v~ with q~_b = -G^T A^-1 b and C~ = G^T A^-1 G.  Solved for the
+    electrode potentials v~, which the CPM then applies: q = A^-1 (G v~ - b).  Returns (q, v~).
+    """
+    G = indicator(el)
+    L = np.linalg.cholesky(A)
+    AiG = sla.cho_solve((L, True), G)
+    Aib = sla.cho_solve((L, True), np.asarray(b, dtype=np.float64))
+    C = G.T @ AiG
+    qb = -(G.T @ Aib)
+    v = np.linalg.solve(C, np.asarray(qtilde, dtype=np.float64) - qb)
+    return AiG @ v - Aib, v
+
+
+# --------------------------------------------------------------------------- finite-field method
+
+def ffield_zeta(el):
+    """zeta of Sec. II.F: z_i / L_z, plus one for the sites of the bottom electrode (the one of lower
+    mean z), so that the two electrodes face each other across the periodic z boundary
+    (conductor-centred cell).  Two electrodes only."""
+    if el.n_groups != 2:
+        raise ValueError("the finite-field method takes two electrodes")
+    z = np.asarray(el.xyz, dtype=np.float64)[:, 2]
+    g = np.asarray(el.group)
+    bottom = 0 if z[g == 0].mean() < z[g == 1].mean() else 1
+    return z / float(el.box[2]) + (g == bottom).astype(np.float64)
+
+
+def ffield_charges(S, el, dv0, b):
+    """q* = S (v - b) with the site potentials v = -dv0 zeta of Eq. (cpm-ffield) (API sign of b)."""
+    return S @ (-float(dv0) * ffield_zeta(el) - np.asarray(b, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------- thermo-potentiostat
+
+#: Boltzmann constant in eV / K
+K_B = 8.617333262e-5
+
+
+def tp_step(A, S, el, q_cap, dv0, b, dt, tau, T, X):
+    """One thermo-potentiostat step (Sec. II.D, Eq. deissenbeck) for two electrodes.
+
+    q_cap is the charge of electrode 1 (electrode 0 carries -q_cap).  The effective potential
+    difference dv = v~_1 - v~_0 of the present charges follows from the constant-charge relation
+    (Eq. ewise-conq); the vacuum capacitance is C0 = g_1^T S g_1 (Sec. III.B); X is the standard
+    normal number of this step.  The new capacitor charge is applied by the constant charge method.
+    Returns (q_new, dv, site charges at (-q_new, q_new)).
+    """
+    if el.n_groups != 2:
+        raise ValueError("the thermo-potentiostat takes two electrodes")
+    C0 = float(electrode_capacitance(S, el)[1, 1])
+    _, v = ccm_charges(A, el, np.array([-q_cap, q_cap]), b)
+    dv = float(v[1] - v[0])
+    a = math.exp(-dt / tau)
+    q_new = q_cap - C0 * (dv - dv0) * (1.0 - a) + X * math.sqrt(K_B * T * C0 * (1.0 - a * a))
+    q_sites, _ = ccm_charges(A, el, np.array([-q_new, q_new]), b)
+    return q_new, dv, q_sites

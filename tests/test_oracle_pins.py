@@ -284,3 +284,137 @@ def test_coaxial_capacitor_sec_IIIB():
         el = s.coaxial_tubes(1, eta=eta)
         C_eta.append(o.electrode_capacitance(o.capacitance_matrix(o.assemble_A(el)), el)[1, 1])
     assert C_eta[0] > C_eta[1] > C_eta[2]
+
+
+# ----------------------------------------------------------------------------- constant charge method (Sec. II.C)
+
+def test_ccm_totals_and_stationarity(tiny):
+    """Eq. (ewise-conq): the charges carry exactly the prescribed electrode totals (also non-neutral ones) and
+    are stationary for the Eq. (coulomb) energy under those constraints: A q + b - G v~ = 0, the electrode
+    potentials v~ being the multipliers of the electrode totals."""
+    el, _, _, A, _, b = tiny
+    G = o.indicator(el)
+    for qt in ([-0.7, 0.7], [0.25, 1.1]):
+        q, v = o.ccm_charges(A, el, qt, b)
+        assert np.abs(G.T @ q - np.asarray(qt)).max() < 1e-12
+        r = A @ q + b - G @ v
+        assert np.abs(r).max() < 1e-10 * np.abs(b).max()
+
+
+def test_ccm_reproduces_cpm_at_its_totals(tiny):
+    """Prescribing the electrode totals that the CPM (Eq. electrode-wise) produces at potentials psi gives back the
+    same charges, and potentials that differ from psi by one constant (S fixes v only up to a uniform shift)."""
+    el, _, psi, A, S, b = tiny
+    q_cpm = o.charges(S, el, psi, b)
+    q, v = o.ccm_charges(A, el, o.indicator(el).T @ q_cpm, b)
+    assert np.linalg.norm(q - q_cpm) < 1e-10 * np.linalg.norm(q_cpm)
+    d = v - np.asarray(psi)
+    assert abs(d[1] - d[0]) < 1e-10
+
+
+def test_ccm_vacuum_capacitor_voltage_slope():
+    """Vacuum plate capacitor at charges (-Q, Q): the potential difference is Q / C0 and grows with the gap at
+    1 / (eps0 Area) per Angstrom per unit charge (parallel-plate law), independent of the CPM path."""
+    Q = 0.8
+    dv = []
+    ds = (20.0, 30.0, 40.0)
+    for d in ds:
+        el = s.au111_slab(gap=d)
+        _, v = o.ccm_charges(o.assemble_A(el), el, [-Q, Q], np.zeros(el.n))
+        dv.append(v[1] - v[0])
+    area = s.au111_slab().area
+    for sl in np.diff(dv) / np.diff(ds):
+        assert abs(sl * o.EPS0 * area / Q - 1) < 1e-6
+
+
+# ----------------------------------------------------------------------------- finite field (Sec. II.F)
+
+def _sheets(gap, Lz=None):
+    el = s.au111_slab(seed_layers=1, gap=gap, slab_factor=12.0)
+    if Lz is None:
+        return el
+    return s.Electrodes(**{**el.__dict__, "box": np.array([el.box[0], el.box[1], Lz]), "boundary": "3d"})
+
+
+def test_ffield_periodic_cell_approaches_the_vacuum_capacitor():
+    """Eq. (cpm-ffield): a plate capacitor in a fully periodic cell driven by the field term, without vacuum
+    padding, carries the charge of the same plates under the CPM with slab correction and a large vacuum,
+    at Delta psi = Delta v0: the difference shrinks as the periodic length grows (about 1/L) and is below
+    1e-2 at L = 600 A.  A wrong sign, or the zeta offset on the wrong electrode, fails by far."""
+    dv0 = 1.0
+    el_v = _sheets(20.0)
+    q_cpm = o.charges(o.capacitance_matrix(o.assemble_A(el_v)), el_v, [0.0, dv0], np.zeros(el_v.n))
+    Q_ref = q_cpm[el_v.group == 1].sum()
+    devs = []
+    for Lz in (150.0, 300.0, 600.0):
+        el = _sheets(20.0, Lz)
+        q = o.ffield_charges(o.capacitance_matrix(o.assemble_A(el)), el, dv0, np.zeros(el.n))
+        assert abs(q.sum()) < 1e-12
+        devs.append(abs(q[el.group == 1].sum() / Q_ref - 1))
+    assert devs[0] > devs[1] > devs[2] and devs[2] < 1e-2, devs
+    assert 1.6 < devs[0] / devs[1] < 2.4 and 1.6 < devs[1] / devs[2] < 2.4
+
+
+def test_ffield_charges_linear_in_field(tiny):
+    el = _sheets(20.0, 150.0)
+    S = o.capacitance_matrix(o.assemble_A(el))
+    z = np.zeros(el.n)
+    assert np.linalg.norm(o.ffield_charges(S, el, 2.0, z) - 2 * o.ffield_charges(S, el, 1.0, z)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- thermo-potentiostat (Sec. II.D)
+
+@pytest.fixture(scope="module")
+def tp_system():
+    el, ely, _ = s.workload_tiny_slab(seed=4)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    return el, A, S, o.bvec(el, ely)
+
+
+def test_tp_deterministic_limit_is_the_cpm_charge(tp_system):
+    """Eq. (deissenbeck) with T = 0 and tau << dt: one step sets the capacitor charge to the CPM charge of
+    electrode 1 at Delta v0 with the same electrolyte (Eq. electrode-wise), and the site charges to the CPM
+    charges."""
+    el, A, S, b = tp_system
+    dv0 = 1.3
+    q_new, _, qs = o.tp_step(A, S, el, 0.37, dv0, b, dt=1.0, tau=1.0 / 60.0, T=0.0, X=0.0)
+    q_cpm = o.charges(S, el, [0.0, dv0], b)
+    assert abs(q_new - q_cpm[el.group == 1].sum()) < 1e-10 * abs(q_new)
+    assert np.linalg.norm(qs - q_cpm) < 1e-10 * np.linalg.norm(q_cpm)
+
+
+def test_tp_relaxes_geometrically(tp_system):
+    """T = 0: q_n - q_eq = a^n (q_0 - q_eq) with a = exp(-dt/tau) exactly (linear response of the circuit)."""
+    el, A, S, b = tp_system
+    dv0, dt, tau = 0.8, 1.0, 3.0
+    q_eq = o.charges(S, el, [0.0, dv0], b)[el.group == 1].sum()
+    q0 = q = -0.4
+    for n in range(1, 6):
+        q, _, _ = o.tp_step(A, S, el, q, dv0, b, dt, tau, 0.0, 0.0)
+        assert abs((q - q_eq) - math.exp(-n * dt / tau) * (q0 - q_eq)) < 1e-11
+
+
+def test_tp_fluctuation_dissipation():
+    """At temperature T the capacitor charge fluctuates about the CPM charge with variance k_B T C0 (the
+    fluctuation-dissipation relation the thermo-potentiostat is built on); 20,000 seeded steps of an 8-site
+    capacitor, variance within 6 % (3.5 standard errors) and mean within 4 standard errors."""
+    rng = np.random.default_rng(5)
+    xyz = np.array([[0, 0, 0], [4, 0, 0], [0, 4, 0], [4, 4, 0], [0, 0, 10], [4, 0, 10], [0, 4, 10], [4, 4, 10.0]])
+    el = _sites(xyz + 1.0, np.full(8, 1.805), [8.0, 8.0, 40.0], "slab", 0.35, 7.0, 1e-10,
+                group=[0, 0, 0, 0, 1, 1, 1, 1], n_groups=2)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    C0 = o.electrode_capacitance(S, el)[1, 1]
+    T, dv0, dt, tau = 300.0, 0.5, 1.0, 1.0 / math.log(2.0)     # a = 1/2
+    b = np.zeros(el.n)
+    q, qs = C0 * dv0, []
+    for k in range(20500):
+        q, _, _ = o.tp_step(A, S, el, q, dv0, b, dt, tau, T, rng.normal())
+        if k >= 500:
+            qs.append(q)
+    qs = np.asarray(qs)
+    var = o.K_B * T * C0
+    assert abs(qs.var() / var - 1) < 0.06
+    n_eff = len(qs) * (1 - 0.5) / (1 + 0.5)
+    assert abs(qs.mean() - C0 * dv0) < 4 * math.sqrt(var / n_eff)
