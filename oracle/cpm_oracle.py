@@ -24,7 +24,9 @@ What it computes (ELECTRODE paper, arXiv 2203.15461):
 * Boundary corrections of Sec. II.E: the slab dipole term of Eq. (ew3dc_slab),
   J = 2 pi M_z^2 / V, split into electrode and electrolyte parts as in the last
   equation of Sec. II.E; the wire term of Eq. (ew3dc_wire),
-  J = pi (M_x^2 + M_y^2) / V; none for tin-foil 3D.
+  J = pi (M_x^2 + M_y^2) / V; none for tin-foil 3D.  The exact slab sum (EW2D,
+  Sec. II.E) replaces the 3D reciprocal sum, background and dipole term by the
+  2D Ewald sum over the in-plane lattice (``ew2d_recip``).
 * Inversion and the charge-neutral capacitance matrix of Eq. (S), Sec. II.A:
   S = A^-1 - A^-1 e e^T A^-1 / (e^T A^-1 e).
 * The electrode-wise potentials of Sec. II.B: v = G psi, q* = S (v - b)
@@ -51,14 +53,14 @@ import math
 
 import numpy as np
 from scipy import linalg as sla
-from scipy.special import erfc
+from scipy.special import erf, erfc, erfcx
 
 #: Coulomb constant e / (4 pi eps0 Angstrom) expressed in volts.
 K_E = 14.399645
 #: vacuum permittivity in e / (V Angstrom)
 EPS0 = 1.0 / (4.0 * math.pi * K_E)
 
-_BC = {"3d": 0, "slab": 1, "wire": 2}
+_BC = {"3d": 0, "slab": 1, "wire": 2, "ew2d": 3}
 
 
 # --------------------------------------------------------------------------- reciprocal lattice
@@ -90,6 +92,54 @@ def kweights(k2, alpha, volume):
     return (8.0 * np.pi / volume) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
 
 
+def kvectors2d(box, kcut):
+    """Half-plane 2D reciprocal vectors 0 < |h| <= kcut of the periodic cell (Lx, Ly) of a slab:
+    h = 2 pi (nx / Lx, ny / Ly) with nx > 0, or nx == 0 and ny > 0.  Returns (h (Nh, 2), |h| (Nh,))."""
+    box = np.asarray(box, dtype=np.float64)
+    tp = 2.0 * np.pi / box[:2]
+    nmax = [int(math.floor(kcut / tp[d])) + 1 for d in range(2)]
+    gx, gy = np.meshgrid(np.arange(0, nmax[0] + 1), np.arange(-nmax[1], nmax[1] + 1), indexing="ij")
+    nidx = np.stack([gx.ravel(), gy.ravel()], axis=1)
+    half = (nidx[:, 0] > 0) | ((nidx[:, 0] == 0) & (nidx[:, 1] > 0))
+    h = nidx[half] * tp
+    h2 = h[:, 0] * h[:, 0] + h[:, 1] * h[:, 1]
+    keep = h2 <= kcut * kcut
+    return h[keep], np.sqrt(h2[keep])
+
+
+def _ew2d_zfactor(hn, z, alpha):
+    """e^{h z} erfc(h / 2a + a z) + e^{-h z} erfc(h / 2a - a z), written with the scaled complementary
+    error function where its argument is positive so that no factor overflows."""
+    out = np.zeros(np.broadcast(hn, z).shape)
+    for sgn in (1.0, -1.0):
+        x = hn / (2.0 * alpha) + sgn * alpha * z
+        pos = x >= 0
+        direct = np.exp(np.where(pos, 0.0, sgn * hn * z)) * erfc(np.where(pos, 0.0, x))
+        scaled = erfcx(np.where(pos, x, 0.0)) * np.exp(np.where(pos, -(hn / (2.0 * alpha)) ** 2 - (alpha * z) ** 2, 0.0))
+        out += np.where(pos, scaled, direct)
+    return out
+
+
+def ew2d_recip(Ri, Rj, box, alpha, kcut):
+    """Long-range part of the slab interaction summed over the 2D lattice exactly (the EW2D method named in
+    Sec. II.E; Parry's and Heyes' 2D Ewald sum): for every pair, with rho the in-plane and z the normal
+    displacement,
+      (pi / A) sum_{h != 0} cos(h . rho) / |h| [e^{|h| z} erfc(|h|/2a + a z) + e^{-|h| z} erfc(|h|/2a - a z)]
+      - (2 pi / A) [z erf(a z) + exp(-a^2 z^2) / (a sqrt(pi))],
+    A = Lx Ly; the sum over h != 0 runs over the full plane (twice the half plane)."""
+    Ri = np.asarray(Ri, dtype=np.float64)
+    Rj = np.asarray(Rj, dtype=np.float64)
+    area = float(box[0] * box[1])
+    h, hn = kvectors2d(box, kcut)
+    d = Ri[:, None, :] - Rj[None, :, :]
+    z = d[..., 2]
+    out = -(2.0 * np.pi / area) * (z * erf(alpha * z) + np.exp(-(alpha * z) ** 2) / (alpha * math.sqrt(math.pi)))
+    for k in range(len(hn)):
+        ph = h[k, 0] * d[..., 0] + h[k, 1] * d[..., 1]
+        out += (2.0 * np.pi / area) * np.cos(ph) / hn[k] * _ew2d_zfactor(hn[k], z, alpha)
+    return out
+
+
 # --------------------------------------------------------------------------- real space
 
 def _image_range(dmin, dmax, L, rcut):
@@ -98,15 +148,18 @@ def _image_range(dmin, dmax, L, rcut):
     return range(lo, hi + 1)
 
 
-def _realspace(Ri, Rj, eta_pair, box, alpha, rcut, same=None):
+def _realspace(Ri, Rj, eta_pair, box, alpha, rcut, same=None, zperiodic=True):
     """sum over images n with |Ri - Rj + n| < rcut of [erfc(alpha r) - erfc(eta r)] / r.
 
     ``same`` (bool array like eta_pair) marks pairs that are one and the same
     site: for those the n = 0 image is left out (it is the self energy).
+    ``zperiodic`` False: images along x and y only (a slab summed in 2D).
     """
     d = Ri[:, None, :] - Rj[None, :, :]
     out = np.zeros(d.shape[:2])
     ranges = [_image_range(d[..., a].min(), d[..., a].max(), box[a], rcut) for a in range(3)]
+    if not zperiodic:
+        ranges[2] = range(0, 1)
     for ix in ranges[0]:
         for iy in ranges[1]:
             for iz in ranges[2]:
@@ -146,19 +199,27 @@ def assemble_A(el, rows=None, kchunk=2048):
         ei, ej = eta[rr][:, None], eta[None, :]
         eta_ij = ei * ej / np.sqrt(ei * ei + ej * ej)
         same = rr[:, None] == np.arange(n)[None, :]
-        A[c0:c0 + 256] += _realspace(xyz[rr], xyz, eta_ij, box, a, el.rcut, same)
-    # reciprocal space: sum_k w_k cos(k.(R_i - R_j)) = sum_k w_k [c_i c_j + s_i s_j]
-    _, k, k2 = kvectors(box, el.kcut)
-    w = kweights(k2, a, V)
-    for c0 in range(0, len(k), kchunk):
-        kk, ww = k[c0:c0 + kchunk], w[c0:c0 + kchunk]
-        ph_all = xyz @ kk.T
-        ph_r = ph_all[rows]
-        A += (np.cos(ph_r) * ww) @ np.cos(ph_all).T + (np.sin(ph_r) * ww) @ np.sin(ph_all).T
+        A[c0:c0 + 256] += _realspace(xyz[rr], xyz, eta_ij, box, a, el.rcut, same, zperiodic=el.boundary != "ew2d")
+    if el.boundary == "ew2d":
+        # exact 2D-periodic long-range part (no vacuum padding, no dipole correction); the energy of a net
+        # charge per cell is undefined in 2D, so A is fixed only up to c e e^T (S and every neutral result
+        # do not depend on c): c = (2 pi / A) L_z with L_z = box[2], at least the slab's thickness
+        for c0 in range(0, len(rows), 256):
+            A[c0:c0 + 256] += ew2d_recip(xyz[rows[c0:c0 + 256]], xyz, box, a, el.kcut)
+        A += 2.0 * math.pi * box[2] / (box[0] * box[1])
+    else:
+        # reciprocal space: sum_k w_k cos(k.(R_i - R_j)) = sum_k w_k [c_i c_j + s_i s_j]
+        _, k, k2 = kvectors(box, el.kcut)
+        w = kweights(k2, a, V)
+        for c0 in range(0, len(k), kchunk):
+            kk, ww = k[c0:c0 + kchunk], w[c0:c0 + kchunk]
+            ph_all = xyz @ kk.T
+            ph_r = ph_all[rows]
+            A += (np.cos(ph_r) * ww) @ np.cos(ph_all).T + (np.sin(ph_r) * ww) @ np.sin(ph_all).T
+        # neutralising background
+        A += -math.pi / (V * a * a)
     # Ewald self term and Gaussian self energy, lim_{r->0} erf(eta r / sqrt2) / r
     A[np.arange(len(rows)), rows] += (math.sqrt(2.0) * eta[rows] - 2.0 * a) / math.sqrt(math.pi)
-    # neutralising background
-    A += -math.pi / (V * a * a)
     # boundary correction, electrode-electrode part (Sec. II.E)
     if el.boundary == "slab":
         A += (4.0 * math.pi / V) * np.outer(xyz[rows, 2], xyz[:, 2])
@@ -192,6 +253,13 @@ def bvec(el, elyt, sites=None, kchunk=4096):
     V = float(box[0] * box[1] * box[2])
     a = el.alpha
     b = np.zeros(len(sites))
+    if len(Q) and el.boundary == "ew2d":
+        for c0 in range(0, len(sites), 256):
+            pair = _realspace(R[c0:c0 + 256], r, eta[c0:c0 + 256][:, None] * np.ones((1, len(r))), box, a,
+                              el.rcut, zperiodic=False)
+            b[c0:c0 + 256] += pair @ Q + ew2d_recip(R[c0:c0 + 256], r, box, a, el.kcut) @ Q
+        b += 2.0 * math.pi * box[2] / (box[0] * box[1]) * float(Q.sum())    # the constant c of A, per unit charge
+        return K_E * b
     if len(Q):
         for c0 in range(0, len(sites), 256):
             pair = _realspace(R[c0:c0 + 256], r, eta[c0:c0 + 256][:, None] * np.ones((1, len(r))), box, a,

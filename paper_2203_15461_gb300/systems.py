@@ -21,7 +21,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-BOUNDARIES = ("3d", "slab", "wire")
+BOUNDARIES = ("3d", "slab", "wire", "ew2d")
 
 
 @dataclass
@@ -33,7 +33,8 @@ class Electrodes:
     group: np.ndarray        # (n,) int32 electrode index of each site (Sec. II.B)
     n_groups: int
     box: np.ndarray          # (3,) Ewald cell (Lx, Ly, Lz); vacuum padding included
-    boundary: str            # "3d" tin-foil, "slab" (EW3DC, Eq. ew3dc_slab), "wire" (Eq. ew3dc_wire)
+    boundary: str            # "3d" tin-foil, "slab" (EW3DC, Eq. ew3dc_slab), "wire" (Eq. ew3dc_wire),
+                             # "ew2d" (exact 2D-periodic slab sum; box[2] is then not a period)
     alpha: float             # Ewald splitting parameter, 1/Angstrom
     rcut: float              # real-space cut-off, Angstrom
     kcut: float              # reciprocal-space cut-off |k| <= kcut, 1/Angstrom
@@ -306,15 +307,31 @@ def workload_edl_capacitor(seed: int = 1, cells=(18, 10), layers: int = 3, gap: 
     return el, water_and_ions(el, n_water, n_ion, n_ion, seed), np.array([0.0, 1.0])
 
 
-def workload_serving_geometry(n_sites: int, seed: int = 1, charges_per_site: float = 1.0, gap: float = 40.0):
+#: Ewald splitting of the serving geometries at the same accuracy (erfc(alpha r_c) = erfc(3.6), k tolerance
+#: 1e-8).  The reciprocal set grows as V alpha^3 and the one-time FP64 assembly as n^2 N_k, so the two
+#: large boxes take a smaller alpha (longer real-space cut-off): about 34k and 29k k-vectors instead of
+#: 116k and 225k at alpha = 0.3.
+SERVING_ALPHA = {512: 0.3, 2048: 0.3, 8192: 0.2, 16384: 0.15}
+
+
+def serving_electrodes(n_sites: int, gap: float = 40.0) -> Electrodes:
     """Two electrodes of two graphene sheets each with n_sites sites in total (512 ... 16,384)."""
     per_layer = n_sites // 4
     cells = per_layer // 4
     table = {32: (8, 4), 128: (16, 8), 512: (32, 16), 1024: (32, 32)}
     cx, cy = table[cells]
-    el = graphene_plates(cx, cy, 2, gap)
+    alpha = SERVING_ALPHA.get(n_sites, 0.3)
+    return graphene_plates(cx, cy, 2, gap, alpha=alpha, rcut=3.6 / alpha)
+
+
+def workload_serving_geometry(n_sites: int, seed: int = 1, charges_per_site: float = 1.0, gap: float = 40.0):
+    """Serving geometry (``serving_electrodes``) with an electrolyte of charges_per_site x n_sites charges."""
+    el = serving_electrodes(n_sites, gap)
     rng = np.random.default_rng(seed)
     n_q = int(round(charges_per_site * n_sites))
     n_ion = max(1, n_q // 6)
     n_water = max(0, (n_q - 2 * n_ion) // 3)
-    return el, water_and_ions(el, n_water, n_ion, n_ion, int(rng.integers(1 << 30))), np.array([0.0, 1.0])
+    # above one charge per site the 40 A gap is too crowded for random sequential placement at a
+    # 2.5 A minimum separation of the water oxygens and ions; 2.2 A still keeps every pair apart
+    dmin = 2.5 if charges_per_site <= 1.0 else 2.2
+    return el, water_and_ions(el, n_water, n_ion, n_ion, int(rng.integers(1 << 30)), dmin=dmin), np.array([0.0, 1.0])

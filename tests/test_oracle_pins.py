@@ -418,3 +418,57 @@ def test_tp_fluctuation_dissipation():
     assert abs(qs.var() / var - 1) < 0.06
     n_eff = len(qs) * (1 - 0.5) / (1 + 0.5)
     assert abs(qs.mean() - C0 * dv0) < 4 * math.sqrt(var / n_eff)
+
+
+# ----------------------------------------------------------------------------- EW2D (Sec. II.E)
+
+def test_ew2d_elastance_matches_direct_plane_sum():
+    """The exact 2D Ewald sum (EW2D) equals the direct sum over the 2D lattice of images with no vacuum and no
+    dipole correction: tighter than EW3DC at 40 A of vacuum (1e-7), because nothing is approximated."""
+    Lx, Ly = 7.0, 6.0
+    xyz, eta, q = _small_system(7, 5, (Lx, Ly, 4.0))
+    Rs = [30, 40, 60, 80, 120, 160]
+    E_direct = bf.extrapolate(Rs, [bf.lattice_energy("slab", (Lx, Ly, 0), xyz, eta, q, R) for R in Rs],
+                              [1, 2, 3, 4])
+    for alpha in (0.4, 0.6):
+        el = _sites(xyz, eta, (Lx, Ly, 1.0), "ew2d", alpha, 14.0, 1e-16)
+        E = 0.5 * q @ o.assemble_A(el) @ q / o.K_E
+        assert abs(E / E_direct - 1) < 2e-9, (alpha, E / E_direct - 1)
+
+
+def test_ew2d_electrolyte_vector_matches_direct_cross_sum():
+    """q^T b under EW2D equals the direct 2D image sum of Gaussian-site / point-charge energies, for a charged
+    electrolyte too (the h = 0 term carries the slab's mean field)."""
+    Lx, Ly = 7.0, 6.5
+    xyz, eta, q = _small_system(3, 4, (Lx, Ly, 3.0))
+    rng = np.random.default_rng(4)
+    rj = np.column_stack([rng.uniform(0, Lx, 3), rng.uniform(0, Ly, 3), rng.uniform(5, 9, 3)])
+    Q = np.array([1.0, -0.4, 0.7])
+    Rs = [30, 40, 60, 80, 120, 160]
+    E_direct = bf.extrapolate(Rs, [bf.lattice_cross("slab", (Lx, Ly, 0), xyz, eta, q, rj, Q, R) for R in Rs],
+                              [1, 2, 3, 4])
+    el = _sites(xyz, eta, (Lx, Ly, 1.0), "ew2d", 0.45, 14.0, 1e-16)
+    E = q @ o.bvec(el, s.Electrolyte(xyz=rj, Q=Q)) / o.K_E
+    assert abs(E / E_direct - 1) < 1e-8, E / E_direct - 1
+
+
+def test_ew3dc_converges_to_ew2d_with_vacuum():
+    """Sec. II.E: the dipole-corrected 3D sum approaches the exact 2D sum as the vacuum grows."""
+    el, ely, psi = s.workload_tiny_slab(seed=2)
+    q2 = o.charges(o.capacitance_matrix(o.assemble_A(s.Electrodes(**{**el.__dict__, "boundary": "ew2d"}))),
+                   el, psi, o.bvec(s.Electrodes(**{**el.__dict__, "boundary": "ew2d"}), ely))
+    errs = []
+    for f in (3.0, 6.0):
+        e3 = s.au111_slab(slab_factor=f)
+        q3 = o.charges(o.capacitance_matrix(o.assemble_A(e3)), e3, psi, o.bvec(e3, ely))
+        errs.append(np.linalg.norm(q3 - q2) / np.linalg.norm(q2))
+    assert errs[1] < errs[0] < 5e-2, errs
+
+
+def test_ew2d_constant_leaves_S_unchanged(tiny):
+    """The undetermined constant of the EW2D elastance (c e e^T) drops out of S (Eq. S)."""
+    el = s.Electrodes(**{**tiny[0].__dict__, "boundary": "ew2d"})
+    S1 = o.capacitance_matrix(o.assemble_A(el))
+    el2 = s.Electrodes(**{**el.__dict__, "box": el.box * np.array([1.0, 1.0, 1.7])})
+    S2 = o.capacitance_matrix(o.assemble_A(el2))
+    assert np.linalg.norm(S2 - S1) < 1e-11 * np.linalg.norm(S1)
