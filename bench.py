@@ -218,66 +218,252 @@ def real_pairs(el, xyz_steps, Q, ne, m, step):
     return tot
 
 
-def kernel_work(ctx, el, nk, ne, m, pairs=None, tensor=False):
-    """Algorithmic work per launch of the per-step kernels (flops or bytes).
+# Algorithmic work per unit (SURVEY-level cost model of the method, not of the kernels' own
+# shortcuts): a real-space pair inside r_c costs two erfc, a square root and a division (60 flop,
+# also for the tabulated single-precision kernel); a reciprocal term costs 16 flop per (charge, k)
+# for the structure factor and 14 per (site, k) for the site sum on the CUDA cores.  On the tensor
+# cores the contraction itself is counted (one complex multiply-add, 8 flop, per (charge, k) and
+# per (site, k)) against the tensor rate of the emulated FP32 product.
+FLOP_PAIR, FLOP_SF, FLOP_SITE, FLOP_CMAC = 60.0, 16.0, 14.0, 8.0
 
-    With ``tensor`` the two reciprocal contractions run on the tensor cores ("tflop": the same
-    algorithmic flops, measured against the tensor-core peak of the emulated FP32 product)."""
+
+def kernel_work(el, nk, ne, m, pairs=None, tensor=False, s_bytes=4):
+    """Algorithmic work per launch of the per-step kernels: (kind, amount) with kind flop | tflop | byte."""
     n = el.n
-    fk = "tflop" if tensor else "flop"
-    w = {
-        "sf": (fk, 8.0 * ne * nk * m),                # one complex multiply-add per (charge, k)
-        "site": (fk, 8.0 * n * nk * m),               # one complex multiply-add per (site, k)
-        "gemv": ("byte", 4.0 * n * n * ((m + 7) // 8)),   # S streamed once (FP32) per 8 replicas
-    }
+    if tensor:
+        w = {"sf": ("tflop", FLOP_CMAC * ne * nk * m), "site": ("tflop", FLOP_CMAC * n * nk * m)}
+    else:
+        w = {"sf": ("flop", FLOP_SF * ne * nk * m), "site": ("flop", FLOP_SITE * n * nk * m)}
+    # S streamed once per pass of eight replicas (single precision) or once per replica (FP64)
+    w["gemv"] = ("byte", float(s_bytes) * n * n * (((m + 7) // 8) if s_bytes == 4 else m))
     if pairs is not None:
-        w["real"] = ("flop", 16.0 * pairs)            # tabulated pair function per pair inside rcut
+        w["real"] = ("flop", FLOP_PAIR * pairs)
     return w
 
 
-def cpu_baseline(el, ely, psi, frac=8):
-    """The oracle's update, timed on a bounded sample and scaled to one full update."""
+def roofline(prof, work, peaks, src, names, alu_peak, alu_src, ms_step):
+    """Roofline entry of the kernel with the largest share of the kernel-by-kernel step."""
+    top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
+    avg_ms = prof[top][0] / prof[top][1]
+    kind, amount = work.get(top, ("flop", float("nan")))
+    if kind == "tflop":
+        # fp16 tensor rate = the measured bf16 rate (same nominal peak); three fp16 products per FP32 product
+        peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": amount / (avg_ms / 1e3) / 1e12, "peak": peak,
+                "peak_source": f"bf16_tflops ({src}) / 3: two-term fp16 operands, three products per FP32 product"}
+    elif kind == "flop":
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": amount / (avg_ms / 1e3) / 1e12, "peak": alu_peak,
+                "peak_source": alu_src}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": amount / (avg_ms / 1e3) / 1e9, "peak": peak,
+                "peak_source": f"hbm_gbs ({src})"}
+    roof["kernel"] = names.get(top, top)
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["ms_per_launch"] = avg_ms
+    roof["share_of_step"] = prof[top][0] / ms_step
+    roof["all_kernels"] = {kk: {"ms_per_launch": prof[kk][0] / max(1, prof[kk][1]),
+                                "achieved": (work[kk][1] / (prof[kk][0] / max(1, prof[kk][1]) / 1e3)
+                                             / (1e9 if work[kk][0] == "byte" else 1e12)),
+                                "unit": "GB/s" if work[kk][0] == "byte" else "TFLOP/s"}
+                           for kk in work if kk in prof and prof[kk][1] > 0}
+    return top, roof
+
+
+# ----------------------------------------------------------------------------- CPU baseline leg
+# The FP64 oracle as it stands, on the host cores of the GPU box.  Only this leg runs the oracle:
+# its own timing, and the oracle charges that the GPU results are compared with.
+
+_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+class _OneThreadEnv:
+    """Processes started inside this block run their BLAS on one thread."""
+
+    def __enter__(self):
+        self.saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+        os.environ.update({k: "1" for k in _THREAD_VARS})
+
+    def __exit__(self, *a):
+        for k, v in self.saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _oracle_sites(args):
+    """Worker: the oracle's b at a chunk of sites (single thread), with its time."""
+    el, ely, sites = args
     from oracle import cpm_oracle as o
-    sites = np.arange(0, el.n, frac)
-    box = np.asarray(el.box)
-    V = float(np.prod(box))
-    _, k, k2 = o.kvectors(box, el.kcut)
-    ksub = np.arange(0, len(k), frac)
     t0 = time.perf_counter()
-    bre = o.bvec(type(el)(**{**el.__dict__, "kcut": 1e-9}), ely, sites=sites)      # real space (+ tiny terms)
+    b = o.bvec(el, ely, sites=sites)
+    return b, time.perf_counter() - t0
+
+
+def _oracle_rows(args):
+    el, rows = args
+    from oracle import cpm_oracle as o
+    return o.assemble_A(el, rows=rows)
+
+
+def _serial_update(el, ely, psi, req, res):
+    """Worker: one complete oracle update on one thread: b for every site, then q = S (v - b) with
+    the S the parent sends once it has it; reports both times and the results."""
+    from oracle import cpm_oracle as o
+    t0 = time.perf_counter()
+    b = o.bvec(el, ely)
+    tb = time.perf_counter() - t0
+    S = req.get()
+    t0 = time.perf_counter()
+    q = o.charges(S, el, psi, b)
+    res.put((tb, time.perf_counter() - t0, b, q))
+
+
+class OraclePool:
+    """The oracle over all host cores (spawned processes, one BLAS thread each): site chunks of b,
+    row chunks of A.  Each chunk of b evaluates its configuration's structure factor once."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or (os.cpu_count() or 1)
+        with _OneThreadEnv():
+            self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+    def assemble_A(self, el):
+        chunks = [c for c in np.array_split(np.arange(el.n), min(el.n, self.procs)) if len(c)]
+        return np.vstack(self.pool.map(_oracle_rows, [(el, c) for c in chunks]))
+
+    def capacitance(self, el):
+        from oracle import cpm_oracle as o
+        return o.capacitance_matrix(self.assemble_A(el))
+
+    def update(self, el, ely, psi, S):
+        """One full oracle update on all cores: (q, b, wall seconds, summed worker seconds)."""
+        from oracle import cpm_oracle as o
+        chunks = [c for c in np.array_split(np.arange(el.n), min(el.n, self.procs)) if len(c)]
+        t0 = time.perf_counter()
+        parts = self.pool.map(_oracle_sites, [(el, ely, c) for c in chunks])
+        b = np.concatenate([p[0] for p in parts])
+        q = o.charges(S, el, psi, b)
+        return q, b, time.perf_counter() - t0, sum(p[1] for p in parts)
+
+
+class SerialOracle:
+    """One oracle update of one configuration in a single-threaded spawned process, started before
+    the first GPU call and run beside the GPU legs (it keeps one of the host's cores busy)."""
+
+    def __init__(self, el, ely, psi):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.req, self.res = ctx.Queue(), ctx.Queue()
+        with _OneThreadEnv():
+            self.proc = ctx.Process(target=_serial_update, args=(el, ely, psi, self.req, self.res), daemon=True)
+            self.proc.start()
+
+    def finish(self, S, timeout=1800.0):
+        self.req.put(S)
+        tb, tq, b, q = self.res.get(timeout=timeout)
+        self.proc.join(timeout=60)
+        return tb, tq, b, q
+
+
+def cpu_baseline_edl(pool, serial, el, ely, psi):
+    """The oracle on the headline system (one configuration, every site, every k-vector): S by the
+    oracle over all cores (not timed: a one-time cost), then one full update single-threaded (the
+    serial worker) and one on all cores; the oracle's q of that configuration is returned too."""
+    t0 = time.perf_counter()
+    S = pool.capacitance(el)
+    t_S = time.perf_counter() - t0
+    tb, tq, b1, q1 = serial.finish(S)
+    q, b, wall, cpu_s = pool.update(el, ely, psi, S)
+    out = {"value": 1.0 / wall, "unit": "updates/s", "cores": pool.procs, "kind": "oracle",
+           "sample": ("one complete, unsampled FP64 oracle update of the EDL capacitor (4,320 sites, 5,700 charges, "
+                      f"every k-vector): b at all sites in {pool.procs} processes over site chunks (each evaluates "
+                      "the structure factor of all charges), then q = S (v - b); S from the oracle beforehand"),
+           "single_thread": {"value": 1.0 / (tb + tq), "seconds": tb + tq, "cores": 1,
+                             "sample": "the same update in one single-threaded process"},
+           "all_cores_seconds": wall, "worker_cpu_seconds": cpu_s, "oracle_S_seconds": t_S,
+           "agree_single_vs_all_cores": float(np.abs(q - q1).max() / np.abs(q1).max())}
+    return out, S, q1
+
+
+def cpu_baseline_small(pool, el_tiny, tiny_elyts, psi_tiny, el_coax10):
+    """Oracle values of the small configurations: q of sampled cfg3 replicas and of the cfg1 step,
+    and the co-axial C0/L of the 10-cell tube (the per-length value the 100-cell tube must repeat)."""
+    from oracle import cpm_oracle as o
+    S = o.capacitance_matrix(o.assemble_A(el_tiny))
+    q = {r: o.charges(S, el_tiny, psi_tiny[r], o.bvec(el_tiny, e)) for r, e in tiny_elyts.items()}
+    Sc = pool.capacitance(el_coax10)
+    c0 = float(o.electrode_capacitance(Sc, el_coax10)[1, 1] / el_coax10.box[2])
+    return q, c0
+
+
+def bench_tiny_flow(torch, CPM, s, n_updates=10):
+    """Configuration 1: the 216-site Au(111) capacitor in FP64, the whole flow: assemble, invert and
+    ten sequential charge updates (positions random-walked by N(0, 0.05 A) per update)."""
+    el, ely, psi = s.workload_tiny_slab(seed=1)
+    rng = np.random.default_rng(2024)
+    confs = []
+    cur = ely
+    for _ in range(n_updates):
+        cur = s.jitter(cur, 0.05, rng)
+        confs.append(cur)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64")
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    ctx.cpm_assemble(dev(el.xyz), dev(el.eta), dev(el.group.astype(np.int32)), el.n_groups)
+    torch.cuda.synchronize()
     t1 = time.perf_counter()
-    rho = o.structure_factor(k[ksub], ely)
+    ctx.cpm_invert()
     t2 = time.perf_counter()
-    w = o.kweights(k2[ksub], el.alpha, V)
-    ph = el.xyz[sites] @ k[ksub].T
-    _ = (np.cos(ph) * rho.real + np.sin(ph) * rho.imag) @ w
+    xs = [dev(c.xyz) for c in confs]
+    Qd = dev(ely.Q)
+    pd = dev(psi[None])
+    b = torch.empty((1, el.n), dtype=torch.float64, device="cuda")
+    q = torch.empty_like(b)
+    qt = torch.empty(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t3 = time.perf_counter()
-    Sfake = np.eye(el.n)
-    v = o.site_potentials(el, psi)
+    e0.record()
+    for x in xs:
+        ctx.cpm_bvec(1, ely.n, x, Qd, b)
+        ctx.cpm_update(1, pd, b, q, qt)
+    e1.record()
+    torch.cuda.synchronize()
     t4 = time.perf_counter()
-    _ = Sfake @ (v - np.zeros(el.n))
-    t5 = time.perf_counter()
-    per_update = (t1 - t0) * frac + (t2 - t1) * frac + (t3 - t2) * frac * frac + (t5 - t4)
-    return {"value": 1.0 / per_update, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"numpy FP64 oracle on the same system: real-space b at 1/{frac} of the sites, structure "
-                       f"factor over 1/{frac} of the k-vectors, site k-sum over both subsets, one n x n matvec; "
-                       f"each part scaled by its sampled fraction to one full update (elementwise numpy on one "
-                       f"thread, BLAS on {os.cpu_count()})"),
-            "sample_seconds": t5 - t0}
+    ms_upd = e0.elapsed_time(e1) / n_updates
+    out = {"workload": "au111_tiny_216, FP64: assemble + invert + 10 sequential updates", "n_sites": el.n,
+           "n_charges": ely.n, "assemble_ms": 1e3 * (t1 - t0), "invert_ms": 1e3 * (t2 - t1),
+           "update_ms": ms_upd, "updates_per_s": 1e3 / ms_upd, "flow_ms": 1e3 * (t2 - t0 + t4 - t3),
+           "max_abs_qtot": float(qt.abs().max())}
+    qlast = q.cpu().numpy()[0]
+    ctx.close()
+    return out, (el, confs[-1], psi, qlast)
 
 
-def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256, k_prec="fp32"):
-    """256 replicas of the 216-site Au(111) capacitor per step (one shared S), graph-captured."""
+def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256, k_prec="fp32", sample=(0, 85, 170, 255)):
+    """Configuration 3: 256 replicas of the 216-site Au(111) capacitor per step (one shared S,
+    each its own seeded electrolyte), graph-captured, with S in FP64, FP32 and split bf16 (three
+    terms, tensor cores).  Returns the q of sampled replicas of the last step for the oracle leg."""
     el, _, psi = s.workload_tiny_slab(seed=1)
     xyz, Q, ne = make_trajectories(el, lambda sd: s.ions_in_gap(el, 100, seed=sd), m, K + W, 5000)
+    psis = np.column_stack([np.zeros(m), np.linspace(0.0, 2.0, m)])
     out = {"workload": "au111_tiny_216 x 256 replicas", "replicas_per_step": m, "k_prec": k_prec}
-    for s_prec in ("fp32", "bf16x3"):
+    qs = {}
+    for s_prec in ("fp64", "fp32", "bf16x3"):
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
             ctx = CPM.for_electrodes(el, s_prec=s_prec, k_prec=k_prec, stream=st).setup(el)
             dx = torch.as_tensor(xyz[0], device="cuda").clone()
             dQ = torch.as_tensor(Q, device="cuda")
-            dp = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
+            dp = torch.as_tensor(psis, device="cuda")
             b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
             q = torch.empty_like(b)
             qt = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -298,112 +484,243 @@ def bench_batched_tiny(torch, CPM, s, flush, K, W, m=256, k_prec="fp32"):
         out[f"value_{s_prec}_S"] = m * K / (tot / 1e3)
         out[f"ms_per_step_{s_prec}_S"] = tot / K
         out[f"max_abs_qtot_{s_prec}_S"] = float(qt.abs().max())
+        qn = q.cpu().numpy()
+        qs[s_prec] = {r: qn[r] for r in sample}
         ctx.close()
     out["unit"] = "updates/s"
+    last = {r: s.Electrolyte(xyz=xyz[W + K - 1, r * ne:(r + 1) * ne], Q=Q[r * ne:(r + 1) * ne]) for r in sample}
+    return out, (el, last, {r: psis[r] for r in sample}, qs)
+
+
+def bench_coax(torch, CPM, s, cells=100, alpha=0.15, rcut=24.0):
+    """Configuration 5: the co-axial (10,10)/(20,20) nanotube capacitor, 100 cells (12,000 sites),
+    1D boundary term, vacuum.  FP64 assembly of A, then the capacitance C0 two ways: FP64 Cholesky,
+    inverse and projection (S, then G^T S G), and FP32 Cholesky with FP64 iterative refinement
+    (no inverse).  Times of each stage and C0/L of each against 2 pi eps0 / ln(R2/R1)."""
+    el = s.coaxial_tubes(cells, alpha=alpha, rcut=rcut, ktol=1e-8)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    ctx = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64")
+    x, e, g = dev(el.xyz), dev(el.eta), dev(el.group.astype(np.int32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.cpm_assemble(x, e, g, el.n_groups)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    C_ir, iters, resid = ctx.cpm_capacitance_ir()
+    t2 = time.perf_counter()
+    ctx.cpm_invert()
+    C64 = ctx.cpm_capacitance()
+    t3 = time.perf_counter()
+    nk = int(len(ctx.cpm_kvectors()))
+    ctx.close()
+    L = float(el.box[2])
+    eps0 = 1.0 / (4.0 * math.pi * 14.399645)
+    ana = 2.0 * math.pi * eps0 / math.log(s.tube_radius(20) / s.tube_radius(10))
+    n = el.n
+    return {"workload": f"coaxial (10,10)/(20,20) tubes, {cells} cells, {n} sites, 1D correction",
+            "n_sites": n, "n_kvectors": nk, "alpha": alpha, "rcut": rcut,
+            "assemble_s": t1 - t0, "assemble_recip_tflops_fp64": 2.0 * n * n * nk / (t1 - t0) / 1e12,
+            "fp64_cholesky_inverse_s": t3 - t2, "fp32_cholesky_ir_s": t2 - t1, "ir_sweeps": iters,
+            "ir_residual": resid, "C0_per_L_fp64": float(C64[1, 1]) / L, "C0_per_L_fp32_ir": float(C_ir[1, 1]) / L,
+            "rel_diff_fp32_ir_vs_fp64": abs(float(C_ir[1, 1]) / float(C64[1, 1]) - 1.0),
+            "C0_per_L_analytic": ana, "ratio_to_analytic": float(C64[1, 1]) / L / ana}
+
+
+def bench_s_products(torch, CPM, s, flush, peaks, src, sizes=((8192, (32, 16)), (16384, (32, 32))),
+                     ms=(8, 64, 128, 256), K=5, W=2):
+    """The S product alone where S is far larger than L2: two graphene electrodes of two sheets,
+    8,192 and 16,384 sites, assembled once with a small Ewald alpha (0.1, r_c = 35 A: few k-vectors,
+    the assembly stays short; the S product does not depend on the split).  For m replicas of a
+    random b: the single-precision S stream (k_gemv_tma, S read once per eight replicas) and the
+    persistent tensor-core product (k_tc_sb with its tuned tile plan, S as three bf16 planes read
+    once per launch), each through cpm_update with L2 flushed before every call; the kernels alone
+    from the library's per-kernel events."""
+    out = {}
+    bf16_peak, hbm = float(peaks.get("bf16_tflops", 1900.0)), float(peaks["hbm_gbs"])
+    for n_target, (cx, cy) in sizes:
+        el = s.graphene_plates(cx, cy, 2, 40.0, alpha=0.1, rcut=35.0)
+        n = el.n
+        t0 = time.perf_counter()
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
+        st.synchronize()
+        res = {"n_sites": n, "setup_seconds": time.perf_counter() - t0, "s_fp32_bytes": 4.0 * n * n,
+               "s_bf16x3_bytes": 6.0 * n * n}
+        rng = np.random.default_rng(7)
+        for m in ms:
+            with torch.cuda.stream(st):
+                b = torch.as_tensor(rng.normal(0.0, 1.0, (m, n)), device="cuda")
+                psi = torch.as_tensor(np.tile([0.0, 1.0], (m, 1)), device="cuda")
+                q = torch.empty((m, n), dtype=torch.float64, device="cuda")
+                qt = torch.empty(m, dtype=torch.float64, device="cuda")
+            row = {}
+            q_prev = None
+            for prec in ("fp32", "bf16x3"):
+                ctx.cpm_set_s_prec(prec)
+                plan = ctx.cpm_gemm_plan(m) if prec == "bf16x3" else None
+                for _ in range(W):
+                    with torch.cuda.stream(st):
+                        ctx.cpm_update(m, psi, b, q, qt)
+                st.synchronize()
+                ctx.cpm_profile_read(reset=True)
+                ctx.cpm_profile(True)
+                evs = []
+                for _ in range(K):
+                    with torch.cuda.stream(st):
+                        flush()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(st)
+                        ctx.cpm_update(m, psi, b, q, qt)
+                        e1.record(st)
+                        evs.append((e0, e1))
+                st.synchronize()
+                ctx.cpm_profile(False)
+                prof = ctx.cpm_profile_read(reset=True)
+                t_upd = sum(a.elapsed_time(bb) for a, bb in evs) / K
+                r = {"update_ms": t_upd, "updates_per_s": m / (t_upd / 1e3),
+                     "max_abs_qtot": float(qt.abs().max())}
+                if prec == "fp32":
+                    kms = prof["gemv"][0] / max(1, prof["gemv"][1])
+                    nbytes = 4.0 * n * n * ((m + 7) // 8)
+                    r.update({"kernel": "k_gemv_tma", "kernel_ms": kms, "achieved_gbs": nbytes / (kms / 1e3) / 1e9,
+                              "hbm_frac": nbytes / (kms / 1e3) / 1e9 / hbm})
+                else:
+                    kms = prof["tcgemm"][0] / max(1, prof["tcgemm"][1])
+                    flop = 2.0 * n * n * m * 6
+                    nbytes = 6.0 * n * n
+                    r.update({"kernel": "k_tc_sb", "kernel_ms": kms, "plan": plan,
+                              "tflops_bf16": flop / (kms / 1e3) / 1e12,
+                              "tensor_frac": flop / (kms / 1e3) / 1e12 / bf16_peak,
+                              "s_gbs": nbytes / (kms / 1e3) / 1e9, "hbm_frac": nbytes / (kms / 1e3) / 1e9 / hbm,
+                              "bound": "tensor" if flop / (bf16_peak * 1e12) > nbytes / (hbm * 1e9) else "hbm"})
+                qn = q.cpu().numpy()
+                if q_prev is not None:
+                    r["rel_diff_vs_fp32"] = float(np.linalg.norm(qn - q_prev) / np.linalg.norm(q_prev))
+                q_prev = qn
+                row[prec] = r
+            row["bf16x3_speedup_vs_fp32"] = row["fp32"]["update_ms"] / row["bf16x3"]["update_ms"]
+            res[f"m{m}"] = row
+        ctx.close()
+        out[str(n)] = res
+    out["peaks"] = {"bf16_tflops": bf16_peak, "hbm_gbs": hbm, "source": src}
+    out["l2"] = "flushed before every update"
     return out
 
 
-def bench_s_stream(torch, CPM, s, flush, peaks, K=10, W=3, m=8):
-    """The single-precision S product alone at the size where S is far larger than L2: two graphene
-    electrodes of two sheets, 16,384 sites (S32 = 1.07 GB), assembled with a small Ewald alpha (0.1,
-    r_c = 35 A: few k-vectors, the assembly stays short; the S product does not depend on the split).
-    b is random; per update the library's profiler times the S stream (k_gemv_tma) on the context
-    stream, with L2 flushed before every update."""
-    import time as _t
-    el = s.graphene_plates(32, 32, 2, 40.0, alpha=0.1, rcut=35.0)
-    n = el.n
-    t0 = _t.perf_counter()
-    st = torch.cuda.Stream()
-    with torch.cuda.stream(st):
-        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
-    st.synchronize()
-    setup_s = _t.perf_counter() - t0
-    rng = np.random.default_rng(7)
-    with torch.cuda.stream(st):
-        b = torch.as_tensor(rng.normal(0.0, 1.0, (m, n)), device="cuda")
-        psi = torch.as_tensor(np.tile([0.0, 1.0], (m, 1)), device="cuda")
-        q = torch.empty((m, n), dtype=torch.float64, device="cuda")
-        qt = torch.empty(m, dtype=torch.float64, device="cuda")
-    for _ in range(W):
-        with torch.cuda.stream(st):
-            ctx.cpm_update(m, psi, b, q, qt)
-    st.synchronize()
-    ctx.cpm_profile_read(reset=True)
-    ctx.cpm_profile(True)
-    for _ in range(K):
-        with torch.cuda.stream(st):
-            flush()
-            ctx.cpm_update(m, psi, b, q, qt)
-    st.synchronize()
-    ctx.cpm_profile(False)
-    prof = ctx.cpm_profile_read(reset=True)
-    ms = prof["gemv"][0] / max(1, prof["gemv"][1])
-    nbytes = 4.0 * n * n
-    gbs = nbytes / (ms / 1e3) / 1e9
-    hbm = float(peaks["hbm_gbs"])
-    ctx.close()
-    return {"workload": f"graphene 32x32, 2 sheets per electrode: {n} sites, {m} replicas per pass",
-            "kernel": "k_gemv_tma", "s_bytes": nbytes, "ms_per_launch": ms, "achieved_gbs": gbs,
-            "hbm_peak_gbs": hbm, "frac": gbs / hbm, "max_abs_qtot": float(qt.abs().max()),
-            "setup_seconds": setup_s, "l2": "flushed before every update"}
-
-
-def bench_serving(torch, s, n_req=600, rate=4000.0, k_prec="fp32"):
-    """Poisson stream of charge-update requests over three slab geometries (216, 512 and 2,048 sites)."""
+def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 32000.0, None), phases=8,
+                  max_batch=16):
+    """Configuration 4: a Poisson stream of charge-update requests over four slab geometries (two
+    graphene electrodes of two sheets, 512, 2,048, 8,192 and 16,384 sites), each request with its
+    own electrolyte (0.5, 1, 1.5 or 2 charges per site: +-1 ions and 3-site water, drawn from four
+    seeded configurations per geometry and density) and electrode potential difference ~ U[0, 2] V.
+    20,000 requests per offered rate; the rate is swept up to saturation (None: all requests at
+    t = 0).  The stream runs in phases: the two small geometries are always asked for, the 8,192-
+    and 16,384-site ones alternate by phase, and the HBM budget holds the small ones with one large
+    one but not both, so admission and eviction act at every phase change (an evicted geometry
+    returns from its host-memory checkpoint).  Latency: arrival to result on the host."""
     from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
-    geoms = {"au111_216": s.workload_tiny_slab(seed=1)[0], "graphene_512": s.workload_serving_geometry(512)[0],
-             "graphene_2048": s.workload_serving_geometry(2048)[0]}
-    be = GpuBackend(s_prec="fp32", k_prec=k_prec, max_batch=16)
-    sch = Scheduler(be, hbm_budget=4 << 30, max_batch=16)
-    for k, el in geoms.items():
-        sch.add_geometry(k, el, context_bytes(el.n, 2 * el.n, 16))
+    sizes = (512, 2048, 8192, 16384)
+    keys = [f"graphene_{n}" for n in sizes]
+    geoms = {k: s.serving_electrodes(n) for k, n in zip(keys, sizes)}
+    dens = (0.5, 1.0, 1.5, 2.0)
+    t0 = time.perf_counter()
+    pools = {k: [s.workload_serving_geometry(n, seed=40 + j, charges_per_site=c)[1] for j, c in enumerate(dens)]
+             for k, n in zip(keys, sizes)}
+    t_inputs = time.perf_counter() - t0
+    ne_max = {k: max(e.n for e in pools[k]) for k in keys}
+    be = GpuBackend(s_prec="fp32", k_prec=k_prec, max_batch=max_batch, ne_max=ne_max)
+    # first admissions (assembly, inversion, host checkpoint) outside the measured streams
+    t0 = time.perf_counter()
+    meas = {}
+    for k in keys:
+        meas[k] = be.create(k, geoms[k])
+        be.release(k)
+    t_setup = time.perf_counter() - t0
+    budget = meas[keys[0]] + meas[keys[1]] + max(meas[keys[2]], meas[keys[3]]) + (64 << 20)
     rng = np.random.default_rng(11)
-    pools = {k: [s.workload_serving_geometry(el.n, seed=40 + j)[1] if k != "au111_216" else
-                 s.ions_in_gap(el, 100, seed=40 + j) for j in range(8)] for k, el in geoms.items()}
-    keys = list(geoms)
-    reqs = []
-    for i in range(n_req):
-        k = keys[int(rng.integers(len(keys)))]
-        e = pools[k][int(rng.integers(8))]
-        reqs.append(Request(rid=i, key=k, xyz=e.xyz + rng.normal(scale=0.05, size=e.xyz.shape), Q=e.Q,
-                            psi=np.array([0.0, rng.uniform(0.0, 2.0)])))
-    # warm the three contexts outside the measured stream
-    warm = [Request(rid=-1 - j, key=k, xyz=pools[k][0].xyz, Q=pools[k][0].Q, psi=np.zeros(2)) for j, k in enumerate(keys)]
-    run_stream(warm, sch, arrivals=np.zeros(len(warm)))
-    sch.finished.clear()
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-    wall = run_stream(reqs, sch, arrivals=arrivals)
-    st = latency_stats(sch.finished)
-    st.update({"requests": n_req, "offered_rate_per_s": rate, "updates_per_s": n_req / wall,
-               "geometries": {k: el.n for k, el in geoms.items()}, "max_batch": 16, "path": "mixed",
-               "k_prec": k_prec})
-    return st
+    per_phase = n_req // phases
+    out = {"workload": "cfg4: Poisson requests over 4 graphene slab geometries", "geometries": dict(zip(keys, sizes)),
+           "requests_per_rate": n_req, "phases": phases, "max_batch": max_batch, "path": "mixed (FP32 S)",
+           "k_prec": k_prec, "device_bytes": meas, "hbm_budget": budget, "input_seconds": t_inputs,
+           "first_admission_seconds": t_setup, "runs": []}
+    for rate in rates:
+        reqs = []
+        for i in range(n_req):
+            ph = min(i // per_phase, phases - 1)
+            big = keys[2] if ph % 2 == 0 else keys[3]
+            k = (keys[0], keys[1], big)[int(rng.choice(3, p=(0.3, 0.3, 0.4)))]
+            e = pools[k][int(rng.integers(len(dens)))]
+            reqs.append(Request(rid=i, key=k, xyz=e.xyz, Q=e.Q, psi=np.array([0.0, rng.uniform(0.0, 2.0)])))
+        sch = Scheduler(be, hbm_budget=budget, max_batch=max_batch)
+        for k in keys:
+            sch.add_geometry(k, geoms[k], meas[k])
+        restores0 = be.restores
+        arrivals = np.zeros(n_req) if rate is None else np.cumsum(rng.exponential(1.0 / rate, n_req))
+        wall = run_stream(reqs, sch, arrivals=arrivals)
+        for k in list(sch.resident):
+            be.release(k)
+        st = latency_stats(sch.finished)
+        by = {}
+        for k in keys:
+            fk = [r for r in sch.finished if r.key == k]
+            if fk:
+                by[k] = {**latency_stats(fk), "requests": len(fk)}
+        st.update({"offered_rate_per_s": rate if rate is not None else "all at t=0", "updates_per_s": n_req / wall,
+                   "wall_s": wall, "admissions": sch.admissions, "evictions": sch.evictions,
+                   "restores_from_host": be.restores - restores0, "peak_resident_bytes": sch.peak_bytes,
+                   "max_abs_qtot": float(max(abs(r.qtot) for r in sch.finished)), "by_geometry": by})
+        out["runs"].append(st)
+    return out
+
+
+def edl_first_config(s, xyz, Q, ne, step):
+    """Replica 0 of the headline trajectories at one step, as an electrolyte of its own."""
+    return s.Electrolyte(xyz=np.ascontiguousarray(xyz[step, :ne]), Q=np.ascontiguousarray(Q[:ne]))
 
 
 def run_reference(args):
-    """--impl reference: the FP64 CPU oracle on the host cores, same workload, sampled per step."""
+    """--impl reference: the FP64 CPU oracle on the host cores, as it stands: every step is one
+    complete, unsampled update of one headline configuration (b at every site over all host cores
+    in site chunks, then q = S (v - b)); S from the oracle once beforehand (not timed)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from paper_2203_15461_gb300 import systems as s
-    el, ely, psi = s.workload_edl_capacitor(seed=1)
-    samples = []
-    for t in range(args.warmup + args.steps):
-        r = cpu_baseline(el, s.jitter(ely, 0.05, np.random.default_rng(t)), psi)
-        if t >= args.warmup:
-            samples.append(1.0 / r["value"])
-    tot = sum(samples)
-    val = args.steps / tot
-    line = {"metric": METRIC, "value": val, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_sites": el.n, "n_charges": ely.n, "replicas_per_step": 1},
+    el, _, psi = s.workload_edl_capacitor(seed=1)
+    W, K = args.warmup, args.steps
+    xyz, Q, ne = make_trajectories(el, lambda sd: s.workload_edl_capacitor(seed=sd)[1], 1, W + K, rank_seed(0))
+    pool = OraclePool()
+    try:
+        t0 = time.perf_counter()
+        S = pool.capacitance(el)
+        t_S = time.perf_counter() - t0
+        walls = []
+        for t in range(W + K):
+            _, _, wall, _ = pool.update(el, edl_first_config(s, xyz, Q, ne, t), psi, S)
+            if t >= W:
+                walls.append(wall)
+    finally:
+        pool.close()
+    tot = sum(walls)
+    val = K / tot
+    line = {"metric": METRIC, "value": val, "unit": "updates/s", "n_gpus": args.gpus, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sites": el.n, "n_charges": ne, "replicas_per_step": 1},
             "impl": "reference",
-            "cpu_baseline": {"value": val, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": r["sample"]},
+            "cpu_baseline": {"value": val, "unit": "updates/s", "cores": pool.procs, "kind": "oracle",
+                             "sample": (f"per step one complete, unsampled FP64 oracle update of the EDL capacitor "
+                                        f"(4,320 sites, {ne} charges, every k-vector) on {pool.procs} processes "
+                                        f"over site chunks; S from the oracle once before the steps "
+                                        f"({t_S:.1f} s, not timed)")},
             "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 def main():
@@ -414,6 +731,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--replicas", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline, kernel split and end-to-end legs only")
     ap.add_argument("--k-prec", default="f16x2", choices=["fp32", "f16x2"],
                     help="b-vector arithmetic of the mixed path (f16x2: reciprocal sums on the tensor cores)")
     args = ap.parse_args()
@@ -422,23 +740,29 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import torch
-    import torch.distributed as dist
-    from paper_2203_15461_gb300 import systems as s
-    from paper_2203_15461_gb300.cpm import CPM
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2203_15461_gb300 import systems as s
 
     el, ely0, psi = s.workload_edl_capacitor(seed=1)
     m, K, W = args.replicas, args.steps, args.warmup
     seed = rank_seed(rank)
     T = K + W
     xyz, Q, ne = make_trajectories(el, lambda sd: s.workload_edl_capacitor(seed=sd)[1], m, T, seed)
+    # the oracle's single-threaded full update of replica 0 at the first timed step runs beside the GPU
+    # legs in a spawned process started before the first GPU call
+    cpu_leg = rank == 0 and not args.no_cpu_baseline
+    ely_ref = edl_first_config(s, xyz, Q, ne, W)
+    serial = SerialOracle(el, ely_ref, psi) if cpu_leg else None
+
+    import torch
+    import torch.distributed as dist
+    from paper_2203_15461_gb300.cpm import CPM
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
     xyz_dev = torch.as_tensor(xyz, device="cuda")
     Q_dev = torch.as_tensor(Q, device="cuda")
     psi_dev = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")
@@ -460,61 +784,24 @@ def main():
     with Clocks(local) as clk:
         ms, launches, q_mix, _ = time_graph(torch, mixed, st, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush)
     value, ms_max = aggregate(ms, m, K, world, dist if world > 1 else None)
-    # the same steps launched kernel by kernel with CUDA events around each kernel: the per-kernel split
-    with torch.cuda.stream(st):
-        ms_prof, _, prof, _, _ = time_path(torch, mixed, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush, profile=True)
 
-    # plain FP64, one replica per step (the 1x of the metric)
-    K64 = max(3, min(K, 10))
-    x1, Q1, ne1 = xyz_dev[:, :ne], Q_dev[:ne], ne
-    ms64, _, _, q64, _ = time_path(torch, plain, x1, Q1, psi_dev[:1], 1, ne1, 3, K64, flush)
-    fp64_value = K64 / (ms64 / 1e3)
-    # mixed, one replica per step
-    with torch.cuda.stream(st):
-        ms1, _, _, q1, _ = time_path(torch, mixed, x1, Q1, psi_dev[:1], 1, ne1, 3, K, flush)
-    seq_value = K / (ms1 / 1e3)
-    # mixed vs FP64 on the same configuration
-    _, _, _, qa, qta = time_path(torch, plain, x1[:1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
-    with torch.cuda.stream(st):
-        _, _, _, qb, qtb = time_path(torch, mixed, x1[:1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
-    st.synchronize()
-    err_mixed = float(torch.linalg.norm(qb[0] - qa[0]) / torch.linalg.norm(qa[0]))
-    qtot_max = float(max(abs(qta).max(), abs(qtb).max()))
-
-    # end to end through the public API: per step the inputs go host -> device from pinned buffers,
-    # the graph-captured step runs (cpm_step_graph), and q and the totals come back to the host
+    # end to end through the public host-buffer call: per step the caller's positions, charges and
+    # potentials go host -> device from pinned buffers, the captured step replays (cpm_step_host on a
+    # context with its own stream) and q and the totals come back to pinned host buffers
     hx = torch.empty((m * ne, 3), dtype=torch.float64).pin_memory()
     hQ = torch.as_tensor(Q).pin_memory()
     hpsi = torch.as_tensor(np.tile(psi, (m, 1))).pin_memory()
     hq = torch.empty((m, el.n), dtype=torch.float64).pin_memory()
     hqt = torch.empty((m,), dtype=torch.float64).pin_memory()
-    with torch.cuda.stream(st):
-        ex = torch.empty((m * ne, 3), dtype=torch.float64, device="cuda")
-        eQ = torch.empty((m * ne,), dtype=torch.float64, device="cuda")
-        ep = torch.empty((m, el.n_groups), dtype=torch.float64, device="cuda")
-        eb = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
-        eq = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
-        eqt = torch.empty((m,), dtype=torch.float64, device="cuda")
     xyz_host = torch.as_tensor(xyz)
-
-    def e2e_step():
-        with torch.cuda.stream(st):
-            ex.copy_(hx, non_blocking=True)
-            eQ.copy_(hQ, non_blocking=True)
-            ep.copy_(hpsi, non_blocking=True)
-            mixed.cpm_step_graph(m, ne, ex, eQ, ep, eb, eq, eqt)
-            hq.copy_(eq, non_blocking=True)
-            hqt.copy_(eqt, non_blocking=True)
-        st.synchronize()
-
     for t in range(W):
         hx.copy_(xyz_host[t % T])
-        e2e_step()
+        mixed.cpm_step_host(m, ne, hx, hQ, hpsi, hq, hqt)
     e2e_times = []
     for t in range(K):
         hx.copy_(xyz_host[(W + t) % T])   # the caller's new positions, already in its pinned buffer
         t0 = time.perf_counter()
-        e2e_step()
+        mixed.cpm_step_host(m, ne, hx, hQ, hpsi, hq, hqt)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value, _ = aggregate(1e3 * sum(e2e_times), m, K, world, dist if world > 1 else None)   # max over ranks
     if rank != 0:
@@ -525,51 +812,60 @@ def main():
     e2e = {"value": e2e_value, "unit": "updates/s",
            "h2d_bytes_per_step": int(8 * (m * ne * 4 + m * el.n_groups)),
            "d2h_bytes_per_step": int(8 * (m * el.n + m)),
-           "path": "pinned host buffers -> cpm_step_graph -> pinned host buffers, wall clock per step"}
+           "path": "cpm_step_host (C ABI, host buffers) on pinned torch buffers: H2D copies, the captured step "
+                   "replayed, D2H of q and the totals, synchronised; wall clock per call"}
 
-    # batched replicas of the tiny capacitor: 256 electrolytes sharing one S, one CUDA graph per step
-    batched = bench_batched_tiny(torch, CPM, s, flush, K, W, k_prec=args.k_prec)
-    # serving stream: Poisson arrivals over three geometries, continuous batching
-    serving = bench_serving(torch, s, k_prec=args.k_prec)
-    s_stream = bench_s_stream(torch, CPM, s, flush, _peaks()[0])
+    # the same steps launched kernel by kernel with CUDA events around each kernel: the per-kernel split
+    with torch.cuda.stream(st):
+        ms_prof, _, prof, _, _ = time_path(torch, mixed, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush, profile=True)
+    # the headline with the reciprocal sums on the CUDA cores (--k-prec fp32) beside it
+    other_k = "fp32" if args.k_prec == "f16x2" else "f16x2"
+    st2 = torch.cuda.Stream()
+    with torch.cuda.stream(st2):
+        mixed2 = CPM.for_electrodes(el, s_prec="fp32", k_prec=other_k, stream=st2).setup(el)
+    ms2, _, _, _ = time_graph(torch, mixed2, st2, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush)
+    mixed2.close()
 
-    # roofline of the dominant kernel
+    # plain FP64, one replica per step (the 1x of the metric), with its kernel split
+    K64 = max(3, min(K, 10))
+    x1, Q1, ne1 = xyz_dev[:, :ne], Q_dev[:ne], ne
+    ms64, _, prof64, q64, _ = time_path(torch, plain, x1, Q1, psi_dev[:1], 1, ne1, 3, K64, flush, profile=True)
+    fp64_value = K64 / (ms64 / 1e3)
+    # mixed, one replica per step (configuration 2's sequential MD updates)
+    with torch.cuda.stream(st):
+        ms1, _, _, q1, _ = time_path(torch, mixed, x1, Q1, psi_dev[:1], 1, ne1, 3, K, flush)
+    seq_value = K / (ms1 / 1e3)
+    # mixed and FP64 on replica 0 at the first timed step (the configuration the oracle leg updates)
+    _, _, _, qa, qta = time_path(torch, plain, x1[W:W + 1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
+    with torch.cuda.stream(st):
+        _, _, _, qb, qtb = time_path(torch, mixed, x1[W:W + 1], Q1, psi_dev[:1], 1, ne1, 0, 1, flush)
+    st.synchronize()
+    q64_ref, qmix_ref = qa[0].cpu().numpy(), qb[0].cpu().numpy()
+    err_mixed = rel_l2(qmix_ref, q64_ref)
+    qtot_max = float(max(abs(qta).max(), abs(qtb).max()))
+
     peaks, src = _peaks()
-    # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the full
-    # workload (cold caches: ncu flushes them before each launch); None for a kernel not captured
-    traffic_ncu = {"real": 0.75e6, "sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
+    alu_peak = _fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    alu_src = f"FP32 FMA issue rate 152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
+    pairs = real_pairs(el, xyz, Q, ne, m, W)
+    work = kernel_work(el, nk, ne, m, pairs, tensor=args.k_prec == "f16x2")
     kname = {"real": "k_real_cells", "sf": "k_tc_sf" if args.k_prec == "f16x2" else "k_sf32",
              "site": "k_tc_site" if args.k_prec == "f16x2" else "k_site32", "gemv": "k_gemv_tma"}
-    pairs = real_pairs(el, xyz, Q, ne, m, W)
-    work = kernel_work(mixed, el, nk, ne, m, pairs, tensor=args.k_prec == "f16x2")
-    top = max((kk for kk in prof if prof[kk][1] > 0), key=lambda kk: prof[kk][0])
-    avg_ms = prof[top][0] / prof[top][1]
-    kind, amount = work.get(top, ("flop", float("nan")))
-    if kind == "tflop":
-        # fp16 tensor rate = the measured bf16 rate (same nominal peak); three fp16 products per FP32 product
-        peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
-        achieved = amount / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": kname.get(top, top), "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_ncu.get(top),
-                "peak_source": f"bf16_tflops ({src}) / 3: two-term fp16 operands, three products per FP32 product"}
-    elif kind == "flop":
-        peak = _fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-        achieved = amount / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": kname.get(top, top), "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_ncu.get(top),
-                "peak_source": f"FP32 FMA issue rate 152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
-    else:
-        peak = float(peaks["hbm_gbs"])
-        achieved = amount / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": kname.get(top, top), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_ncu.get(top), "peak_source": f"hbm_gbs ({src})"}
-    roof["share_of_step"] = prof[top][0] / ms_prof
-    roof["all_kernels"] = {kk: {"ms_per_launch": prof[kk][0] / max(1, prof[kk][1]),
-                                "achieved": (work[kk][1] / (prof[kk][0] / max(1, prof[kk][1]) / 1e3)
-                                             / (1e9 if work[kk][0] == "byte" else 1e12)),
-                                "unit": "GB/s" if work[kk][0] == "byte" else "TFLOP/s"}
-                           for kk in work if kk in prof and prof[kk][1] > 0}
+    top, roof = roofline(prof, work, peaks, src, kname, alu_peak, alu_src, ms_prof)
     roof["pairs_in_rcut_per_launch"] = pairs
+    roof["flop_per_unit"] = {"real_pair": FLOP_PAIR, "sf_charge_k": FLOP_SF, "site_k": FLOP_SITE,
+                             "tensor_complex_mac": FLOP_CMAC}
+    # DRAM bytes (read + write) per launch from the committed ncu capture of these kernels on this
+    # workload (cold caches); a stored figure, not measured by this run
+    traffic_ncu = {"real": 0.75e6, "sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
+    roof["traffic"] = traffic_ncu.get(top)
+    roof["traffic_source"] = ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                              "profiles/kernels_full_edl_capacitor_4320.md")
+    pairs1 = real_pairs(el, xyz, Q, ne, 1, W)
+    work64 = kernel_work(el, nk, ne, 1, pairs1, tensor=False, s_bytes=8)
+    k64 = {"real": "k_real_b<double>", "sf": "k_sf<double>", "site": "k_site<double>", "gemv": "k_gemv_t<double>"}
+    fp64_peak = 1.25   # nominal GB300 FP64 rate (TFLOP/s); no measured FP64 peak on this machine
+    _, roof64 = roofline(prof64, work64, peaks, src, k64, fp64_peak, "nominal GB300 FP64 rate, 1.25 TFLOP/s", ms64)
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -585,20 +881,62 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "launch": "one CUDA graph per step (cpm_step_graph), positions copied in place"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
-            "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value, "sequential_mixed_value": seq_value,
+            f"value_k_prec_{other_k}": m * K / (ms2 / 1e3),
+            "fp64_value": fp64_value, "speedup_vs_fp64": value / fp64_value,
+            "fp64_kernel_ms_per_step": {kk: v[0] / K64 for kk, v in prof64.items()}, "fp64_roofline": roof64,
+            "cfg2_sequential": {"workload": "edl_capacitor_4320, one replica, sequential updates (MD semantics)",
+                                "mixed_value": seq_value, "fp64_value": fp64_value, "unit": "updates/s"},
             "rel_err_mixed_vs_fp64": err_mixed, "max_abs_qtot": qtot_max, "setup_seconds": t_setup,
             "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items()},
-            "ms_per_step_kernel_by_kernel": ms_prof / K,
-            "batched_tiny_256": batched, "serving": serving, "s_stream_16384": s_stream}
+            "ms_per_step_kernel_by_kernel": ms_prof / K}
+    plain.close()
+    mixed.close()
     clocks = clk.summary()
     line["clocks"] = clocks
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(el, ely0, psi)
+
+    if not args.no_extra:
+        cfg1, cfg1_q = bench_tiny_flow(torch, CPM, s)
+        cfg3, cfg3_q = bench_batched_tiny(torch, CPM, s, flush, K, W, k_prec=args.k_prec)
+        line["cfg1_tiny_fp64"] = cfg1
+        line["cfg3_batched_tiny_256"] = cfg3
+        line["cfg4_serving"] = bench_serving(torch, s, k_prec=args.k_prec)
+        line["cfg5_coax_12000"] = bench_coax(torch, CPM, s)
+        sp = bench_s_products(torch, CPM, s, flush, peaks, src)
+        line["s_products"] = sp
+        f16 = sp.get("16384", {}).get("m8", {}).get("fp32", {})
+        line["s_stream_16384"] = {"kernel": "k_gemv_tma", "replicas": 8, "ms_per_launch": f16.get("kernel_ms"),
+                                  "achieved_gbs": f16.get("achieved_gbs"), "frac": f16.get("hbm_frac"),
+                                  "hbm_peak_gbs": float(peaks["hbm_gbs"]), "l2": "flushed before every update"}
+
+    if cpu_leg:
+        pool = OraclePool()
+        try:
+            cb, _, q_or = cpu_baseline_edl(pool, serial, el, ely_ref, psi)
+            cb["rel_err_vs_oracle"] = {"mixed_headline_path": rel_l2(qmix_ref, q_or), "fp64_path": rel_l2(q64_ref, q_or)}
+            if not args.no_extra:
+                el_t, last, psis, qs = cfg3_q
+                el1, conf1, psi1, q1last = cfg1_q
+                tiny = dict(last)
+                tiny[-1] = conf1
+                psis = dict(psis)
+                psis[-1] = psi1
+                q_small, c0_10 = cpu_baseline_small(pool, el_t, tiny, psis,
+                                                    s.coaxial_tubes(10, alpha=0.15, rcut=24.0, ktol=1e-8))
+                line["cfg1_tiny_fp64"]["rel_err_vs_oracle"] = rel_l2(q1last, q_small[-1])
+                line["cfg3_batched_tiny_256"]["rel_err_vs_oracle"] = {
+                    sp: max(rel_l2(qs[sp][r], q_small[r]) for r in last) for sp in qs}
+                line["cfg3_batched_tiny_256"]["rel_err_replicas_checked"] = sorted(last)
+                c5 = line["cfg5_coax_12000"]
+                c5["C0_per_L_oracle_10_cells"] = c0_10
+                c5["rel_err_vs_oracle_fp64"] = abs(c5["C0_per_L_fp64"] / c0_10 - 1.0)
+                c5["rel_err_vs_oracle_fp32_ir"] = abs(c5["C0_per_L_fp32_ir"] / c0_10 - 1.0)
+        finally:
+            pool.close()
+        line["cpu_baseline"] = cb
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -55,7 +55,13 @@ typedef enum {
 typedef enum {
     CPM_BC_3D = 0,    /* 3D periodic, tin-foil: no correction */
     CPM_BC_SLAB = 1,  /* x, y periodic; z padded with vacuum; J = 2 pi M_z^2 / V (Eq. ew3dc_slab) */
-    CPM_BC_WIRE = 2   /* z periodic; x, y padded with vacuum; J = pi (M_x^2 + M_y^2) / V (Eq. ew3dc_wire) */
+    CPM_BC_WIRE = 2,  /* z periodic; x, y padded with vacuum; J = pi (M_x^2 + M_y^2) / V (Eq. ew3dc_wire) */
+    CPM_BC_EW2D = 3   /* x, y periodic, z not: the exact 2D Ewald sum (EW2D, Sec. II.E) in place of the 3D
+                         reciprocal sum, background and dipole term.  box[2] is no period: it fixes the
+                         undetermined constant (2 pi / (Lx Ly)) box[2] of the elastance of a 2D-periodic
+                         system (A += c e e^T, b += c Q_tot; S and every neutral result do not depend on
+                         it) and must exceed the z range of all sites and charges by rcut.  k_prec FP64 or
+                         FP32 (not F16X2); not for cpm_bvec_noalloc. */
 } cpm_boundary;
 
 /* Arithmetic of a per-step stage. */
@@ -70,6 +76,13 @@ typedef enum {
                            FP32 accumulation */
 } cpm_precision;
 
+/* Factorisation of A in cpm_invert (Sec. II.A: A is inverted once per electrode geometry). */
+typedef enum {
+    CPM_CHOL_FP64 = 0,    /* FP64 blocked Cholesky, triangular inverse, A^-1 = L^-T L^-1 */
+    CPM_CHOL_FP32_IR = 1  /* FP32 blocked Cholesky; A X = I refined in FP64 (residual against the FP64 A)
+                             until the residual stops shrinking; X symmetrised */
+} cpm_chol;
+
 typedef struct {
     double box[3];       /* Ewald cell (Lx, Ly, Lz) in Angstrom, vacuum padding included */
     int32_t boundary;    /* cpm_boundary */
@@ -81,6 +94,7 @@ typedef struct {
     int32_t s_prec;      /* cpm_precision of the S (v - b) product */
     int32_t k_prec;      /* cpm_precision of the b-vector sums (real and reciprocal space) */
     size_t hbm_budget;   /* bytes of device memory this context may allocate; 0 = no limit */
+    int32_t chol;        /* cpm_chol of cpm_invert */
 } cpm_params;
 
 typedef struct cpm_ctx cpm_ctx;
@@ -115,7 +129,30 @@ cpm_status cpm_assemble(cpm_ctx* ctx, int64_t n, const double* xyz, const double
                         const int32_t* group, int32_t n_groups);
 
 /*
- * Factor A = L L^T (FP64 blocked Cholesky), form A^-1 and, with symm = 1, the
+ * Everything cpm_assemble does except the elastance matrix itself: the sites, the reciprocal
+ * set, the phase tables and the real-space site chunks, and room for S.  For a context that
+ * receives S from a checkpoint (cpm_import, cpm_load) instead of cpm_invert, e.g. a geometry that
+ * a server evicted and admits again.  Arguments and errors as cpm_assemble; afterwards
+ * cpm_invert, cpm_capacitance_ir and cpm_get_matrix(A) return CPM_E_STATE.
+ */
+cpm_status cpm_prepare(cpm_ctx* ctx, int64_t n, const double* xyz, const double* eta,
+                       const int32_t* group, int32_t n_groups);
+
+/*
+ * Free A and the factor workspace (2 n^2 doubles) of an inverted context: only S, SG and u are
+ * needed for cpm_bvec / cpm_update.  cpm_invert, cpm_capacitance_ir and cpm_get_matrix(A)
+ * return CPM_E_STATE afterwards.  Synchronises the stream.  Errors: CPM_E_STATE (not inverted).
+ */
+cpm_status cpm_release_assembly(cpm_ctx* ctx);
+
+/*
+ * Refinement sweeps and final max-norm residual of A X = I of the last cpm_invert with
+ * chol = CPM_CHOL_FP32_IR (0 and 0.0 for CPM_CHOL_FP64).  Errors: CPM_E_STATE (not inverted).
+ */
+cpm_status cpm_inversion_info(cpm_ctx* ctx, int32_t* sweeps, double* resid);
+
+/*
+ * Factor A = L L^T (FP64 blocked Cholesky, or FP32 with FP64 refinement: cpm_params.chol), form A^-1 and, with symm = 1, the
  * neutral capacitance matrix S = A^-1 - A^-1 e e^T A^-1 / (e^T A^-1 e)
  * (Eq. S, Sec. II.A), the electrode response SG = S G (n x N_g) and the
  * neutraliser u = A^-1 e / (e^T A^-1 e).  Synchronises the stream.
@@ -150,6 +187,50 @@ cpm_status cpm_update(cpm_ctx* ctx, int32_t m, const double* psi, const double* 
                       double* qtot_out);
 
 /*
+ * Electrodes at prescribed total charge (constant charge method, Sec. II.C, Eq. ewise-conq).
+ * qtilde: device, m x n_groups - the total charge of every electrode per replica (any values;
+ * their sum is the total electrode charge).  With the capacitance matrix A^-1 the totals are
+ * q~ = G^T A^-1 (G v~ - b); the call solves this for the electrode potentials v~ of each replica
+ * (vtilde_out: device, m x n_groups, may be NULL) and applies them: q = A^-1 (G v~ - b), written
+ * to q_out (device, m x n) with qtot_out (device, m, may be NULL) = e^T q.  The S product runs in
+ * the context's s_prec; b as for cpm_update.  Asynchronous on the context stream.
+ * Errors: CPM_E_STATE (not inverted), CPM_E_ARG, CPM_E_NOT_SPD (G^T A^-1 G singular).
+ */
+cpm_status cpm_update_ccm(cpm_ctx* ctx, int32_t m, const double* qtilde, const double* b, double* q_out,
+                          double* qtot_out, double* vtilde_out);
+
+/* Thermo-potentiostat parameters (Sec. II.D): time step dt and relaxation time tau (any one unit),
+ * temperature T (K) and the target potential difference dv0 = v_1 - v_0 (V). */
+typedef struct {
+    double dt, tau, T, dv0;
+} cpm_tp_params;
+
+/*
+ * One thermo-potentiostat step (Sec. II.D, Eq. deissenbeck) for a two-electrode context: with the
+ * capacitor charge q = qcap[r] on electrode 1 (and -q on electrode 0), the effective potential
+ * difference Delta v = v~_1 - v~_0 follows from the constant-charge relation of cpm_update_ccm for
+ * this b; the new charge
+ *   q' = q - C0 (Delta v - dv0)(1 - exp(-dt/tau)) + X_r sqrt(k_B T C0 (1 - exp(-2 dt/tau))),
+ * C0 = g_1^T S g_1 (the vacuum capacitance, Sec. III.B), X: device, m standard normal numbers the
+ * caller draws, is applied with the constant charge method.  qcap, X: device, m; q_out: device,
+ * m x n; qcap_out: device, m (may alias qcap); dv_out: device, m (Delta v before the step, may be NULL).
+ * Errors: CPM_E_STATE, CPM_E_ARG (not two electrodes, dt or tau <= 0, T < 0).
+ */
+cpm_status cpm_update_tp(cpm_ctx* ctx, int32_t m, const cpm_tp_params* tp, const double* qcap, const double* X,
+                         const double* b, double* q_out, double* qcap_out, double* dv_out);
+
+/*
+ * Finite-field charges (Sec. II.F, Eq. cpm-ffield): q = S (v - b) with the site potentials
+ * v = -dv0 zeta, zeta_i = z_i / L_z plus one for the sites of the bottom electrode (the electrode
+ * of lower mean z), so that the potential difference dv0 acts across the electrolyte of a fully
+ * periodic cell.  Needs CPM_BC_3D and two electrodes.  dv0: device, m; b, q_out, qtot_out as for
+ * cpm_update.  The first call forms S zeta (FP64) and keeps it with S.
+ * Errors: CPM_E_STATE, CPM_E_ARG (boundary, electrode count).
+ */
+cpm_status cpm_update_ffield(cpm_ctx* ctx, int32_t m, const double* dv0, const double* b, double* q_out,
+                             double* qtot_out);
+
+/*
  * One complete charge update from HOST buffers: copy the m * n_e charges and the
  * potentials to the device, run cpm_bvec and cpm_update, copy q and qtot back
  * and synchronise.  xyz: host, (m * n_e) x 3; Q: host, m * n_e; psi: host,
@@ -157,8 +238,7 @@ cpm_status cpm_update(cpm_ctx* ctx, int32_t m, const double* psi, const double* 
  * Host buffers may be pageable; page-locked memory gives faster copies.
  * On a context created with its own (non-default) stream the device part runs as
  * the CUDA graph of cpm_step_graph, captured once on the context's staging buffers
- * for each (m, n_e) and replayed; the context keeps one graph, shared with
- * cpm_step_graph, so alternating the two calls re-captures.  On the default stream,
+ * for each (m, n_e) and replayed (the graphs are kept as for cpm_step_graph).  On the default stream,
  * or while cpm_profile is on, the kernels launch one by one.
  */
 cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
@@ -168,8 +248,9 @@ cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz
  * cpm_bvec followed by cpm_update as one CUDA graph (device buffers as in those calls;
  * b_out receives b).  The first call for given (m, n_e, buffer addresses) reserves the
  * scratch, captures the launches on the context stream and instantiates the graph; later
- * calls with the same arguments replay it with one launch.  Different arguments re-capture
- * (one graph per context).  Needs a context created on a non-default stream.
+ * calls with the same arguments replay it with one launch.  The context keeps up to eight
+ * such graphs (least recently used replaced first); a call that has to grow the scratch drops
+ * them all.  Needs a context created on a non-default stream.
  * Errors: as cpm_bvec / cpm_update; CPM_E_ARG for the default stream.
  */
 cpm_status cpm_step_graph(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
@@ -254,11 +335,23 @@ cpm_status cpm_capacitance_ir(cpm_ctx* ctx, double* C_out, int32_t* iters_out, d
  */
 cpm_status cpm_kvectors(cpm_ctx* ctx, int32_t* nidx_out, int64_t cap, int64_t* nk);
 
-/* Save / load S and SG with a header that records n, the parameters and a
+/* Save / load S, SG and u with a header that records n, the parameters and a
  * hash of the geometry (the write_inv / read_inv files of SI Sec. 1.A).
- * Load requires cpm_assemble of the same geometry first. */
+ * Load requires cpm_assemble or cpm_prepare of the same geometry first. */
 cpm_status cpm_save(cpm_ctx* ctx, const char* path);
 cpm_status cpm_load(cpm_ctx* ctx, const char* path);
+
+/*
+ * The same checkpoint in caller-owned host memory (page-locked memory copies fastest).
+ * cpm_export writes header + S (n x n) + SG (n x N_g) + u (n) doubles into buf (cap bytes) and
+ * the size into *bytes; buf = NULL only reports the size.  cpm_import reads it back into a
+ * context of the same geometry and parameters (after cpm_assemble or cpm_prepare) and marks it
+ * inverted.  Both synchronise the stream.
+ * Errors: CPM_E_STATE (export before cpm_invert, import before assembly), CPM_E_ARG (buffer too
+ * small, or a checkpoint of another geometry or other parameters).
+ */
+cpm_status cpm_export(cpm_ctx* ctx, void* buf, size_t cap, size_t* bytes);
+cpm_status cpm_import(cpm_ctx* ctx, const void* buf, size_t bytes);
 
 /* Bytes of device memory currently held by the context. */
 size_t cpm_device_bytes(const cpm_ctx* ctx);

@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libcpm_gb300.so")
 
 STATUS = {0: "CPM_OK", 1: "CPM_E_ARG", 2: "CPM_E_OOM", 3: "CPM_E_BUDGET", 4: "CPM_E_NOT_SPD", 5: "CPM_E_STATE",
           6: "CPM_E_CUDA", 7: "CPM_E_TIMEOUT", 8: "CPM_E_NONFINITE"}
-BOUNDARY = {"3d": 0, "slab": 1, "wire": 2}
+BOUNDARY = {"3d": 0, "slab": 1, "wire": 2, "ew2d": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2, "f16x2": 3}
 MATRIX = {"A": 0, "S": 1, "SG": 2, "u": 3}
+CHOL = {"fp64": 0, "fp32_ir": 1}
 
 
 class CPMError(RuntimeError):
@@ -29,10 +30,15 @@ class CPMError(RuntimeError):
         self.name = STATUS.get(status, str(status))
 
 
+class cpm_tp_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("tau", ctypes.c_double), ("T", ctypes.c_double), ("dv0", ctypes.c_double)]
+
+
 class cpm_params(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double * 3), ("boundary", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("rcut", ctypes.c_double), ("kcut", ctypes.c_double), ("symm", ctypes.c_int32),
-                ("s_prec", ctypes.c_int32), ("k_prec", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t)]
+                ("s_prec", ctypes.c_int32), ("k_prec", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t),
+                ("chol", ctypes.c_int32)]
 
 
 _lib = None
@@ -45,9 +51,16 @@ _SIGS = {
     "cpm_destroy": ([_P], None),
     "cpm_assemble": ([_P, _I64, _P, _P, _P, _I32], _I32),
     "cpm_invert": ([_P], _I32),
+    "cpm_prepare": ([_P, _I64, _P, _P, _P, _I32], _I32),
+    "cpm_release_assembly": ([_P], _I32),
+    "cpm_export": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "cpm_import": ([_P, _P, ctypes.c_size_t], _I32),
     "cpm_bvec": ([_P, _I32, _I64, _P, _P, _P], _I32),
     "cpm_update": ([_P, _I32, _P, _P, _P, _P], _I32),
     "cpm_step_host": ([_P, _I32, _I64, _P, _P, _P, _P, _P], _I32),
+    "cpm_update_ccm": ([_P, _I32, _P, _P, _P, _P, _P], _I32),
+    "cpm_update_tp": ([_P, _I32, ctypes.POINTER(cpm_tp_params), _P, _P, _P, _P, _P, _P], _I32),
+    "cpm_update_ffield": ([_P, _I32, _P, _P, _P, _P], _I32),
     "cpm_step_graph": ([_P, _I32, _I64, _P, _P, _P, _P, _P, _P], _I32),
     "cpm_sync": ([_P], _I32),
     "cpm_selftest_timeout": ([_P, _D], _I32),
@@ -64,6 +77,7 @@ _SIGS = {
     "cpm_gemm_plan": ([_P, _I32, _P, ctypes.POINTER(_D)], _I32),
     "cpm_gemm_set_plan": ([_P, _I32, _P], _I32),
     "cpm_set_s_prec": ([_P, _I32], _I32),
+    "cpm_inversion_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_D)], _I32),
     "cpm_profile": ([_P, _I32], _I32),
     "cpm_profile_read": ([_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32], _I32),
 }
@@ -163,7 +177,7 @@ class CPM:
     """One CPM context: one electrode geometry on the current CUDA device and one stream."""
 
     def __init__(self, box, boundary: str, alpha: float, rcut: float, kcut: float, symm: bool = True,
-                 s_prec: str = "fp64", k_prec: str = "fp64", hbm_budget: int = 0, stream=None):
+                 s_prec: str = "fp64", k_prec: str = "fp64", hbm_budget: int = 0, stream=None, chol: str = "fp64"):
         self.lib = load_library()
         p = cpm_params()
         p.box[:] = [float(b) for b in box]
@@ -172,6 +186,7 @@ class CPM:
         p.symm = 1 if symm else 0
         p.s_prec, p.k_prec = PRECISION[s_prec], PRECISION[k_prec]
         p.hbm_budget = int(hbm_budget)
+        p.chol = CHOL[chol]
         self.params = p
         self.stream = stream
         h = _P()
@@ -211,6 +226,30 @@ class CPM:
     def cpm_invert(self):
         self._check(self.lib.cpm_invert(self.handle))
 
+    def cpm_prepare(self, xyz, eta, group, n_groups: int):
+        self.n, self.n_groups = int(xyz.shape[0]), int(n_groups)
+        self._check(self.lib.cpm_prepare(self.handle, self.n, _ptr(xyz), _ptr(eta), _ptr(group), self.n_groups))
+
+    def cpm_release_assembly(self):
+        self._check(self.lib.cpm_release_assembly(self.handle))
+
+    def cpm_export(self, buf=None):
+        """Checkpoint of S, SG and u into ``buf`` (a host tensor or array of uint8; allocated pinned when None)."""
+        need = ctypes.c_size_t(0)
+        self._check(self.lib.cpm_export(self.handle, None, 0, ctypes.byref(need)))
+        if buf is None:
+            import torch
+            buf = torch.empty(need.value, dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+        nbytes = buf.numel() if hasattr(buf, "numel") else buf.nbytes
+        self._check(self.lib.cpm_export(self.handle, _P(ptr), nbytes, ctypes.byref(need)))
+        return buf
+
+    def cpm_import(self, buf):
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+        nbytes = buf.numel() if hasattr(buf, "numel") else buf.nbytes
+        self._check(self.lib.cpm_import(self.handle, _P(ptr), nbytes))
+
     def cpm_bvec(self, m: int, n_e: int, xyz, Q, b_out):
         self._check(self.lib.cpm_bvec(self.handle, int(m), int(n_e), _ptr(xyz) if n_e else None,
                                       _ptr(Q) if n_e else None, _ptr(b_out)))
@@ -218,6 +257,21 @@ class CPM:
     def cpm_update(self, m: int, psi, b, q_out, qtot_out=None):
         self._check(self.lib.cpm_update(self.handle, int(m), _ptr(psi), _ptr(b), _ptr(q_out),
                                         _ptr(qtot_out) if qtot_out is not None else None))
+
+    def cpm_update_ccm(self, m: int, qtilde, b, q_out, qtot_out=None, vtilde_out=None):
+        self._check(self.lib.cpm_update_ccm(self.handle, int(m), _ptr(qtilde), _ptr(b), _ptr(q_out),
+                                            _ptr(qtot_out) if qtot_out is not None else None,
+                                            _ptr(vtilde_out) if vtilde_out is not None else None))
+
+    def cpm_update_tp(self, m: int, dt: float, tau: float, T: float, dv0: float, qcap, X, b, q_out, qcap_out,
+                      dv_out=None):
+        tp = cpm_tp_params(float(dt), float(tau), float(T), float(dv0))
+        self._check(self.lib.cpm_update_tp(self.handle, int(m), ctypes.byref(tp), _ptr(qcap), _ptr(X), _ptr(b),
+                                           _ptr(q_out), _ptr(qcap_out), _ptr(dv_out) if dv_out is not None else None))
+
+    def cpm_update_ffield(self, m: int, dv0, b, q_out, qtot_out=None):
+        self._check(self.lib.cpm_update_ffield(self.handle, int(m), _ptr(dv0), _ptr(b), _ptr(q_out),
+                                               _ptr(qtot_out) if qtot_out is not None else None))
 
     def cpm_step_host(self, m: int, n_e: int, xyz: np.ndarray, Q: np.ndarray, psi: np.ndarray, q_out: np.ndarray,
                       qtot_out: np.ndarray | None = None):
@@ -247,6 +301,12 @@ class CPM:
         self._check(self.lib.cpm_gemm_plan(self.handle, int(m), plan.ctypes.data, ctypes.byref(ms)))
         return {"BN": int(plan[0]), "stages": int(plan[1]), "splits": int(plan[2]), "ctas": int(plan[3]),
                 "candidates": int(plan[4]), "ms": float(ms.value)}
+
+    def cpm_inversion_info(self):
+        """(refinement sweeps, final residual) of the last FP32-factor inversion."""
+        it, res = _I32(0), _D(0.0)
+        self._check(self.lib.cpm_inversion_info(self.handle, ctypes.byref(it), ctypes.byref(res)))
+        return int(it.value), float(res.value)
 
     def cpm_set_s_prec(self, s_prec: str):
         self._check(self.lib.cpm_set_s_prec(self.handle, PRECISION[s_prec]))

@@ -128,10 +128,9 @@ __global__ void k_soa(const double* xyz, const double* eta, const int32_t* grp, 
 }
 
 static void drop_graph(cpm_ctx* c) {
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->graph_exec = nullptr;
-    c->graph = nullptr;
+    for (auto& gr : c->graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    c->graphs.clear();
     c->graph_valid = false;
 }
 
@@ -140,7 +139,8 @@ static void free_geometry(cpm_ctx* c) {
     free_ktable(c);
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
-                    c->sperm, c->schunks, c->rqueue, c->tcz, c->tcxy, c->c0e};
+                    c->sperm, c->schunks, c->rqueue, c->tcz, c->tcxy, c->c0e, c->ccm_buf, c->ccm_scr, c->SGx,
+                    c->h2d_idx, c->h2d_norm};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
@@ -148,11 +148,14 @@ static void free_geometry(cpm_ctx* c) {
     c->rtab = nullptr; c->rtab_id = nullptr; c->nrtab = 0;
     c->sperm = nullptr; c->schunks = nullptr; c->rqueue = nullptr; c->nschunk = 0;
     c->tcz = nullptr; c->tcxy = nullptr; c->c0e = nullptr;
+    c->ccm_buf = nullptr; c->ccm_scr = nullptr; c->SGx = nullptr; c->ccm_scr_bytes = 0; c->ccm_ready = false;
+    c->h2d_idx = nullptr; c->h2d_norm = nullptr; c->nh2d = 0;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
     c->n = 0;
     c->assembled = c->inverted = false;
+    c->has_A = false;
 }
 
 static uint64_t fnv1a(uint64_t h, const void* data, size_t bytes) {
@@ -165,13 +168,23 @@ static uint64_t fnv1a(uint64_t h, const void* data, size_t bytes) {
 // instantiated on the first call for given (m, n_e, buffer addresses), replayed afterwards.
 static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q,
                              const double* psi, double* b_out, double* q_out, double* qtot_out) {
-    const void* ptrs[7] = {xyz, Q, psi, b_out, q_out, qtot_out, nullptr};
+    const void* ptrs[6] = {xyz, Q, psi, b_out, q_out, qtot_out};
     CPM_TRY(reserve_bvec(c, m, n_e));
     CPM_TRY(reserve_update(c, m));
-    bool same = c->graph_valid && c->graph_m == m && c->graph_ne == n_e;
-    for (int k = 0; k < 6 && same; ++k) same = c->graph_ptrs[k] == ptrs[k];
-    if (!same) {
-        drop_graph(c);
+    if (!c->graph_valid) drop_graph(c);   // a scratch buffer moved: every captured graph is stale
+    cpm_ctx::StepGraph* hit = nullptr;
+    for (auto& gr : c->graphs) {
+        bool same = gr.m == m && gr.ne == n_e;
+        for (int k = 0; k < 6 && same; ++k) same = gr.ptrs[k] == ptrs[k];
+        if (same) { hit = &gr; break; }
+    }
+    if (!hit) {
+        if ((int)c->graphs.size() >= CPM_MAX_GRAPHS) {
+            auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                        [](const cpm_ctx::StepGraph& a, const cpm_ctx::StepGraph& b) { return a.used < b.used; });
+            if (lru->exec) cudaGraphExecDestroy(lru->exec);
+            c->graphs.erase(lru);
+        }
         const bool prof = c->prof_on;
         c->prof_on = false;
         const int64_t l0 = c->launches;
@@ -184,17 +197,22 @@ static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* x
         c->prof_on = prof;
         if (s2 != CPM_OK) { if (g) cudaGraphDestroy(g); return s2; }
         if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
-        c->graph = g;
-        CPM_CUDA(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
-        c->graph_launches = c->launches - l0;
+        cpm_ctx::StepGraph gr;
+        gr.m = m;
+        gr.ne = n_e;
+        for (int k = 0; k < 6; ++k) gr.ptrs[k] = ptrs[k];
+        e = cudaGraphInstantiate(&gr.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_check(c, e, "cudaGraphInstantiate");
+        gr.launches = c->launches - l0;
         c->launches = l0;
+        c->graphs.push_back(gr);
+        hit = &c->graphs.back();
         c->graph_valid = true;
-        c->graph_m = m;
-        c->graph_ne = n_e;
-        for (int k = 0; k < 7; ++k) c->graph_ptrs[k] = ptrs[k];
     }
-    CPM_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += c->graph_launches;
+    hit->used = ++c->graph_clock;
+    CPM_CUDA(c, cudaGraphLaunch(hit->exec, c->stream));
+    c->launches += hit->launches;
     return CPM_OK;
 }
 
@@ -210,7 +228,9 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
     for (int d = 0; d < 3; ++d)
         if (!(p->box[d] > 0.0)) return CPM_E_ARG;
     if (!(p->alpha > 0.0) || !(p->rcut > 0.0) || !(p->kcut > 0.0)) return CPM_E_ARG;
-    if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_WIRE) return CPM_E_ARG;
+    if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_EW2D) return CPM_E_ARG;
+    if (p->boundary == CPM_BC_EW2D && p->k_prec == CPM_PREC_F16X2) return CPM_E_ARG;
+    if (p->chol != CPM_CHOL_FP64 && p->chol != CPM_CHOL_FP32_IR) return CPM_E_ARG;
     if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32 && p->s_prec != CPM_PREC_BF16X3) ||
         (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32 && p->k_prec != CPM_PREC_F16X2))
         return CPM_E_ARG;
@@ -256,8 +276,10 @@ size_t cpm_device_bytes(const cpm_ctx* c) { return c ? c->bytes : 0; }
 
 int64_t cpm_launch_count(const cpm_ctx* c) { return c ? c->launches : 0; }
 
-cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* eta, const int32_t* group,
-                        int32_t n_groups) {
+// The geometry part of cpm_assemble (sites, k table, phase tables, real-space chunks, dense buffers
+// for S); with_A also allocates A and the factor workspace and assembles A.
+static cpm_status assemble_impl(cpm_ctx* c, int64_t n, const double* xyz, const double* eta, const int32_t* group,
+                                int32_t n_groups, bool with_A) {
     if (!c) return CPM_E_ARG;
     c->err.clear();
     if (n < 1 || n_groups < 1 || n_groups > 16 || !xyz || !eta || !group)
@@ -362,6 +384,21 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
         c->geom_hash = h;
     }
     CPM_TRY(build_ktable(c));
+    if (c->g.bc == CPM_BC_EW2D) {
+        // z is not periodic: every real-space pair must stay within one period of the cell height
+        double zmin = 1e300, zmax = -1e300;
+        {
+            std::vector<double> zz(n);
+            CPM_CUDA(c, cudaMemcpyAsync(zz.data(), c->sx + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+            CPM_CUDA(c, cudaStreamSynchronize(st));
+            for (double z : zz) { zmin = std::min(zmin, z); zmax = std::max(zmax, z); }
+        }
+        if (!(zmax - zmin + c->g.rcut < c->g.boxL[2])) {
+            free_geometry(c);
+            return set_err(c, CPM_E_ARG, "EW2D: box[2] must exceed the sites' z range (%g) by rcut", zmax - zmin);
+        }
+        CPM_TRY(build_ew2d(c));
+    }
     const KTable& k = c->kt;
     const size_t pe = phase_elems(k, n);
     const int64_t tX = (int64_t)(k.NX + 1) * n, tY = (int64_t)(2 * k.NY + 1) * n, tZ = (int64_t)pe - tX - tY;
@@ -378,16 +415,40 @@ cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* 
     if (c->p.k_prec == CPM_PREC_F16X2) CPM_TRY(tc_recip_prepare(c));
     CPM_TRY(build_col0_sites(c));
     const size_t nn = (size_t)n * n;
-    CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));
-    CPM_TRY(dev_alloc(c, (void**)&c->W, sizeof(double) * nn));
+    if (with_A) {
+        CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));
+        CPM_TRY(dev_alloc(c, (void**)&c->W, sizeof(double) * nn));
+    }
     CPM_TRY(dev_alloc(c, (void**)&c->S, sizeof(double) * nn));
     CPM_TRY(dev_alloc(c, (void**)&c->S32, sizeof(float) * nn));
     CPM_TRY(dev_alloc(c, (void**)&c->SG, sizeof(double) * n * n_groups));
     CPM_TRY(dev_alloc(c, (void**)&c->u, sizeof(double) * n));
     CPM_TRY(dev_alloc(c, (void**)&c->dvec, sizeof(double) * n));
-    CPM_TRY(assemble_A(c));
+    if (with_A) CPM_TRY(assemble_A(c));
     CPM_CUDA(c, cudaStreamSynchronize(st));
+    c->has_A = with_A;
     c->assembled = true;
+    return CPM_OK;
+}
+
+cpm_status cpm_assemble(cpm_ctx* c, int64_t n, const double* xyz, const double* eta, const int32_t* group,
+                        int32_t n_groups) {
+    return assemble_impl(c, n, xyz, eta, group, n_groups, true);
+}
+
+cpm_status cpm_prepare(cpm_ctx* c, int64_t n, const double* xyz, const double* eta, const int32_t* group,
+                       int32_t n_groups) {
+    return assemble_impl(c, n, xyz, eta, group, n_groups, false);
+}
+
+cpm_status cpm_release_assembly(cpm_ctx* c) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_release_assembly before cpm_invert");
+    CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, c->A);
+    dev_free(c, c->W);
+    c->A = c->W = nullptr;
+    c->has_A = false;
     return CPM_OK;
 }
 
@@ -395,11 +456,12 @@ cpm_status cpm_invert(cpm_ctx* c) {
     if (!c) return CPM_E_ARG;
     c->err.clear();
     if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_invert before cpm_assemble");
+    if (!c->has_A) return set_err(c, CPM_E_STATE, "cpm_invert: A is not held (cpm_prepare or cpm_release_assembly)");
     c->inverted = false;
     dev_free(c, c->Sb);
     c->Sb = nullptr;
     drop_graph(c);
-    CPM_TRY(invert_and_project(c));
+    CPM_TRY(c->p.chol == CPM_CHOL_FP32_IR ? invert_ir(c) : invert_and_project(c));
     c->inverted = true;
     return CPM_OK;
 }
@@ -510,6 +572,14 @@ cpm_status cpm_set_s_prec(cpm_ctx* c, int32_t s_prec) {
     return CPM_OK;
 }
 
+cpm_status cpm_inversion_info(cpm_ctx* c, int32_t* sweeps, double* resid) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_inversion_info before cpm_invert");
+    if (sweeps) *sweeps = c->p.chol == CPM_CHOL_FP32_IR ? c->ir_sweeps : 0;
+    if (resid) *resid = c->p.chol == CPM_CHOL_FP32_IR ? c->ir_resid : 0.0;
+    return CPM_OK;
+}
+
 cpm_status cpm_gemm_set_plan(cpm_ctx* c, int32_t m, const int32_t* plan) {
     if (!c || m < 1 || !plan) return CPM_E_ARG;
     if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_gemm_set_plan before cpm_invert");
@@ -536,7 +606,7 @@ cpm_status cpm_get_matrix(cpm_ctx* c, int32_t which, double* out) {
     size_t cnt = 0;
     const size_t n = (size_t)c->n;
     switch (which) {
-        case CPM_MAT_A: if (!c->assembled) return CPM_E_STATE; src = c->A; cnt = n * n; break;
+        case CPM_MAT_A: if (!c->assembled || !c->has_A) return CPM_E_STATE; src = c->A; cnt = n * n; break;
         case CPM_MAT_S: if (!c->inverted) return CPM_E_STATE; src = c->S; cnt = n * n; break;
         case CPM_MAT_SG: if (!c->inverted) return CPM_E_STATE; src = c->SG; cnt = n * c->ng; break;
         case CPM_MAT_U: if (!c->inverted) return CPM_E_STATE; src = c->u; cnt = n; break;
@@ -587,28 +657,34 @@ struct FileHeader {
     uint64_t hash;
     double alpha, rcut, kcut;
     int32_t boundary, symm;
+    double etd;          // e^T A^-1 e
 };
 
-cpm_status cpm_save(cpm_ctx* c, const char* path) {
-    if (!c || !path) return CPM_E_ARG;
-    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_save before cpm_invert");
+static size_t export_bytes(const cpm_ctx* c) {
+    const size_t n = (size_t)c->n;
+    return sizeof(FileHeader) + sizeof(double) * (n * n + n * c->ng + n);
+}
+
+cpm_status cpm_export(cpm_ctx* c, void* buf, size_t cap, size_t* bytes) {
+    if (!c) return CPM_E_ARG;
+    if (!c->inverted) return set_err(c, CPM_E_STATE, "cpm_export before cpm_invert");
+    const size_t need = export_bytes(c);
+    if (bytes) *bytes = need;
+    if (!buf) return CPM_OK;
+    if (cap < need) return set_err(c, CPM_E_ARG, "cpm_export: %zu bytes needed, %zu given", need, cap);
     const size_t n = (size_t)c->n;
     FileHeader h{};
     memcpy(h.magic, "CPMSMAT", 8);
-    h.version = 1; h.ng = c->ng; h.n = c->n; h.hash = c->geom_hash;
+    h.version = 2; h.ng = c->ng; h.n = c->n; h.hash = c->geom_hash;
     h.alpha = c->p.alpha; h.rcut = c->p.rcut; h.kcut = c->p.kcut; h.boundary = c->p.boundary; h.symm = c->p.symm;
-    std::vector<double> buf(n * n + n * c->ng + n);
-    CPM_CUDA(c, cudaMemcpyAsync(buf.data(), c->S, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(buf.data() + n * n, c->SG, sizeof(double) * n * c->ng, cudaMemcpyDeviceToHost,
-                                c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(buf.data() + n * n + n * c->ng, c->u, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                                c->stream));
+    h.etd = c->etd;
+    memcpy(buf, &h, sizeof h);
+    double* d = (double*)((char*)buf + sizeof h);
+    CPM_CUDA(c, cudaMemcpyAsync(d, c->S, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(d + n * n, c->SG, sizeof(double) * n * c->ng, cudaMemcpyDeviceToHost, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(d + n * n + n * c->ng, c->u, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
-    FILE* f = fopen(path, "wb");
-    if (!f) return set_err(c, CPM_E_ARG, "cpm_save: cannot open %s", path);
-    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
-    ok = (fclose(f) == 0) && ok;
-    return ok ? CPM_OK : set_err(c, CPM_E_ARG, "cpm_save: write failed for %s", path);
+    return CPM_OK;
 }
 
 __global__ void k_tofloat(const double* a, float* b, int64_t cnt) {
@@ -616,36 +692,59 @@ __global__ void k_tofloat(const double* a, float* b, int64_t cnt) {
     if (i < cnt) b[i] = (float)a[i];
 }
 
-cpm_status cpm_load(cpm_ctx* c, const char* path) {
-    if (!c || !path) return CPM_E_ARG;
-    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_load before cpm_assemble");
-    FILE* f = fopen(path, "rb");
-    if (!f) return set_err(c, CPM_E_ARG, "cpm_load: cannot open %s", path);
-    FileHeader h{};
+cpm_status cpm_import(cpm_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return CPM_E_ARG;
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_import before cpm_assemble or cpm_prepare");
     const size_t n = (size_t)c->n;
-    bool ok = fread(&h, sizeof h, 1, f) == 1 && memcmp(h.magic, "CPMSMAT", 8) == 0 && h.version == 1;
-    if (!ok || h.n != c->n || h.ng != c->ng || h.hash != c->geom_hash || h.alpha != c->p.alpha ||
-        h.rcut != c->p.rcut || h.kcut != c->p.kcut || h.boundary != c->p.boundary || h.symm != c->p.symm) {
-        fclose(f);
-        return set_err(c, CPM_E_ARG, "cpm_load: %s does not match this geometry and parameters", path);
-    }
-    std::vector<double> buf(n * n + n * c->ng + n);
-    ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
-    fclose(f);
-    if (!ok) return set_err(c, CPM_E_ARG, "cpm_load: short file %s", path);
-    CPM_CUDA(c, cudaMemcpyAsync(c->S, buf.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(c->SG, buf.data() + n * n, sizeof(double) * n * c->ng, cudaMemcpyHostToDevice,
-                                c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(c->u, buf.data() + n * n + n * c->ng, sizeof(double) * n, cudaMemcpyHostToDevice,
-                                c->stream));
+    FileHeader h{};
+    if (bytes < sizeof h) return set_err(c, CPM_E_ARG, "cpm_import: %zu bytes is shorter than the header", bytes);
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "CPMSMAT", 8) != 0 || h.version != 2 || h.n != c->n || h.ng != c->ng ||
+        h.hash != c->geom_hash || h.alpha != c->p.alpha || h.rcut != c->p.rcut || h.kcut != c->p.kcut ||
+        h.boundary != c->p.boundary || h.symm != c->p.symm)
+        return set_err(c, CPM_E_ARG, "cpm_import: the checkpoint does not match this geometry and parameters");
+    if (bytes < export_bytes(c)) return set_err(c, CPM_E_ARG, "cpm_import: short checkpoint (%zu bytes)", bytes);
+    const double* d = (const double*)((const char*)buf + sizeof h);
+    CPM_CUDA(c, cudaMemcpyAsync(c->S, d, sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->SG, d + n * n, sizeof(double) * n * c->ng, cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->u, d + n * n + n * c->ng, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
     dev_free(c, c->Sb);
     c->Sb = nullptr;
     drop_graph(c);
     k_tofloat<<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(c->S, c->S32, (int64_t)(n * n));
     CPM_LAUNCH(c, "k_tofloat");
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->etd = h.etd;
+    ccm_invalidate(c);
     c->inverted = true;
     return CPM_OK;
+}
+
+cpm_status cpm_save(cpm_ctx* c, const char* path) {
+    if (!c || !path) return CPM_E_ARG;
+    size_t need = 0;
+    CPM_TRY(cpm_export(c, nullptr, 0, &need));
+    std::vector<char> buf(need);
+    CPM_TRY(cpm_export(c, buf.data(), need, &need));
+    FILE* f = fopen(path, "wb");
+    if (!f) return set_err(c, CPM_E_ARG, "cpm_save: cannot open %s", path);
+    bool ok = fwrite(buf.data(), 1, need, f) == need;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? CPM_OK : set_err(c, CPM_E_ARG, "cpm_save: write failed for %s", path);
+}
+
+cpm_status cpm_load(cpm_ctx* c, const char* path) {
+    if (!c || !path) return CPM_E_ARG;
+    if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_load before cpm_assemble");
+    FILE* f = fopen(path, "rb");
+    if (!f) return set_err(c, CPM_E_ARG, "cpm_load: cannot open %s", path);
+    std::vector<char> buf(export_bytes(c));
+    const size_t got = fread(buf.data(), 1, buf.size(), f);
+    fclose(f);
+    if (got < sizeof(FileHeader)) return set_err(c, CPM_E_ARG, "cpm_load: %s does not match this geometry and parameters", path);
+    cpm_status st = cpm_import(c, buf.data(), got);
+    if (st == CPM_E_ARG) return set_err(c, CPM_E_ARG, "cpm_load: %s does not match this geometry and parameters", path);
+    return st;
 }
 
 cpm_status cpm_profile(cpm_ctx* c, int32_t enable) {

@@ -47,7 +47,7 @@ __global__ void k_A_real(const double* __restrict__ sx, int64_t n, Geometry g, d
             }
         }
         if (i == j) acc += (sqrt(2.0) * ei - 2.0 * a) / sqrt(PI);
-        acc += -PI / (g.V * a * a);
+        if (g.bc != CPM_BC_EW2D) acc += -PI / (g.V * a * a);
         if (g.bc == CPM_BC_SLAB) acc += (4.0 * PI / g.V) * (Z[i] * Z[j]);
         else if (g.bc == CPM_BC_WIRE) acc += (2.0 * PI / g.V) * (X[i] * X[j] + Y[i] * Y[j]);
         A[i * n + j] = KE * acc;
@@ -132,6 +132,7 @@ cpm_status assemble_A(cpm_ctx* c) {
     dim3 g1((unsigned)((n + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
     k_A_real<<<g1, 256, 0, c->stream>>>(c->sx, n, c->g, c->A);
     CPM_LAUNCH(c, "k_A_real");
+    if (c->g.bc == CPM_BC_EW2D) return assemble_ew2d(c);
     if (c->kt.nk > 0) {
         const int64_t nt = (n + KA_BM - 1) / KA_BM;
         const int64_t blocks = nt * (nt + 1) / 2;

@@ -44,13 +44,14 @@ constexpr int ST_THREADS = 256;
 // Binning and the per-replica totals in one pass: grid (charge blocks, m), one thread per charge.
 // Each charge gets its wrapped position and its cell (cells of the real-space grid); each block sums
 // (Q, Q x, Q y, Q z) over its charges into part[r][b][4], and the replica's last block adds the
-// block sums in order (stats[r]).
+// block sums in order (stats[r]).  Charges with Q = 0 (padding) get no cell (key -1) and are not
+// counted: nzc[r] counts the replica's others, and the cell list holds only those.
 constexpr int ST_Q = 4;   // totals per replica
 template <typename T>
 __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ xyz, const double* __restrict__ Q,
                                                   int64_t ne, Geometry g, CellGrid cg, float3 inv_h, int* key,
                                                   int* count, typename V4<T>::t* wpos, double* part,
-                                                  int* tickets, double* stats) {
+                                                  int* tickets, double* stats, int* nzc) {
     const int b = blockIdx.x, nb = gridDim.x, r = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t j = (int64_t)b * ST_THREADS + threadIdx.x;
@@ -71,11 +72,16 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
         }
         a[0] = q;
         const int k = r * cg.ncells + (ci[2] * cg.nc[1] + ci[1]) * cg.nc[0] + ci[0];
-        key[p] = k;
-        atomicAdd(&count[k], 1);
+        key[p] = q != 0.0 ? k : -1;
+        if (q != 0.0) atomicAdd(&count[k], 1);
         typename V4<T>::t v;
         v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)q;
         wpos[p] = v;
+    }
+    {   // nonzero charges of the replica, one atomic per warp
+        const bool nz = j < ne && Q[(int64_t)r * ne + j] != 0.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0 && bal) atomicAdd(&nzc[r], __popc(bal));
     }
     // block sums in a fixed order: the thread values through shared memory, warp t of the first four
     // takes quantity t (each lane adds eight threads' values, then a shuffle tree)
@@ -113,16 +119,22 @@ __global__ void __launch_bounds__(ST_THREADS) k_bin(const double* __restrict__ x
     if (threadIdx.x < ST_Q) stats[4 * r + threadIdx.x] = v;
 }
 
-// Per-replica exclusive scan of cell counts into global start offsets (replica r starts at r * ne):
+// Per-replica exclusive scan of cell counts into global start offsets (replica r starts after the
+// nonzero charges of the replicas before it, so the cells of all replicas are contiguous):
 // one block per replica; each thread takes CS_PER consecutive cells of a tile of CS_THREADS x CS_PER.
 // The block is small enough to run beside a structure-factor CTA on its SM.
 constexpr int CS_THREADS = 256, CS_PER = 8;
-__global__ void __launch_bounds__(CS_THREADS) k_cellscan(const int* count, int* start, int ncells, int64_t ne, int m) {
+__global__ void __launch_bounds__(CS_THREADS) k_cellscan(const int* count, int* start, int ncells, int64_t ne, int m,
+                                                         const int* nzc) {
     __shared__ int warp_tot[CS_THREADS / 32];
     __shared__ int carry;
     const int r = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = (int)(r * ne);
+    if (threadIdx.x == 0) {
+        int c0 = 0;
+        for (int q = 0; q < r; ++q) c0 += nzc[q];
+        carry = c0;
+    }
     __syncthreads();
     for (int base = 0; base < ncells; base += CS_THREADS * CS_PER) {
         const int i0 = base + (int)threadIdx.x * CS_PER;
@@ -158,13 +170,14 @@ __global__ void __launch_bounds__(CS_THREADS) k_cellscan(const int* count, int* 
         if (threadIdx.x == CS_THREADS - 1) carry = run;
         __syncthreads();
     }
-    if (r == m - 1 && threadIdx.x == 0) start[m * ncells] = (int)(m * ne);
+    if (r == m - 1 && threadIdx.x == 0) start[m * ncells] = carry;
 }
 
 __global__ void k_scatter(const int* key, const int* start, int* cursor, int64_t ptot, int* order) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ptot) return;
     int k = key[p];
+    if (k < 0) return;   // a zero charge: in no cell
     order[start[k] + atomicAdd(&cursor[k], 1)] = (int)p;
 }
 
@@ -1153,7 +1166,7 @@ __global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols
 template <typename T>
 __global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const int* zmap,
                           int nzu, const double* stats, const double* sx, int64_t n, int m, Geometry g, double* b,
-                          float2* bhl) {
+                          float2* bhl, const double* ew) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
@@ -1182,7 +1195,8 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     s += rl;
     if (b0) s += bz;
     const double* st = stats + 4 * r;
-    s += -PI * st[0] / (g.V * g.alpha * g.alpha);
+    if (ew) s += ew[t];   // EW2D: the 2D long-range sum with its constant, no background or dipole term
+    else s += -PI * st[0] / (g.V * g.alpha * g.alpha);
     if (g.bc == CPM_BC_SLAB) s += (4.0 * PI / g.V) * sx[2 * n + i] * st[3];
     else if (g.bc == CPM_BC_WIRE) s += (2.0 * PI / g.V) * (sx[i] * st[1] + sx[n + i] * st[2]);
     const double v = KE * s;
@@ -1202,7 +1216,8 @@ struct BvecPlan {
     int splits, nctiles, ctiles, ztiles;
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
-        off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, total;
+        off_nzc, off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, off_ew,
+        off_ewT, total;
     int c0chunks;
     bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
     size_t off_qabs, off_tcpart, off_w16, off_spart, off_qpart, off_c0q;
@@ -1254,6 +1269,7 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_key = o; o += al(sizeof(int) * ptot);
     p.off_cnt = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
     p.off_cur = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
+    p.off_nzc = o; o += al(sizeof(int) * (size_t)m);
     p.off_start = o; o += al(sizeof(int) * ((size_t)m * p.cg.ncells + 1));
     p.off_wpos = o; o += al(sizeof(typename V4<T>::t) * ptot);
     p.off_sorted = o; o += al(sizeof(typename V4<T>::t) * ptot);
@@ -1269,6 +1285,11 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_qabs = o; o += al(sizeof(float2) * m);
     p.off_spart = o; o += al(sizeof(double) * ST_Q * (size_t)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS) * m);
     p.off_qpart = o; o += al(sizeof(double) * 2 * (size_t)std::max<int64_t>(1, (ne + FR_THREADS - 1) / FR_THREADS) * m);
+    p.off_ew = p.off_ewT = o;
+    if (c->g.bc == CPM_BC_EW2D) {
+        p.off_ew = o; o += al(sizeof(double) * (size_t)m * c->n);
+        p.off_ewT = o; o += al(ew2d_T_bytes(c, m));
+    }
     p.off_tcpart = p.off_w16 = o;
     if (p.tc) {
         p.off_tcpart = o; o += al(tc_recip_part_bytes(td, m, k.nzw));
@@ -1363,12 +1384,13 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     // binning and the per-replica totals (one pass over the charges)
     prof_begin(c, CPM_K_CELLS);
     float2* qabs = (float2*)(scr + p.off_qabs);
-    CPM_CUDA(c, cudaMemsetAsync(cnt, 0, p.off_start - p.off_cnt, st));   // counts and cursors
+    CPM_CUDA(c, cudaMemsetAsync(cnt, 0, p.off_start - p.off_cnt, st));   // counts, cursors, nonzero counts
+    int* nzc = (int*)(scr + p.off_nzc);
     {
         const float3 inv_h = make_float3((float)(1.0 / p.cg.h[0]), (float)(1.0 / p.cg.h[1]), (float)(1.0 / p.cg.h[2]));
         const unsigned nbx = (unsigned)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS);
         k_bin<T><<<dim3(nbx, m), ST_THREADS, 0, st>>>(xyz, Q, ne, c->g, p.cg, inv_h, key, cnt, wpos,
-                                                     (double*)(scr + p.off_spart), c->tickets, stats);
+                                                     (double*)(scr + p.off_spart), c->tickets, stats, nzc);
         CPM_LAUNCH(c, "k_bin");
     }
     prof_end(c, CPM_K_CELLS);
@@ -1420,8 +1442,15 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     } else {
         CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, s1));
     }
+    double* ew = nullptr;
+    if (c->g.bc == CPM_BC_EW2D) {
+        ew = (double*)(scr + p.off_ew);
+        prof_begin(c, CPM_K_SF);
+        CPM_TRY(ew2d_run<T>(c, s1, m, ne, xyz, Q, scr + p.off_ewT, ew));
+        prof_end(c, CPM_K_SF);
+    }
     prof_begin(c, CPM_K_CELLS);
-    k_cellscan<<<m, CS_THREADS, 0, st>>>(cnt, start, p.cg.ncells, ne, m);
+    k_cellscan<<<m, CS_THREADS, 0, st>>>(cnt, start, p.cg.ncells, ne, m, nzc);
     CPM_LAUNCH(c, "k_cellscan");
     if (ptot > 0) {
         k_scatter<<<(unsigned)((ptot + 255) / 256), 256, 0, st>>>(key, start, cur, ptot, order);
@@ -1462,7 +1491,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
-                                                                          stats, c->sx, n, m, c->g, b_out, bhl);
+                                                                          stats, c->sx, n, m, c->g, b_out, bhl, ew);
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;

@@ -124,6 +124,9 @@ struct cpm_ctx {
     int nrtab = 0;
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
     cpm::KTable kt;
+    int2* h2d_idx = nullptr;     // EW2D: half-plane 2D vectors (nx, ny), 0 < |h| <= kcut
+    double* h2d_norm = nullptr;  // their |h|
+    int nh2d = 0;
     cpm::Phases<double> site64;
     cpm::Phases<float> site32;
     uint64_t geom_hash = 0;
@@ -144,6 +147,19 @@ struct cpm_ctx {
     double* nbuf = nullptr;      // neutrality fix: per-block partial sums of q
     size_t nbuf_bytes = 0;
     bool assembled = false, inverted = false;
+    bool has_A = false;          // A (and the factor workspace W) allocated and valid
+    double etd = 0.0;            // e^T A^-1 e (FP64), kept with S
+    int ir_sweeps = 0;           // refinement sweeps of the last FP32-factor inversion
+    double ir_resid = 0.0;       // its final max-norm residual of A X = I
+    // constant charge / thermo-potentiostat / finite field (ccm.cu), rebuilt after every inversion
+    bool ccm_ready = false;
+    double* ccm_buf = nullptr;   // inverse of G^T A^-1 G (N_g x N_g), then G^T u (N_g)
+    double ccm_C0 = 0.0;         // g_1^T S g_1
+    void* ccm_scr = nullptr;     // per-call electrode potentials and totals
+    size_t ccm_scr_bytes = 0;
+    double* SGx = nullptr;       // [n][N_g + 1]: SG and S zeta (finite field)
+    const double* sg_over = nullptr;   // when set, the update reads these responses and columns
+    int ng_over = 0;
 
     // per-step scratch, grown on demand
     int cap_m = 0;
@@ -157,14 +173,20 @@ struct cpm_ctx {
     size_t dstage_bytes = 0;
     void* ubuf = nullptr;        // cpm_update scratch (split partial sums, b hi/lo)
     size_t ubuf_bytes = 0;
-    // cpm_step_graph: one captured bvec + update sequence
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
+    // cpm_step_graph: captured bvec + update sequences, one per (m, n_e, buffer addresses), at most
+    // CPM_MAX_GRAPHS, least recently used replaced first; graph_valid = false (set when a scratch
+    // buffer is reallocated) drops them all at the next step
+    struct StepGraph {
+        int m = 0;
+        int64_t ne = 0;
+        const void* ptrs[6] = {};
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+        uint64_t used = 0;
+    };
+    std::vector<StepGraph> graphs;
+    uint64_t graph_clock = 0;
     bool graph_valid = false;
-    int graph_m = 0;
-    int64_t graph_ne = 0;
-    const void* graph_ptrs[7] = {};
-    int64_t graph_launches = 0;
     void* Sb = nullptr;          // S as three bf16 planes [3][n][ld] for the tensor-core update
     double* SZ = nullptr;        // [n][tc_ngrp] S times the centring-group indicators
     int tc_ngrp = 0;
@@ -191,6 +213,8 @@ struct cpm_ctx {
 };
 
 namespace cpm {
+
+constexpr int CPM_MAX_GRAPHS = 8;
 
 // error helpers (api.cu)
 cpm_status set_err(cpm_ctx* c, cpm_status s, const char* fmt, ...);
@@ -259,8 +283,20 @@ __device__ __forceinline__ bool last_block_of(int* ticket, int nblocks) {
 // assemble.cu
 cpm_status assemble_A(cpm_ctx* c);
 
+// ew2d.cu: the exact 2D-periodic slab sum
+cpm_status build_ew2d(cpm_ctx* c);
+cpm_status assemble_ew2d(cpm_ctx* c);
+size_t ew2d_T_bytes(const cpm_ctx* c, int m);
+template <typename T>
+cpm_status ew2d_run(cpm_ctx* c, cudaStream_t st, int m, int64_t ne, const double* xyz, const double* Q, void* Tbuf,
+                    double* ew);
+
 // dense.cu
 cpm_status invert_and_project(cpm_ctx* c);
+// the projection tail once S holds A^-1 (dense.cu)
+cpm_status project_inverse(cpm_ctx* c);
+// A^-1 by an FP32 Cholesky factor and FP64 iterative refinement of A X = I, then the projection (refine.cu)
+cpm_status invert_ir(cpm_ctx* c);
 cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int lower,
                         int tri, const unsigned* status);
@@ -284,6 +320,11 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
 float2* update_bhl(cpm_ctx* c, int m);
 
 cpm_status reserve_update(cpm_ctx* c, int m);
+// the electrode responses and their count the update uses (SG, or the override of the finite field)
+inline const double* upd_sg(const cpm_ctx* c) { return c->sg_over ? c->sg_over : c->SG; }
+inline int upd_ng(const cpm_ctx* c) { return c->sg_over ? c->ng_over : c->ng; }
+// after S changes (cpm_invert, cpm_import): the constant-charge tables are stale
+void ccm_invalidate(cpm_ctx* c);
 
 // tc_gemm.cu
 cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, double* q);

@@ -284,6 +284,15 @@ cpm_status invert_and_project(cpm_ctx* c) {
     dim3 g2((unsigned)((n + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
     k_mirror_lower<<<g2, 256, 0, st>>>(c->S, n);
     CPM_LAUNCH(c, "k_mirror_lower");
+    return project_inverse(c);
+}
+
+// With A^-1 in S: d = A^-1 e, e^T d, the projection of Eq. (S) (symm = 1), the FP32 copy of S, u and
+// SG = S G; synchronises.
+cpm_status project_inverse(cpm_ctx* c) {
+    const int64_t n = c->n;
+    cudaStream_t st = c->stream;
+    dim3 g2((unsigned)((n + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
     k_rowsum<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(c->S, n, c->dvec);
     CPM_LAUNCH(c, "k_rowsum");
     k_sum1<<<1, 1024, 0, st>>>(c->dvec, n, c->red);
@@ -292,7 +301,9 @@ cpm_status invert_and_project(cpm_ctx* c) {
     CPM_LAUNCH(c, "k_project");
     k_sg<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(c->S, c->group, n, c->ng, c->SG);
     CPM_LAUNCH(c, "k_sg");
+    CPM_CUDA(c, cudaMemcpyAsync(&c->etd, c->red, sizeof(double), cudaMemcpyDeviceToHost, st));
     CPM_CUDA(c, cudaStreamSynchronize(st));
+    ccm_invalidate(c);
     return CPM_OK;
 }
 

@@ -139,7 +139,9 @@ cpm_status build_ktable(cpm_ctx* c) {
     KTable& k = c->kt;
     const Geometry& g = c->g;
     const double tx = (2.0 * PI) / g.boxL[0], ty = (2.0 * PI) / g.boxL[1], tz = (2.0 * PI) / g.boxL[2];
-    const double kc2 = g.kcut * g.kcut;
+    // EW2D: no 3D reciprocal set (the 2D sum of ew2d.cu replaces it); the harmonic ranges, and with
+    // them the site phase tables, still follow kcut
+    const double kc2 = g.bc == CPM_BC_EW2D ? 0.0 : g.kcut * g.kcut;
     k.NX = (int)(g.kcut / tx) + 1;
     k.NY = (int)(g.kcut / ty) + 1;
     k.NZ = (int)(g.kcut / tz) + 1;

@@ -168,6 +168,127 @@ __global__ void k_gsum(const double* X, const int* group, int64_t n, int ng, int
     GX[t] = a;
 }
 
+__global__ void k_add_identity(double* R, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) R[i * n + i] += 1.0;
+}
+// X <- (X + X^T) / 2 (A^-1 is symmetric; the refined columns agree with it to the refinement residual)
+__global__ void k_symmetrize(double* X, int64_t n) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < j && j < n; i += gridDim.y) {
+        const double v = 0.5 * (X[i * n + j] + X[j * n + i]);
+        X[i * n + j] = v;
+        X[j * n + i] = v;
+    }
+}
+
+// FP32 blocked Cholesky of A into L (lower, in place) with the inverses of its diagonal blocks
+static cpm_status factor32(cpm_ctx* c, float* L, float* Linv) {
+    const int64_t n = c->n;
+    const int nb = (int)((n + RB - 1) / RB);
+    cudaStream_t st = c->stream;
+    CPM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), st));
+    k_d2f<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(c->A, L, n * n);
+    for (int kb0 = 0; kb0 < nb; ++kb0) {
+        const int64_t k0 = (int64_t)kb0 * RB;
+        const int kb = (int)std::min<int64_t>(RB, n - k0);
+        k_spotrf<<<1, 256, 0, st>>>(L + k0 * n + k0, n, kb, Linv + (int64_t)kb0 * RB * RB, c->status);
+        const int rows = (int)(n - k0 - kb);
+        if (rows > 0) {
+            float* P = L + (k0 + kb) * n + k0;
+            CPM_TRY(sgemm(st, false, true, rows, kb, kb, 1.f, P, n, Linv + (int64_t)kb0 * RB * RB, RB, 0.f, P, n, 0,
+                          c->status));
+            CPM_TRY(sgemm(st, false, true, rows, rows, kb, -1.f, P, n, P, n, 1.f, L + (k0 + kb) * (n + 1), n, 1,
+                          c->status));
+        }
+    }
+    unsigned hst = 0;
+    CPM_CUDA(c, cudaMemcpyAsync(&hst, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(c, cudaStreamSynchronize(st));
+    if (hst & ST_NOT_SPD) return set_err(c, CPM_E_NOT_SPD, "elastance matrix is not positive definite (FP32 factor)");
+    return CPM_OK;
+}
+
+// Y <- (L L^T)^-1 Y for nr right-hand sides in FP32: forward then backward block substitution
+static cpm_status solve32(cpm_ctx* c, const float* L, const float* Linv, float* Y, int nr) {
+    const int64_t n = c->n;
+    const int nb = (int)((n + RB - 1) / RB);
+    cudaStream_t st = c->stream;
+    for (int ib = 0; ib < nb; ++ib) {
+        const int64_t i0 = (int64_t)ib * RB;
+        const int kb = (int)std::min<int64_t>(RB, n - i0);
+        CPM_TRY(sgemm(st, false, false, kb, nr, kb, 1.f, Linv + (int64_t)ib * RB * RB, RB, Y + i0 * nr, nr, 0.f,
+                      Y + i0 * nr, nr, 0, nullptr));
+        const int below = (int)(n - i0 - kb);
+        if (below > 0)
+            CPM_TRY(sgemm(st, false, false, below, nr, kb, -1.f, L + (i0 + kb) * n + i0, n, Y + i0 * nr, nr, 1.f,
+                          Y + (i0 + kb) * nr, nr, 0, nullptr));
+    }
+    for (int ib = nb - 1; ib >= 0; --ib) {
+        const int64_t i0 = (int64_t)ib * RB;
+        const int kb = (int)std::min<int64_t>(RB, n - i0);
+        CPM_TRY(sgemm(st, true, false, kb, nr, kb, 1.f, Linv + (int64_t)ib * RB * RB, RB, Y + i0 * nr, nr, 0.f,
+                      Y + i0 * nr, nr, 0, nullptr));
+        if (i0 > 0)
+            CPM_TRY(sgemm(st, true, false, (int)i0, nr, kb, -1.f, L + i0 * n, n, Y + i0 * nr, nr, 1.f, Y, nr, 0, nullptr));
+    }
+    return CPM_OK;
+}
+
+// A^-1 from the FP32 factor, refined in FP64 (X <- X + (L L^T)^-1 (I - A X), residual against the FP64
+// A) until the residual stops shrinking; X is kept in S and the residual in the factor workspace W.
+cpm_status invert_ir(cpm_ctx* c) {
+    const int64_t n = c->n;
+    const int nb = (int)((n + RB - 1) / RB);
+    cudaStream_t st = c->stream;
+    float *L = nullptr, *Linv = nullptr, *Y = nullptr;
+    double* red = nullptr;
+    auto cleanup = [&]() { dev_free(c, L); dev_free(c, Linv); dev_free(c, Y); dev_free(c, red); };
+    cpm_status s = CPM_OK;
+#define IR_TRY(expr)       \
+    do {                   \
+        s = (expr);        \
+        if (s != CPM_OK) { \
+            cleanup();     \
+            return s;      \
+        }                  \
+    } while (0)
+    IR_TRY(dev_alloc(c, (void**)&L, sizeof(float) * n * n));
+    IR_TRY(dev_alloc(c, (void**)&Linv, sizeof(float) * RB * RB * nb));
+    IR_TRY(dev_alloc(c, (void**)&Y, sizeof(float) * n * n));
+    IR_TRY(dev_alloc(c, (void**)&red, sizeof(double) * 8));
+    IR_TRY(factor32(c, L, Linv));
+    double* X = c->S;
+    double* R = c->W;
+    IR_TRY(cuda_check(c, cudaMemsetAsync(X, 0, sizeof(double) * n * n, st), "memset"));
+    double resid = 1.0, prev = 1e300;
+    int it = 0;
+    for (; it < 30; ++it) {
+        // R = I - A X (FP64)
+        IR_TRY(launch_dgemm(st, false, false, (int)n, (int)n, (int)n, -1.0, c->A, n, X, n, 0.0, R, n, 0, 0, nullptr));
+        k_add_identity<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(R, n);
+        k_maxabs<<<1, 1024, 0, st>>>(R, n * n, red);
+        double rmax = 0.0;
+        IR_TRY(cuda_check(c, cudaMemcpyAsync(&rmax, red, sizeof(double), cudaMemcpyDeviceToHost, st), "copy"));
+        IR_TRY(cuda_check(c, cudaStreamSynchronize(st), "sync"));
+        resid = rmax;
+        if (!(resid < prev * 0.9) && it > 0) break;   // no longer shrinking
+        prev = resid;
+        if (resid < 1e-15) break;
+        k_d2f<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(R, Y, n * n);
+        IR_TRY(solve32(c, L, Linv, Y, (int)n));
+        k_axpy_f2d<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(Y, X, n * n);
+    }
+    c->ir_sweeps = it;
+    c->ir_resid = resid;
+    dim3 g2((unsigned)((n + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+    k_symmetrize<<<g2, 256, 0, st>>>(X, n);
+    IR_TRY(cuda_check(c, cudaGetLastError(), "k_symmetrize"));
+    cleanup();
+#undef IR_TRY
+    return project_inverse(c);
+}
+
 }  // namespace cpm
 
 using namespace cpm;
@@ -175,6 +296,7 @@ using namespace cpm;
 extern "C" cpm_status cpm_capacitance_ir(cpm_ctx* c, double* C_out, int32_t* iters_out, double* resid_out) {
     if (!c || !C_out) return CPM_E_ARG;
     if (!c->assembled) return set_err(c, CPM_E_STATE, "cpm_capacitance_ir before cpm_assemble");
+    if (!c->has_A) return set_err(c, CPM_E_STATE, "cpm_capacitance_ir: A is not held (cpm_prepare or cpm_release_assembly)");
     const int64_t n = c->n;
     const int ng = c->ng, nr = ng + 1;
     cudaStream_t st = c->stream;

@@ -546,7 +546,7 @@ cpm_status tc_update(cpm_ctx* c, int m, const double* psi, const double* b, doub
     CPM_LAUNCH(c, "k_gmeans");
     int splits = 0;
     CPM_TRY(tc_sb(c, m, b, part, &splits, bsplit, gmean, gid, c->tc_ngrp));
-    k_tc_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, c->stream>>>(part, splits, c->SG, c->ng, psi, c->SZ, gmean,
+    k_tc_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, c->stream>>>(part, splits, upd_sg(c), upd_ng(c), psi, c->SZ, gmean,
                                                                         c->tc_ngrp, n, m, q);
     CPM_LAUNCH(c, "k_tc_reduce");
     c->launches += 4;

@@ -576,10 +576,10 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     prof_begin(c, CPM_K_NEUTRAL);
     const dim3 rgrid((unsigned)reduce_blocks(n), m);
     if (f32 && gemv_tma_supported(c))
-        k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, c->SG, c->ng, psi, n, m, q,
+        k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, upd_sg(c), upd_ng(c), psi, n, m, q,
                                                       c->nbuf, c->u, c->p.symm, c->tickets, qtot);
     else
-        k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, c->SG, c->ng, psi, n, m, q, c->nbuf, c->u,
+        k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, upd_sg(c), upd_ng(c), psi, n, m, q, c->nbuf, c->u,
                                                       c->p.symm, c->tickets, qtot);
     prof_end(c, CPM_K_NEUTRAL);
     CPM_LAUNCH(c, "k_gemv");

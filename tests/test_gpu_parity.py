@@ -304,3 +304,103 @@ def test_step_host_on_a_stream_replays_the_graph(tiny):
             ref.cpm_step_graph(m, ne, dev(xyz), dev(Q), dev(psis), b, qd, qtd)
         ref.stream.synchronize()
         assert np.array_equal(q, qd.cpu().numpy()) and np.array_equal(qt, qtd.cpu().numpy())
+
+
+def test_checkpoint_in_host_memory_restores_without_assembly(tiny):
+    """cpm_export / cpm_import through host memory, into a context prepared without A (cpm_prepare):
+    the same S and the same charges as the assembled, inverted context; cpm_release_assembly frees A
+    and W and the context still updates."""
+    from paper_2203_15461_gb300.cpm import CPMError
+    el, ely, psi, _, _ = tiny
+    a = make_ctx(el).setup(el)
+    buf = a.cpm_export()
+    b = make_ctx(el)
+    b.cpm_prepare(dev(el.xyz), dev(el.eta), dev(el.group, torch.int32), el.n_groups)
+    with pytest.raises(CPMError, match="CPM_E_STATE"):
+        b.cpm_invert()
+    b.cpm_import(buf)
+    assert torch.equal(a.cpm_get_matrix("S"), b.cpm_get_matrix("S"))
+    q_a, _ = run_update(a, psi, run_bvec(a, [ely]))
+    q_b, _ = run_update(b, psi, run_bvec(b, [ely]))
+    assert np.array_equal(q_a, q_b)
+    held = a.cpm_device_bytes()
+    a.cpm_release_assembly()
+    assert held - a.cpm_device_bytes() >= 2 * 8 * el.n * el.n
+    with pytest.raises(CPMError, match="CPM_E_STATE"):
+        a.cpm_get_matrix("A")
+    q_c, _ = run_update(a, psi, run_bvec(a, [ely]))
+    assert np.array_equal(q_a, q_c)
+    other = s.au111_slab(gap=22.0)
+    c = make_ctx(other)
+    c.cpm_prepare(dev(other.xyz), dev(other.eta), dev(other.group, torch.int32), other.n_groups)
+    with pytest.raises(CPMError, match="CPM_E_ARG"):
+        c.cpm_import(buf)
+
+
+def test_several_captured_graphs_are_kept(tiny):
+    """Graphs for different batch sizes are kept side by side and replay the same charges as the
+    separate calls."""
+    el, _, psi, _, _ = tiny
+    st = torch.cuda.Stream()
+    ctx = make_ctx(el, s_prec="fp32", k_prec="fp32", stream=st).setup(el)
+    from gpu_util import stack_replicas
+    bufs = {}
+    for m in (1, 2, 4, 1, 4, 2):
+        elyts = [s.ions_in_gap(el, 100, seed=60 * m + r) for r in range(m)]
+        xyz, Q, ne = stack_replicas(elyts, n_e=100)
+        if m not in bufs:
+            with torch.cuda.stream(st):
+                bufs[m] = [torch.empty((m * ne, 3), dtype=torch.float64, device="cuda"),
+                           torch.empty(m * ne, dtype=torch.float64, device="cuda"),
+                           dev(np.tile(psi, (m, 1))), torch.empty((m, el.n), dtype=torch.float64, device="cuda"),
+                           torch.empty((m, el.n), dtype=torch.float64, device="cuda"),
+                           torch.empty(m, dtype=torch.float64, device="cuda")]
+        dx, dQ, dp, b, q, qt = bufs[m]
+        with torch.cuda.stream(st):
+            dx.copy_(dev(xyz)); dQ.copy_(dev(Q))
+            ctx.cpm_step_graph(m, ne, dx, dQ, dp, b, q, qt)
+        st.synchronize()
+        got = q.cpu().numpy().copy()
+        ref = make_ctx(el, s_prec="fp32", k_prec="fp32").setup(el)
+        qr, _ = run_update(ref, psi, run_bvec(ref, elyts))
+        assert np.array_equal(got, qr)
+
+
+@pytest.mark.parametrize("which", ["tiny", "coax"])
+def test_fp32_factor_with_fp64_refinement_forms_S(which):
+    """cpm_params.chol = FP32_IR: A X = I solved with the FP32 Cholesky factor and refined in FP64 against the
+    FP64 A; S (Eq. S) and the charges match the oracle to the FP64 tolerances."""
+    need_gpu()
+    el = s.au111_slab() if which == "tiny" else s.coaxial_tubes(2)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    ctx = make_ctx(el, chol="fp32_ir").setup(el)
+    sweeps, resid = ctx.cpm_inversion_info()
+    assert sweeps >= 1 and resid < 1e-10
+    assert rel_l2(ctx.cpm_get_matrix("S").cpu().numpy(), S) <= 1e-10
+    ely = s.ions_in_gap(el, 60, seed=2) if which == "tiny" else s.Electrolyte(
+        xyz=np.column_stack([np.full(6, 40.0), np.full(6, 41.0), np.linspace(0.5, 4.0, 6)]), Q=np.tile([1.0, -1.0], 3))
+    b = run_bvec(ctx, [ely])
+    q, qt = run_update(ctx, np.array([0.0, 1.0]), b)
+    q_ref = o.charges(S, el, np.array([0.0, 1.0]), o.bvec(el, ely))
+    assert rel_l2(q[0], q_ref) <= 1e-10 and abs(qt[0]) <= 1e-12
+
+
+def test_zero_charge_padding_is_left_out(tiny):
+    """Replicas padded with Q = 0 charges stacked on one position (as a server pads a batch) give the same b as
+    without padding: zero charges enter no cell of the real-space list."""
+    el, ely, _, _, _ = tiny
+    ctx = make_ctx(el).setup(el)
+    ref = run_bvec(ctx, [ely])[0]
+    m, ne = 3, 10 * ely.n
+    xyz = np.zeros((m, ne, 3))
+    Q = np.zeros((m, ne))
+    xyz[:] = ely.xyz[0]
+    xyz[1, :ely.n] = ely.xyz
+    Q[1, :ely.n] = ely.Q
+    b = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+    ctx.cpm_bvec(m, ne, dev(xyz.reshape(-1, 3)), dev(Q.reshape(-1)), b)
+    torch.cuda.synchronize()
+    b = b.cpu().numpy()
+    assert rel_l2(b[1], ref) <= 1e-13
+    assert np.abs(b[0]).max() == 0.0 and np.abs(b[2]).max() == 0.0
