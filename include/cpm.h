@@ -248,7 +248,7 @@ cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz
  * cpm_bvec followed by cpm_update as one CUDA graph (device buffers as in those calls;
  * b_out receives b).  The first call for given (m, n_e, buffer addresses) reserves the
  * scratch, captures the launches on the context stream and instantiates the graph; later
- * calls with the same arguments replay it with one launch.  The context keeps up to eight
+ * calls with the same arguments replay it with one launch.  The context keeps up to 24
  * such graphs (least recently used replaced first); a call that has to grow the scratch drops
  * them all.  Needs a context created on a non-default stream.
  * Errors: as cpm_bvec / cpm_update; CPM_E_ARG for the default stream.

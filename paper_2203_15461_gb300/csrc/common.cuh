@@ -174,7 +174,7 @@ struct cpm_ctx {
     void* ubuf = nullptr;        // cpm_update scratch (split partial sums, b hi/lo)
     size_t ubuf_bytes = 0;
     // cpm_step_graph: captured bvec + update sequences, one per (m, n_e, buffer addresses), at most
-    // CPM_MAX_GRAPHS, least recently used replaced first; graph_valid = false (set when a scratch
+    // CPM_MAX_GRAPHS (24), least recently used replaced first; graph_valid = false (set when a scratch
     // buffer is reallocated) drops them all at the next step
     struct StepGraph {
         int m = 0;
@@ -214,7 +214,7 @@ struct cpm_ctx {
 
 namespace cpm {
 
-constexpr int CPM_MAX_GRAPHS = 8;
+constexpr int CPM_MAX_GRAPHS = 24;
 
 // error helpers (api.cu)
 cpm_status set_err(cpm_ctx* c, cpm_status s, const char* fmt, ...);

@@ -7,6 +7,11 @@ capacitor that bench.py measures against the HBM peak.
 
     python -m paper_2203_15461_gb300.run_steps --steps 4 [--k-prec f16x2|fp32] [--replicas 8]
     python -m paper_2203_15461_gb300.run_steps --steps 4 --s-product-only
+    python -m paper_2203_15461_gb300.run_steps --steps 4 --tc-product --sites 8192 --replicas 256
+
+With --tc-product the driver runs the batched tensor-core S product (S as three bf16 planes,
+persistent tcgen05 kernel with its tuned tile plan) of a two-sheet graphene capacitor of --sites
+sites (8,192 or 16,384) on a random b of --replicas replicas.
 """
 import argparse
 
@@ -19,12 +24,37 @@ def main():
     ap.add_argument("--replicas", type=int, default=8)
     ap.add_argument("--k-prec", default="f16x2", choices=["fp32", "f16x2"])
     ap.add_argument("--s-product-only", action="store_true")
+    ap.add_argument("--tc-product", action="store_true")
+    ap.add_argument("--sites", type=int, default=8192, choices=[8192, 16384])
+    ap.add_argument("--plan", default="", help="BN,stages,splits,ctas of the tensor-core product (default: tuned)")
     args = ap.parse_args()
 
     import torch
 
     from . import systems as s
     from .cpm import CPM
+
+    if args.tc_product:
+        cells = (32, 16) if args.sites == 8192 else (32, 32)
+        el = s.graphene_plates(cells[0], cells[1], 2, 40.0, alpha=0.1, rcut=35.0)
+        m = args.replicas
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = CPM.for_electrodes(el, s_prec="bf16x3", k_prec="fp32", stream=st).setup(el)
+            ctx.cpm_release_assembly()
+            if args.plan:
+                ctx.cpm_gemm_set_plan(m, *[int(v) for v in args.plan.split(",")])
+            plan = ctx.cpm_gemm_plan(m)
+            b = torch.as_tensor(np.random.default_rng(7).normal(0.0, 1.0, (m, el.n)), device="cuda")
+            psi = torch.as_tensor(np.tile([0.0, 1.0], (m, 1)), device="cuda")
+            q = torch.empty((m, el.n), dtype=torch.float64, device="cuda")
+            qt = torch.empty((m,), dtype=torch.float64, device="cuda")
+            for _ in range(args.steps):
+                ctx.cpm_update(m, psi, b, q, qt)
+        st.synchronize()
+        print(f"{args.steps} tensor-core S products, n = {el.n}, m = {m}, plan {plan}, "
+              f"max |sum q| = {float(qt.abs().max()):.3e}")
+        return
 
     if args.s_product_only:
         el = s.graphene_plates(32, 32, 2, 40.0, alpha=0.1, rcut=35.0)

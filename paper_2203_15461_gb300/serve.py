@@ -156,8 +156,10 @@ class GpuBackend:
     page-locked host memory (``cpm_export``) and frees A and the factor workspace; a later admission
     after an eviction restores the context from that checkpoint (``cpm_prepare`` + ``cpm_import``)
     without assembling again.  Batches are padded to a power-of-two replica count (zero-charge
-    replicas) and every replica to ``ne_max[key]`` charges, so a geometry replays at most
-    log2(max_batch) + 1 captured step graphs (``cpm_step_graph``), all captured at admission."""
+    replicas) and every replica to the batch's charge bucket (quarters of ``ne_max[key]``; zero
+    charges enter no cell list and cost only reciprocal-space work), so a geometry replays at most
+    (log2(max_batch) + 1) x 4 captured step graphs (``cpm_step_graph``); the largest is captured at
+    admission (it sizes the scratch), the others at their first use."""
 
     def __init__(self, s_prec: str = "fp32", k_prec: str = "fp32", max_batch: int = 16, ne_max=None,
                  graphs: bool = True):
@@ -210,9 +212,8 @@ class GpuBackend:
         if key not in self.ne_max:
             self.ne_max[key] = 2 * el.n
         if self.graphs:
-            # capture every padded batch size now, the largest first (it sizes the scratch)
-            for mp in self._sizes():
-                self._launch(key, [], mp)
+            # the largest batch and charge bucket first: it sizes the scratch for every later graph
+            self._launch(key, [], self.max_batch, self._bucket(key, self.ne_max[key]))
             st.synchronize()
         self.create_seconds[key].append(time.perf_counter() - t0)
         return ctx.cpm_device_bytes()
@@ -232,14 +233,22 @@ class GpuBackend:
             self.bufs[key][name] = b
         return b
 
-    def _launch(self, key, batch, mp):
+    def _bucket(self, key, ne_batch):
+        """Charges per replica of a batch: the geometry's maximum in four steps (multiples of 64)."""
+        ne_max = self.ne_max[key]
+        step = max(64, ((ne_max + 3) // 4 + 63) // 64 * 64)
+        return min(max(step, -(-ne_batch // step) * step), -(-ne_max // 64) * 64)
+
+    def _launch(self, key, batch, mp, ne=None):
         torch = self.torch
         ctx, st = self.ctx[key], self.stream[key]
-        ne = self.ne_max[key]
+        if ne is None:
+            ne = self._bucket(key, max((r.Q.shape[0] for r in batch), default=0))
         ng = ctx.n_groups
-        hx = self._buf(key, f"hx{mp}", (mp * ne, 3), torch.float64, pinned=True)
-        hQ = self._buf(key, f"hQ{mp}", (mp * ne,), torch.float64, pinned=True)
-        hp = self._buf(key, f"hp{mp}", (mp, ng), torch.float64, pinned=True)
+        tag = f"{mp}_{ne}"
+        hx = self._buf(key, f"hx{tag}", (mp * ne, 3), torch.float64, pinned=True)
+        hQ = self._buf(key, f"hQ{tag}", (mp * ne,), torch.float64, pinned=True)
+        hp = self._buf(key, f"hp{tag}", (mp, ng), torch.float64, pinned=True)
         xv, Qv, pv = hx.numpy().reshape(mp, ne, 3), hQ.numpy().reshape(mp, ne), hp.numpy()
         for r, req in enumerate(batch):
             k = req.Q.shape[0]
@@ -253,14 +262,14 @@ class GpuBackend:
         xv[len(batch):] = 0.0
         Qv[len(batch):] = 0.0
         pv[len(batch):] = 0.0
-        dx = self._buf(key, f"dx{mp}", (mp * ne, 3), torch.float64)
-        dQ = self._buf(key, f"dQ{mp}", (mp * ne,), torch.float64)
-        dp = self._buf(key, f"dp{mp}", (mp, ng), torch.float64)
-        b = self._buf(key, f"b{mp}", (mp, ctx.n), torch.float64)
-        q = self._buf(key, f"q{mp}", (mp, ctx.n), torch.float64)
-        qt = self._buf(key, f"qt{mp}", (mp,), torch.float64)
-        hq = self._buf(key, f"hq{mp}", (mp, ctx.n), torch.float64, pinned=True)
-        hqt = self._buf(key, f"hqt{mp}", (mp,), torch.float64, pinned=True)
+        dx = self._buf(key, f"dx{tag}", (mp * ne, 3), torch.float64)
+        dQ = self._buf(key, f"dQ{tag}", (mp * ne,), torch.float64)
+        dp = self._buf(key, f"dp{tag}", (mp, ng), torch.float64)
+        b = self._buf(key, f"b{tag}", (mp, ctx.n), torch.float64)
+        q = self._buf(key, f"q{tag}", (mp, ctx.n), torch.float64)
+        qt = self._buf(key, f"qt{tag}", (mp,), torch.float64)
+        hq = self._buf(key, f"hq{tag}", (mp, ctx.n), torch.float64, pinned=True)
+        hqt = self._buf(key, f"hqt{tag}", (mp,), torch.float64, pinned=True)
         with torch.cuda.stream(st):
             dx.copy_(hx, non_blocking=True)
             dQ.copy_(hQ, non_blocking=True)
