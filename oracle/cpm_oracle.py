@@ -35,6 +35,9 @@ What it computes (ELECTRODE paper, arXiv 2203.15461):
 * Electrodes at prescribed total charge (Sec. II.C, Eq. ewise-conq), the
   thermo-potentiostat step (Sec. II.D, Eq. deissenbeck) and the finite-field
   site potentials (Sec. II.F, Eq. cpm-ffield).
+* The reciprocal part of b by P3M, the mesh solver of the paper's package
+  (Introduction; SI Sec. 1.A-B), when the electrodes carry a mesh and an order (``p3m_recip``);
+  A keeps the Ewald sum.
 
 Readings of what the paper leaves open (units, cut-offs, the slab vacuum) are
 fixed by the arguments: positions in Angstrom, charges in e, potentials in V,
@@ -260,7 +263,13 @@ def bvec(el, elyt, sites=None, kchunk=4096):
             b[c0:c0 + 256] += pair @ Q + ew2d_recip(R[c0:c0 + 256], r, box, a, el.kcut) @ Q
         b += 2.0 * math.pi * box[2] / (box[0] * box[1]) * float(Q.sum())    # the constant c of A, per unit charge
         return K_E * b
-    if len(Q):
+    if len(Q) and getattr(el, "p3m_order", 0):
+        for c0 in range(0, len(sites), 256):
+            pair = _realspace(R[c0:c0 + 256], r, eta[c0:c0 + 256][:, None] * np.ones((1, len(r))), box, a,
+                              el.rcut)
+            b[c0:c0 + 256] += pair @ Q
+        b += p3m_recip(el, elyt, sites)
+    elif len(Q):
         for c0 in range(0, len(sites), 256):
             pair = _realspace(R[c0:c0 + 256], r, eta[c0:c0 + 256][:, None] * np.ones((1, len(r))), box, a,
                               el.rcut)
@@ -279,6 +288,76 @@ def bvec(el, elyt, sites=None, kchunk=4096):
     elif el.boundary == "wire" and len(Q):
         b += (2.0 * math.pi / V) * (R[:, 0] * float(Q @ r[:, 0]) + R[:, 1] * float(Q @ r[:, 1]))
     return K_E * b
+
+
+# --------------------------------------------------------------------------- P3M reciprocal part
+
+def bspline(p, x):
+    """Cardinal B-spline M_p(x) of order p (support [0, p)) by its recursion:
+    M_1 = 1 on [0, 1), M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    if p == 1:
+        return ((x >= 0) & (x < 1)).astype(np.float64)
+    return (x * bspline(p - 1, x) + (p - x) * bspline(p - 1, x - 1)) / (p - 1)
+
+
+def p3m_weights(x, L, K, p):
+    """Charge-assignment weights of points x (N,) on the K mesh points m h (h = L / K) of one periodic
+    axis: W((x - m h) / h) with W(s) = M_p(s + p / 2), the order-p assignment function centred on the
+    point, taken at the nearest periodic image; dense (N, K)."""
+    h = L / K
+    u = np.mod(np.asarray(x, dtype=np.float64), L) / h
+    d = u[:, None] - np.arange(K)[None, :]
+    d -= K * np.round(d / K)
+    return bspline(p, d + p / 2.0)
+
+
+def p3m_influence(box, K, p, alpha, nalias=2):
+    """Optimal influence function for potentials (Hockney and Eastwood) on the mesh wave vectors
+    k = 2 pi n / L (FFT order): G(k) = sum_m U^2(k_m) R(k_m) / (sum_m U^2(k_m))^2 over the aliases
+    k_m = k + 2 pi m / h, m in [-nalias, nalias]^3, with U(k) = prod_d sinc(k_d h_d / 2)^p the
+    transform of the assignment function and R(k) = 4 pi exp(-k^2 / 4 alpha^2) / k^2; G(0) = 0."""
+    box = np.asarray(box, dtype=np.float64)
+    h = [box[d] / K[d] for d in range(3)]
+    ks = [2.0 * np.pi * np.fft.fftfreq(K[d], d=h[d]) for d in range(3)]
+    ms = range(-nalias, nalias + 1)
+    u2 = [[np.sinc((ks[d] + 2.0 * np.pi * m / h[d]) * h[d] / (2.0 * np.pi)) ** (2 * p) for m in ms] for d in range(3)]
+    num = np.zeros(tuple(K))
+    for ix, mx in enumerate(ms):
+        kx = ks[0] + 2.0 * np.pi * mx / h[0]
+        for iy, my in enumerate(ms):
+            ky = ks[1] + 2.0 * np.pi * my / h[1]
+            for iz, mz in enumerate(ms):
+                kz = ks[2] + 2.0 * np.pi * mz / h[2]
+                k2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    R = np.where(k2 > 0, 4.0 * np.pi * np.exp(-k2 / (4.0 * alpha * alpha)) / k2, 0.0)
+                num += u2[0][ix][:, None, None] * u2[1][iy][None, :, None] * u2[2][iz][None, None, :] * R
+    den = sum(u2[0])[:, None, None] * sum(u2[1])[None, :, None] * sum(u2[2])[None, None, :]
+    G = num / (den * den)
+    G[0, 0, 0] = 0.0
+    return G
+
+
+def p3m_recip(el, elyt, sites=None):
+    """Reciprocal part of b (before K_E) by P3M (particle-particle particle-mesh, the k-space solver
+    of the paper's package): the charges assigned to the mesh, the mesh transformed, multiplied by
+    the influence function and transformed back, the mesh potential interpolated at the sites with
+    the same assignment function:  phi_m = (1/V) sum_{n != 0} G(k_n) rho^(n) e^{i k_n x_m}.  The mesh
+    (el.p3m_mesh) and the order (el.p3m_order) come with the electrodes."""
+    box = np.asarray(el.box, dtype=np.float64)
+    K, p = tuple(int(v) for v in el.p3m_mesh), int(el.p3m_order)
+    V = float(box[0] * box[1] * box[2])
+    xyz = np.asarray(el.xyz, dtype=np.float64)
+    R = xyz if sites is None else xyz[np.asarray(sites)]
+    r = np.asarray(elyt.xyz, dtype=np.float64)
+    Q = np.asarray(elyt.Q, dtype=np.float64)
+    Wq = [p3m_weights(r[:, d], box[d], K[d], p) for d in range(3)]
+    rho = np.einsum("j,jx,jy,jz->xyz", Q, Wq[0], Wq[1], Wq[2], optimize=True)
+    G = p3m_influence(box, K, p, el.alpha)
+    phi = (K[0] * K[1] * K[2] / V) * np.real(np.fft.ifftn(G * np.fft.fftn(rho)))
+    Ws = [p3m_weights(R[:, d], box[d], K[d], p) for d in range(3)]
+    return np.einsum("ix,iy,iz,xyz->i", Ws[0], Ws[1], Ws[2], phi, optimize=True)
 
 
 # --------------------------------------------------------------------------- inversion and charges

@@ -41,6 +41,8 @@ class Electrodes:
     area: float = 0.0        # electrode area in the periodic plane (slab only)
     z_inner: tuple = ()      # z of the inner surface layer of the bottom / top electrode
     name: str = ""
+    p3m_mesh: tuple = ()     # P3M mesh points per axis (powers of two) for the reciprocal part of b
+    p3m_order: int = 0       # P3M assignment order (0: Ewald sum)
 
     @property
     def n(self) -> int:

@@ -472,3 +472,53 @@ def test_ew2d_constant_leaves_S_unchanged(tiny):
     el2 = s.Electrodes(**{**el.__dict__, "box": el.box * np.array([1.0, 1.0, 1.7])})
     S2 = o.capacitance_matrix(o.assemble_A(el2))
     assert np.linalg.norm(S2 - S1) < 1e-11 * np.linalg.norm(S1)
+
+
+# ----------------------------------------------------------------------------- P3M (Introduction; SI Sec. 1.A-B; Hockney and Eastwood)
+
+def _p3m(el, K, p):
+    return s.Electrodes(**{**el.__dict__, "p3m_mesh": K, "p3m_order": p})
+
+
+def test_p3m_converges_to_the_ewald_sum(tiny):
+    """The mesh solution approaches the (pinned) Ewald reciprocal sum as the mesh is refined, at least as
+    fast as h^p: order 7 reaches 1e-8 of the reciprocal part on a 32 x 32 x 128 mesh and 1e-10 on 64 x 64 x 256."""
+    el, ely, _, _, _, _ = tiny
+    elk = s.Electrodes(**{**el.__dict__, "kcut": s.kcut_from_tol(el.alpha, 1e-14)})
+    box = np.asarray(el.box)
+    _, k, k2 = o.kvectors(box, elk.kcut)
+    rho = o.structure_factor(k, ely)
+    ph = el.xyz @ k.T
+    ref = (np.cos(ph) * rho.real + np.sin(ph) * rho.imag) @ o.kweights(k2, el.alpha, float(np.prod(box)))
+    errs = {}
+    for p in (5, 7):
+        for K in ((16, 16, 64), (32, 32, 128), (64, 64, 256)):
+            b = o.p3m_recip(_p3m(elk, K, p), ely)
+            errs[p, K] = np.linalg.norm(b - ref) / np.linalg.norm(ref)
+    for p in (5, 7):
+        e = [errs[p, K] for K in ((16, 16, 64), (32, 32, 128), (64, 64, 256))]
+        assert e[0] / e[1] > 2 ** (p - 1) and e[1] / e[2] > 2 ** (p - 1), (p, e)
+    assert errs[7, (32, 32, 128)] < 1e-8 and errs[7, (64, 64, 256)] < 1e-10
+
+
+def test_p3m_shift_by_one_mesh_spacing(tiny):
+    """Moving every site and charge by one mesh spacing along each axis leaves the mesh solution unchanged
+    (to rounding): the assignment, the periodic wrap and the transforms use one and the same mesh."""
+    el, ely, _, _, _, _ = tiny
+    K = (16, 16, 64)
+    elp = _p3m(el, K, 5)
+    b0 = o.p3m_recip(elp, ely)
+    for d in range(3):
+        sh = np.zeros(3)
+        sh[d] = el.box[d] / K[d]
+        b1 = o.p3m_recip(s.Electrodes(**{**elp.__dict__, "xyz": el.xyz + sh}), s.Electrolyte(xyz=ely.xyz + sh, Q=ely.Q))
+        assert np.abs(b1 - b0).max() < 1e-12 * np.abs(b0).max()
+
+
+def test_p3m_weights_partition_unity():
+    """The order-p assignment weights of any point sum to one over the mesh and vanish beyond p points."""
+    x = np.random.default_rng(3).uniform(0, 10.0, 50)
+    for p in (2, 5, 7):
+        W = o.p3m_weights(x, 10.0, 32, p)
+        assert np.abs(W.sum(axis=1) - 1).max() < 1e-13
+        assert ((W > 0).sum(axis=1) <= p).all()
