@@ -83,6 +83,24 @@ typedef enum {
                              until the residual stops shrinking; X symmetrised */
 } cpm_chol;
 
+/*
+ * Reciprocal-space solver of the per-step electrolyte vector b (cpm_params.kspace).  The paper's
+ * package offers an Ewald sum and a particle-particle particle-mesh (P3M) solver (Introduction; SI
+ * Sec. 1.A-B).  With CPM_KSPACE_P3M the reciprocal part of b is
+ *   phi_i = (1/V) sum_x W_i(x) IFFT[G FFT[rho_mesh]](x),   rho_mesh(x) = sum_j Q_j W_j(x),
+ * W the order-p cardinal B-spline assignment function per axis (W(s) = M_p(s + p/2), s in mesh
+ * spacings), G the optimal influence function for potentials of Hockney and Eastwood with alias
+ * sums over m in [-2, 2]^3:
+ *   G(k) = sum_m U^2(k_m) R(k_m) / (sum_m U^2(k_m))^2,  k_m = k + 2 pi m / h,
+ *   U(k) = prod_d sinc(k_d h_d / 2)^p,  R(k) = 4 pi exp(-k^2 / 4 alpha^2) / k^2,  G(0) = 0.
+ * The elastance matrix A is always assembled with the Ewald sum; the background and the boundary
+ * term of b are those of the Ewald path.  Not with CPM_BC_EW2D.
+ */
+typedef enum {
+    CPM_KSPACE_EWALD = 0,
+    CPM_KSPACE_P3M = 1
+} cpm_kspace;
+
 typedef struct {
     double box[3];       /* Ewald cell (Lx, Ly, Lz) in Angstrom, vacuum padding included */
     int32_t boundary;    /* cpm_boundary */
@@ -95,6 +113,12 @@ typedef struct {
     int32_t k_prec;      /* cpm_precision of the b-vector sums (real and reciprocal space) */
     size_t hbm_budget;   /* bytes of device memory this context may allocate; 0 = no limit */
     int32_t chol;        /* cpm_chol of cpm_invert */
+    int32_t kspace;      /* cpm_kspace of the reciprocal part of b (0: Ewald) */
+    int32_t p3m_order;   /* P3M assignment order p, 2..7 (kspace = CPM_KSPACE_P3M) */
+    int32_t p3m_mesh[3]; /* P3M mesh points per axis: powers of two in [8, 512]; one complex xy plane
+                            (Kx Ky x 8 bytes, x 16 with k_prec = CPM_PREC_FP64) at most 128 KiB.
+                            The charge assignment sums exact fixed-point integers: every charge
+                            and the charge of every mesh point must stay below 2,048 e */
 } cpm_params;
 
 typedef struct cpm_ctx cpm_ctx;
@@ -104,7 +128,8 @@ typedef struct cpm_ctx cpm_ctx;
  * (a cudaStream_t; NULL = the legacy default stream).  The context owns all
  * device state it allocates and frees it in cpm_destroy.
  * Errors: CPM_E_ARG for a null `p`/`out` or non-positive box, alpha, rcut or
- * kcut; CPM_E_CUDA when no CUDA device is usable (there is no CPU fallback).
+ * kcut, or a P3M order or mesh outside the limits above; CPM_E_CUDA when no CUDA device is usable
+ * (there is no CPU fallback).
  */
 cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out);
 
@@ -373,7 +398,8 @@ typedef enum {
     CPM_K_NEUTRAL = 9,  /* neutrality fix and total charge */
     CPM_K_COL0 = 10,    /* FP64 k_perp = 0 column of the single-precision path */
     CPM_K_TCGEMM = 11,  /* the tensor-core product alone (inside CPM_K_GEMV when s_prec = BF16X3) */
-    CPM_K_COUNT = 12
+    CPM_K_P3M = 12,     /* P3M reciprocal part (assignment, transforms, interpolation) */
+    CPM_K_COUNT = 13
 } cpm_kernel;
 
 /*
@@ -413,7 +439,8 @@ cpm_status cpm_profile_read(cpm_ctx* ctx, int32_t kernel, double* total_ms, int6
  * n x 3, xyz n_e x 3 and Q n_e (the Python binding checks them).  Real-space pairs
  * are summed directly over all charges and images (no cell list), so the cost grows
  * as n * n_e.
- * Errors: CPM_E_ARG (bad parameters or pointers), CPM_E_BUDGET (grid too large),
+ * Errors: CPM_E_ARG (bad parameters or pointers, CPM_BC_EW2D, kspace other than
+ * CPM_KSPACE_EWALD), CPM_E_BUDGET (grid too large),
  * CPM_E_STATE (first call on a device inside a stream capture), CPM_E_CUDA (no device,
  * or a launch failed).
  */

@@ -38,7 +38,8 @@ class cpm_params(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double * 3), ("boundary", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("rcut", ctypes.c_double), ("kcut", ctypes.c_double), ("symm", ctypes.c_int32),
                 ("s_prec", ctypes.c_int32), ("k_prec", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t),
-                ("chol", ctypes.c_int32)]
+                ("chol", ctypes.c_int32), ("kspace", ctypes.c_int32), ("p3m_order", ctypes.c_int32),
+                ("p3m_mesh", ctypes.c_int32 * 3)]
 
 
 _lib = None
@@ -81,7 +82,8 @@ _SIGS = {
     "cpm_profile": ([_P, _I32], _I32),
     "cpm_profile_read": ([_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32], _I32),
 }
-KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral", "col0", "tcgemm"]
+KERNELS = ["stats", "cells", "real", "phases", "sf", "sfred", "site", "combine", "gemv", "neutral", "col0", "tcgemm",
+           "p3m"]
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -177,7 +179,8 @@ class CPM:
     """One CPM context: one electrode geometry on the current CUDA device and one stream."""
 
     def __init__(self, box, boundary: str, alpha: float, rcut: float, kcut: float, symm: bool = True,
-                 s_prec: str = "fp64", k_prec: str = "fp64", hbm_budget: int = 0, stream=None, chol: str = "fp64"):
+                 s_prec: str = "fp64", k_prec: str = "fp64", hbm_budget: int = 0, stream=None, chol: str = "fp64",
+                 p3m=None):
         self.lib = load_library()
         p = cpm_params()
         p.box[:] = [float(b) for b in box]
@@ -187,6 +190,10 @@ class CPM:
         p.s_prec, p.k_prec = PRECISION[s_prec], PRECISION[k_prec]
         p.hbm_budget = int(hbm_budget)
         p.chol = CHOL[chol]
+        if p3m is not None:   # (mesh (Kx, Ky, Kz), order): the reciprocal part of b by P3M
+            mesh, order = p3m
+            p.kspace, p.p3m_order = 1, int(order)
+            p.p3m_mesh[:] = [int(v) for v in mesh]
         self.params = p
         self.stream = stream
         h = _P()
@@ -199,6 +206,9 @@ class CPM:
 
     @classmethod
     def for_electrodes(cls, el, **kw):
+        """A context for the electrodes' cell and splitting; P3M when they carry a mesh and an order."""
+        if getattr(el, "p3m_order", 0) and "p3m" not in kw:
+            kw["p3m"] = (tuple(el.p3m_mesh), el.p3m_order)
         return cls(el.box, el.boundary, el.alpha, el.rcut, el.kcut, **kw)
 
     # -- plumbing

@@ -231,6 +231,8 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
     if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_EW2D) return CPM_E_ARG;
     if (p->boundary == CPM_BC_EW2D && p->k_prec == CPM_PREC_F16X2) return CPM_E_ARG;
     if (p->chol != CPM_CHOL_FP64 && p->chol != CPM_CHOL_FP32_IR) return CPM_E_ARG;
+    if (p->kspace != CPM_KSPACE_EWALD && p->kspace != CPM_KSPACE_P3M) return CPM_E_ARG;
+    if (p->kspace == CPM_KSPACE_P3M && (p->boundary == CPM_BC_EW2D || !p3m_mesh_ok(p))) return CPM_E_ARG;
     if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32 && p->s_prec != CPM_PREC_BF16X3) ||
         (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32 && p->k_prec != CPM_PREC_F16X2))
         return CPM_E_ARG;
@@ -414,6 +416,7 @@ static cpm_status assemble_impl(cpm_ctx* c, int64_t n, const double* xyz, const 
     CPM_LAUNCH(c, "k_phases(sites)");
     if (c->p.k_prec == CPM_PREC_F16X2) CPM_TRY(tc_recip_prepare(c));
     CPM_TRY(build_col0_sites(c));
+    if (c->p.kspace == CPM_KSPACE_P3M) CPM_TRY(p3m_prepare(c));
     const size_t nn = (size_t)n * n;
     if (with_A) {
         CPM_TRY(dev_alloc(c, (void**)&c->A, sizeof(double) * nn));

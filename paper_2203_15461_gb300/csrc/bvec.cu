@@ -1166,7 +1166,7 @@ __global__ void __launch_bounds__(256, 2) k_site32(const int2* __restrict__ cols
 template <typename T>
 __global__ void k_combine(const T* partial, int nctiles, const double* real, const double* b0, const int* zmap,
                           int nzu, const double* stats, const double* sx, int64_t n, int m, Geometry g, double* b,
-                          float2* bhl, const double* ew) {
+                          float2* bhl, const double* ew, const double* pm) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * n) return;
     const int r = (int)(t / n);
@@ -1194,6 +1194,7 @@ __global__ void k_combine(const T* partial, int nctiles, const double* real, con
     for (; k < nctiles; ++k) s += (double)pp[(int64_t)k * n];
     s += rl;
     if (b0) s += bz;
+    if (pm) s += pm[t];   // P3M: the mesh potential in place of the Ewald tiles
     const double* st = stats + 4 * r;
     if (ew) s += ew[t];   // EW2D: the 2D long-range sum with its constant, no background or dipole term
     else s += -PI * st[0] / (g.V * g.alpha * g.alpha);
@@ -1217,8 +1218,9 @@ struct BvecPlan {
     int64_t chunk;
     size_t off_EX, off_EY, off_EZ, off_Q, off_rp, off_wr, off_part, off_real, off_stats, off_key, off_cnt, off_cur,
         off_nzc, off_start, off_wpos, off_sorted, off_order, off_c0part, off_c0w, off_b0, off_u, off_c0e1, off_ew,
-        off_ewT, total;
+        off_ewT, off_pm, off_p3m, total;
     int c0chunks;
+    bool p3m;                           // reciprocal part of b by P3M (p3m.cu)
     bool tc;                            // reciprocal sums on the tensor cores (tc_recip.cu)
     size_t off_qabs, off_tcpart, off_w16, off_spart, off_qpart, off_c0q;
 };
@@ -1232,8 +1234,9 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     // odd number 2h + 1 of BN-wide z tiles centred on nz = 0, covering -NZ..NZ
     const int zh = k.NZ + 1 - SF_BN / 2 > 0 ? (k.NZ + 1 - SF_BN / 2 + SF_BN - 1) / SF_BN : 0;
     p.ztiles = 2 * zh + 1;
-    p.nctiles = p.ctiles;
-    p.tc = std::is_same<T, float>::value && c->p.k_prec == CPM_PREC_F16X2 && tc_recip_supported(k);
+    p.p3m = c->p.kspace == CPM_KSPACE_P3M;
+    p.nctiles = p.p3m ? 0 : p.ctiles;
+    p.tc = !p.p3m && std::is_same<T, float>::value && c->p.k_prec == CPM_PREC_F16X2 && tc_recip_supported(k);
     TcRecipDims td{};
     if (p.tc) {
         td = tc_recip_dims(c, m, ne);
@@ -1249,15 +1252,16 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.chunk = (ne + p.splits - 1) / p.splits;
     p.chunk = ((p.chunk + SF_BK - 1) / SF_BK) * SF_BK;
     const int64_t ptot = (int64_t)m * ne;
-    const size_t pe = phase_elems(k, ptot);
+    const int64_t pph = p.p3m ? 0 : ptot;   // points with electrolyte phase tables (none with P3M)
+    const size_t pe = phase_elems(k, pph);
     const size_t grid = (size_t)k.ncols * k.nzw;
     size_t o = 0;
-    const int64_t tabX = (int64_t)(k.NX + 1) * ptot, tabY = (int64_t)(2 * k.NY + 1) * ptot;
+    const int64_t tabX = (int64_t)(k.NX + 1) * pph, tabY = (int64_t)(2 * k.NY + 1) * pph;
     p.off_EX = o; o += al(sizeof(c2<T>) * tabX);
     p.off_EY = o; o += al(sizeof(c2<T>) * tabY);
     p.off_EZ = o; o += al(sizeof(c2<T>) * (pe - tabX - tabY));
     p.off_Q = o; o += al(sizeof(T) * ptot);
-    if (p.tc) {   // the CUDA-core structure-factor buffers are not used
+    if (p.tc || p.p3m) {   // the CUDA-core structure-factor buffers are not used
         p.off_rp = p.off_wr = o;
     } else {
         p.off_rp = o; o += al(sizeof(c2<T>) * grid * m * p.splits);
@@ -1279,9 +1283,9 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     p.off_c0part = o; o += al(sizeof(double2) * (size_t)m * p.c0chunks * nz0);
     p.off_c0w = o; o += al(sizeof(double2) * (size_t)m * nz0);
     p.off_b0 = o; o += al(sizeof(double) * (size_t)m * std::max(c->nzu, 1));
-    p.off_u = o; o += al(sizeof(uint64_t) * 3 * ptot);
-    p.off_c0e1 = o; o += al(sizeof(float4) * ptot);
-    p.off_c0q = o; o += al(sizeof(float2) * ptot);
+    p.off_u = o; o += al(sizeof(uint64_t) * 3 * pph);
+    p.off_c0e1 = o; o += al(sizeof(float4) * pph);
+    p.off_c0q = o; o += al(sizeof(float2) * pph);
     p.off_qabs = o; o += al(sizeof(float2) * m);
     p.off_spart = o; o += al(sizeof(double) * ST_Q * (size_t)std::max<int64_t>(1, (ne + ST_THREADS - 1) / ST_THREADS) * m);
     p.off_qpart = o; o += al(sizeof(double) * 2 * (size_t)std::max<int64_t>(1, (ne + FR_THREADS - 1) / FR_THREADS) * m);
@@ -1289,6 +1293,11 @@ static BvecPlan<T> plan_bvec(const cpm_ctx* c, int m, int64_t ne) {
     if (c->g.bc == CPM_BC_EW2D) {
         p.off_ew = o; o += al(sizeof(double) * (size_t)m * c->n);
         p.off_ewT = o; o += al(ew2d_T_bytes(c, m));
+    }
+    p.off_pm = p.off_p3m = o;
+    if (p.p3m) {
+        p.off_pm = o; o += al(sizeof(double) * (size_t)m * c->n);
+        p.off_p3m = o; o += al(p3m_scratch_bytes<T>(c, m, ne));
     }
     p.off_tcpart = p.off_w16 = o;
     if (p.tc) {
@@ -1331,14 +1340,14 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     V4T* sorted = (V4T*)(scr + p.off_sorted);
     int* order = (int*)(scr + p.off_order);
     const int nc = m * p.cg.ncells;
-    c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0) ? 5 : 0);
+    c->launches += 4 + (ptot > 0 ? 2 : 0) + ((k.nk > 0 && ptot > 0 && !p.p3m) ? 5 : 0);
 
     // Three chains: the origin stream bins the charges (per-replica totals) and runs the cell list and
     // the real-space sum; side stream 1 takes the fractions, the charges in the working precision and
     // their scales in one pass, then the phase tables and the reciprocal sums; side stream 2 sums the
     // k_perp = 0 column once the fractions are written.  k_combine joins them.  With per-kernel
     // profiling on, everything runs on the origin stream in the same order.
-    const bool recip = k.nk > 0 && ptot > 0;
+    const bool recip = k.nk > 0 && ptot > 0 && !p.p3m;
     const bool fork = !c->prof_on;
     cudaStream_t s0 = st, s1 = st, s2 = st;
     if (fork) {
@@ -1361,7 +1370,7 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     if (fork) CPM_CUDA(c, cudaStreamWaitEvent(s2, c->fev[1], 0));
     double* b0 = nullptr;
-    if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0) {
+    if (std::is_same<T, float>::value && k.ext0 > 0 && ptot > 0 && !p.p3m) {
         // the k_perp = 0 column in FP64 (its single-precision weights are zero)
         double2* c0part = (double2*)(scr + p.off_c0part);
         double2* c0w = (double2*)(scr + p.off_c0w);
@@ -1439,8 +1448,15 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
         prof_end(c, CPM_K_SITE);
         CPM_LAUNCH(c, "k_site");
         }
-    } else {
+    } else if (p.nctiles > 0) {
         CPM_CUDA(c, cudaMemsetAsync(part, 0, sizeof(T) * (size_t)m * p.nctiles * n, s1));
+    }
+    double* pm = nullptr;
+    if (p.p3m && ptot > 0) {
+        pm = (double*)(scr + p.off_pm);
+        prof_begin(c, CPM_K_P3M);
+        CPM_TRY(p3m_run<T>(c, s1, m, ne, xyz, Q, scr + p.off_p3m, pm));
+        prof_end(c, CPM_K_P3M);
     }
     double* ew = nullptr;
     if (c->g.bc == CPM_BC_EW2D) {
@@ -1491,7 +1507,8 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_begin(c, CPM_K_COMBINE);
     k_combine<T><<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(part, p.nctiles, real, b0, c->zmap, c->nzu,
-                                                                          stats, c->sx, n, m, c->g, b_out, bhl, ew);
+                                                                          stats, c->sx, n, m, c->g, b_out, bhl, ew,
+                                                                          pm);
     prof_end(c, CPM_K_COMBINE);
     CPM_LAUNCH(c, "k_combine");
     return CPM_OK;

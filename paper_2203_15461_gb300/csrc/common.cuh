@@ -200,6 +200,8 @@ struct cpm_ctx {
     float tc_wmax = 0.f;         // bound on the k-space weights
     int tc_mx[32] = {};          // largest harmonic extent of each 128-column structure-factor tile
     int tc_nmx = 0;              // tiles in tc_mx (0: the kernel finds them)
+    void* p3m_G = nullptr;       // P3M (kspace = CPM_KSPACE_P3M): influence function / V on the mesh (k_prec's T)
+    void* p3m_tw = nullptr;      // its FFT twiddles exp(-2 pi i j / K), j < K / 2, for K = Kx, Ky, Kz
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 
@@ -354,5 +356,17 @@ size_t tc_recip_w16_bytes(const TcRecipDims& d);
 cpm_status tc_recip_prepare(cpm_ctx* c);
 cpm_status tc_recip_run(cpm_ctx* c, int m, int64_t ne, const float2* EX, const float2* EY, const float2* EZ,
                         const float* Qv, const float2* qabs, void* part, void* w16, float* site_partial);
+
+// p3m.cu: the reciprocal part of b by P3M (cpm_params.kspace = CPM_KSPACE_P3M)
+constexpr int P3M_MAX_MESH = 512;                 // mesh points per axis (powers of two, at least 8)
+constexpr size_t P3M_PLANE_BYTES = 128 * 1024;    // one complex xy plane must fit in shared memory
+bool p3m_mesh_ok(const cpm_params* p);
+cpm_status p3m_prepare(cpm_ctx* c);
+template <typename T>
+size_t p3m_scratch_bytes(const cpm_ctx* c, int m, int64_t ne);
+// pm: m x n doubles, the mesh potential at every site (e / Angstrom, before K_E)
+template <typename T>
+cpm_status p3m_run(cpm_ctx* c, cudaStream_t st, int m, int64_t ne, const double* xyz, const double* Q, char* scr,
+                   double* pm);
 
 }  // namespace cpm

@@ -128,6 +128,7 @@ extern "C" cpm_status cpm_bvec_noalloc(const cpm_params* p, int64_t n, const dou
         if (!(p->box[d] > 0.0)) return CPM_E_ARG;
     if (!(p->alpha > 0.0) || !(p->rcut > 0.0) || !(p->kcut > 0.0)) return CPM_E_ARG;
     if (p->boundary < CPM_BC_3D || p->boundary > CPM_BC_WIRE) return CPM_E_ARG;   // EW2D: not here
+    if (p->kspace != CPM_KSPACE_EWALD) return CPM_E_ARG;                           // P3M: not here
     Geometry g;
     for (int d = 0; d < 3; ++d) { g.boxL[d] = p->box[d]; g.inv[d] = 1.0 / p->box[d]; }
     g.V = p->box[0] * p->box[1] * p->box[2];

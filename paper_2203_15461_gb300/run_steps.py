@@ -8,10 +8,12 @@ capacitor that bench.py measures against the HBM peak.
     python -m paper_2203_15461_gb300.run_steps --steps 4 [--k-prec f16x2|fp32] [--replicas 8]
     python -m paper_2203_15461_gb300.run_steps --steps 4 --s-product-only
     python -m paper_2203_15461_gb300.run_steps --steps 4 --tc-product --sites 8192 --replicas 256
+    python -m paper_2203_15461_gb300.run_steps --steps 4 --p3m 32,32,128,7
 
 With --tc-product the driver runs the batched tensor-core S product (S as three bf16 planes,
 persistent tcgen05 kernel with its tuned tile plan) of a two-sheet graphene capacitor of --sites
-sites (8,192 or 16,384) on a random b of --replicas replicas.
+sites (8,192 or 16,384) on a random b of --replicas replicas.  With --p3m Kx,Ky,Kz,order the EDL step
+takes the reciprocal part of b from P3M on that mesh instead of the Ewald sum.
 """
 import argparse
 
@@ -27,6 +29,7 @@ def main():
     ap.add_argument("--tc-product", action="store_true")
     ap.add_argument("--sites", type=int, default=8192, choices=[8192, 16384])
     ap.add_argument("--plan", default="", help="BN,stages,splits,ctas of the tensor-core product (default: tuned)")
+    ap.add_argument("--p3m", default="", help="Kx,Ky,Kz,order: P3M reciprocal part of b (default: Ewald)")
     args = ap.parse_args()
 
     import torch
@@ -83,7 +86,11 @@ def main():
         Q[r, :e.n] = e.Q
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec=args.k_prec, stream=st).setup(el)
+        kw = {}
+        if args.p3m:
+            v = [int(t) for t in args.p3m.split(",")]
+            kw["p3m"] = (tuple(v[:3]), v[3])
+        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec=args.k_prec, stream=st, **kw).setup(el)
         dx = torch.as_tensor(xyz.reshape(-1, 3), device="cuda")
         dQ = torch.as_tensor(Q.reshape(-1), device="cuda")
         dp = torch.as_tensor(np.tile(psi, (m, 1)), device="cuda")

@@ -48,6 +48,28 @@ def test_create_rejects_bad_arguments_without_touching_a_gpu(lib):
     lib.cpm_destroy(None)
 
 
+def test_create_rejects_bad_p3m_parameters_without_touching_a_gpu(lib):
+    """P3M order outside 2..7, a mesh axis not a power of two in [8, 512], an xy plane beyond 128 KiB of
+    complex values, or the 2D Ewald boundary: CPM_E_ARG before any device is looked up."""
+    def params(order, mesh, boundary=1, k_prec=1):
+        p = cpm.cpm_params()
+        p.box[:] = [20.0, 20.0, 60.0]
+        p.alpha, p.rcut, p.kcut = 0.3, 10.0, 2.0
+        p.boundary, p.k_prec, p.s_prec = boundary, k_prec, 1
+        p.kspace, p.p3m_order = 1, order
+        p.p3m_mesh[:] = list(mesh)
+        return p
+    h = ctypes.c_void_p()
+    bad = [params(1, (16, 16, 64)), params(8, (16, 16, 64)), params(5, (12, 16, 64)), params(5, (16, 16, 4)),
+           params(5, (16, 16, 1024)), params(5, (256, 128, 64)), params(5, (128, 128, 64), k_prec=0),
+           params(5, (16, 16, 64), boundary=3)]
+    for p in bad:
+        assert lib.cpm_create(ctypes.byref(p), None, ctypes.byref(h)) == 1   # CPM_E_ARG
+    q = params(5, (16, 16, 64))
+    q.kspace = 2
+    assert lib.cpm_create(ctypes.byref(q), None, ctypes.byref(h)) == 1
+
+
 def test_no_cpu_fallback_without_a_device(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
