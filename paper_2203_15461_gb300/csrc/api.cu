@@ -716,6 +716,7 @@ cpm_status cpm_import(cpm_ctx* c, const void* buf, size_t bytes) {
     drop_graph(c);
     k_tofloat<<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(c->S, c->S32, (int64_t)(n * n));
     CPM_LAUNCH(c, "k_tofloat");
+    CPM_TRY(fp32_rowsums(c));
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->etd = h.etd;
     ccm_invalidate(c);

@@ -138,7 +138,7 @@ struct cpm_ctx {
     float* S32 = nullptr;
     double* SG = nullptr;        // [n * ng]
     double* u = nullptr;         // [n]
-    double* dvec = nullptr;      // [n] scratch
+    double* dvec = nullptr;      // [n] scratch; with symm = 0 the row sums of the single-precision S
     double* red = nullptr;       // [64] scratch scalars
     unsigned* status = nullptr;  // device status word
     int* tickets = nullptr;      // [tickets_n] per-replica arrival counters, zero between launches
@@ -297,6 +297,8 @@ cpm_status ew2d_run(cpm_ctx* c, cudaStream_t st, int m, int64_t ne, const double
 cpm_status invert_and_project(cpm_ctx* c);
 // the projection tail once S holds A^-1 (dense.cu)
 cpm_status project_inverse(cpm_ctx* c);
+// symm = 0: the FP64 row sums of the single-precision S into dvec (the centred products add b_i times them)
+cpm_status fp32_rowsums(cpm_ctx* c);
 // A^-1 by an FP32 Cholesky factor and FP64 iterative refinement of A X = I, then the projection (refine.cu)
 cpm_status invert_ir(cpm_ctx* c);
 cpm_status launch_dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,

@@ -287,6 +287,26 @@ cpm_status invert_and_project(cpm_ctx* c) {
     return project_inverse(c);
 }
 
+// Row sums of the single-precision S in FP64 (one warp per row, a fixed order), into dvec.  The
+// single-precision products centre b per output, sum_j S_ij (b_j - b_i); without the projection
+// (symm = 0) the rows of A^-1 do not sum to zero, and the update adds b_i times these sums back.
+__global__ void k_rowsum32(const float* S32, int64_t n, double* out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += (double)S32[row * n + j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[row] = s;
+}
+
+cpm_status fp32_rowsums(cpm_ctx* c) {
+    if (c->p.symm) return CPM_OK;
+    k_rowsum32<<<(unsigned)((c->n * 32 + 255) / 256), 256, 0, c->stream>>>(c->S32, c->n, c->dvec);
+    CPM_LAUNCH(c, "k_rowsum32");
+    return CPM_OK;
+}
+
 // With A^-1 in S: d = A^-1 e, e^T d, the projection of Eq. (S) (symm = 1), the FP32 copy of S, u and
 // SG = S G; synchronises.
 cpm_status project_inverse(cpm_ctx* c) {
@@ -301,6 +321,7 @@ cpm_status project_inverse(cpm_ctx* c) {
     CPM_LAUNCH(c, "k_project");
     k_sg<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(c->S, c->group, n, c->ng, c->SG);
     CPM_LAUNCH(c, "k_sg");
+    CPM_TRY(fp32_rowsums(c));
     CPM_CUDA(c, cudaMemcpyAsync(&c->etd, c->red, sizeof(double), cudaMemcpyDeviceToHost, st));
     CPM_CUDA(c, cudaStreamSynchronize(st));
     ccm_invalidate(c);

@@ -11,7 +11,8 @@ namespace cpm {
 // rows j are split over blocks (partial sums reduced in FP64 in a fixed order).
 //
 // Single precision: the sum is centred per output, sum_j S_ij (b_j - b_i), which equals S b
-// because the rows of S sum to zero (Eq. S).  S rounded to FP32 then only perturbs the
+// because the rows of S sum to zero (Eq. S); without the projection (symm = 0, S = A^-1) the
+// reduction adds b_i sum_j S_ij back, from the FP64 row sums of the stored single-precision S.  S rounded to FP32 then only perturbs the
 // products where b_j differs from b_i, i.e. mostly far sites where S_ij is small; b enters as
 // an FP32 hi + lo pair so the differences are formed to about 2^-24 of themselves, and each
 // thread's partial sum is Kahan-compensated.
@@ -289,7 +290,8 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
                                                       const double* __restrict__ psi, int64_t n, int m,
                                                       double* __restrict__ q, double* __restrict__ p1,
                                                       const double* __restrict__ u, int symm,
-                                                      int* __restrict__ tickets, double* __restrict__ qtot) {
+                                                      int* __restrict__ tickets, double* __restrict__ qtot,
+                                                      const double* __restrict__ b, const double* __restrict__ srow) {
     __shared__ double sh[NB_T / 32];
     __shared__ double buf[NB_T];
     __shared__ double s_sum;
@@ -312,7 +314,8 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         for (; sp < splits; ++sp) v.add(pi[(int64_t)sp * stride]);
         double sv = 0.0;
         for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
-        qi = sv - v.value();
+        // the centred products give sum_j S_ij (b_j - b_i): add b_i sum_j S_ij back where rows do not sum to zero
+        qi = sv - (srow ? v.value() + b[(int64_t)r * n + i] * srow[i] : v.value());
         qr[i] = qi;
         __threadfence();   // this slice of q is visible device-wide before the block takes its ticket
     }
@@ -575,12 +578,13 @@ cpm_status update(cpm_ctx* c, int m, const double* psi, const double* b, double*
     CPM_TRY(reserve_neutral(c, m));
     prof_begin(c, CPM_K_NEUTRAL);
     const dim3 rgrid((unsigned)reduce_blocks(n), m);
+    const double* srow = (f32 && !c->p.symm) ? c->dvec : nullptr;
     if (f32 && gemv_tma_supported(c))
         k_gemv_reduce<float2><<<rgrid, NB_T, 0, st>>>((const float2*)part, (int)splits, upd_sg(c), upd_ng(c), psi, n, m, q,
-                                                      c->nbuf, c->u, c->p.symm, c->tickets, qtot);
+                                                      c->nbuf, c->u, c->p.symm, c->tickets, qtot, b, srow);
     else
         k_gemv_reduce<double><<<rgrid, NB_T, 0, st>>>(part, (int)splits, upd_sg(c), upd_ng(c), psi, n, m, q, c->nbuf, c->u,
-                                                      c->p.symm, c->tickets, qtot);
+                                                      c->p.symm, c->tickets, qtot, b, srow);
     prof_end(c, CPM_K_NEUTRAL);
     CPM_LAUNCH(c, "k_gemv");
     return CPM_OK;

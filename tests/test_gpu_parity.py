@@ -106,6 +106,28 @@ def test_symm_off_gives_inverse(tiny):
     assert abs(qt[0] - ref.sum()) <= 1e-10
 
 
+@pytest.mark.parametrize("s_prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("big", [False, True], ids=["216", "512"])
+def test_symm_off_single_precision_products(tiny, s_prec, big):
+    """S = A^-1 (no projection) with the single-precision and tensor-core products: the rows of A^-1 do
+    not sum to zero, so the centred products must add b_i sum_j S_ij back (216 sites: the two-column
+    kernel; 512 sites: the TMA stream)."""
+    if big:
+        el, ely = s.workload_serving_geometry(512, seed=4)[:2]
+        A = o.assemble_A(el)
+    else:
+        el, ely, _, A, _ = tiny
+    psi = np.array([0.0, 1.0])
+    Ainv = o.capacitance_matrix(A, symm=False)
+    ctx = make_ctx(el, symm=False, s_prec=s_prec, k_prec="fp64").setup(el)
+    b = run_bvec(ctx, [ely, ely])
+    q, qt = run_update(ctx, psi, b)
+    ref = Ainv @ (o.site_potentials(el, psi) - o.bvec(el, ely))
+    for r in range(2):
+        assert rel_l2(q[r], ref) <= 1e-5, (r, rel_l2(q[r], ref))
+        assert abs(qt[r] - q[r].sum()) <= 1e-10 * np.abs(q[r]).sum()
+
+
 def test_step_host_equals_device_path(tiny):
     el, ely, psi, _, _ = tiny
     ctx = make_ctx(el).setup(el)
