@@ -372,6 +372,12 @@ class SerialOracle:
         return tb, tq, b, q
 
 
+def oracle_bvec(el, ely):
+    """The oracle's b of one configuration (the P3M leg's accuracy check)."""
+    from oracle import cpm_oracle as o
+    return o.bvec(el, ely)
+
+
 def cpu_baseline_edl(pool, serial, el, ely, psi):
     """The oracle on the headline system (one configuration, every site, every k-vector): S by the
     oracle over all cores (not timed: a one-time cost), then one full update single-threaded (the
@@ -674,6 +680,48 @@ def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 
     return out
 
 
+P3M_MESH, P3M_ORDER = (32, 32, 128), 7
+
+
+def bvec_once(torch, ctx, st, xyz_dev, Q_dev, m, ne):
+    """b of m replicas (one cpm_bvec on the context's stream) as a host array."""
+    with torch.cuda.stream(st):
+        b = torch.empty((m, ctx.n), dtype=torch.float64, device="cuda")
+        ctx.cpm_bvec(m, ne, xyz_dev, Q_dev, b)
+    st.synchronize()
+    return b.cpu().numpy()
+
+
+def bench_p3m(torch, CPM, el, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush):
+    """The headline step with the reciprocal part of b from P3M (mesh 32 x 32 x 128, order 7) instead of
+    the Ewald sum: graph-captured step, kernel split, and b of replica 0 at the first timed step against
+    the Ewald b (both FP64 on the GPU) and against the mixed P3M path."""
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ctx = CPM.for_electrodes(el, s_prec="fp32", k_prec="fp32", stream=st, p3m=(P3M_MESH, P3M_ORDER)).setup(el)
+    ms, launches, _, _ = time_graph(torch, ctx, st, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush)
+    with torch.cuda.stream(st):
+        msp, _, prof, _, _ = time_path(torch, ctx, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush, profile=True)
+    x1, Q1 = xyz_dev[W][:ne], Q_dev[:ne]
+    b_mix = bvec_once(torch, ctx, st, x1, Q1, 1, ne)[0]
+    ctx.close()
+    st64 = torch.cuda.Stream()
+    with torch.cuda.stream(st64):
+        p64 = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64", stream=st64, p3m=(P3M_MESH, P3M_ORDER)).setup(el)
+        e64 = CPM.for_electrodes(el, s_prec="fp64", k_prec="fp64", stream=st64).setup(el)
+    b_p3m = bvec_once(torch, p64, st64, x1, Q1, 1, ne)[0]
+    b_ew = bvec_once(torch, e64, st64, x1, Q1, 1, ne)[0]
+    p64.close()
+    e64.close()
+    return {"workload": f"edl_capacitor_4320, {m} replicas per graph step, P3M mesh {P3M_MESH} order {P3M_ORDER}",
+            "value": m * K / (ms / 1e3), "unit": "updates/s", "ms_per_step": ms / K, "gpu_launches": int(launches),
+            "kernel_ms_per_step": {kk: v[0] / K for kk, v in prof.items() if v[1]},
+            "ms_per_step_kernel_by_kernel": msp / K,
+            "b_rel_diff_p3m_vs_ewald_fp64": rel_l2(b_p3m, b_ew),
+            "b_rel_diff_mixed_vs_fp64_p3m": rel_l2(b_mix, b_p3m),
+            "path": "mixed: FP32 real space, FP32 P3M (fixed-point charge assignment, FP32 transforms), FP32 S"}, b_p3m
+
+
 def edl_first_config(s, xyz, Q, ne, step):
     """Replica 0 of the headline trajectories at one step, as an electrolyte of its own."""
     return s.Electrolyte(xyz=np.ascontiguousarray(xyz[step, :ne]), Q=np.ascontiguousarray(Q[:ne]))
@@ -907,12 +955,16 @@ def main():
         line["s_stream_16384"] = {"kernel": "k_gemv_tma", "replicas": 8, "ms_per_launch": f16.get("kernel_ms"),
                                   "achieved_gbs": f16.get("achieved_gbs"), "frac": f16.get("hbm_frac"),
                                   "hbm_peak_gbs": float(peaks["hbm_gbs"]), "l2": "flushed before every update"}
+        line["p3m_edl_4320"], b_p3m0 = bench_p3m(torch, CPM, el, xyz_dev, Q_dev, psi_dev, m, ne, W, K, flush)
 
     if cpu_leg:
         pool = OraclePool()
         try:
             cb, _, q_or = cpu_baseline_edl(pool, serial, el, ely_ref, psi)
             cb["rel_err_vs_oracle"] = {"mixed_headline_path": rel_l2(qmix_ref, q_or), "fp64_path": rel_l2(q64_ref, q_or)}
+            if not args.no_extra:   # the GPU's FP64 P3M b against the oracle's P3M b (same mesh and order)
+                el_p = s.Electrodes(**{**el.__dict__, "p3m_mesh": P3M_MESH, "p3m_order": P3M_ORDER})
+                line["p3m_edl_4320"]["b_rel_err_fp64_vs_oracle"] = rel_l2(b_p3m0, oracle_bvec(el_p, ely_ref))
             if not args.no_extra:
                 el_t, last, psis, qs = cfg3_q
                 el1, conf1, psi1, q1last = cfg1_q
