@@ -156,3 +156,47 @@ def test_p3m_refuses_bad_parameters(tiny):
             make_ctx(with_p3m(el0, mesh, order), k_prec="fp32")
     with pytest.raises(CPMError, match="cpm_create"):
         make_ctx(with_p3m(s.Electrodes(**{**el0.__dict__, "boundary": "ew2d"}), (16, 16, 64), 5))
+
+
+@pytest.mark.parametrize("m", [1, 20])
+def test_p3m_replica_counts(tiny, m):
+    """One replica (a half-empty mesh pair) and twenty (ten pairs, charge splits over many bricks)."""
+    el0, _, _, _ = tiny
+    el = with_p3m(el0, (16, 16, 64), 6)
+    elyts = [s.ions_in_gap(el0, 40 + 3 * r, seed=700 + r) for r in range(m)]
+    b = run_bvec(make_ctx(el, k_prec="fp32").setup(el), elyts)
+    for r in sorted({0, m // 2, m - 1}):
+        assert rel_l2(b[r], o.bvec(el, elyts[r])) <= 2e-6, r
+
+
+def test_p3m_fp64_largest_plane_and_host_step(tiny):
+    """FP64 with a 64 x 64 xy plane (64 KiB of complex doubles in shared memory), through the host-buffer
+    step (cpm_step_host: copies, captured step, q back)."""
+    el0, psi, S, elyts = tiny
+    el = with_p3m(el0, (64, 64, 32), 4)
+    ctx = make_ctx(el, stream=torch.cuda.Stream()).setup(el)
+    xyz, Q, ne = stack_replicas(elyts)
+    m = len(elyts)
+    q = np.zeros((m, el.n))
+    qt = np.zeros(m)
+    ctx.cpm_step_host(m, ne, xyz, Q, np.tile(psi, (m, 1)), q, qt)
+    for r, e in enumerate(elyts):
+        assert rel_l2(q[r], o.charges(S, el, psi, o.bvec(el, e))) <= 1e-10
+        assert abs(qt[r]) <= 1e-12
+
+
+def test_p3m_with_constant_charge(tiny):
+    """The constant charge method (Sec. II.C) on a P3M b."""
+    el0, _, _, elyts = tiny
+    el = with_p3m(el0, (32, 32, 128), 7)
+    A = o.assemble_A(el0)
+    ctx = make_ctx(el).setup(el)
+    b = run_bvec(ctx, elyts[:2])
+    qt = np.array([[0.3, -0.3], [0.0, 0.5]])
+    q = torch.empty((2, el.n), dtype=torch.float64, device="cuda")
+    ctx.cpm_update_ccm(2, dev(qt), dev(b), q, None, None)
+    ctx.cpm_sync()
+    q = q.cpu().numpy()
+    for r in range(2):
+        q_ref, _ = o.ccm_charges(A, el, qt[r], o.bvec(el, elyts[r]))
+        assert rel_l2(q[r], q_ref) <= 1e-10
