@@ -263,8 +263,12 @@ cpm_status cpm_update_ffield(cpm_ctx* ctx, int32_t m, const double* dv0, const d
  * Host buffers may be pageable; page-locked memory gives faster copies.
  * On a context created with its own (non-default) stream the device part runs as
  * the CUDA graph of cpm_step_graph, captured once on the context's staging buffers
- * for each (m, n_e) and replayed (the graphs are kept as for cpm_step_graph).  On the default stream,
- * or while cpm_profile is on, the kernels launch one by one.
+ * for each (m, n_e) and replayed (the graphs are kept as for cpm_step_graph).  When all
+ * five host buffers are page-locked (cudaHostAlloc, cudaHostRegister, pinned torch
+ * tensors) the copies are nodes of that graph as well, captured for those buffer
+ * addresses: one graph launch and one synchronisation per call, and the buffers must stay
+ * allocated while the context may replay the graph.  On the default stream, or while
+ * cpm_profile is on, the kernels launch one by one.
  */
 cpm_status cpm_step_host(cpm_ctx* ctx, int32_t m, int64_t n_e, const double* xyz, const double* Q,
                          const double* psi, double* q_out, double* qtot_out);

@@ -166,16 +166,24 @@ static uint64_t fnv1a(uint64_t h, const void* data, size_t bytes) {
 
 // cpm_bvec followed by cpm_update as one CUDA graph on the context stream: captured and
 // instantiated on the first call for given (m, n_e, buffer addresses), replayed afterwards.
+// Pinned host buffers of cpm_step_host whose copies go into the captured graph (null: device only).
+struct HostIO {
+    const double *xyz, *Q, *psi;
+    double *q, *qtot;
+};
+
 static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q,
-                             const double* psi, double* b_out, double* q_out, double* qtot_out) {
-    const void* ptrs[6] = {xyz, Q, psi, b_out, q_out, qtot_out};
+                             const double* psi, double* b_out, double* q_out, double* qtot_out,
+                             const HostIO* hio = nullptr) {
+    const void* ptrs[11] = {xyz, Q, psi, b_out, q_out, qtot_out, hio ? hio->xyz : nullptr, hio ? hio->Q : nullptr,
+                            hio ? hio->psi : nullptr, hio ? hio->q : nullptr, hio ? hio->qtot : nullptr};
     CPM_TRY(reserve_bvec(c, m, n_e));
     CPM_TRY(reserve_update(c, m));
     if (!c->graph_valid) drop_graph(c);   // a scratch buffer moved: every captured graph is stale
     cpm_ctx::StepGraph* hit = nullptr;
     for (auto& gr : c->graphs) {
         bool same = gr.m == m && gr.ne == n_e;
-        for (int k = 0; k < 6 && same; ++k) same = gr.ptrs[k] == ptrs[k];
+        for (int k = 0; k < 11 && same; ++k) same = gr.ptrs[k] == ptrs[k];
         if (same) { hit = &gr; break; }
     }
     if (!hit) {
@@ -190,8 +198,26 @@ static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* x
         const int64_t l0 = c->launches;
         CPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         float2* bhl = update_bhl(c, m);
-        cpm_status s1 = bvec(c, m, n_e, xyz, Q, b_out, bhl);
+        cpm_status s1 = CPM_OK;
+        if (hio) {   // the host-to-device copies as graph nodes (pinned buffers)
+            const size_t pt = (size_t)m * n_e;
+            cudaError_t ce = cudaSuccess;
+            if (pt) ce = cudaMemcpyAsync((void*)xyz, hio->xyz, sizeof(double) * 3 * pt, cudaMemcpyHostToDevice, c->stream);
+            if (pt && ce == cudaSuccess)
+                ce = cudaMemcpyAsync((void*)Q, hio->Q, sizeof(double) * pt, cudaMemcpyHostToDevice, c->stream);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync((void*)psi, hio->psi, sizeof(double) * m * c->ng, cudaMemcpyHostToDevice,
+                                     c->stream);
+            if (ce != cudaSuccess) s1 = cuda_check(c, ce, "cudaMemcpyAsync (captured)");
+        }
+        if (s1 == CPM_OK) s1 = bvec(c, m, n_e, xyz, Q, b_out, bhl);
         cpm_status s2 = s1 == CPM_OK ? update(c, m, psi, b_out, q_out, qtot_out, bhl != nullptr) : s1;
+        if (s2 == CPM_OK && hio) {   // and the results back
+            cudaError_t ce = cudaMemcpyAsync(hio->q, q_out, sizeof(double) * m * c->n, cudaMemcpyDeviceToHost, c->stream);
+            if (ce == cudaSuccess && hio->qtot)
+                ce = cudaMemcpyAsync(hio->qtot, qtot_out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream);
+            if (ce != cudaSuccess) s2 = cuda_check(c, ce, "cudaMemcpyAsync (captured)");
+        }
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         c->prof_on = prof;
@@ -200,7 +226,7 @@ static cpm_status step_graph(cpm_ctx* c, int32_t m, int64_t n_e, const double* x
         cpm_ctx::StepGraph gr;
         gr.m = m;
         gr.ne = n_e;
-        for (int k = 0; k < 6; ++k) gr.ptrs[k] = ptrs[k];
+        for (int k = 0; k < 11; ++k) gr.ptrs[k] = ptrs[k];
         e = cudaGraphInstantiate(&gr.exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_check(c, e, "cudaGraphInstantiate");
@@ -485,6 +511,17 @@ cpm_status cpm_update(cpm_ctx* c, int32_t m, const double* psi, const double* b,
     return update(c, m, psi, b, q_out, qtot_out);
 }
 
+// page-locked host memory (cudaHostAlloc / cudaHostRegister): copies from it can be graph nodes
+static bool pinned_host(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, const double* Q, const double* psi,
                          double* q_out, double* qtot_out) {
     if (!c) return CPM_E_ARG;
@@ -509,6 +546,14 @@ cpm_status cpm_step_host(cpm_ctx* c, int32_t m, int64_t n_e, const double* xyz, 
     double* dq = take(sizeof(double) * m * c->n);
     double* dqt = take(sizeof(double) * m);
     cudaStream_t st = c->stream;
+    if (c->stream && !c->prof_on && pinned_host(xyz) && pinned_host(Q) && pinned_host(psi) && pinned_host(q_out) &&
+        (!qtot_out || pinned_host(qtot_out))) {
+        // pinned buffers: the copies are nodes of the captured step, one graph launch per call
+        const HostIO hio{xyz, Q, psi, q_out, qtot_out};
+        CPM_TRY(step_graph(c, m, n_e, dxyz, dQ, dpsi, db, dq, dqt, &hio));
+        CPM_CUDA(c, cudaStreamSynchronize(st));
+        return CPM_OK;
+    }
     if (pt) {
         CPM_CUDA(c, cudaMemcpyAsync(dxyz, xyz, sizeof(double) * 3 * pt, cudaMemcpyHostToDevice, st));
         CPM_CUDA(c, cudaMemcpyAsync(dQ, Q, sizeof(double) * pt, cudaMemcpyHostToDevice, st));

@@ -179,7 +179,7 @@ struct cpm_ctx {
     struct StepGraph {
         int m = 0;
         int64_t ne = 0;
-        const void* ptrs[6] = {};
+        const void* ptrs[11] = {};   // device buffers, then the pinned host buffers of cpm_step_host (or null)
         cudaGraphExec_t exec = nullptr;
         int64_t launches = 0;
         uint64_t used = 0;

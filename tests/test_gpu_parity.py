@@ -139,6 +139,30 @@ def test_step_host_equals_device_path(tiny):
     assert np.array_equal(q, q_dev) and np.array_equal(qt, qt_dev)
 
 
+@pytest.mark.parametrize("s_prec,k_prec", [("fp64", "fp64"), ("fp32", "f16x2")])
+def test_step_host_pinned_buffers(tiny, s_prec, k_prec):
+    """Page-locked host buffers on a context with its own stream: the copies become nodes of the captured
+    step.  Each call must read the caller's current positions and write fresh charges, equal to the
+    device path's; pageable buffers (the other path) give the same bits."""
+    el, ely, psi, _, _ = tiny
+    ctx = make_ctx(el, s_prec=s_prec, k_prec=k_prec, stream=torch.cuda.Stream()).setup(el)
+    m, ne = 2, ely.n
+    rng = np.random.default_rng(17)
+    hx = torch.empty((m * ne, 3), dtype=torch.float64).pin_memory()
+    hQ = torch.as_tensor(np.tile(ely.Q, m)).pin_memory()
+    hpsi = torch.as_tensor(np.tile(psi, (m, 1))).pin_memory()
+    hq = torch.empty((m, el.n), dtype=torch.float64).pin_memory()
+    hqt = torch.empty((m,), dtype=torch.float64).pin_memory()
+    for step in range(3):
+        x = np.concatenate([ely.xyz + rng.normal(0, 0.05, ely.xyz.shape) for _ in range(m)])
+        hx.copy_(torch.as_tensor(x))
+        ctx.cpm_step_host(m, ne, hx, hQ, hpsi, hq, hqt)
+        q_ref = np.zeros((m, el.n))
+        qt_ref = np.zeros(m)
+        ctx.cpm_step_host(m, ne, np.ascontiguousarray(x), np.tile(ely.Q, m), np.tile(psi, (m, 1)), q_ref, qt_ref)
+        assert np.array_equal(hq.numpy(), q_ref) and np.array_equal(hqt.numpy(), qt_ref), step
+
+
 def test_save_load_roundtrip(tiny, tmp_path):
     el, ely, psi, _, _ = tiny
     a = make_ctx(el).setup(el)
