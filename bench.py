@@ -218,7 +218,7 @@ def real_pairs(el, xyz_steps, Q, ne, m, step):
     return tot
 
 
-# Algorithmic work per unit (SURVEY-level cost model of the method, not of the kernels' own
+# Algorithmic work per unit (a cost model of the method itself, not of the kernels' own
 # shortcuts): a real-space pair inside r_c costs two erfc, a square root and a division (60 flop,
 # also for the tabulated single-precision kernel); a reciprocal term costs 16 flop per (charge, k)
 # for the structure factor and 14 per (site, k) for the site sum on the CUDA cores.  On the tensor
