@@ -11,6 +11,8 @@ production kernels run.
   input, so the product alone is measured: the 216-site capacitor for 1, 20, 64 and 130 replicas,
   and the 2,048-site geometry for 64 and 128 replicas.
 * The FP64 path at 2,048 sites.
+* The 16,384-site serving geometry, where the oracle cannot form S: sampled rows of A and b give
+  the stationarity residual of the FP64 path; the mixed path against the FP64 path.
 
 Tolerances: relative L2 error of q at most 1e-5 (mixed) and 1e-10 (FP64) for every replica, total
 electrode charge within 1e-12 e (Eq. S, Sec. II.A; Eq. electrode-wise, Sec. II.B).  The oracle
@@ -225,3 +227,47 @@ def test_autotuned_plan_is_timed_and_kept(serving):
     assert ctx.cpm_gemm_plan(m) == plan            # kept per (n, m), not tuned again
     other = make_ctx(el, s_prec="bf16x3").setup(el)
     assert other.cpm_gemm_plan(m) == plan          # another context of the same n reuses it
+
+
+# ----------------------------------------------------------------------------- the largest serving geometry
+
+def test_serving_16384_sampled_rows_against_oracle():
+    """16,384 sites (the largest serving geometry), where the oracle cannot form S: sampled rows of the
+    oracle's A and b give the stationarity residual A q + b - v, which for the charges of Eq. (S) is the
+    same constant (the neutrality multiplier) on every site (Sec. II.A).  Checked for the GPU's FP64
+    path at six sampled sites of both electrodes, with the FP64 b of those sites against the oracle
+    element by element; the mixed path (FP32 S stream, tensor-core reciprocal sums) against the FP64
+    path for every site."""
+    need_gpu()
+    el, ely, psi = s.workload_serving_geometry(16384, seed=5)
+    rng = np.random.default_rng(3)
+    rows = np.sort(np.concatenate([rng.choice(np.where(el.group == g)[0], 3, replace=False) for g in (0, 1)]))
+    A_rows = o.assemble_A(el, rows=rows)
+    b_rows = o.bvec(el, ely, sites=rows)
+    v = o.site_potentials(el, psi)
+    ctx = make_ctx(el).setup(el)
+    ctx.cpm_release_assembly()
+    (q64, b64), qt64 = _bvec_update_b(ctx, [ely], psi[None])
+    assert np.abs(b64[0][rows] - b_rows).max() <= 1e-10 * np.abs(b_rows).max()
+    res = A_rows @ q64[0] + b_rows - v[rows]
+    assert np.abs(res - res.mean()).max() <= 1e-8 * np.abs(v[rows] - b_rows).max(), res
+    assert abs(qt64[0]) <= QTOT_TOL
+    del ctx
+    mixed = make_ctx(el, s_prec="fp32", k_prec="f16x2").setup(el)
+    mixed.cpm_release_assembly()
+    (qm, _), qtm = _bvec_update_b(mixed, [ely], psi[None])
+    assert rel_l2(qm[0], q64[0]) <= MIXED_TOL
+    assert abs(qtm[0]) <= QTOT_TOL
+
+
+def _bvec_update_b(ctx, elyts, psi):
+    """(q, b) and the totals of one bvec + update."""
+    xyz, Q, n_e = stack_replicas(elyts)
+    m = len(elyts)
+    b = torch.empty((m, ctx.n), dtype=torch.float64, device="cuda")
+    q = torch.empty_like(b)
+    qt = torch.empty((m,), dtype=torch.float64, device="cuda")
+    ctx.cpm_bvec(m, n_e, dev(xyz), dev(Q), b)
+    ctx.cpm_update(m, dev(psi), b, q, qt)
+    ctx.cpm_sync()
+    return (q.cpu().numpy(), b.cpu().numpy()), qt.cpu().numpy()
