@@ -37,7 +37,8 @@ What it computes (ELECTRODE paper, arXiv 2203.15461):
   site potentials (Sec. II.F, Eq. cpm-ffield).
 * The reciprocal part of b by P3M, the mesh solver of the paper's package
   (Introduction; SI Sec. 1.A-B), when the electrodes carry a mesh and an order (``p3m_recip``);
-  A keeps the Ewald sum.
+  with ``p3m_matrix`` the reciprocal part of A by the same mesh operator (``p3m_matrix_recip``),
+  otherwise A keeps the Ewald sum.
 
 Readings of what the paper leaves open (units, cut-offs, the slab vacuum) are
 fixed by the arguments: positions in Angstrom, charges in e, potentials in V,
@@ -210,6 +211,11 @@ def assemble_A(el, rows=None, kchunk=2048):
         for c0 in range(0, len(rows), 256):
             A[c0:c0 + 256] += ew2d_recip(xyz[rows[c0:c0 + 256]], xyz, box, a, el.kcut)
         A += 2.0 * math.pi * box[2] / (box[0] * box[1])
+    elif getattr(el, "p3m_matrix", False) and getattr(el, "p3m_order", 0):
+        # reciprocal space by P3M: row i is the mesh potential of a unit charge at site i, interpolated at
+        # every site (the operator of p3m_recip applied to one site at a time)
+        A += p3m_matrix_recip(el, rows)
+        A += -math.pi / (V * a * a)
     else:
         # reciprocal space: sum_k w_k cos(k.(R_i - R_j)) = sum_k w_k [c_i c_j + s_i s_j]
         _, k, k2 = kvectors(box, el.kcut)
@@ -337,6 +343,27 @@ def p3m_influence(box, K, p, alpha, nalias=2):
     G = num / (den * den)
     G[0, 0, 0] = 0.0
     return G
+
+
+def p3m_matrix_recip(el, rows=None, batch=16):
+    """Reciprocal part of A (before K_E) by P3M: entry (i, j) is the potential at site j of the mesh
+    solution for a unit charge at site i (rows i, default all), with the assignment function,
+    influence function and interpolation of ``p3m_recip``."""
+    box = np.asarray(el.box, dtype=np.float64)
+    K, p = tuple(int(v) for v in el.p3m_mesh), int(el.p3m_order)
+    V = float(box[0] * box[1] * box[2])
+    xyz = np.asarray(el.xyz, dtype=np.float64)
+    rows = np.arange(len(xyz)) if rows is None else np.asarray(rows)
+    W = [p3m_weights(xyz[:, d], box[d], K[d], p) for d in range(3)]
+    G = p3m_influence(box, K, p, el.alpha)
+    out = np.zeros((len(rows), len(xyz)))
+    for c0 in range(0, len(rows), batch):
+        rr = rows[c0:c0 + batch]
+        rho = np.einsum("bx,by,bz->bxyz", W[0][rr], W[1][rr], W[2][rr])
+        phi = (K[0] * K[1] * K[2] / V) * np.real(np.fft.ifftn(G[None] * np.fft.fftn(rho, axes=(1, 2, 3)),
+                                                               axes=(1, 2, 3)))
+        out[c0:c0 + batch] = np.einsum("ix,iy,iz,bxyz->bi", W[0], W[1], W[2], phi, optimize=True)
+    return out
 
 
 def p3m_recip(el, elyt, sites=None):

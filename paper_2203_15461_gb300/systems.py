@@ -43,6 +43,7 @@ class Electrodes:
     name: str = ""
     p3m_mesh: tuple = ()     # P3M mesh points per axis (powers of two) for the reciprocal part of b
     p3m_order: int = 0       # P3M assignment order (0: Ewald sum)
+    p3m_matrix: bool = False # the reciprocal part of A by P3M as well (else the Ewald sum)
 
     @property
     def n(self) -> int:

@@ -522,3 +522,38 @@ def test_p3m_weights_partition_unity():
         W = o.p3m_weights(x, 10.0, 32, p)
         assert np.abs(W.sum(axis=1) - 1).max() < 1e-13
         assert ((W > 0).sum(axis=1) <= p).all()
+
+
+def _p3m_matrix(el, K, p):
+    return s.Electrodes(**{**el.__dict__, "p3m_mesh": K, "p3m_order": p, "p3m_matrix": True})
+
+
+def test_p3m_matrix_converges_to_the_ewald_elastance(tiny):
+    """A with its reciprocal part from P3M approaches the (pinned) Ewald A at least as h^(p-1) per mesh
+    doubling (order 7: within 1e-8 at 32 x 32 x 128); the charges follow."""
+    el, ely, psi, _, _, _ = tiny
+    elk = s.Electrodes(**{**el.__dict__, "kcut": s.kcut_from_tol(el.alpha, 1e-14)})
+    Ae = o.assemble_A(elk)
+    for p in (5, 7):
+        e = [np.linalg.norm(o.assemble_A(_p3m_matrix(el, K, p)) - Ae) / np.linalg.norm(Ae)
+             for K in ((16, 16, 64), (32, 32, 128))]
+        assert e[0] / e[1] > 2 ** (p - 1), (p, e)
+    elp = _p3m_matrix(el, (32, 32, 128), 7)
+    Ap = o.assemble_A(elp)
+    assert np.linalg.norm(Ap - Ae) / np.linalg.norm(Ae) < 1e-8
+    q_ew = o.charges(o.capacitance_matrix(Ae), el, psi, o.bvec(elk, ely))
+    q_p3m = o.charges(o.capacitance_matrix(Ap), el, psi, o.bvec(elp, ely))
+    assert np.linalg.norm(q_p3m - q_ew) / np.linalg.norm(q_ew) < 1e-7
+
+
+def test_p3m_matrix_is_the_b_operator(tiny):
+    """The matrix applied to charges q at the sites equals the mesh potential that the b path computes
+    for point charges q placed at the same positions (one operator, two evaluations: site by site, and
+    all charges in one mesh), and it is symmetric."""
+    el, _, _, _, _, _ = tiny
+    elp = _p3m_matrix(el, (16, 16, 64), 6)
+    R = o.p3m_matrix_recip(elp)
+    q = np.random.default_rng(5).normal(size=el.n)
+    b = o.p3m_recip(elp, s.Electrolyte(xyz=el.xyz, Q=q))
+    assert np.linalg.norm(R @ q - b) <= 1e-13 * np.linalg.norm(b)
+    assert np.linalg.norm(R - R.T) <= 1e-14 * np.linalg.norm(R)
