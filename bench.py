@@ -519,11 +519,25 @@ def bench_coax(torch, CPM, s, cells=100, alpha=0.15, rcut=24.0):
     t3 = time.perf_counter()
     nk = int(len(ctx.cpm_kvectors()))
     ctx.close()
+    # the same capacitor with the reciprocal part of A from P3M (FP64 mesh, 64 x 64 x 128, order 7)
+    elp = s.Electrodes(**{**el.__dict__, "p3m_mesh": (64, 64, 128), "p3m_order": 7, "p3m_matrix": True})
+    ctxp = CPM.for_electrodes(elp, s_prec="fp64", k_prec="fp64")
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    ctxp.cpm_assemble(x, e, g, el.n_groups)
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    ctxp.cpm_invert()
+    Cp = ctxp.cpm_capacitance()
+    ctxp.close()
     L = float(el.box[2])
     eps0 = 1.0 / (4.0 * math.pi * 14.399645)
     ana = 2.0 * math.pi * eps0 / math.log(s.tube_radius(20) / s.tube_radius(10))
     n = el.n
     return {"workload": f"coaxial (10,10)/(20,20) tubes, {cells} cells, {n} sites, 1D correction",
+            "assemble_p3m_matrix_s": t5 - t4, "p3m_matrix": {"mesh": [64, 64, 128], "order": 7},
+            "C0_per_L_p3m_matrix": float(Cp[1, 1]) / L,
+            "rel_diff_p3m_matrix_vs_ewald": abs(float(Cp[1, 1]) / float(C64[1, 1]) - 1.0),
             "n_sites": n, "n_kvectors": nk, "alpha": alpha, "rcut": rcut,
             "assemble_s": t1 - t0, "assemble_recip_tflops_fp64": 2.0 * n * n * nk / (t1 - t0) / 1e12,
             "fp64_cholesky_inverse_s": t3 - t2, "fp32_cholesky_ir_s": t2 - t1, "ir_sweeps": iters,

@@ -119,6 +119,10 @@ typedef struct {
                             (Kx Ky x 8 bytes, x 16 with k_prec = CPM_PREC_FP64) at most 128 KiB.
                             The charge assignment sums exact fixed-point integers: every charge
                             and the charge of every mesh point must stay below 2,048 e */
+    int32_t p3m_matrix;  /* 1 (with kspace = CPM_KSPACE_P3M): the reciprocal part of A by the same
+                            mesh operator as b, in FP64 (row i is the interpolated mesh potential of a
+                            unit charge at site i; the package's pppm/electrode matrix); the xy plane
+                            limit above then applies with 16 bytes per point.  0: A by the Ewald sum */
 } cpm_params;
 
 typedef struct cpm_ctx cpm_ctx;

@@ -39,7 +39,7 @@ class cpm_params(ctypes.Structure):
                 ("rcut", ctypes.c_double), ("kcut", ctypes.c_double), ("symm", ctypes.c_int32),
                 ("s_prec", ctypes.c_int32), ("k_prec", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t),
                 ("chol", ctypes.c_int32), ("kspace", ctypes.c_int32), ("p3m_order", ctypes.c_int32),
-                ("p3m_mesh", ctypes.c_int32 * 3)]
+                ("p3m_mesh", ctypes.c_int32 * 3), ("p3m_matrix", ctypes.c_int32)]
 
 
 _lib = None
@@ -180,7 +180,7 @@ class CPM:
 
     def __init__(self, box, boundary: str, alpha: float, rcut: float, kcut: float, symm: bool = True,
                  s_prec: str = "fp64", k_prec: str = "fp64", hbm_budget: int = 0, stream=None, chol: str = "fp64",
-                 p3m=None):
+                 p3m=None, p3m_matrix: bool = False):
         self.lib = load_library()
         p = cpm_params()
         p.box[:] = [float(b) for b in box]
@@ -194,6 +194,7 @@ class CPM:
             mesh, order = p3m
             p.kspace, p.p3m_order = 1, int(order)
             p.p3m_mesh[:] = [int(v) for v in mesh]
+        p.p3m_matrix = 1 if p3m_matrix else 0
         self.params = p
         self.stream = stream
         h = _P()
@@ -209,6 +210,7 @@ class CPM:
         """A context for the electrodes' cell and splitting; P3M when they carry a mesh and an order."""
         if getattr(el, "p3m_order", 0) and "p3m" not in kw:
             kw["p3m"] = (tuple(el.p3m_mesh), el.p3m_order)
+            kw.setdefault("p3m_matrix", bool(getattr(el, "p3m_matrix", False)))
         return cls(el.box, el.boundary, el.alpha, el.rcut, el.kcut, **kw)
 
     # -- plumbing

@@ -259,6 +259,7 @@ cpm_status cpm_create(const cpm_params* p, void* cuda_stream, cpm_ctx** out) {
     if (p->chol != CPM_CHOL_FP64 && p->chol != CPM_CHOL_FP32_IR) return CPM_E_ARG;
     if (p->kspace != CPM_KSPACE_EWALD && p->kspace != CPM_KSPACE_P3M) return CPM_E_ARG;
     if (p->kspace == CPM_KSPACE_P3M && (p->boundary == CPM_BC_EW2D || !p3m_mesh_ok(p))) return CPM_E_ARG;
+    if (p->p3m_matrix != 0 && (p->p3m_matrix != 1 || p->kspace != CPM_KSPACE_P3M)) return CPM_E_ARG;
     if ((p->s_prec != CPM_PREC_FP64 && p->s_prec != CPM_PREC_FP32 && p->s_prec != CPM_PREC_BF16X3) ||
         (p->k_prec != CPM_PREC_FP64 && p->k_prec != CPM_PREC_FP32 && p->k_prec != CPM_PREC_F16X2))
         return CPM_E_ARG;

@@ -133,6 +133,7 @@ cpm_status assemble_A(cpm_ctx* c) {
     k_A_real<<<g1, 256, 0, c->stream>>>(c->sx, n, c->g, c->A);
     CPM_LAUNCH(c, "k_A_real");
     if (c->g.bc == CPM_BC_EW2D) return assemble_ew2d(c);
+    if (c->p.kspace == CPM_KSPACE_P3M && c->p.p3m_matrix) return p3m_assemble_recip(c);
     if (c->kt.nk > 0) {
         const int64_t nt = (n + KA_BM - 1) / KA_BM;
         const int64_t blocks = nt * (nt + 1) / 2;

@@ -202,6 +202,8 @@ struct cpm_ctx {
     int tc_nmx = 0;              // tiles in tc_mx (0: the kernel finds them)
     void* p3m_G = nullptr;       // P3M (kspace = CPM_KSPACE_P3M): influence function / V on the mesh (k_prec's T)
     void* p3m_tw = nullptr;      // its FFT twiddles exp(-2 pi i j / K), j < K / 2, for K = Kx, Ky, Kz
+    void* p3m_G64 = nullptr;     // the same in FP64 for the P3M elastance when k_prec is single precision
+    void* p3m_tw64 = nullptr;
 
     int64_t launches = 0;        // kernels launched by cpm_bvec / cpm_update / cpm_step_host
 
@@ -370,5 +372,7 @@ size_t p3m_scratch_bytes(const cpm_ctx* c, int m, int64_t ne);
 template <typename T>
 cpm_status p3m_run(cpm_ctx* c, cudaStream_t st, int m, int64_t ne, const double* xyz, const double* Q, char* scr,
                    double* pm);
+// p3m_matrix: A += K_E x the P3M reciprocal part (rows of unit charges at the sites, FP64), symmetrised
+cpm_status p3m_assemble_recip(cpm_ctx* c);
 
 }  // namespace cpm

@@ -44,7 +44,7 @@ bool p3m_mesh_ok(const cpm_params* p) {
         const int K = p->p3m_mesh[d];
         if (K < 8 || K > P3M_MAX_MESH || (K & (K - 1))) return false;
     }
-    const size_t cs = p->k_prec == CPM_PREC_FP64 ? 16 : 8;
+    const size_t cs = (p->k_prec == CPM_PREC_FP64 || p->p3m_matrix) ? 16 : 8;
     return (size_t)p->p3m_mesh[0] * p->p3m_mesh[1] * cs <= P3M_PLANE_BYTES;
 }
 
@@ -489,11 +489,11 @@ template size_t p3m_scratch_bytes<float>(const cpm_ctx*, int, int64_t);
 template size_t p3m_scratch_bytes<double>(const cpm_ctx*, int, int64_t);
 
 template <typename T>
-static cpm_status p3m_prepare_t(cpm_ctx* c) {
+static cpm_status p3m_prepare_t(cpm_ctx* c, void** Gp, void** twp) {
     const int Kx = c->p.p3m_mesh[0], Ky = c->p.p3m_mesh[1], Kz = c->p.p3m_mesh[2];
     const int64_t N = mesh_pts(c);
-    CPM_TRY(dev_alloc(c, &c->p3m_G, sizeof(T) * N));
-    CPM_TRY(dev_alloc(c, &c->p3m_tw, sizeof(c2<T>) * (Kx + Ky + Kz) / 2));
+    CPM_TRY(dev_alloc(c, Gp, sizeof(T) * N));
+    CPM_TRY(dev_alloc(c, twp, sizeof(c2<T>) * (Kx + Ky + Kz) / 2));
     std::vector<c2<T>> tw((Kx + Ky + Kz) / 2);
     size_t o = 0;
     for (int K : {Kx, Ky, Kz})
@@ -501,10 +501,10 @@ static cpm_status p3m_prepare_t(cpm_ctx* c) {
             const double a = 2.0 * PI * j / K;
             tw[o++] = cmake<T>((T)std::cos(a), (T)-std::sin(a));
         }
-    CPM_CUDA(c, cudaMemcpyAsync(c->p3m_tw, tw.data(), sizeof(c2<T>) * tw.size(), cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(*twp, tw.data(), sizeof(c2<T>) * tw.size(), cudaMemcpyHostToDevice, c->stream));
     k_p3m_green<T><<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(Kx, Ky, Kz, c->p.p3m_order, c->g.boxL[0],
                                                                      c->g.boxL[1], c->g.boxL[2], c->g.alpha, c->g.V,
-                                                                     (T*)c->p3m_G);
+                                                                     (T*)*Gp);
     CPM_LAUNCH(c, "k_p3m_green");
     // the twiddles are copied from pageable host memory: wait before the vector goes out of scope
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -513,7 +513,18 @@ static cpm_status p3m_prepare_t(cpm_ctx* c) {
 
 cpm_status p3m_prepare(cpm_ctx* c) {
     if (c->p3m_G) return CPM_OK;   // depends on the cell and the parameters only
-    return c->p.k_prec == CPM_PREC_FP64 ? p3m_prepare_t<double>(c) : p3m_prepare_t<float>(c);
+    if (c->p.k_prec == CPM_PREC_FP64) return p3m_prepare_t<double>(c, &c->p3m_G, &c->p3m_tw);
+    CPM_TRY(p3m_prepare_t<float>(c, &c->p3m_G, &c->p3m_tw));
+    if (c->p.p3m_matrix) CPM_TRY(p3m_prepare_t<double>(c, &c->p3m_G64, &c->p3m_tw64));   // the elastance: FP64
+    return CPM_OK;
+}
+
+// the influence function and twiddles in T (the FP64 copies of a single-precision context for T = double)
+template <typename T> static const T* p3m_green(const cpm_ctx* c) {
+    return (const T*)((std::is_same<T, double>::value && c->p.k_prec != CPM_PREC_FP64) ? c->p3m_G64 : c->p3m_G);
+}
+template <typename T> static const c2<T>* p3m_twiddles(const cpm_ctx* c) {
+    return (const c2<T>*)((std::is_same<T, double>::value && c->p.k_prec != CPM_PREC_FP64) ? c->p3m_tw64 : c->p3m_tw);
 }
 
 template <typename T, int P>
@@ -529,7 +540,7 @@ static cpm_status launch_p3m_pp(cudaStream_t st, cpm_ctx* c, int m, int64_t ne, 
     k_p3m_spread<T, P><<<dim3(sp.nbricks, npairs, sp.nsplit), NT, ssm, st>>>(key, fq, ne, m, Kx, Ky, Kz, sp.BX, sp.BY,
                                                                              sp.BZ, sp.cps, mesh);
     const int64_t sstride = (int64_t)npairs * Kx * Ky * Kz;
-    const c2<T>* tw = (const c2<T>*)c->p3m_tw;
+    const c2<T>* tw = p3m_twiddles<T>(c);
     const size_t psm = sizeof(c2<T>) * ((size_t)Kx * Ky + Kx / 2 + Ky / 2);
     CPM_CUDA(c, cudaFuncSetAttribute(k_p3m_plane<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
     CPM_CUDA(c, cudaFuncSetAttribute(k_p3m_plane<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
@@ -538,7 +549,7 @@ static cpm_status launch_p3m_pp(cudaStream_t st, cpm_ctx* c, int m, int64_t ne, 
     const int tx = std::min(Kx, P3M_ZTX);
     const size_t zsm = sizeof(c2<T>) * ((size_t)Kz * tx + Kz / 2);
     CPM_CUDA(c, cudaFuncSetAttribute(k_p3m_zline<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
-    k_p3m_zline<T><<<dim3(Kx / tx, Ky, npairs), P3M_THREADS, zsm, st>>>(mesh, Kx, Ky, Kz, tx, (const T*)c->p3m_G,
+    k_p3m_zline<T><<<dim3(Kx / tx, Ky, npairs), P3M_THREADS, zsm, st>>>(mesh, Kx, Ky, Kz, tx, p3m_green<T>(c),
                                                                         tw + Kx / 2 + Ky / 2);
     k_p3m_plane<T, true><<<dim3(Kz, npairs), P3M_THREADS, psm, st>>>(mesh, Kx, Ky, Kz, tw, tw + Kx / 2, 1, 0);
     const int64_t warps = c->n * npairs;
@@ -570,6 +581,60 @@ cpm_status p3m_run(cpm_ctx* c, cudaStream_t st, int m, int64_t ne, const double*
         default: return launch_p3m_pp<T, 7>(st, c, m, ne, key, fq, mesh, pm);
     }
 }
+// ----------------------------------------------------------------------------- the P3M elastance
+__global__ void k_p3m_add_rows(double* __restrict__ A, const double* __restrict__ pm, int64_t cnt, double s) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) A[t] += s * pm[t];
+}
+
+// A <- (A + A^T) / 2 (the mesh operator is symmetric up to rounding): one thread per lower entry
+__global__ void k_p3m_sym(double* __restrict__ A, int64_t n) {
+    const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= i || i >= n) return;
+    const double v = 0.5 * (A[i * n + j] + A[j * n + i]);
+    A[i * n + j] = v;
+    A[j * n + i] = v;
+}
+
+__global__ void k_p3m_ones(double* __restrict__ q, int64_t cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) q[t] = 1.0;
+}
+
+cpm_status p3m_assemble_recip(cpm_ctx* c) {
+    const int64_t n = c->n;
+    const int B = (int)std::min<int64_t>(n, 512);   // sites per batch: every site one replica of one unit charge
+    const size_t sbytes = p3m_scratch_bytes<double>(c, B, 1);
+    char* scr = nullptr;
+    double* pm = nullptr;
+    double* ones = nullptr;
+    cpm_status st = dev_alloc(c, (void**)&scr, sbytes);
+    if (st == CPM_OK) st = dev_alloc(c, (void**)&pm, sizeof(double) * B * n);
+    if (st == CPM_OK) st = dev_alloc(c, (void**)&ones, sizeof(double) * B);
+    const int64_t l0 = c->launches;   // assembly work is not counted with the per-step launches
+    if (st == CPM_OK) {
+        k_p3m_ones<<<(B + 255) / 256, 256, 0, c->stream>>>(ones, B);
+        for (int64_t r0 = 0; r0 < n && st == CPM_OK; r0 += B) {
+            const int mb = (int)std::min<int64_t>(B, n - r0);
+            st = p3m_run<double>(c, c->stream, mb, 1, c->sxyz + 3 * r0, ones, scr, pm);
+            if (st == CPM_OK) {
+                const int64_t cnt = (int64_t)mb * n;
+                k_p3m_add_rows<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->A + r0 * n, pm, cnt, KE);
+            }
+        }
+        if (st == CPM_OK) {
+            k_p3m_sym<<<dim3((unsigned)((n + 255) / 256), (unsigned)n), 256, 0, c->stream>>>(c->A, n);
+            st = cuda_check(c, cudaGetLastError(), "k_p3m (elastance)");
+        }
+    }
+    c->launches = l0;
+    if (scr || pm || ones) cudaStreamSynchronize(c->stream);   // the buffers are in use until the stream has passed
+    dev_free(c, scr);
+    dev_free(c, pm);
+    dev_free(c, ones);
+    return st;
+}
+
 template cpm_status p3m_run<float>(cpm_ctx*, cudaStream_t, int, int64_t, const double*, const double*, char*, double*);
 template cpm_status p3m_run<double>(cpm_ctx*, cudaStream_t, int, int64_t, const double*, const double*, char*,
                                     double*);

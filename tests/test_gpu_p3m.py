@@ -200,3 +200,54 @@ def test_p3m_with_constant_charge(tiny):
     for r in range(2):
         q_ref, _ = o.ccm_charges(A, el, qt[r], o.bvec(el, elyts[r]))
         assert rel_l2(q[r], q_ref) <= 1e-10
+
+
+# ----------------------------------------------------------------------------- the P3M elastance
+
+def with_p3m_matrix(el, mesh, order):
+    return s.Electrodes(**{**el.__dict__, "p3m_mesh": tuple(mesh), "p3m_order": int(order), "p3m_matrix": True})
+
+
+@pytest.mark.parametrize("mesh,order", [((16, 16, 64), 5), ((32, 32, 128), 7)])
+def test_p3m_elastance_matches_oracle(tiny, mesh, order):
+    """A with the P3M reciprocal part (FP64 mesh arithmetic) within 1e-12 of the oracle's, S within 1e-10, the
+    charges of the FP64 path within 1e-10 and of the mixed path within 1e-5 of the oracle's (P3M A and b)."""
+    el0, psi, _, elyts = tiny
+    el = with_p3m_matrix(el0, mesh, order)
+    A = o.assemble_A(el)
+    S = o.capacitance_matrix(A)
+    ctx = make_ctx(el).setup(el)
+    Ag = ctx.cpm_get_matrix("A").cpu().numpy()
+    assert np.abs(Ag - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.array_equal(Ag, Ag.T)
+    assert rel_l2(ctx.cpm_get_matrix("S").cpu().numpy(), S) <= 1e-10
+    for s_prec, k_prec, tol in (("fp64", "fp64", 1e-10), ("fp32", "fp32", 1e-5), ("fp32", "f16x2", 1e-5)):
+        c = ctx if s_prec == "fp64" else make_ctx(el, s_prec=s_prec, k_prec=k_prec).setup(el)
+        b = run_bvec(c, elyts)
+        q, qt = run_update(c, psi, b)
+        for r, e in enumerate(elyts):
+            assert rel_l2(q[r], o.charges(S, el, psi, o.bvec(el, e))) <= tol, (s_prec, k_prec, r)
+            assert abs(qt[r]) <= 1e-12
+
+
+def test_p3m_elastance_other_boundaries():
+    """3D periodic and the wire correction (co-axial tubes): A against the oracle."""
+    need_gpu()
+    base, _, _ = s.workload_tiny_slab(seed=9)
+    el3 = s.Electrodes(**{**base.__dict__, "box": np.array([base.box[0], base.box[1], 40.0]), "boundary": "3d"})
+    for el, mesh in ((el3, (16, 16, 32)), (s.coaxial_tubes(4), (32, 32, 16))):
+        elp = with_p3m_matrix(el, mesh, 5)
+        A = o.assemble_A(elp)
+        Ag = make_ctx(elp, k_prec="fp32").setup(elp).cpm_get_matrix("A").cpu().numpy()
+        assert np.abs(Ag - A).max() <= 1e-12 * np.abs(A).max(), el.boundary
+
+
+def test_p3m_elastance_edl_capacitor_sampled_rows():
+    """The 4,320-site EDL capacitor: sampled rows of the P3M elastance against the oracle's rows."""
+    need_gpu()
+    el0, _, _ = s.workload_edl_capacitor(seed=1)
+    el = with_p3m_matrix(el0, (32, 32, 128), 7)
+    rows = np.array([0, 777, 2159, 2160, 3001, 4319])
+    A_ref = o.assemble_A(el, rows=rows)
+    Ag = make_ctx(el, s_prec="fp32", k_prec="f16x2").setup(el).cpm_get_matrix("A").cpu().numpy()
+    assert np.abs(Ag[rows] - A_ref).max() <= 1e-12 * np.abs(A_ref).max()

@@ -68,6 +68,11 @@ def test_create_rejects_bad_p3m_parameters_without_touching_a_gpu(lib):
     q = params(5, (16, 16, 64))
     q.kspace = 2
     assert lib.cpm_create(ctypes.byref(q), None, ctypes.byref(h)) == 1
+    # the P3M elastance: only with kspace = P3M, 0 or 1, and its FP64 planes within the limit
+    for kspace, flag, mesh in ((0, 1, (16, 16, 64)), (1, 2, (16, 16, 64)), (1, 1, (128, 128, 64))):
+        r = params(5, mesh)
+        r.kspace, r.p3m_matrix = kspace, flag
+        assert lib.cpm_create(ctypes.byref(r), None, ctypes.byref(h)) == 1
 
 
 def test_no_cpu_fallback_without_a_device(lib):
