@@ -629,7 +629,7 @@ def bench_s_products(torch, CPM, s, flush, peaks, src, sizes=((8192, (32, 16)), 
 
 
 def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 32000.0, None), phases=8,
-                  max_batch=16):
+                  max_batch=16, p3m_large=False):
     """Configuration 4: a Poisson stream of charge-update requests over four slab geometries (two
     graphene electrodes of two sheets, 512, 2,048, 8,192 and 16,384 sites), each request with its
     own electrolyte (0.5, 1, 1.5 or 2 charges per site: +-1 ions and 3-site water, drawn from four
@@ -638,11 +638,16 @@ def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 
     t = 0).  The stream runs in phases: the two small geometries are always asked for, the 8,192-
     and 16,384-site ones alternate by phase, and the HBM budget holds the small ones with one large
     one but not both, so admission and eviction act at every phase change (an evicted geometry
-    returns from its host-memory checkpoint).  Latency: arrival to result on the host."""
+    returns from its host-memory checkpoint).  Latency: arrival to result on the host.  With p3m_large
+    the 8,192- and 16,384-site geometries take the reciprocal part of b from P3M (order 7, mesh by
+    systems.with_p3m) instead of the Ewald sum."""
     from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
     sizes = (512, 2048, 8192, 16384)
     keys = [f"graphene_{n}" for n in sizes]
     geoms = {k: s.serving_electrodes(n) for k, n in zip(keys, sizes)}
+    if p3m_large:
+        for k in keys[2:]:
+            geoms[k] = s.with_p3m(geoms[k])
     dens = (0.5, 1.0, 1.5, 2.0)
     t0 = time.perf_counter()
     pools = {k: [s.workload_serving_geometry(n, seed=40 + j, charges_per_site=c)[1] for j, c in enumerate(dens)]
@@ -663,6 +668,8 @@ def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 
     out = {"workload": "cfg4: Poisson requests over 4 graphene slab geometries", "geometries": dict(zip(keys, sizes)),
            "requests_per_rate": n_req, "phases": phases, "max_batch": max_batch, "path": "mixed (FP32 S)",
            "k_prec": k_prec, "device_bytes": meas, "hbm_budget": budget, "input_seconds": t_inputs,
+           "reciprocal_b": {k: (f"P3M {tuple(geoms[k].p3m_mesh)} order {geoms[k].p3m_order}"
+                                if geoms[k].p3m_order else "Ewald") for k in keys},
            "first_admission_seconds": t_setup, "runs": []}
     for rate in rates:
         reqs = []
@@ -968,6 +975,8 @@ def main():
         line["cfg1_tiny_fp64"] = cfg1
         line["cfg3_batched_tiny_256"] = cfg3
         line["cfg4_serving"] = bench_serving(torch, s, k_prec=args.k_prec)
+        line["cfg4_serving_p3m_large"] = bench_serving(torch, s, k_prec=args.k_prec, rates=(8000.0, 32000.0, None),
+                                                       p3m_large=True)
         line["cfg5_coax_12000"] = bench_coax(torch, CPM, s)
         sp = bench_s_products(torch, CPM, s, flush, peaks, src)
         line["s_products"] = sp

@@ -327,6 +327,14 @@ def serving_electrodes(n_sites: int, gap: float = 40.0) -> Electrodes:
     return graphene_plates(cx, cy, 2, gap, alpha=alpha, rcut=3.6 / alpha)
 
 
+def with_p3m(el: Electrodes, order: int = 7, h_alpha: float = 0.35, matrix: bool = False) -> Electrodes:
+    """The electrodes with the reciprocal part of b (and with ``matrix`` of A) from P3M: per axis the
+    smallest power-of-two mesh (at least 8 points) whose spacing h keeps h alpha <= h_alpha (0.35 with
+    order 7 puts b within about 1e-7 of the Ewald sum for the geometries here)."""
+    K = tuple(int(max(8, 2 ** math.ceil(math.log2(math.ceil(L * el.alpha / h_alpha))))) for L in el.box)
+    return Electrodes(**{**el.__dict__, "p3m_mesh": K, "p3m_order": order, "p3m_matrix": matrix})
+
+
 def workload_serving_geometry(n_sites: int, seed: int = 1, charges_per_site: float = 1.0, gap: float = 40.0):
     """Serving geometry (``serving_electrodes``) with an electrolyte of charges_per_site x n_sites charges."""
     el = serving_electrodes(n_sites, gap)
