@@ -639,15 +639,15 @@ def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 
     and 16,384-site ones alternate by phase, and the HBM budget holds the small ones with one large
     one but not both, so admission and eviction act at every phase change (an evicted geometry
     returns from its host-memory checkpoint).  Latency: arrival to result on the host.  With p3m_large
-    the 8,192- and 16,384-site geometries take the reciprocal part of b from P3M (order 7, mesh by
-    systems.with_p3m) instead of the Ewald sum."""
+    the 8,192- and 16,384-site geometries take the reciprocal parts of b and of A from P3M (order 7,
+    mesh by systems.with_p3m) instead of the Ewald sum."""
     from paper_2203_15461_gb300.serve import GpuBackend, Request, Scheduler, context_bytes, latency_stats, run_stream
     sizes = (512, 2048, 8192, 16384)
     keys = [f"graphene_{n}" for n in sizes]
     geoms = {k: s.serving_electrodes(n) for k, n in zip(keys, sizes)}
-    if p3m_large:
+    if p3m_large:   # the same mesh operator for b and for the elastance (the package's pppm/electrode)
         for k in keys[2:]:
-            geoms[k] = s.with_p3m(geoms[k])
+            geoms[k] = s.with_p3m(geoms[k], matrix=True)
     dens = (0.5, 1.0, 1.5, 2.0)
     t0 = time.perf_counter()
     pools = {k: [s.workload_serving_geometry(n, seed=40 + j, charges_per_site=c)[1] for j, c in enumerate(dens)]
@@ -668,8 +668,8 @@ def bench_serving(torch, s, k_prec="f16x2", n_req=20000, rates=(2000.0, 8000.0, 
     out = {"workload": "cfg4: Poisson requests over 4 graphene slab geometries", "geometries": dict(zip(keys, sizes)),
            "requests_per_rate": n_req, "phases": phases, "max_batch": max_batch, "path": "mixed (FP32 S)",
            "k_prec": k_prec, "device_bytes": meas, "hbm_budget": budget, "input_seconds": t_inputs,
-           "reciprocal_b": {k: (f"P3M {tuple(geoms[k].p3m_mesh)} order {geoms[k].p3m_order}"
-                                if geoms[k].p3m_order else "Ewald") for k in keys},
+           "reciprocal_A_and_b": {k: (f"P3M {tuple(geoms[k].p3m_mesh)} order {geoms[k].p3m_order}"
+                                      if geoms[k].p3m_order else "Ewald") for k in keys},
            "first_admission_seconds": t_setup, "runs": []}
     for rate in rates:
         reqs = []
