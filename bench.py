@@ -921,7 +921,7 @@ def main():
     alu_src = f"FP32 FMA issue rate 152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
     pairs = real_pairs(el, xyz, Q, ne, m, W)
     work = kernel_work(el, nk, ne, m, pairs, tensor=args.k_prec == "f16x2")
-    kname = {"real": "k_real_cells", "sf": "k_tc_sf" if args.k_prec == "f16x2" else "k_sf32",
+    kname = {"real": "k_real_blk", "sf": "k_tc_sf" if args.k_prec == "f16x2" else "k_sf32",
              "site": "k_tc_site" if args.k_prec == "f16x2" else "k_site32", "gemv": "k_gemv_tma"}
     top, roof = roofline(prof, work, peaks, src, kname, alu_peak, alu_src, ms_prof)
     roof["pairs_in_rcut_per_launch"] = pairs
@@ -929,7 +929,7 @@ def main():
                              "tensor_complex_mac": FLOP_CMAC}
     # DRAM bytes (read + write) per launch from the committed ncu capture of these kernels on this
     # workload (cold caches); a stored figure, not measured by this run
-    traffic_ncu = {"real": 0.75e6, "sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
+    traffic_ncu = {"sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
     roof["traffic"] = traffic_ncu.get(top)
     roof["traffic_source"] = ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
                               "profiles/kernels_full_edl_capacitor_4320.md")

@@ -140,7 +140,8 @@ static void free_geometry(cpm_ctx* c) {
     void* ptrs[] = {c->sx, c->group, c->s32, c->site64.X, c->site64.Y, c->site64.Z, c->site32.X, c->site32.Y,
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
                     c->sperm, c->schunks, c->rqueue, c->tcz, c->tcxy, c->c0e, c->ccm_buf, c->ccm_scr, c->SGx,
-                    c->h2d_idx, c->h2d_norm};
+                    c->h2d_idx, c->h2d_norm, c->rsite, c->rsite_tab, c->rrun_cell, c->rrun_sh,
+                    c->rrun_off};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
@@ -150,6 +151,8 @@ static void free_geometry(cpm_ctx* c) {
     c->tcz = nullptr; c->tcxy = nullptr; c->c0e = nullptr;
     c->ccm_buf = nullptr; c->ccm_scr = nullptr; c->SGx = nullptr; c->ccm_scr_bytes = 0; c->ccm_ready = false;
     c->h2d_idx = nullptr; c->h2d_norm = nullptr; c->nh2d = 0;
+    c->rsite = nullptr; c->rsite_tab = nullptr; c->rpoly = cpm::RealPoly{}; c->rpoly_blocks = 0;
+    c->rrun_cell = nullptr; c->rrun_sh = nullptr; c->rrun_off = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;
@@ -400,6 +403,7 @@ static cpm_status assemble_impl(cpm_ctx* c, int64_t n, const double* xyz, const 
             CPM_CUDA(c, cudaMemcpyAsync(c->rtab_id, em.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
             CPM_TRY(build_pair_tables(c, eu));
             c->nrtab = (int)eu.size();
+            CPM_TRY(build_real_poly(c, eu));
         }
         CPM_TRY(dev_alloc(c, (void**)&c->zmap, sizeof(int) * n));
         CPM_TRY(dev_alloc(c, (void**)&c->zuniq, sizeof(double) * zu.size()));

@@ -35,7 +35,6 @@ CellGrid make_grid(const Geometry& g) {
     return cg;
 }
 
-__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // ----------------------------------------------------------------------------- per-replica totals
 constexpr int ST_THREADS = 256;
@@ -203,13 +202,9 @@ template <typename T> __device__ __forceinline__ T erfc_t(T x);
 template <> __device__ __forceinline__ float erfc_t<float>(float x) { return erfcf(x); }
 template <> __device__ __forceinline__ double erfc_t<double>(double x) { return erfc(x); }
 
-// Pair function f(r) = (erfc(alpha r) - erfc(eta r)) / r of a site's Gaussian width eta, tabulated
-// for the single-precision path: cubic Hermite pieces on RT_N equal intervals of [0, rcut], built
+// Pair-function tables (RT_N, RT_S): cubic Hermite pieces on RT_N equal intervals of [0, rcut], built
 // in FP64 from f and f' (f is even and smooth, f(0) = 2 (eta - alpha) / sqrt(pi)); the
-// interpolation error is below 1e-8 of f(0) for the widths and cut-offs used here.  Each table has
-// one more, all-zero row (index RT_N) for distances at or past the cut-off.
-constexpr int RT_N = 1024;
-constexpr int RT_S = RT_N + 1;   // rows per table
+// interpolation error is below 1e-8 of f(0) for the widths and cut-offs used here.
 
 __device__ inline void pair_f_df(double r, double a, double e, double* f, double* df) {
     if (r == 0.0) {
@@ -1476,7 +1471,9 @@ cpm_status bvec_run(cpm_ctx* c, int m, int64_t ne, const double* xyz, const doub
     }
     prof_end(c, CPM_K_CELLS);
     prof_begin(c, CPM_K_REAL);
-    if (std::is_same<T, float>::value && c->rtab && c->schunks) {
+    if (std::is_same<T, float>::value && c->rpoly.deg) {
+        CPM_TRY(real_poly_run(c, st, m, p.cg, start, (const float4*)sorted, real));
+    } else if (std::is_same<T, float>::value && c->rtab && c->schunks) {
         const int4* ch4 = (const int4*)c->schunks;
         const float4* tab4 = (const float4*)c->rtab;
         const unsigned rg = real_grid(c->nschunk, m);

@@ -33,6 +33,40 @@ template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
     V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
 }
 
+// ----------------------------------------------------------------------------- packed FP32 pairs
+// Two FP32 values in one 64-bit register for the packed (f32x2) arithmetic of sm_100 and later;
+// each lane of an operation rounds once, exactly like the scalar instruction.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ----------------------------------------------------------------------------- device status word
 // Kernels never trap: they set one of these bits and return.  The host reads the
 // word when it synchronises.
@@ -81,6 +115,24 @@ struct CellGrid {
     int ncells;
 };
 
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Single-precision pair function f(r) = (erfc(alpha r) - erfc(eta r)) / r of a site's Gaussian width
+// eta, tabulated as RT_N cubic Hermite pieces on [0, rcut] plus an all-zero row (index RT_N) for
+// distances at or past the cut-off; one table per distinct eta.
+constexpr int RT_N = 1024;
+constexpr int RT_S = RT_N + 1;   // rows per table
+
+// The same pair function as 1/r - alpha g(alpha^2 r^2) - erfc(eta r)/r with g(u) = erf(sqrt u)/sqrt u,
+// g replaced by a polynomial in v = 2u/U - 1 on [0, U], U = (alpha r_c)^2 (real_poly.cu).
+constexpr int RP_DEG_MAX = 18;
+struct RealPoly {
+    float c[RP_DEG_MAX + 1];   // alpha times the monomial coefficients in v
+    float cv;                  // 2 alpha^2 / U, so that v = r^2 cv - 1
+    float rc2;                 // r_c^2 in FP32
+    int deg;                   // 0: not available (the tabulated kernel runs)
+};
+
 struct Geometry {
     double boxL[3];
     double inv[3];       // 1 / L
@@ -123,6 +175,15 @@ struct cpm_ctx {
     int* rtab_id = nullptr;      // [n] table of each site
     int nrtab = 0;
     float* s32 = nullptr;        // [4 * n] wrapped single-precision x | y | z | eta
+    float4* rsite = nullptr;     // [nschunk * 32] sites of each chunk (x, y, z, r_eta^2), slots past the
+                                 // chunk's count repeat its first site
+    int* rsite_tab = nullptr;    // [nschunk * 32] pair-table offset of each slot
+    int2* rrun_cell = nullptr;   // per chunk, its cell-list runs: first cell and one past the last
+                                 // (cell indices within one replica's cell list)
+    float4* rrun_sh = nullptr;   // the image shift of each run
+    int* rrun_off = nullptr;     // [nschunk + 1] first run of each chunk
+    cpm::RealPoly rpoly{};       // fitted pair function of the gathered real-space kernel
+    int rpoly_blocks = 0;        // its persistent grid (resident blocks per SM x SMs)
     cpm::KTable kt;
     int2* h2d_idx = nullptr;     // EW2D: half-plane 2D vectors (nx, ny), 0 < |h| <= kcut
     double* h2d_norm = nullptr;  // their |h|
@@ -317,6 +378,15 @@ cpm_status reserve_bvec(cpm_ctx* c, int m, int64_t ne);
 cpm_status ensure_aux(cpm_ctx* c);
 cpm_status build_col0_sites(cpm_ctx* c);
 cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
+
+// real_poly.cu: real-space b from per-chunk candidate lists and the fitted pair function
+// fit of g for this splitting (deg = 0 when no supported degree reaches the accuracy)
+RealPoly fit_real_poly(double alpha, double rcut);
+// after the site chunks and pair tables: the chunk site slots and the fit (rpoly.deg = 0 if the
+// geometry cannot take the kernel)
+cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas);
+cpm_status real_poly_run(cpm_ctx* c, cudaStream_t st, int m, const CellGrid& cg, const int* start,
+                         const float4* sorted, double* out);
 
 // update.cu
 // bhl_ready: the split of b is already in update_bhl(c, m) (written by bvec in the same step)

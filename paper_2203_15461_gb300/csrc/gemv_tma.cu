@@ -40,32 +40,6 @@ constexpr int GV_SPT = (GV_JMAX * GV_MR + GV_T - 1) / GV_T;   // staged entries 
 constexpr int GV_SMEM = 1024 + GV_STAGES * GV_STAGE_BYTES + GV_JMAX * 2 * GV_MR * 4 + 256;
 constexpr uint64_t GV_WAIT_NS = 2000000000ull;
 
-__device__ __forceinline__ uint64_t pk2(float a, float b) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 up2(uint64_t v) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // compensated sum of packed pairs (Kahan): the sum is s - c; every step is one rounding
 struct Kahan2 {
     uint64_t s = 0ull, c = 0ull;
