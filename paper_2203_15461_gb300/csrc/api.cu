@@ -141,7 +141,7 @@ static void free_geometry(cpm_ctx* c) {
                     c->site32.Z, c->A, c->W, c->S, c->S32, c->SG, c->u, c->dvec, c->sxyz, c->zmap, c->zuniq, c->Sb, c->SZ, c->rtab, c->rtab_id,
                     c->sperm, c->schunks, c->rqueue, c->tcz, c->tcxy, c->c0e, c->ccm_buf, c->ccm_scr, c->SGx,
                     c->h2d_idx, c->h2d_norm, c->rsite, c->rsite_tab, c->rrun_cell, c->rrun_sh,
-                    c->rrun_off};
+                    c->rchunk, c->rsite_idx, c->rbox};
     for (void* p : ptrs) dev_free(c, p);
     c->sx = nullptr; c->group = nullptr; c->s32 = nullptr; c->sxyz = nullptr;
     c->zmap = nullptr; c->zuniq = nullptr; c->nzu = 0;
@@ -152,7 +152,8 @@ static void free_geometry(cpm_ctx* c) {
     c->ccm_buf = nullptr; c->ccm_scr = nullptr; c->SGx = nullptr; c->ccm_scr_bytes = 0; c->ccm_ready = false;
     c->h2d_idx = nullptr; c->h2d_norm = nullptr; c->nh2d = 0;
     c->rsite = nullptr; c->rsite_tab = nullptr; c->rpoly = cpm::RealPoly{}; c->rpoly_blocks = 0;
-    c->rrun_cell = nullptr; c->rrun_sh = nullptr; c->rrun_off = nullptr;
+    c->rrun_cell = nullptr; c->rrun_sh = nullptr; c->rchunk = nullptr; c->rrun_stride = 0;
+    c->rsite_idx = nullptr; c->rbox = nullptr;
     c->site64 = Phases<double>{}; c->site32 = Phases<float>{};
     c->A = c->W = c->S = c->SG = c->u = c->dvec = nullptr;
     c->S32 = nullptr;

@@ -178,10 +178,13 @@ struct cpm_ctx {
     float4* rsite = nullptr;     // [nschunk * 32] sites of each chunk (x, y, z, r_eta^2), slots past the
                                  // chunk's count repeat its first site
     int* rsite_tab = nullptr;    // [nschunk * 32] pair-table offset of each slot
-    int2* rrun_cell = nullptr;   // per chunk, its cell-list runs: first cell and one past the last
-                                 // (cell indices within one replica's cell list)
+    int* rsite_idx = nullptr;    // [nschunk * 32] site index of each slot
+    float4* rbox = nullptr;      // [nschunk * 2] bounding box of each chunk's single-precision sites
+    int4* rchunk = nullptr;      // [nschunk] per chunk: first site in sperm, site count, run count
+    int2* rrun_cell = nullptr;   // [nschunk * rrun_stride] runs of each chunk: first cell and one past
+                                 // the last (cell indices within one replica's cell list)
     float4* rrun_sh = nullptr;   // the image shift of each run
-    int* rrun_off = nullptr;     // [nschunk + 1] first run of each chunk
+    int rrun_stride = 0;         // run slots per chunk
     cpm::RealPoly rpoly{};       // fitted pair function of the gathered real-space kernel
     int rpoly_blocks = 0;        // its persistent grid (resident blocks per SM x SMs)
     cpm::KTable kt;

@@ -16,12 +16,12 @@
 // and the blocks sharing an SM overlap one another's phases:
 //   1. every stencil row of the cell list, trimmed to the bounding box of the chunk's sites grown by
 //      r_c, is one contiguous range of the cell-sorted charges per image shift along x (a "run"); the
-//      runs of each chunk are fixed by the geometry and listed once on the host, so per item a thread
-//      per run reads its two cell starts and a block scan numbers the charges of all runs;
-//   2. the charges are read in rounds of up to 1,536, in two passes of up to six loads in flight per
-//      thread (each charge finds its run in a shared-memory map), shifted to their image, and those
-//      within r_c of the box are kept in a structure-of-arrays list, in the order (pass, warp, slot,
-//      lane);
+//      runs of each chunk are fixed by the geometry and listed once on the host (read together with the
+//      chunk's sites), so per item a thread per run reads its two cell starts and a block scan numbers
+//      the charges of all runs;
+//   2. the charges are read in rounds of up to 1,536, up to twelve loads in flight per thread (each
+//      charge finds its run in a shared-memory map), shifted to their image, and those within r_c of
+//      the box are kept in a structure-of-arrays list, in the order (warp, slot, lane);
 //   3. the list is evaluated against the chunk's sites in groups of four: each warp takes (group,
 //      part of the list) units, every lane two candidates (one packed pair) against the four sites
 //      of the group, the lane sums reduced by a fixed butterfly; the parts of a group are added in
@@ -37,9 +37,8 @@ namespace cpm {
 
 constexpr int RB_T = 128;                       // threads per block
 constexpr int RB_W = RB_T / 32;
-constexpr int RB_K = 6;                         // charges per thread in one pass of a round
-constexpr int RB_SUB = RB_T * RB_K;             // charges read per pass; a round is two passes
-constexpr int RB_CAP = 2 * RB_SUB;              // charges read per round (the kept ones fit the list)
+constexpr int RB_K = 12;                        // charges per thread and round, all loads in flight
+constexpr int RB_CAP = RB_T * RB_K;             // charges read per round (the kept ones fit the list)
 constexpr int RB_RUNS = 256;                    // runs of one chunk, at most
 constexpr int RB_UNITS = 32;                    // (group, list part) units of an item, at most
 constexpr float RP_XETA = 4.5f;                 // eta r past which erfc(eta r) / r is dropped
@@ -102,7 +101,7 @@ RealPoly fit_real_poly(double alpha, double rcut) {
 // ----------------------------------------------------------------------------- chunk site slots
 __global__ void k_real_sites(const int4* __restrict__ chunks, int nchunks, const int* __restrict__ perm,
                              const float* __restrict__ s32, int64_t n, const int* __restrict__ tabid,
-                             float4* __restrict__ rsite, int* __restrict__ rsite_tab) {
+                             float4* __restrict__ rsite, int* __restrict__ rsite_tab, int* __restrict__ rsite_idx) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nchunks * 32) return;
     const int4 ci = chunks[t >> 5];
@@ -111,6 +110,7 @@ __global__ void k_real_sites(const int4* __restrict__ chunks, int nchunks, const
     const float rl = RP_XETA / s32[3 * n + i];
     rsite[t] = make_float4(s32[i], s32[n + i], s32[2 * n + i], fmaxf(rl * rl, 1e-6f));
     rsite_tab[t] = tabid[i] * RT_S;
+    rsite_idx[t] = i;
 }
 
 // ----------------------------------------------------------------------------- the kernel
@@ -155,35 +155,64 @@ struct RbGrid {
     float inv_h;      // RT_N / r_c: table rows per unit distance
 };
 
-// Block shared memory of one item.
+// cp.async copies into shared memory (completion per thread by cp.async.wait_all, visibility to
+// the block by the barrier after it)
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The inputs of one item, copied into shared memory at its start.
+struct RbItem {
+    float4 site[32];          // the chunk's sites (x, y, z, r_eta^2), slots past the count repeat the first
+    float4 box[2];            // their bounding box: lo, hi
+    int4 chunk;               // (first site, site count, run count, 0)
+    int sidx[32];             // site index of each slot
+    int toff[32];             // pair-table offset of each slot
+    int2 rcell[RB_RUNS];      // runs: first cell and one past the last (one replica's cell list)
+    float4 rsh[RB_RUNS];      // their image shifts
+    int rb[RB_RUNS];          // per run, the first charge in the sorted order ...
+    int re[RB_RUNS];          // ... and one past its last
+    int item;
+};
+
+// Block shared memory.
 struct RbShared {
     float2 cx[RB_CAP / 2], cy[RB_CAP / 2], cz[RB_CAP / 2], cq[RB_CAP / 2];   // kept charges, in list order
-    float4 site[32];          // the item's sites (x, y, z, r_eta^2)
-    int toff[32];             // their pair-table offsets
-    int rbeg[RB_RUNS];        // runs: first charge in the sorted order, exclusive prefix of lengths, shift
-    int rpre[RB_RUNS + 1];
-    float4 rsh[RB_RUNS];
+    RbItem it;                // the current item's inputs
+    int rpre[RB_RUNS + 1];    // exclusive prefix of the run lengths
     short erun[RB_CAP];       // the run of each charge of the round
     int wsum[RB_W + 1];       // block scan of the run lengths: warp totals
-    int wkept[2][RB_W];       // kept charges per (pass, warp)
+    int wkept[RB_W];          // kept charges per warp
     float part[RB_UNITS][4];  // per unit: the sums of the group's four sites
     float acc[32];            // per site: the sums of the rounds so far
-    float box[6];             // bounding box of the sites (lo xyz, hi xyz)
     int next;                 // the next item (taken from the queue one item ahead)
 };
 
 // One (group, list part) unit: the four sites of group gi against the list's 64-charge batches
 // [b0, b1); the four sums go to part[u].
 template <int DEG>
-__device__ __forceinline__ void rb_unit(RbShared& sm, int gi, int b0, int b1, int u, const uint64_t (&C)[DEG + 1],
-                                        const RealPoly& rp, const float4* __restrict__ tab, float inv_h) {
+__device__ __forceinline__ void rb_unit(RbShared& sm, const RbItem& I, int gi, int b0, int b1, int u,
+                                        const uint64_t (&C)[DEG + 1], const RealPoly& rp,
+                                        const float4* __restrict__ tab, float inv_h) {
     const int lane = threadIdx.x & 31;
     const uint64_t CV = pk2(rp.cv, rp.cv), M1 = pk2(-1.f, -1.f), RC2 = pk2(rp.rc2, rp.rc2);
     const uint64_t BIG2 = pk2(RP_BIG, RP_BIG), TINY2 = pk2(RP_TINY, RP_TINY);
     uint64_t SX[4], SY[4], SZ[4], NL[4], acc[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-        const float4 a = sm.site[4 * gi + s];
+        const float4 a = I.site[4 * gi + s];
         SX[s] = pk2(a.x, a.x);
         SY[s] = pk2(a.y, a.y);
         SZ[s] = pk2(a.z, a.z);
@@ -204,7 +233,7 @@ __device__ __forceinline__ void rb_unit(RbShared& sm, int gi, int b0, int b1, in
             const float hx[2] = {qx.x, qx.y}, hy[2] = {qy.x, qy.y}, hz[2] = {qz.x, qz.y}, hq[2] = {qq.x, qq.y};
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                const float4 st = sm.site[4 * gi + s];
+                const float4 st = I.site[4 * gi + s];
                 const float2 A = up2(acc[s]);
                 float av[2] = {A.x, A.y};
 #pragma unroll
@@ -217,7 +246,7 @@ __device__ __forceinline__ void rb_unit(RbShared& sm, int gi, int b0, int b1, in
                         const float uu = sqrtf(rr) * inv_h;
                         const int k = min((int)uu, RT_N);
                         const float t = uu - (float)k;
-                        const float4 cf = tab[sm.toff[4 * gi + s] + k];
+                        const float4 cf = tab[I.toff[4 * gi + s] + k];
                         av[h] = fmaf(hq[h], cf.x + t * (cf.y + t * (cf.z + t * cf.w)), av[h]);
                     }
                 }
@@ -242,18 +271,58 @@ __device__ __forceinline__ void rb_unit(RbShared& sm, int gi, int b0, int b1, in
     if ((lane & 7) == 0) sm.part[u][lane >> 3] = kk;
 }
 
+struct RbInputs {
+    const float4* site;       // [nchunks * 32] sites of each chunk slot
+    const int* sidx;          // [nchunks * 32] their site indices
+    const int* toff;          // [nchunks * 32] their pair-table offsets
+    const float4* box;        // [nchunks * 2] bounding box of each chunk
+    const int4* chunk;        // [nchunks] (first site, site count, run count, 0)
+    const int2* rcell;        // [nchunks * stride] runs of each chunk
+    const float4* rsh;        // [nchunks * stride] their image shifts
+    int stride;
+    int nchunks;
+};
+
+// Copies the fixed inputs of item `item` (chunk item / m) into I; one commit group per thread.
+__device__ __forceinline__ void rb_fetch_static(RbItem& I, const RbInputs& in, int item, int m) {
+    const int tid = threadIdx.x, ch = item / m;
+    if (tid < 32) {
+        cpa16(&I.site[tid], &in.site[(int64_t)ch * 32 + tid]);
+        cpa4(&I.sidx[tid], &in.sidx[(int64_t)ch * 32 + tid]);
+        cpa4(&I.toff[tid], &in.toff[(int64_t)ch * 32 + tid]);
+    } else if (tid < 34) {
+        cpa16(&I.box[tid - 32], &in.box[2 * (int64_t)ch + tid - 32]);
+    } else if (tid == 34) {
+        cpa16(&I.chunk, &in.chunk[ch]);
+    }
+    for (int j = tid; j < in.stride; j += RB_T) {
+        cpa8(&I.rcell[j], &in.rcell[(int64_t)ch * in.stride + j]);
+        cpa16(&I.rsh[j], &in.rsh[(int64_t)ch * in.stride + j]);
+    }
+    cpa_commit();
+}
+
+// Copies the charge ranges of the runs of I (whose fixed inputs have landed) from the cell list.
+__device__ __forceinline__ void rb_fetch_starts(RbItem& I, const int* __restrict__ start, int ncells, int m) {
+    const int r = I.item % m, nr = I.chunk.z;
+    for (int j = threadIdx.x; j < nr; j += RB_T) {
+        const int2 ce = I.rcell[j];
+        cpa4(&I.rb[j], &start[(int64_t)r * ncells + ce.x]);
+        cpa4(&I.re[j], &start[(int64_t)r * ncells + ce.y]);
+    }
+    cpa_commit();
+}
+
 template <int DEG>
-__global__ void __launch_bounds__(RB_T, 5)
-    k_real_blk(const float4* __restrict__ rsite, const int* __restrict__ rsite_tab, const int* __restrict__ perm,
-               const int4* __restrict__ chunks, int nchunks, int64_t n, RbGrid gr, int ncells,
-               const int2* __restrict__ run_cell, const float4* __restrict__ run_sh, const int* __restrict__ run_off,
-               const int* __restrict__ start, const float4* __restrict__ sorted, const float4* __restrict__ tab,
-               RealPoly rp, int m, int* __restrict__ rqueue, double* __restrict__ out) {
+__global__ void __launch_bounds__(RB_T, 4)
+    k_real_blk(RbInputs in, RbGrid gr, int ncells, const int* __restrict__ start, const float4* __restrict__ sorted,
+               const float4* __restrict__ tab, RealPoly rp, int m, int64_t n, int* __restrict__ rqueue,
+               double* __restrict__ out) {
     __shared__ RbShared sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float rc2 = rp.rc2;
     const float inv_h = gr.inv_h;
-    const int nitems = nchunks * m;
+    const int nitems = in.nchunks * m;
     uint64_t C[DEG + 1];
 #pragma unroll
     for (int k = 0; k <= DEG; ++k) C[k] = pk2(rp.c[k], rp.c[k]);
@@ -263,50 +332,32 @@ __global__ void __launch_bounds__(RB_T, 5)
     float* fq = (float*)sm.cq;
     if (tid == 0) sm.next = atomicAdd(&rqueue[0], 1);
     __syncthreads();
+    RbItem& I = sm.it;
     for (;;) {
         const int item = sm.next;
         if (item >= nitems) break;   // uniform
         __syncthreads();             // every thread has read the item before the next one is taken
-        if (tid == 0) sm.next = atomicAdd(&rqueue[0], 1);
-        const int ch = item / m, r = item - ch * m;
-        const int4 ci = chunks[ch];   // (first, count, cell, 0)
-        if (tid < 32) {
-            // slots past the count repeat the first site, so they leave the box unchanged
-            const float4 sv = rsite[ch * 32 + tid];
-            sm.site[tid] = sv;
-            sm.toff[tid] = rsite_tab[ch * 32 + tid];
-            sm.acc[tid] = 0.f;
-            float b0 = sv.x, b1 = sv.y, b2 = sv.z, b3 = sv.x, b4 = sv.y, b5 = sv.z;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
-                b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
-                b2 = fminf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
-                b3 = fmaxf(b3, __shfl_xor_sync(0xffffffffu, b3, o));
-                b4 = fmaxf(b4, __shfl_xor_sync(0xffffffffu, b4, o));
-                b5 = fmaxf(b5, __shfl_xor_sync(0xffffffffu, b5, o));
-            }
-            if (tid == 0) {
-                sm.box[0] = b0; sm.box[1] = b1; sm.box[2] = b2;
-                sm.box[3] = b3; sm.box[4] = b4; sm.box[5] = b5;
-            }
+        if (tid == 0) {
+            sm.next = atomicAdd(&rqueue[0], 1);
+            I.item = item;
         }
+        // the item's fixed inputs, then the charge ranges of its runs
+        rb_fetch_static(I, in, item, m);
+        cpa_wait_all();
         __syncthreads();
-        const float bx0 = sm.box[0], by0 = sm.box[1], bz0 = sm.box[2];
-        const float bx1 = sm.box[3], by1 = sm.box[4], bz1 = sm.box[5];
-        // phase 1: the cell starts of the chunk's runs (at most RB_RUNS, checked by the host)
-        const int r0 = run_off[ch], nslots = run_off[ch + 1] - r0;
-        for (int j = tid; j < nslots; j += RB_T) {
-            const int2 ce = run_cell[r0 + j];
-            const int b = start[r * ncells + ce.x];
-            sm.rbeg[j] = b;
-            sm.rpre[j] = start[r * ncells + ce.y] - b;   // turned into the exclusive prefix below
-            sm.rsh[j] = run_sh[r0 + j];
-        }
+        rb_fetch_starts(I, start, ncells, m);
+        cpa_wait_all();
         __syncthreads();
-        {   // exclusive block scan of the run lengths, two slots per thread
+        const int r = item % m;
+        const int4 ci = I.chunk;
+        const float bx0 = I.box[0].x, by0 = I.box[0].y, bz0 = I.box[0].z;
+        const float bx1 = I.box[1].x, by1 = I.box[1].y, bz1 = I.box[1].z;
+        if (tid < 32) sm.acc[tid] = 0.f;
+        // phase 1: exclusive block scan of the run lengths, two runs per thread
+        const int nslots = ci.z;
+        {
             const int i0 = 2 * tid, i1 = i0 + 1;
-            const int l0 = i0 < nslots ? sm.rpre[i0] : 0, l1 = i1 < nslots ? sm.rpre[i1] : 0;
+            const int l0 = i0 < nslots ? I.re[i0] - I.rb[i0] : 0, l1 = i1 < nslots ? I.re[i1] - I.rb[i1] : 0;
             int v = l0 + l1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -337,67 +388,61 @@ __global__ void __launch_bounds__(RB_T, 5)
                 for (int v = vb; v < ve; ++v) sm.erun[v - v0] = (short)j;
             }
             __syncthreads();
-            // phase 2: in pass h, charge v0 + h RB_SUB + k RB_T + tid of the concatenated runs, all loads
-            // of the pass in flight
-            int nk = 0;
-            for (int h = 0; h < 2; ++h) {
-                const int p0 = v0 + h * RB_SUB;
-                if (p0 >= vend) break;   // uniform
-                const int kk = min(RB_K, (vend - p0 + RB_T - 1) / RB_T);
-                int e[RB_K];
-                float4 q[RB_K];
+            // phase 2: charge v0 + k RB_T + tid of the concatenated runs, all loads in flight
+            const int kk = (vend - v0 + RB_T - 1) / RB_T;
+            int e[RB_K];
+            float4 q[RB_K];
 #pragma unroll
-                for (int k = 0; k < RB_K; ++k) {
-                    const int v = p0 + k * RB_T + tid;
-                    e[k] = -1;
-                    q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k < kk && v < vend) {
-                        e[k] = sm.erun[v - v0];
-                        q[k] = sorted[sm.rbeg[e[k]] + (v - sm.rpre[e[k]])];
-                    }
+            for (int k = 0; k < RB_K; ++k) {
+                const int v = v0 + k * RB_T + tid;
+                e[k] = -1;
+                q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < kk && v < vend) {
+                    e[k] = sm.erun[v - v0];
+                    q[k] = sorted[I.rb[e[k]] + (v - sm.rpre[e[k]])];
                 }
-                int rk[RB_K];
-                unsigned keepbits = 0u;
-                int wk = 0;   // kept by this warp in the slots before k
+            }
+            int rk[RB_K];
+            unsigned keepbits = 0u;
+            int wk = 0;   // kept by this warp in the slots before k
 #pragma unroll
-                for (int k = 0; k < RB_K; ++k) {
-                    if (k >= kk) break;   // uniform
-                    bool keep = false;
-                    if (e[k] >= 0) {
-                        const float4 sh = sm.rsh[e[k]];
-                        q[k].x += sh.x;
-                        q[k].y += sh.y;
-                        q[k].z += sh.z;
-                        // only charges within r_c of the sites' box can reach a site
-                        const float ex = fmaxf(0.f, fmaxf(bx0 - q[k].x, q[k].x - bx1));
-                        const float ey = fmaxf(0.f, fmaxf(by0 - q[k].y, q[k].y - by1));
-                        const float ez = fmaxf(0.f, fmaxf(bz0 - q[k].z, q[k].z - bz1));
-                        keep = ex * ex + ey * ey + ez * ez < rc2;
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                    rk[k] = wk + __popc(bal & ((1u << lane) - 1u));
-                    wk += __popc(bal);
-                    keepbits |= keep ? 1u << k : 0u;
+            for (int k = 0; k < RB_K; ++k) {
+                if (k >= kk) break;   // uniform
+                bool keep = false;
+                if (e[k] >= 0) {
+                    const float4 sh = I.rsh[e[k]];
+                    q[k].x += sh.x;
+                    q[k].y += sh.y;
+                    q[k].z += sh.z;
+                    // only charges within r_c of the sites' box can reach a site
+                    const float ex = fmaxf(0.f, fmaxf(bx0 - q[k].x, q[k].x - bx1));
+                    const float ey = fmaxf(0.f, fmaxf(by0 - q[k].y, q[k].y - by1));
+                    const float ez = fmaxf(0.f, fmaxf(bz0 - q[k].z, q[k].z - bz1));
+                    keep = ex * ex + ey * ey + ez * ez < rc2;
                 }
-                if (lane == 0) sm.wkept[h][warp] = wk;
-                __syncthreads();
-                int before = nk;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                rk[k] = wk + __popc(bal & ((1u << lane) - 1u));
+                wk += __popc(bal);
+                keepbits |= keep ? 1u << k : 0u;
+            }
+            if (lane == 0) sm.wkept[warp] = wk;
+            __syncthreads();
+            int before = 0, nk = 0;
 #pragma unroll
-                for (int w = 0; w < RB_W; ++w) {
-                    const int c = sm.wkept[h][w];
-                    before += w < warp ? c : 0;
-                    nk += c;
-                }
+            for (int w = 0; w < RB_W; ++w) {
+                const int c = sm.wkept[w];
+                before += w < warp ? c : 0;
+                nk += c;
+            }
 #pragma unroll
-                for (int k = 0; k < RB_K; ++k) {
-                    if (k >= kk) break;   // uniform
-                    if (keepbits & (1u << k)) {
-                        const int pos = before + rk[k];
-                        fx[pos] = q[k].x;
-                        fy[pos] = q[k].y;
-                        fz[pos] = q[k].z;
-                        fq[pos] = q[k].w;
-                    }
+            for (int k = 0; k < RB_K; ++k) {
+                if (k >= kk) break;   // uniform
+                if (keepbits & (1u << k)) {
+                    const int pos = before + rk[k];
+                    fx[pos] = q[k].x;
+                    fy[pos] = q[k].y;
+                    fz[pos] = q[k].z;
+                    fq[pos] = q[k].w;
                 }
             }
             __syncthreads();
@@ -418,7 +463,7 @@ __global__ void __launch_bounds__(RB_T, 5)
                 const int nu = ngrp * P;
                 for (int u = warp; u < nu; u += RB_W) {
                     const int gi = u / P, pi = u - gi * P;
-                    rb_unit<DEG>(sm, gi, pi * nb / P, (pi + 1) * nb / P, u, C, rp, tab, inv_h);
+                    rb_unit<DEG>(sm, I, gi, pi * nb / P, (pi + 1) * nb / P, u, C, rp, tab, inv_h);
                 }
                 __syncthreads();
                 if (tid < ci.y) {
@@ -430,7 +475,7 @@ __global__ void __launch_bounds__(RB_T, 5)
             }
             __syncthreads();   // the next round rewrites the list and the counts
         }
-        if (tid < ci.y) out[(int64_t)r * n + perm[ci.x + tid]] = (double)sm.acc[tid];
+        if (tid < ci.y) out[(int64_t)r * n + I.sidx[tid]] = (double)sm.acc[tid];
     }
     // every take of this block is done; the last block to finish puts the queue back to zero for the
     // next launch (launches on one context are stream-ordered)
@@ -493,13 +538,16 @@ static cpm_status chunk_runs(cpm_ctx* c, const std::vector<int4>& chunks, const 
 }
 
 cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
-    void* old[] = {c->rsite, c->rsite_tab, c->rrun_cell, c->rrun_sh, c->rrun_off};
+    void* old[] = {c->rsite, c->rsite_tab, c->rsite_idx, c->rbox, c->rrun_cell, c->rrun_sh, c->rchunk};
     for (void* p : old) dev_free(c, p);
     c->rsite = nullptr;
     c->rsite_tab = nullptr;
+    c->rsite_idx = nullptr;
+    c->rbox = nullptr;
     c->rrun_cell = nullptr;
     c->rrun_sh = nullptr;
-    c->rrun_off = nullptr;
+    c->rchunk = nullptr;
+    c->rrun_stride = 0;
     c->rpoly = RealPoly{};
     if (!c->schunks || !c->rtab || !c->rtab_id || c->nschunk == 0 || etas.empty()) return CPM_OK;
     // with Gaussian cores wider than half the cut-off most pairs would take the table: keep the
@@ -511,8 +559,9 @@ cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
     const size_t slots = (size_t)c->nschunk * 32;
     CPM_TRY(dev_alloc(c, (void**)&c->rsite, sizeof(float4) * slots));
     CPM_TRY(dev_alloc(c, (void**)&c->rsite_tab, sizeof(int) * slots));
+    CPM_TRY(dev_alloc(c, (void**)&c->rsite_idx, sizeof(int) * slots));
     k_real_sites<<<(unsigned)((slots + 255) / 256), 256, 0, c->stream>>>(
-        (const int4*)c->schunks, c->nschunk, c->sperm, c->s32, c->n, c->rtab_id, c->rsite, c->rsite_tab);
+        (const int4*)c->schunks, c->nschunk, c->sperm, c->s32, c->n, c->rtab_id, c->rsite, c->rsite_tab, c->rsite_idx);
     CPM_LAUNCH(c, "k_real_sites");
     // the runs from the same single-precision sites the kernel reads
     std::vector<float4> hs(slots);
@@ -526,19 +575,45 @@ cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
     if (chunk_runs(c, hch, hs, rp.rc2, cells, shifts, off) != CPM_OK || cells.empty()) {
         dev_free(c, c->rsite);
         dev_free(c, c->rsite_tab);
+        dev_free(c, c->rsite_idx);
         c->rsite = nullptr;
         c->rsite_tab = nullptr;
+        c->rsite_idx = nullptr;
         return CPM_OK;   // a chunk with more runs than a block holds: the tabulated kernel runs
     }
-    CPM_TRY(dev_alloc(c, (void**)&c->rrun_cell, sizeof(int2) * cells.size()));
-    CPM_TRY(dev_alloc(c, (void**)&c->rrun_sh, sizeof(float4) * shifts.size()));
-    CPM_TRY(dev_alloc(c, (void**)&c->rrun_off, sizeof(int) * off.size()));
-    CPM_CUDA(c, cudaMemcpyAsync(c->rrun_cell, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice,
-                                c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(c->rrun_sh, shifts.data(), sizeof(float4) * shifts.size(), cudaMemcpyHostToDevice,
-                                c->stream));
-    CPM_CUDA(c, cudaMemcpyAsync(c->rrun_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, c->stream));
+    // runs at a fixed stride per chunk (empty runs past each chunk's count) and the chunk records
+    int stride = 0;
+    for (int ch = 0; ch < c->nschunk; ++ch) stride = std::max(stride, off[ch + 1] - off[ch]);
+    std::vector<int2> pc((size_t)c->nschunk * stride, make_int2(0, 0));
+    std::vector<float4> ps((size_t)c->nschunk * stride, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<int4> rch(c->nschunk);
+    std::vector<float4> box(2 * (size_t)c->nschunk);
+    for (int ch = 0; ch < c->nschunk; ++ch) {
+        float4 lo = hs[(size_t)ch * 32], hi = lo;
+        for (int l = 1; l < 32; ++l) {
+            const float4 v = hs[(size_t)ch * 32 + l];
+            lo.x = std::min(lo.x, v.x); lo.y = std::min(lo.y, v.y); lo.z = std::min(lo.z, v.z);
+            hi.x = std::max(hi.x, v.x); hi.y = std::max(hi.y, v.y); hi.z = std::max(hi.z, v.z);
+        }
+        lo.w = hi.w = 0.f;
+        box[2 * (size_t)ch] = lo;
+        box[2 * (size_t)ch + 1] = hi;
+        for (int j = off[ch]; j < off[ch + 1]; ++j) {
+            pc[(size_t)ch * stride + j - off[ch]] = cells[j];
+            ps[(size_t)ch * stride + j - off[ch]] = shifts[j];
+        }
+        rch[ch] = make_int4(hch[ch].x, hch[ch].y, off[ch + 1] - off[ch], 0);
+    }
+    CPM_TRY(dev_alloc(c, (void**)&c->rrun_cell, sizeof(int2) * pc.size()));
+    CPM_TRY(dev_alloc(c, (void**)&c->rrun_sh, sizeof(float4) * ps.size()));
+    CPM_TRY(dev_alloc(c, (void**)&c->rchunk, sizeof(int4) * rch.size()));
+    CPM_TRY(dev_alloc(c, (void**)&c->rbox, sizeof(float4) * box.size()));
+    CPM_CUDA(c, cudaMemcpyAsync(c->rbox, box.data(), sizeof(float4) * box.size(), cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->rrun_cell, pc.data(), sizeof(int2) * pc.size(), cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->rrun_sh, ps.data(), sizeof(float4) * ps.size(), cudaMemcpyHostToDevice, c->stream));
+    CPM_CUDA(c, cudaMemcpyAsync(c->rchunk, rch.data(), sizeof(int4) * rch.size(), cudaMemcpyHostToDevice, c->stream));
     CPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->rrun_stride = stride;
     int dev = 0, nsm = 0, occ = 0;
     CPM_CUDA(c, cudaGetDevice(&dev));
     CPM_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -554,18 +629,23 @@ cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
 cpm_status real_poly_run(cpm_ctx* c, cudaStream_t st, int m, const CellGrid& cg, const int* start,
                          const float4* sorted, double* out) {
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->nschunk * m, c->rpoly_blocks));
-    const int4* ch = (const int4*)c->schunks;
     const float4* tab = (const float4*)c->rtab;
     RbGrid gr;
     gr.inv_h = (float)(RT_N / c->g.rcut);
+    RbInputs in;
+    in.site = c->rsite;
+    in.sidx = c->rsite_idx;
+    in.toff = c->rsite_tab;
+    in.box = c->rbox;
+    in.chunk = c->rchunk;
+    in.rcell = c->rrun_cell;
+    in.rsh = c->rrun_sh;
+    in.stride = c->rrun_stride;
+    in.nchunks = c->nschunk;
     if (c->rpoly.deg == 14)
-        k_real_blk<14><<<grid, RB_T, 0, st>>>(c->rsite, c->rsite_tab, c->sperm, ch, c->nschunk, c->n, gr, cg.ncells,
-                                              c->rrun_cell, c->rrun_sh, c->rrun_off, start, sorted, tab, c->rpoly, m,
-                                              c->rqueue, out);
+        k_real_blk<14><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
     else
-        k_real_blk<18><<<grid, RB_T, 0, st>>>(c->rsite, c->rsite_tab, c->sperm, ch, c->nschunk, c->n, gr, cg.ncells,
-                                              c->rrun_cell, c->rrun_sh, c->rrun_off, start, sorted, tab, c->rpoly, m,
-                                              c->rqueue, out);
+        k_real_blk<18><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
     CPM_LAUNCH(c, "k_real_blk");
     return CPM_OK;
 }
