@@ -929,10 +929,10 @@ def main():
                              "tensor_complex_mac": FLOP_CMAC}
     # DRAM bytes (read + write) per launch from the committed ncu capture of these kernels on this
     # workload (cold caches); a stored figure, not measured by this run
-    traffic_ncu = {"sf": 58.59e6, "site": 15.57e6, "gemv": 75.06e6}
+    traffic_ncu = {"sf": 58.60e6, "site": 15.56e6, "gemv": 75.07e6, "real": 1.42e6}
     roof["traffic"] = traffic_ncu.get(top)
     roof["traffic_source"] = ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                              "profiles/kernels_full_edl_capacitor_4320.md")
+                              "profiles/launches_edl_capacitor_4320.md")
     pairs1 = real_pairs(el, xyz, Q, ne, 1, W)
     work64 = kernel_work(el, nk, ne, 1, pairs1, tensor=False, s_bytes=8)
     k64 = {"real": "k_real_b<double>", "sf": "k_sf<double>", "site": "k_site<double>", "gemv": "k_gemv_t<double>"}
