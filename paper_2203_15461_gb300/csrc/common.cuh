@@ -67,6 +67,25 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     return d;
 }
 
+// sum of the split partials of one output: FP64 partials added in FP64; FP32 pairs (sum, low part)
+// added in double-float arithmetic (the exact error of each high-part addition, by the two-sum of
+// Knuth, is carried in the low part) and converted to FP64 once
+struct PartSumD {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+struct PartSumF2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float2 x) {
+        const float s = __fadd_rn(hi, x.x);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x.x, bb));
+        lo = __fadd_rn(lo, __fadd_rn(e, x.y));
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 // ----------------------------------------------------------------------------- device status word
 // Kernels never trap: they set one of these bits and return.  The host reads the
 // word when it synchronises.

@@ -256,25 +256,6 @@ __global__ void __launch_bounds__(G2_T, 2) k_gemv32x2(const float* __restrict__ 
 // q[r][i] = sum_g SG[i][g] psi[r][g] - sum_split part[split][r][i]; grid (sites / NB_T, m); with p1,
 // each block also writes the sum of its q values (the first pass of the neutrality fix)
 constexpr int NB_T = 256;
-// sum of the split partials of one output: FP64 partials added in FP64; FP32 pairs (sum, low part)
-// added in double-float arithmetic (the exact error of each high-part addition, by the two-sum of
-// Knuth, is carried in the low part) and converted to FP64 once
-struct PartSumD {
-    double v = 0.0;
-    __device__ __forceinline__ void add(double x) { v += x; }
-    __device__ __forceinline__ double value() const { return v; }
-};
-struct PartSumF2 {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float2 x) {
-        const float s = __fadd_rn(hi, x.x);
-        const float bb = __fsub_rn(s, hi);
-        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x.x, bb));
-        lo = __fadd_rn(lo, __fadd_rn(e, x.y));
-        hi = s;
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
 template <typename P> struct PartSum;
 template <> struct PartSum<double> { using type = PartSumD; };
 template <> struct PartSum<float2> { using type = PartSumF2; };
@@ -303,15 +284,14 @@ __global__ void __launch_bounds__(NB_T) k_gemv_reduce(const P* __restrict__ part
         typename PartSum<P>::type v;
         const P* pi = part + (int64_t)r * n + i;
         const int64_t stride = (int64_t)m * n;
-        int sp = 0;
-        for (; sp + 16 <= splits; sp += 16) {   // sixteen loads in flight, added in split order
+        for (int sp = 0; sp < splits; sp += 16) {   // sixteen loads in flight, added in split order
             P x[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = pi[(int64_t)(sp + k) * stride];
+            for (int k = 0; k < 16; ++k) x[k] = sp + k < splits ? pi[(int64_t)(sp + k) * stride] : P{};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v.add(x[k]);
+            for (int k = 0; k < 16; ++k)
+                if (sp + k < splits) v.add(x[k]);
         }
-        for (; sp < splits; ++sp) v.add(pi[(int64_t)sp * stride]);
         double sv = 0.0;
         for (int g = 0; g < ng; ++g) sv += SG[i * ng + g] * psi[(int64_t)r * ng + g];
         // the centred products give sum_j S_ij (b_j - b_i): add b_i sum_j S_ij back where rows do not sum to zero
