@@ -142,12 +142,13 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 constexpr int RT_N = 1024;
 constexpr int RT_S = RT_N + 1;   // rows per table
 
-// The same pair function as 1/r - alpha g(alpha^2 r^2) - erfc(eta r)/r with g(u) = erf(sqrt u)/sqrt u,
-// g replaced by a polynomial in v = 2u/U - 1 on [0, U], U = (alpha r_c)^2 (real_poly.cu).
-constexpr int RP_DEG_MAX = 18;
+// Outside the Gaussian cores the same pair function as e^{-alpha^2 r^2} P(r) / r, P a polynomial in
+// v = r s1 + s0 replacing erfcx(alpha r) on [r_lo, r_c] (real_poly.cu), r_lo the smallest core radius.
+constexpr int RP_DEG_MAX = 14;
 struct RealPoly {
-    float c[RP_DEG_MAX + 1];   // alpha times the monomial coefficients in v
-    float cv;                  // 2 alpha^2 / U, so that v = r^2 cv - 1
+    float c[RP_DEG_MAX + 1];   // monomial coefficients of P in v
+    float s1, s0;              // v = r s1 + s0 maps [r_lo, r_c] onto [-1, 1]
+    float ke;                  // -alpha^2 log2(e): e^{-alpha^2 r^2} = 2^(ke r^2)
     float rc2;                 // r_c^2 in FP32
     int deg;                   // 0: not available (the tabulated kernel runs)
 };
@@ -403,7 +404,7 @@ cpm_status build_pair_tables(cpm_ctx* c, const std::vector<double>& etas);
 
 // real_poly.cu: real-space b from per-chunk candidate lists and the fitted pair function
 // fit of g for this splitting (deg = 0 when no supported degree reaches the accuracy)
-RealPoly fit_real_poly(double alpha, double rcut);
+RealPoly fit_real_poly(double alpha, double rcut, double rlo);
 // after the site chunks and pair tables: the chunk site slots and the fit (rpoly.deg = 0 if the
 // geometry cannot take the kernel)
 cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas);

@@ -2,13 +2,15 @@
 // of the Ewald sum between the electrolyte charges and the electrode Gaussians, Eq. (b)).
 //
 // b_i(real) = sum_j Q_j f_i(r_ij) over the pairs within r_c, f_i(r) = (erfc(alpha r) - erfc(eta_i r)) / r.
-// Since erfc(x) = 1 - x g(x^2) with g(u) = erf(sqrt u) / sqrt u, an entire function of u,
-//     erfc(alpha r) / r = 1/r - alpha g(alpha^2 r^2),
-// and g on [0, (alpha r_c)^2] is replaced by its Chebyshev interpolant, fitted here in FP64 and
-// evaluated as a polynomial in r^2: a pair costs one reciprocal square root and a Horner chain, run
-// for two candidates at a time with packed FP32 instructions.  The site term erfc(eta r) / r is
-// below 5e-11 eta once eta r >= 4.5; the rare pairs closer than r_eta = 4.5 / eta take the tabulated
-// pair function (cubic Hermite, FP64-built) instead, in a branch taken per warp.
+// The site term erfc(eta r) / r is below 5e-11 eta once eta r >= 4.5; the rare pairs closer than
+// r_eta = 4.5 / eta take the tabulated pair function (cubic Hermite, FP64-built) instead, in a
+// branch taken per warp.  Outside the cores, with erfcx(x) = e^{x^2} erfc(x),
+//     erfc(alpha r) / r = e^{-alpha^2 r^2} erfcx(alpha r) / r,
+// and erfcx(alpha r), smooth and slowly varying, is replaced on [r_lo, r_c] (r_lo the smallest core
+// radius) by its Chebyshev interpolant, fitted here in FP64 (degree 12, or 14 where 12 does not
+// reach 1e-7 alpha in f): a pair costs a reciprocal square root, an exponential and a Horner chain,
+// run for two charges at a time with packed FP32 instructions, and every factor of f is accurate
+// relative to f itself.
 //
 // Work: persistent blocks of four warps take (chunk, replica) items from a queue, a chunk being at
 // most 32 sites of one real-space cell.  A block works on one item at a time, in three phases
@@ -46,26 +48,25 @@ constexpr float RP_BIG = 1099511627776.0f;      // 2^40: turns a sign into a 0/1
 constexpr float RP_TINY = 1e-30f;               // keeps 1 / sqrt(r^2) finite at r = 0
 
 // ----------------------------------------------------------------------------- the fit (host, FP64)
-static double g_erf(double u) {
-    if (u < 1e-300) return 2.0 / std::sqrt(PI);
-    const double r = std::sqrt(u);
-    return std::erf(r) / r;
-}
+// erfcx(x) = e^{x^2} erfc(x), for 0 <= x <= 7 (e^{49} erfc(7) stays well inside FP64)
+static double erfcx_d(double x) { return std::exp(x * x) * std::erfc(x); }
 
-RealPoly fit_real_poly(double alpha, double rcut) {
+RealPoly fit_real_poly(double alpha, double rcut, double rlo) {
     RealPoly rp{};
     const float rc2 = (float)(rcut * rcut);
-    // the kernel takes pairs with r^2 < rc2 in FP32; the interval covers them with a margin
-    const double U = alpha * alpha * (double)rc2 * (1.0 + 1e-6);
-    for (int d : {14, 18}) {
+    // the kernel takes pairs with r^2 < rc2 in FP32 and, outside the cores, r > rlo; the interval
+    // covers them with a margin
+    const double hi = rcut * (1.0 + 1e-6), lo = rlo * (1.0 - 1e-6);
+    if (!(lo > 0.0 && lo < hi) || alpha * hi > 7.0) return rp;
+    for (int d : {12, 14}) {
         const int N = d + 1;
-        // Chebyshev interpolation at the N Chebyshev points of [0, U]
+        // Chebyshev interpolation of erfcx(alpha r) at the N Chebyshev points of [lo, hi]
         std::vector<double> gk(N), ch(N);
-        for (int k = 0; k < N; ++k) gk[k] = g_erf(0.5 * U * (1.0 + std::cos(PI * (k + 0.5) / N)));
+        for (int k = 0; k < N; ++k) gk[k] = erfcx_d(alpha * (0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos(PI * (k + 0.5) / N)));
         for (int j = 0; j < N; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < N; ++k) s += gk[k] * std::cos(PI * j * (k + 0.5) / N);
-            ch[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+            double sum = 0.0;
+            for (int k = 0; k < N; ++k) sum += gk[k] * std::cos(PI * j * (k + 0.5) / N);
+            ch[j] = (j == 0 ? 1.0 : 2.0) * sum / N;
         }
         // to monomials in v: T_0 = 1, T_1 = v, T_{j+1} = 2 v T_j - T_{j-1}
         std::vector<double> mono(N, 0.0), t0(N, 0.0), t1(N, 0.0), tn(N, 0.0);
@@ -79,18 +80,20 @@ RealPoly fit_real_poly(double alpha, double rcut) {
             t0.swap(t1);
             t1.swap(tn);
         }
-        for (int k = 0; k < N; ++k) rp.c[k] = (float)(alpha * mono[k]);
-        // the FP32 coefficients against alpha g on a fine grid (Horner in FP64)
+        for (int k = 0; k <= RP_DEG_MAX; ++k) rp.c[k] = k < N ? (float)mono[k] : 0.f;
+        // the pair function from the FP32 coefficients against erfc(alpha r) / r on a fine grid
         double err = 0.0;
         for (int i = 0; i <= 8192; ++i) {
-            const double u = U * i / 8192.0, v = 2.0 * u / U - 1.0;
+            const double r = lo + (hi - lo) * i / 8192.0, v = (2.0 * r - lo - hi) / (hi - lo);
             double p = rp.c[d];
             for (int k = d - 1; k >= 0; --k) p = p * v + rp.c[k];
-            err = std::max(err, std::fabs(p - alpha * g_erf(u)));
+            err = std::max(err, std::fabs(std::exp(-alpha * alpha * r * r) * p / r - std::erfc(alpha * r) / r));
         }
         if (err <= 1e-7 * alpha) {
             rp.deg = d;
-            rp.cv = (float)(2.0 * alpha * alpha / U);
+            rp.s1 = (float)(2.0 / (hi - lo));
+            rp.s0 = (float)(-(hi + lo) / (hi - lo));
+            rp.ke = (float)(-alpha * alpha / std::log(2.0));
             rp.rc2 = rc2;
             return rp;
         }
@@ -125,24 +128,34 @@ __device__ __forceinline__ float mul_sat(float a, float b) {
     return y;
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Two (site, charge) pairs in the two halves of packed registers (here one site, its coordinates in
 // both halves, against two charges): acc += Q w f for the pairs with r_eta^2 < r^2 < r_c^2 (w is 1
-// there and 0 elsewhere); det <= 0 marks a pair inside a Gaussian core.
+// there and 0 elsewhere), f = 2^(ke r^2) P(r s1 + s0) / r; det <= 0 marks a pair inside a Gaussian
+// core.  Every factor of f carries a relative rounding error, so f is accurate relative to itself
+// also where it is small (no difference of two terms of size 1/r).
 template <int DEG>
 __device__ __forceinline__ void rp_pair2(uint64_t SX, uint64_t SY, uint64_t SZ, uint64_t NL, uint64_t QX,
                                          uint64_t QY, uint64_t QZ, uint64_t QW, const uint64_t (&C)[DEG + 1],
-                                         uint64_t CV, uint64_t M1, uint64_t RC2, uint64_t BIG2, uint64_t TINY2,
-                                         uint64_t& acc, float& det) {
+                                         uint64_t S1, uint64_t S0, uint64_t KE, uint64_t RC2, uint64_t BIG2,
+                                         uint64_t TINY2, uint64_t& acc, float& det) {
     const uint64_t dx = sub2(SX, QX), dy = sub2(SY, QY), dz = sub2(SZ, QZ);
     uint64_t r2 = fma2(dx, dx, TINY2);
     r2 = fma2(dy, dy, r2);
     r2 = fma2(dz, dz, r2);
-    const uint64_t v = fma2(r2, CV, M1);
+    const float2 r2s = up2(r2);
+    const uint64_t rs = pk2(rsqrt_approx(r2s.x), rsqrt_approx(r2s.y));   // 1 / r
+    const uint64_t v = fma2(mul2(r2, rs), S1, S0);
     uint64_t p = fma2(C[DEG], v, C[DEG - 1]);
 #pragma unroll
     for (int k = DEG - 2; k >= 0; --k) p = fma2(p, v, C[k]);
-    const float2 r2s = up2(r2);
-    const uint64_t f = sub2(pk2(rsqrt_approx(r2s.x), rsqrt_approx(r2s.y)), p);
+    const float2 y = up2(mul2(r2, KE));
+    const uint64_t f = mul2(mul2(pk2(ex2_approx(y.x), ex2_approx(y.y)), p), rs);
     const float2 a = up2(sub2(RC2, r2)), bq = up2(fma2(r2, BIG2, NL));
     const uint64_t w = mul2(pk2(mul_sat(a.x, bq.x), mul_sat(a.y, bq.y)), QW);
     acc = fma2(w, f, acc);
@@ -207,7 +220,7 @@ __device__ __forceinline__ void rb_unit(RbShared& sm, const RbItem& I, int gi, i
                                         const uint64_t (&C)[DEG + 1], const RealPoly& rp,
                                         const float4* __restrict__ tab, float inv_h) {
     const int lane = threadIdx.x & 31;
-    const uint64_t CV = pk2(rp.cv, rp.cv), M1 = pk2(-1.f, -1.f), RC2 = pk2(rp.rc2, rp.rc2);
+    const uint64_t S1 = pk2(rp.s1, rp.s1), S0 = pk2(rp.s0, rp.s0), KE = pk2(rp.ke, rp.ke), RC2 = pk2(rp.rc2, rp.rc2);
     const uint64_t BIG2 = pk2(RP_BIG, RP_BIG), TINY2 = pk2(RP_TINY, RP_TINY);
     uint64_t SX[4], SY[4], SZ[4], NL[4], acc[4];
 #pragma unroll
@@ -226,7 +239,7 @@ __device__ __forceinline__ void rb_unit(RbShared& sm, const RbItem& I, int gi, i
         float d[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s)
-            rp_pair2<DEG>(SX[s], SY[s], SZ[s], NL[s], QX, QY, QZ, QW, C, CV, M1, RC2, BIG2, TINY2, acc[s], d[s]);
+            rp_pair2<DEG>(SX[s], SY[s], SZ[s], NL[s], QX, QY, QZ, QW, C, S1, S0, KE, RC2, BIG2, TINY2, acc[s], d[s]);
         if (__any_sync(0xffffffffu, fminf(fminf(d[0], d[1]), fminf(d[2], d[3])) <= 0.f)) {
             // pairs inside a Gaussian core: the tabulated pair function, with r^2 and the core test
             // computed exactly as above (same operations, same roundings)
@@ -554,7 +567,8 @@ cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
     // tabulated kernel for such electrodes
     const double emin = *std::min_element(etas.begin(), etas.end());
     if (!(RP_XETA / emin < 0.5 * c->g.rcut)) return CPM_OK;
-    const RealPoly rp = fit_real_poly(c->g.alpha, c->g.rcut);
+    const double emax = *std::max_element(etas.begin(), etas.end());
+    const RealPoly rp = fit_real_poly(c->g.alpha, c->g.rcut, RP_XETA / emax);
     if (rp.deg == 0) return CPM_OK;
     const size_t slots = (size_t)c->nschunk * 32;
     CPM_TRY(dev_alloc(c, (void**)&c->rsite, sizeof(float4) * slots));
@@ -617,10 +631,10 @@ cpm_status build_real_poly(cpm_ctx* c, const std::vector<double>& etas) {
     int dev = 0, nsm = 0, occ = 0;
     CPM_CUDA(c, cudaGetDevice(&dev));
     CPM_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    if (rp.deg == 14)
-        CPM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_blk<14>, RB_T, 0));
+    if (rp.deg == 12)
+        CPM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_blk<12>, RB_T, 0));
     else
-        CPM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_blk<18>, RB_T, 0));
+        CPM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_blk<14>, RB_T, 0));
     c->rpoly = rp;
     c->rpoly_blocks = std::max(1, occ) * std::max(1, nsm);
     return CPM_OK;
@@ -642,10 +656,10 @@ cpm_status real_poly_run(cpm_ctx* c, cudaStream_t st, int m, const CellGrid& cg,
     in.rsh = c->rrun_sh;
     in.stride = c->rrun_stride;
     in.nchunks = c->nschunk;
-    if (c->rpoly.deg == 14)
-        k_real_blk<14><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
+    if (c->rpoly.deg == 12)
+        k_real_blk<12><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
     else
-        k_real_blk<18><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
+        k_real_blk<14><<<grid, RB_T, 0, st>>>(in, gr, cg.ncells, start, sorted, tab, c->rpoly, m, c->n, c->rqueue, out);
     CPM_LAUNCH(c, "k_real_blk");
     return CPM_OK;
 }

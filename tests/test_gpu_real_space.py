@@ -87,9 +87,10 @@ def test_charges_on_the_periodic_faces():
     assert rel_l2(b[0], o.bvec(el, ely)) <= 2e-6
 
 
-@pytest.mark.parametrize("rcut", [12.0, 15.0, 20.0], ids=["deg14", "deg18", "table"])
+@pytest.mark.parametrize("rcut", [12.0, 15.0, 20.0, 24.0], ids=["deg12", "deg12_wide", "deg14", "table"])
 def test_splittings(rcut):
-    """alpha r_c = 3.6, 4.5 and 6: the degree-14 fit, the degree-18 fit, and the tabulated kernel."""
+    """alpha r_c = 3.6, 4.5, 6 and 7.2: the degree-12 fit of erfcx (twice), the degree-14 fit, and the
+    tabulated kernel (the fit is not used past alpha r_c = 7)."""
     need_gpu()
     el = s.au111_slab(rcut=rcut)
     elyts = [s.ions_in_gap(el, 100, seed=20 + k) for k in range(3)]
