@@ -24,11 +24,11 @@
 //   2. the charges are read in rounds of up to 1,536, up to twelve loads in flight per thread (each
 //      charge finds its run in a shared-memory map), shifted to their image, and those within r_c of
 //      the box are kept in a structure-of-arrays list, in the order (warp, slot, lane);
-//   3. the list is evaluated against the chunk's sites in groups of four: each warp takes (group,
-//      part of the list) units, every lane two candidates (one packed pair) against the four sites
-//      of the group, the lane sums reduced by a fixed butterfly; the parts of a group are added in
-//      part order and the rounds in round order.
-// The list order and the unit split depend only on the item, so the result does not depend on
+//   3. the list is evaluated against the chunk's sites in groups of four: the (group, 64-charge
+//      batch) work is cut into four equal contiguous ranges, one per warp, every lane two candidates
+//      (one packed pair) against the four sites of a group, the lane sums reduced by a fixed
+//      butterfly; a group's sums from the warps are added in warp order and the rounds in round order.
+// The list order and the work split depend only on the item, so the result does not depend on
 // scheduling.
 
 #include <cmath>
@@ -42,7 +42,7 @@ constexpr int RB_W = RB_T / 32;
 constexpr int RB_K = 12;                        // charges per thread and round, all loads in flight
 constexpr int RB_CAP = RB_T * RB_K;             // charges read per round (the kept ones fit the list)
 constexpr int RB_RUNS = 256;                    // runs of one chunk, at most
-constexpr int RB_UNITS = 32;                    // (group, list part) units of an item, at most
+constexpr int RB_G = 8;                         // groups of four sites of a chunk, at most
 constexpr float RP_XETA = 4.5f;                 // eta r past which erfc(eta r) / r is dropped
 constexpr float RP_BIG = 1099511627776.0f;      // 2^40: turns a sign into a 0/1 weight (saturated product)
 constexpr float RP_TINY = 1e-30f;               // keeps 1 / sqrt(r^2) finite at r = 0
@@ -208,7 +208,7 @@ struct RbShared {
     short erun[RB_CAP];       // the run of each charge of the round
     int wsum[RB_W + 1];       // block scan of the run lengths: warp totals
     int wkept[RB_W];          // kept charges per warp
-    float part[RB_UNITS][4];  // per unit: the sums of the group's four sites
+    float part[RB_W * RB_G][4];   // per (warp, group): the warp's sums of the group's four sites
     float acc[32];            // per site: the sums of the rounds so far
     int next;                 // the next item (taken from the queue one item ahead)
 };
@@ -470,19 +470,23 @@ __global__ void __launch_bounds__(RB_T, 4)
                     fq[k] = 0.f;
                 }
                 __syncthreads();
-                // phase 3: (group, part) units; P parts per group so that the units fill the warps
+                // phase 3: the (group, batch) work split into four equal contiguous ranges, one per
+                // warp; a warp evaluates the part of each group its range covers and keeps the sums
+                // in its own slot of that group (slots it does not reach stay zero)
                 const int ngrp = (ci.y + 3) >> 2;
-                const int P = (ngrp & 1) ? 4 : ((ngrp & 2) ? 2 : 1);
-                const int nu = ngrp * P;
-                for (int u = warp; u < nu; u += RB_W) {
-                    const int gi = u / P, pi = u - gi * P;
-                    rb_unit<DEG>(sm, I, gi, pi * nb / P, (pi + 1) * nb / P, u, C, rp, tab, inv_h);
+                const int work = ngrp * nb;
+                sm.part[warp * RB_G + (lane >> 2)][lane & 3] = 0.f;
+                __syncwarp();
+                for (int f = warp * work / RB_W, f1 = (warp + 1) * work / RB_W; f < f1;) {
+                    const int gi = f / nb, b0 = f - gi * nb, b1 = min(nb, b0 + (f1 - f));
+                    rb_unit<DEG>(sm, I, gi, b0, b1, warp * RB_G + gi, C, rp, tab, inv_h);
+                    f += b1 - b0;
                 }
                 __syncthreads();
                 if (tid < ci.y) {
                     const int gi = tid >> 2, s = tid & 3;
                     float t = 0.f;
-                    for (int pi = 0; pi < P; ++pi) t += sm.part[gi * P + pi][s];
+                    for (int w = 0; w < RB_W; ++w) t += sm.part[w * RB_G + gi][s];   // warp order
                     sm.acc[tid] += t;
                 }
             }
